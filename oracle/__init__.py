@@ -1,0 +1,249 @@
+"""FP64 CPU oracle for the DBIE quadrature -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously-correct restatement of what Wang, Yan & Tan (arXiv 1306.1122) compute:
+the quadrature of Eq. 6 in the discrete form of Eq. 16 (midpoint rule at pixel centres), its
+spatial derivatives at fixed lambda (the zeroth-order rule of Eq. 13), J = curl B (Eq. 14), the
+measures f (Eq. 8) and g (Eq. 9), and the per-point Downhill Simplex search for lambda
+(Sect. 2.1, Nelder & Mead 1965).  The arithmetic lives in ``dbie_oracle.c`` (FP64, Neumaier
+compensated, row-major order); this module only marshals numpy arrays.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may import
+this package.  It shares no code with the CUDA path and never imports it.
+
+Parity pins (closed forms, invariants, a library Nelder-Mead) live in ``tests/test_oracle_*.py``.
+Parity unpinned: the reading of Delta V / Delta sigma in Eq. 9 (``g_scale``), the objective
+combination Phi = f + w_g g, the initial simplex and the thresholds eps_f / eps_g, which the paper
+leaves open.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc, FP64, no FMA contraction, OpenMP over points)."""
+    src = os.path.join(_HERE, "dbie_oracle.c")
+    hdr = os.path.join(_HERE, "dbie_oracle.h")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Boundary(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("hx", ctypes.c_double), ("hy", ctypes.c_double), ("dA", ctypes.c_double),
+                ("Bx", ctypes.c_void_p), ("By", ctypes.c_void_p), ("Bz", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("eps_f", ctypes.c_double), ("eps_g", ctypes.c_double), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int32), ("lambda_mode", ctypes.c_int32),
+                ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
+                ("g_scale", ctypes.c_double), ("deriv", ctypes.c_int32),
+                ("fd_delta", ctypes.c_double)]
+
+
+class _NMResult(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double * 3), ("fx", ctypes.c_double), ("iters", ctypes.c_int32),
+                ("nfev", ctypes.c_int32), ("status", ctypes.c_int32), ("ncodes", ctypes.c_int32)]
+
+
+FUN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                       ctypes.POINTER(ctypes.c_int32))
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            lib.orc_field.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P, P, P]
+            lib.orc_objective.argtypes = [P, P, ctypes.c_double, ctypes.c_double, P, P, P, P, P]
+            lib.orc_eval_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32, ctypes.c_double,
+                                          P, P, P, ctypes.c_int32]
+            lib.orc_solve_many.argtypes = [P, ctypes.c_int64, P, P, P, P, P, P, P, P, P, P, P, P,
+                                           ctypes.c_int32, ctypes.c_int32]
+            lib.orc_vjp.argtypes = [P, ctypes.c_int64, P, P, P, P, ctypes.c_int32]
+            lib.orc_nelder_mead_sim.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_int32,
+                                                FUN, P, P, P, ctypes.c_int32]
+            _lib = lib
+    return _lib
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Grid:
+    """Magnetogram geometry (Eq. 3): pixel (i, j) centred at (x0 + i hx, y0 + j hy, 0)."""
+    nx: int
+    ny: int
+    x0: float = 0.0
+    y0: float = 0.0
+    hx: float = 1.0
+    hy: float = 1.0
+    dA: float | None = None
+
+    @property
+    def area(self) -> float:
+        return self.hx * self.hy if self.dA is None else self.dA
+
+
+class Boundary:
+    """Boundary data held as float32 (ny, nx) arrays, the precision the library receives."""
+
+    def __init__(self, grid: Grid, Bx, By, Bz):
+        self.grid = grid
+        self.B = [np.ascontiguousarray(np.asarray(c, dtype=np.float32).reshape(grid.ny, grid.nx))
+                  for c in (Bx, By, Bz)]
+        g = grid
+        self._c = _Boundary(g.nx, g.ny, g.x0, g.y0, g.hx, g.hy, g.area,
+                            self.B[0].ctypes.data, self.B[1].ctypes.data, self.B[2].ctypes.data)
+
+    @property
+    def ref(self):
+        return ctypes.byref(self._c)
+
+
+@dataclass
+class Options:
+    """Lambda-search options; defaults are the readings stated in the design notes."""
+    eps_f: float = 1e-3
+    eps_g: float = 1e-4
+    tol: float = 1e-6
+    max_iter: int = 50
+    lambda_mode: int = 0
+    simplex_step: float = 0.0   # 0 -> 1 / (max(nx, ny) * hx)
+    w_g: float = 1.0
+    g_scale: float = 0.0        # 0 -> hx / 6 (cubic cell: dV / dSigma = h^3 / 6 h^2)
+    deriv: int = 0
+    fd_delta: float = 0.0       # 0 -> 1e-3 * hx (one thousandth of a pixel, Sect. 2.1)
+
+    def resolved(self, grid: Grid) -> "Options":
+        o = Options(**self.__dict__)
+        if o.simplex_step == 0.0:
+            o.simplex_step = 1.0 / (max(grid.nx, grid.ny) * grid.hx)
+        if o.g_scale == 0.0:
+            o.g_scale = grid.hx / 6.0
+        if o.fd_delta == 0.0:
+            o.fd_delta = 1e-3 * grid.hx
+        return o
+
+    def c(self, grid: Grid) -> _Options:
+        o = self.resolved(grid)
+        return _Options(o.eps_f, o.eps_g, o.tol, o.max_iter, o.lambda_mode, o.simplex_step,
+                        o.w_g, o.g_scale, o.deriv, o.fd_delta)
+
+
+def _threads(nthreads):
+    return int(nthreads) if nthreads else (os.cpu_count() or 1)
+
+
+def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthreads=None):
+    """B (n,3), G (n,3,3) with G[i,p,j] = dB_p/dx_j, and dB/dlambda (n,3) at given lambda (n,3)."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    n = xyz.shape[0]
+    B = np.zeros((n, 3)); G = np.zeros((n, 3, 3)); dl = np.zeros((n, 3))
+    lib.orc_eval_many(bd.ref, n, _ptr(xyz), _ptr(lam), deriv, fd_delta, _ptr(B), _ptr(G), _ptr(dl),
+                      _threads(nthreads))
+    return B, G, dl
+
+
+def objective(B, G, g_scale: float, w_g: float = 1.0):
+    """Per-point f (Eq. 8), g (Eq. 9), Phi, J = curl B (Eq. 14) and div B."""
+    lib = _load()
+    B = _f64(B).reshape(-1, 3)
+    G = _f64(G).reshape(-1, 9)
+    n = B.shape[0]
+    f = np.zeros(n); g = np.zeros(n); phi = np.zeros(n); J = np.zeros((n, 3)); D = np.zeros(n)
+    fv, gv, pv, dv = (ctypes.c_double() for _ in range(4))
+    Jv = (ctypes.c_double * 3)()
+    for i in range(n):
+        lib.orc_objective(_ptr(B[i]), _ptr(G[i]), g_scale, w_g, ctypes.byref(fv), ctypes.byref(gv),
+                          ctypes.byref(pv), Jv, ctypes.byref(dv))
+        f[i], g[i], phi[i], D[i] = fv.value, gv.value, pv.value, dv.value
+        J[i] = list(Jv)
+    return f, g, phi, J, D
+
+
+def solve(bd: Boundary, xyz, opt: Options | None = None, lam0=None, nthreads=None, codes_cap=128):
+    """Per-point Downhill Simplex over lambda; returns a dict of per-point results."""
+    lib = _load()
+    opt = opt or Options()
+    xyz = _f64(xyz).reshape(-1, 3)
+    n = xyz.shape[0]
+    oc = opt.c(bd.grid)
+    lam = np.zeros((n, 3)); B = np.zeros((n, 3))
+    f = np.zeros(n); g = np.zeros(n); phi = np.zeros(n)
+    iters = np.zeros(n, np.int32); nfev = np.zeros(n, np.int32); status = np.zeros(n, np.int32)
+    codes = np.zeros((n, codes_cap), np.uint8)
+    l0 = None if lam0 is None else _f64(lam0).reshape(-1, 3)
+    lib.orc_solve_many(bd.ref, n, _ptr(xyz), ctypes.byref(oc), None if l0 is None else _ptr(l0),
+                       _ptr(lam), _ptr(B), _ptr(f), _ptr(g), _ptr(phi), _ptr(iters), _ptr(nfev),
+                       _ptr(status), _ptr(codes), codes_cap, _threads(nthreads))
+    code_str = [bytes(row[: int(it)]).decode() for row, it in zip(codes, np.minimum(iters, codes_cap))]
+    return dict(lam=lam, B=B, f=f, g=g, phi=phi, iters=iters, nfev=nfev, status=status,
+                codes=code_str)
+
+
+def vjp(bd: Boundary, xyz, lam, gB, nthreads=None):
+    """dL/dB0 (ny, nx, 3) for dL/dB = gB (n, 3) at fixed lambda: the transpose of Eq. 16."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    gB = _f64(gB).reshape(-1, 3)
+    g = bd.grid
+    out = np.zeros((g.ny * g.nx, 3))
+    lib.orc_vjp(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), _ptr(out), _threads(nthreads))
+    return out.reshape(g.ny, g.nx, 3)
+
+
+def nelder_mead(fun, sim0, tol: float, max_iter: int, codes_cap: int = 256):
+    """Generic simplex search (the oracle's own) from an explicit (n+1, n) initial simplex.
+
+    ``fun(x) -> (value, flag)``; flag != 0 means the point meets the stopping test of Eq. 12."""
+    lib = _load()
+    sim0 = _f64(sim0)
+    n = sim0.shape[1]
+
+    def cb(_ctx, xp, flagp):
+        v, fl = fun(np.array([xp[d] for d in range(n)]))
+        flagp[0] = int(fl)
+        return float(v)
+
+    cfun = FUN(cb)
+    res = _NMResult()
+    codes = ctypes.create_string_buffer(codes_cap)
+    lib.orc_nelder_mead_sim(n, _ptr(sim0), tol, max_iter, cfun, None, ctypes.byref(res), codes,
+                            codes_cap)
+    return dict(x=np.array(res.x[:n]), fx=res.fx, iters=res.iters, nfev=res.nfev,
+                status=res.status, codes=codes.value.decode())

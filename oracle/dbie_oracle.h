@@ -1,0 +1,86 @@
+/*
+ * dbie_oracle.h -- FP64 CPU oracle for the DBIE quadrature (TEST INFRASTRUCTURE ONLY).
+ *
+ * Plain, slow, obviously-correct restatement of the direct boundary integral equation of
+ * Wang, Yan & Tan (Solar Phys., arXiv 1306.1122), Sect. 2.1, Eqs. 6, 8, 9, 13, 14, 16, and of the
+ * per-point Downhill Simplex (Nelder & Mead 1965) search for the pseudo-force-free factor lambda.
+ * Only tests, the package's smoke check and the benchmark's CPU-baseline leg may call this
+ * library; the product path never does. It shares no code with the CUDA path.
+ */
+#ifndef DBIE_ORACLE_H
+#define DBIE_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Bottom boundary (Eq. 3): an nx-by-ny magnetogram, pixel (i, j) centred at
+ * (x0 + i*hx, y0 + j*hy, 0), row-major storage index j*nx + i, pixel area dA.
+ * The field vanishes outside the magnetogram (Sect. 2.1). */
+typedef struct {
+  int32_t nx, ny;
+  double x0, y0, hx, hy, dA;
+  const float *Bx, *By, *Bz;
+} orc_boundary;
+
+/* Options of the lambda search (Sect. 2.1, Eqs. 8-12). */
+typedef struct {
+  double eps_f, eps_g;   /* stopping thresholds of Eq. 12 */
+  double tol;            /* simplex value-spread tolerance */
+  int32_t max_iter;      /* maximum number of simplex iterations */
+  int32_t lambda_mode;   /* 0: three factors (lx, ly, lz) per point, 1: one shared factor */
+  double simplex_step;   /* edge of the initial simplex */
+  double w_g;            /* objective Phi = f + w_g * g */
+  double g_scale;        /* Delta V_i / Delta sigma_i of Eq. 9 */
+  int32_t deriv;         /* 0: analytic derivative at fixed lambda, 1: forward difference */
+  double fd_delta;       /* difference step for deriv = 1 */
+} orc_options;
+
+/* Field and its derivatives at one point for a given lambda triple:
+ *   B[p], G[p][j] = d B_p / d x_j (j = x, y, z), dBdl[p] = d B_p / d lambda_p. */
+void orc_field(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+               double B[3], double G[9], double dBdl[3]);
+
+/* Same, with the spatial derivatives by first-order forward differences of step delta
+ * taken at the same lambda (the zeroth-order rule of Eq. 13). */
+void orc_field_fd(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                  double delta, double B[3], double G[9]);
+
+/* Force-freeness f (Eq. 8), divergence measure g (Eq. 9), J = curl B (Eq. 14), D = div B. */
+void orc_objective(const double B[3], const double G[9], double g_scale, double w_g,
+                   double* f, double* g, double* phi, double J[3], double* D);
+
+/* Generic Downhill Simplex in n dimensions (n <= 3).  fun(ctx, x, &flag) returns the
+ * objective and sets flag != 0 when the point meets the problem's own stopping test. */
+typedef double (*orc_fun)(void* ctx, const double* x, int32_t* flag);
+typedef struct {
+  double x[3];        /* best vertex */
+  double fx;          /* its value */
+  int32_t iters;      /* simplex iterations performed */
+  int32_t nfev;       /* objective evaluations */
+  int32_t status;     /* 0 converged, 1 iteration limit */
+  int32_t ncodes;     /* number of step codes written */
+} orc_nm_result;
+void orc_nelder_mead(int32_t n, const double x0[3], double step, double tol, int32_t max_iter,
+                     orc_fun fun, void* ctx, orc_nm_result* res, char* codes, int32_t codes_cap);
+/* Same, from an explicit initial simplex sim[(n+1)*n]. */
+void orc_nelder_mead_sim(int32_t n, const double* sim, double tol, int32_t max_iter,
+                         orc_fun fun, void* ctx, orc_nm_result* res, char* codes, int32_t codes_cap);
+
+/* Batched entry points over n points (OpenMP over points when nthreads > 1). */
+void orc_eval_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                   int32_t deriv, double fd_delta, double* B, double* G, double* dBdl,
+                   int32_t nthreads);
+void orc_solve_many(const orc_boundary* bd, int64_t n, const double* xyz, const orc_options* opt,
+                    const double* lam0, double* lam, double* B, double* f, double* g,
+                    double* phi, int32_t* iters, int32_t* nfev, int32_t* status,
+                    char* codes, int32_t codes_stride, int32_t nthreads);
+/* Boundary adjoint: gB0[k][p] = sum_i gB[i][p] * a_ik(lambda_pi), the transpose of Eq. 16. */
+void orc_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+             const double* gB, double* gB0, int32_t nthreads);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
