@@ -1,0 +1,372 @@
+"""Benchmark of the DBIE hot path: one step = stage a magnetogram, solve lambda at every point
+(on-device Downhill Simplex, every objective evaluation a full boundary quadrature), then the
+backward pass (boundary adjoint dL/dB0 and dL/dlambda for L = sum |B|^2).
+
+Workload: Low & Lou field (n=1, m=1, l=0.3, Phi=pi/4) on a 128 x 128 boundary, points on the
+64 x 64 x 32 grid x, y in 32..95, z in 1..32 (131,072 points), mixed precision.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is point x pixel pair evaluations per second over the K timed
+steps with inputs resident on the device; `e2e` is the same through the C ABI with host buffers
+(host<->device copies inside the timed region).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("point×boundary pair evals/s and solve time at ≤1e-5 rel err vs FP64, "
+          "fwd+bwd")
+WORKLOAD = "ll128: Low&Lou n=1 m=1 l=0.3 Phi=pi/4, 128x128 boundary, 64x64x32 points (131072)"
+SMS, MUFU_PER_SM_CLK, MAX_SM_MHZ = 152, 16, 2070.0
+MUFU_PER_PAIR = 7           # objective variant, one lambda per component: rsqrt + 3 x (sin, cos)
+FP32_PER_PAIR = 44
+THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
+                 0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
+                 0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
+                 0x100: "display_clock_setting"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def workload():
+    from synth import workloads
+    return workloads.ll128(with_truth=False)
+
+
+# ----------------------------------------------------------------------------- clocks ----
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], 0
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 4:
+                    continue
+                try:
+                    s, m = float(parts[0]), float(parts[1])
+                    r = int(parts[3], 16)
+                except ValueError:
+                    continue
+                if s > 0:
+                    sm.append(s)
+                    mx.append(m)
+                    reasons |= r & ~0x1
+        except OSError:
+            pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": [n for b, n in THROTTLE_BITS.items() if reasons & b]}
+
+
+# ----------------------------------------------------------------------- our arm (GPU) ----
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1306_1122_gb300 as dbie
+    from paper_1306_1122_gb300 import _native as N
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload()
+    m = w.mag
+    npix = m.nx * m.ny
+    n = len(w.points)
+    B0_dev = [torch.from_numpy(c).to(dev) for c in (m.Bx, m.By, m.Bz)]
+    xyz_dev = torch.from_numpy(w.points).to(dev)
+    opt = dbie.Options()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+
+    stream0 = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    h = N.dbie_create(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA, *(ptr(c) for c in B0_dev),
+                      N.DBIE_MEM_DEVICE, stream0)
+    N.dbie_set_profiling(h, 1)
+
+    def step(stats_out):
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        # a1: stage the boundary (B0 -> tile-blocked SoA, pre-scaled) on the device
+        N.dbie_set_boundary(h, *(ptr(c) for c in B0_dev), N.DBIE_MEM_DEVICE, stream)
+        r = dict(B=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                 lam=torch.empty((n, 3), dtype=torch.float64, device=dev),
+                 iters=torch.empty(n, dtype=torch.int32, device=dev),
+                 status=torch.empty(n, dtype=torch.int32, device=dev),
+                 f=torch.empty(n, dtype=torch.float64, device=dev),
+                 g=torch.empty(n, dtype=torch.float64, device=dev))
+        so = N.dbie_solve_out()
+        so.B, so.lambda_, so.iters, so.status, so.f, so.g = (
+            ptr(r[k]) for k in ("B", "lam", "iters", "status", "f", "g"))
+        N.dbie_solve(h, n, ptr(xyz_dev), opt.c(), None, N.DBIE_MEM_DEVICE, so, stream)
+        gB = 2.0 * r["B"]
+        gB0 = torch.empty((m.ny, m.nx, 3), dtype=torch.float64, device=dev)
+        glam = torch.empty((n, 3), dtype=torch.float64, device=dev)
+        N.dbie_vjp(h, n, ptr(xyz_dev), ptr(r["lam"]), ptr(gB), opt.c(), N.DBIE_MEM_DEVICE,
+                   ptr(gB0), ptr(glam), 0, stream)
+        st = N.dbie_get_stats(h, True)   # synchronises: pair-sum kernel event timings
+        stats_out.append(dict(queries=st.queries, rounds=st.rounds, obj_ms=st.objective_ms,
+                              launches=st.launches, obj_pairs=st.objective_pairs))
+        return r
+
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    hh = N.dbie_create(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA, P(m.Bx), P(m.By), P(m.Bz),
+                       N.DBIE_MEM_HOST, None)
+
+    def step_host(h2d, d2h):
+        """Same step through the C ABI with host buffers (copies inside the calls)."""
+        h = hh
+        N.dbie_set_boundary(h, P(m.Bx), P(m.By), P(m.Bz), N.DBIE_MEM_HOST, None)
+        out = dict(B=np.empty((n, 3)), lam=np.empty((n, 3)), iters=np.empty(n, np.int32),
+                   status=np.empty(n, np.int32), f=np.empty(n), g=np.empty(n))
+        so = N.dbie_solve_out()
+        so.B, so.lambda_, so.iters, so.status, so.f, so.g = (
+            P(out[k]) for k in ("B", "lam", "iters", "status", "f", "g"))
+        N.dbie_solve(h, n, P(w.points), opt.c(), None, N.DBIE_MEM_HOST, so, None)
+        gB = 2.0 * out["B"]
+        gB0 = np.empty((m.ny, m.nx, 3))
+        glam = np.empty((n, 3))
+        N.dbie_vjp(h, n, P(w.points), P(out["lam"]), P(gB), opt.c(), N.DBIE_MEM_HOST,
+                   P(gB0), P(glam), 0, None)
+        # inputs: B0 (3 x float32 maps), points for solve and adjoint, lambda and gB for the adjoint
+        h2d.append(3 * npix * 4 + n * 12 + n * 12 + n * 24 + n * 24)
+        # outputs: B, lambda, iters, status, f, g; dL/dB0; dL/dlambda
+        d2h.append(n * (24 + 24 + 4 + 4 + 8 + 8) + npix * 24 + n * 24)
+        return out
+
+    # warm-up
+    for _ in range(args.warmup):
+        step([])
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # timed region: K steps, L2 flushed before each step (outside its events)
+    stats, times = [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record()
+            step(stats)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if world > 1:
+            dist.barrier()
+    times = [a.elapsed_time(b) for a, b in ev]
+    step_ms = sum(times) / len(times)
+    clocks = clk.summary()
+
+    # pair evaluations of one step: simplex queries x pixels + adjoint + dB/dlambda pass
+    q = stats[-1]["queries"]
+    pairs_step = q * npix + 2 * n * npix
+    t_tot = sum(times) / 1e3
+    local_pairs = pairs_step * args.steps
+    if world > 1:
+        t = torch.tensor([t_tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_tot = float(t.item())
+        pr = torch.tensor([float(local_pairs)], device=dev, dtype=torch.float64)
+        dist.all_reduce(pr, op=dist.ReduceOp.SUM)
+        total_pairs = float(pr.item())
+    else:
+        total_pairs = float(local_pairs)
+    value = total_pairs / t_tot
+
+    # roofline of the dominant kernel (objective pair sums), live CUDA-event timing
+    obj_pairs = sum(s["obj_pairs"] for s in stats)
+    obj_ms = sum(s["obj_ms"] for s in stats)
+    launches = sum(s["launches"] for s in stats)
+    achieved = obj_pairs * MUFU_PER_PAIR / (obj_ms / 1e3) / 1e12 if obj_ms > 0 else None
+    peak = SMS * MUFU_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12
+    rounds = stats[-1]["rounds"]
+
+    # e2e through the C ABI with host buffers
+    h2d, d2h = [], []
+    e2e_times = []
+    step_host(h2d, d2h)   # warm
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step_host(h2d, d2h)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = pairs_step / statistics.mean(e2e_times) * (world if world > 1 else 1)
+    N.dbie_destroy(hh)
+    N.dbie_destroy(h)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "pair-evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded Low & Lou field, no observational data)",
+        "config": {"workload": WORKLOAD, "points": n, "boundary": [m.ny, m.nx],
+                   "precision": "mixed (FP32 pair terms, float-float sums, FP64 near field "
+                                "z<=2px, FP64 objective and simplex)",
+                   "fwd_bwd": "solve (Nelder-Mead, tol 1e-6, max 50 it) + adjoint + dL/dlambda",
+                   "pairs_per_step": pairs_step, "simplex_rounds": rounds,
+                   "objective_evals": q, "l2": "flushed before each step (256 MB write)",
+                   "parallelism": f"replicas x{world} (points are independent)"},
+        "solve_ms": step_ms,
+        "roofline": {"bound": "alu", "pipe": "MUFU (rsqrt, sin, cos)",
+                     "kernel": "g1_kernel<float, objective, per-component lambda>",
+                     "achieved": achieved, "peak": peak, "unit": "T MUFU-op/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "per_pair": {"mufu": MUFU_PER_PAIR, "fp32": FP32_PER_PAIR},
+                     "kernel_ms_per_step": obj_ms / args.steps,
+                     "kernel_launches_per_step": launches / args.steps,
+                     "peak_source": "152 SMs x 16 MUFU ops/clk/SM (measured per-clock rate) x "
+                                    "2070 MHz max SM clock"},
+        "e2e": {"value": e2e_value, "unit": "pair-evals/s",
+                "h2d_bytes_per_step": int(h2d[-1]), "d2h_bytes_per_step": int(d2h[-1])},
+        # per step: staging 1, solve 3 + 4 per round (plan, pair sums, near field, simplex),
+        # backward 9 (pack, plan, adjoint, finalize; pack, plan, pair sums, near field, finalize)
+        "gpu_launches": int(args.steps * (1 + 3 + 4 * rounds + 9)),
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# --------------------------------------------------------------------- oracle (CPU) ----
+def oracle_sample_step(w, npts, seed, nthreads):
+    """One sample step of the oracle: lambda search at npts points of the workload plus the
+    adjoint for those points.  Returns (pair evaluations, seconds)."""
+    import oracle
+    m = w.mag
+    bd = oracle.Boundary(oracle.Grid(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA), m.Bx, m.By, m.Bz)
+    idx = np.random.default_rng(seed).choice(len(w.points), npts, replace=False)
+    pts = w.points[idx].astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.solve(bd, pts, oracle.Options(), nthreads=nthreads)
+    oracle.vjp(bd, pts, r["lam"], 2 * r["B"], nthreads=nthreads)
+    oracle.field(bd, pts, r["lam"], nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    npix = m.nx * m.ny
+    pairs = (int(r["nfev"].sum()) + len(pts)) * npix + 2 * len(pts) * npix
+    return pairs, dt
+
+
+def cpu_baseline(w, seconds):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    p, dt = oracle_sample_step(w, max(cores, 16), 1, cores)
+    npts = int(max(cores, min(len(w.points), max(cores, 16) * seconds / max(dt, 1e-3))))
+    p, dt = oracle_sample_step(w, npts, 2, cores)
+    return {"value": p / dt, "unit": "pair-evals/s", "cores": cores, "kind": "oracle",
+            "sample": f"{npts} random points of the workload: full lambda search + adjoint + "
+                      f"dB/dlambda pass, {dt:.1f} s on {cores} host threads"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    w = workload()
+    cores = os.cpu_count() or 1
+    _, dt = oracle_sample_step(w, max(cores, 16), 0, cores)
+    per_step = max(10.0, 150.0 / max(1, args.steps + args.warmup))
+    npts = int(max(cores, min(len(w.points), max(cores, 16) * per_step / max(dt, 1e-3))))
+    for k in range(args.warmup):
+        oracle_sample_step(w, max(cores, 8), 100 + k, cores)
+    tot_p, tot_t = 0, 0.0
+    for k in range(args.steps):
+        p, dt = oracle_sample_step(w, npts, 200 + k, cores)
+        tot_p += p
+        tot_t += dt
+    value = tot_p / tot_t
+    sample = (f"{npts} random points of the workload per step: full lambda search + adjoint + "
+              f"dB/dlambda pass, FP64 oracle on {cores} host threads")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "pair-evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tot_t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Low & Lou field)",
+        "config": {"workload": WORKLOAD, "sample_points_per_step": npts},
+        "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": cores,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,180 @@
+/*
+ * dbie.h -- C ABI of the GB300 DBIE library (libdbie.so).
+ *
+ * The library evaluates the direct boundary integral equation (DBIE) of Wang, Yan & Tan
+ * (Solar Phys., arXiv 1306.1122) for non-linear force-free coronal fields:
+ *
+ *   Eq. 6 / Eq. 16   B_p(r_i) = sum_k a_ik(lambda_pi) B_p0,k,  p = x, y, z,
+ *                    a_ik = z_i [lambda r sin(lambda r) + cos(lambda r)] / (2 pi r^3) * dA,
+ *                    r^2 = (x_k - x_i)^2 + (y_k - y_i)^2 + z_i^2,
+ *
+ * summed over every pixel k of the bottom-boundary magnetogram (Eq. 3; zero field outside it),
+ * with the pixel-centre (midpoint) rule.  lambda_pi is the pseudo-force-free factor of point i
+ * and component p (Sect. 2.1).  On top of the quadrature the library runs the paper's per-point
+ * Downhill Simplex search for lambda (Sect. 2.1), minimising f (Eq. 8) and g (Eq. 9) with the
+ * spatial derivatives of B taken at fixed lambda (the zeroth-order rule of Eq. 13), and the
+ * adjoint of Eq. 16 for gradients.
+ *
+ * Conventions shared by every entry point:
+ *  - Coordinates (x, y, z) and pixel spacings are in one length unit; lambda in 1/length;
+ *    magnetic fields in any unit (the map is linear in B0).
+ *  - Arrays of points are row-major (n, 3) float32: x, y, z per point; z must be > 0.
+ *  - Magnetogram components are row-major (ny, nx) float32: element j*nx + i is the pixel
+ *    centred at (x0 + i*hx, y0 + j*hy).
+ *  - mem_kind says where EVERY pointer argument of that call lives: DBIE_MEM_HOST (ordinary or
+ *    pinned host memory; the call copies in and out and returns when results are in place) or
+ *    DBIE_MEM_DEVICE (device memory of the current CUDA device; the call is asynchronous on
+ *    `stream` unless stated otherwise).
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *  - The caller owns every buffer it passes; the library never frees caller memory.  The
+ *    context owns copies of the boundary and its own scratch; dbie_destroy frees them.
+ *  - Errors are returned as dbie_status; no exception crosses the ABI.  Argument errors are
+ *    detected on the host before any launch.  dbie_last_error() gives a thread-local message.
+ *    Device-side waits are bounded: a wait that does not complete sets an error word that the
+ *    next synchronising call reports as DBIE_ETIMEOUT.
+ */
+#ifndef DBIE_H
+#define DBIE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dbie_ctx dbie_ctx; /* opaque; created by dbie_create, owned by the library */
+
+typedef enum {
+  DBIE_OK = 0,
+  DBIE_EINVAL = 1,     /* invalid argument (null pointer, n < 0, z <= 0, non-finite input ...) */
+  DBIE_ENOMEM = 2,     /* device or host allocation failed */
+  DBIE_ECUDA = 3,      /* a CUDA call failed; message from dbie_last_error() */
+  DBIE_ETIMEOUT = 4,   /* a bounded device-side wait gave up (kernel returned early) */
+  DBIE_EINTERNAL = 5   /* inconsistent internal state */
+} dbie_status;
+
+enum { DBIE_MEM_HOST = 0, DBIE_MEM_DEVICE = 1 };
+enum { DBIE_PREC_MIXED = 0, DBIE_PREC_FP64 = 1 };
+enum { DBIE_LAMBDA_PER_COMPONENT = 0, DBIE_LAMBDA_TIED = 1 };
+/* Per-point result status of dbie_solve. */
+enum { DBIE_PT_CONVERGED = 0, DBIE_PT_MAXITER = 1 };
+
+/* Options of the lambda search (Sect. 2.1, Eqs. 8-12) and of the arithmetic.
+ * Fill with dbie_default_options() and override fields. */
+typedef struct {
+  double eps_f;        /* Eq. 12 threshold on f (default 1e-3) */
+  double eps_g;        /* Eq. 12 threshold on g (default 1e-4) */
+  double tol;          /* stop when the simplex value spread max Phi - min Phi <= tol (1e-6) */
+  int32_t max_iter;    /* maximum simplex iterations per point (default 50) */
+  int32_t lambda_mode; /* DBIE_LAMBDA_PER_COMPONENT (lx, ly, lz; the paper) or DBIE_LAMBDA_TIED */
+  double simplex_step; /* initial simplex edge; <= 0 selects 1 / (max(nx, ny) * hx) */
+  double w_g;          /* objective Phi = f + w_g * g (default 1) */
+  double g_scale;      /* Delta V_i / Delta sigma_i of Eq. 9; <= 0 selects hx / 6 */
+  int32_t precision;   /* DBIE_PREC_MIXED (FP32 pair terms, compensated sums, FP64 near field
+                          and FP64 reductions) or DBIE_PREC_FP64 (FP64 throughout) */
+  int32_t reserved0;
+  double near_z;       /* mixed precision: points with z <= near_z get their near-field pixels
+                          (a 17 x 17 window) summed in FP64; < 0 selects 2 * hx, 0 disables */
+} dbie_options;
+
+/* Per-point outputs of dbie_solve; every pointer may be NULL except B and lambda. */
+typedef struct {
+  double* B;           /* (n, 3): field at the converged lambda */
+  double* lambda;      /* (n, 3): |lambda*| per component (the kernel is even in lambda) */
+  int32_t* iters;      /* (n): simplex iterations */
+  int32_t* status;     /* (n): DBIE_PT_CONVERGED or DBIE_PT_MAXITER */
+  double* f;           /* (n): Eq. 8 at lambda* */
+  double* g;           /* (n): Eq. 9 at lambda* */
+  int32_t* nfev;       /* (n): objective evaluations */
+  char* codes;         /* (n, codes_stride): simplex step codes R/E/O/I/S, NUL-padded */
+  int32_t codes_stride;
+  int32_t reserved0;
+} dbie_solve_out;
+
+/* Timing of the pair-sum kernels recorded while profiling is on (see dbie_set_profiling). */
+typedef struct {
+  int64_t launches;        /* pair-sum kernel launches timed */
+  double kernel_ms;        /* summed CUDA-event time of those launches */
+  double pair_evals;       /* point x pixel pairs they evaluated */
+  double objective_pairs;  /* pairs of the 12-sum objective launches of dbie_solve */
+  double objective_ms;     /* CUDA-event time of those launches */
+  int64_t rounds;          /* simplex rounds run by dbie_solve calls */
+  int64_t queries;         /* objective evaluations (points x trial lambdas) */
+} dbie_stats;
+
+/* Fill `opt` with the defaults listed above. */
+void dbie_default_options(dbie_options* opt);
+
+/* Create a context holding one magnetogram (Eq. 3, Eq. 16 with a_ik's dA = pixel_area).
+ *   nx, ny >= 1; hx, hy > 0; pixel_area > 0 (usually hx * hy); Bx, By, Bz: (ny, nx) float32,
+ *   finite.  The boundary is copied (and pre-scaled by pixel_area / 2 pi) into the context; the
+ *   caller may free its arrays after the call returns.  Synchronises `stream`.
+ *   Errors: DBIE_EINVAL for bad sizes, null or non-finite data; DBIE_ENOMEM; DBIE_ECUDA. */
+dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, double y0, double hx,
+                        double hy, double pixel_area, const float* Bx, const float* By,
+                        const float* Bz, int32_t mem_kind, void* stream);
+
+/* Replace the magnetogram values of an existing context (same grid).  Used when B0 is a
+ * variable (gradients through dbie_vjp).  Asynchronous for device memory. */
+dbie_status dbie_set_boundary(dbie_ctx* ctx, const float* Bx, const float* By, const float* Bz,
+                              int32_t mem_kind, void* stream);
+
+/* Evaluate Eq. 16 at n points for given lambda (n, 3) float32, and optionally
+ *   gradB  (n, 9): gradB[9i + 3p + j] = d B_p / d x_j at fixed lambda (Eq. 13, delta -> 0),
+ *   dBdlam (n, 3): d B_p / d lambda_p,
+ *   fgphi  (n, 3): f (Eq. 8), g (Eq. 9), Phi = f + w_g g (needs gradB's sums; opt gives g_scale, w_g).
+ * B is required when n > 0, the others may be NULL.  opt may be NULL (defaults; precision and near_z are
+ * read from it).  n = 0 is a no-op. */
+dbie_status dbie_eval(dbie_ctx* ctx, int64_t n, const float* xyz, const float* lambda,
+                      const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
+                      double* dBdlam, double* fgphi, void* stream);
+
+/* Solve for lambda point by point (Sect. 2.1): Nelder-Mead on Phi(lambda) = f + w_g g from the
+ * simplex lambda_init + simplex_step * e_j (lambda_init (n, 3) float64, NULL = 0), stopping on
+ * Eq. 12, on the value spread tol, or after max_iter iterations.  The whole iteration runs on
+ * the device (no host round trip per evaluation).  Synchronous: returns when outputs are
+ * written.  out->B and out->lambda are required. */
+dbie_status dbie_solve(dbie_ctx* ctx, int64_t n, const float* xyz, const dbie_options* opt,
+                       const double* lambda_init, int32_t mem_kind, const dbie_solve_out* out,
+                       void* stream);
+
+/* Solve nprob independent problems (each its own context and point set) in one persistent
+ * pair-sum launch per simplex round, with per-problem compaction of converged points.
+ * Arrays of length nprob: ctxs, n, xyz, out (lambda_init may be NULL or hold NULL entries).
+ * All contexts must live on the current device.  Synchronous. */
+dbie_status dbie_solve_batched(int32_t nprob, dbie_ctx* const* ctxs, const int64_t* n,
+                               const float* const* xyz, const dbie_options* opt,
+                               const double* const* lambda_init, int32_t mem_kind,
+                               const dbie_solve_out* out, void* stream);
+
+/* Gradients at fixed lambda (n, 3) float64 for an upstream gradient gB = dL/dB (n, 3) float64:
+ *   gB0  ((ny*nx), 3) float64: dL/dB0_pk = sum_i gB_pi a_ik(lambda_pi), the transpose of Eq. 16,
+ *        computed by recomputing a_ik (no n x N matrix is stored); accumulate != 0 adds to gB0;
+ *   glam (n, 3) float64 or NULL: dL/dlambda_p = gB_p dB_p/dlambda_p.
+ * opt may be NULL (precision is read from it). */
+dbie_status dbie_vjp(dbie_ctx* ctx, int64_t n, const float* xyz, const double* lambda,
+                     const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
+                     double* glam, int32_t accumulate, void* stream);
+
+/* Turn CUDA-event timing of the pair-sum kernels on or off, and read or reset the counters. */
+dbie_status dbie_set_profiling(dbie_ctx* ctx, int32_t enable);
+dbie_status dbie_get_stats(dbie_ctx* ctx, dbie_stats* stats, int32_t reset);
+
+/* Pick launch parameters (CTA size, points per thread) for this device by timing candidates on
+ * the context's boundary; results are cached per (device, variant, boundary size class) in
+ * memory and in the file named by $DBIE_TUNE_CACHE when set.  Synchronises `stream`. */
+dbie_status dbie_autotune(dbie_ctx* ctx, void* stream);
+
+/* Release the context and everything it owns.  NULL is a no-op. */
+void dbie_destroy(dbie_ctx* ctx);
+
+/* Message of the last error on this thread ("" if none). */
+const char* dbie_last_error(void);
+
+/* Library version string. */
+const char* dbie_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBIE_H */

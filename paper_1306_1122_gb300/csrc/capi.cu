@@ -1,0 +1,979 @@
+// capi.cu -- the C ABI (include/dbie.h): contexts, validation, staging, and the host drivers of
+// evaluation, the on-device lambda search and the adjoint.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dbie.h"
+#include "kernels.h"
+
+using namespace dbie;
+
+namespace {
+
+thread_local std::string g_err;
+
+dbie_status fail(dbie_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      return fail(e_ == cudaErrorMemoryAllocation ? DBIE_ENOMEM : DBIE_ECUDA,                \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                       \
+    }                                                                                        \
+  } while (0)
+
+#define DBIE_TRY(expr)                      \
+  do {                                      \
+    dbie_status s_ = (expr);                \
+    if (s_ != DBIE_OK) return s_;           \
+  } while (0)
+
+// Growable device buffer (contents are not preserved when it grows).
+struct DBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+dbie_status ensure(DBuf& b, size_t bytes) {
+  if (bytes <= b.cap && b.p) return DBIE_OK;
+  b.release();
+  const size_t nb = std::max<size_t>(bytes, 256);
+  CUDA_TRY(cudaMalloc(&b.p, nb));
+  b.cap = nb;
+  return DBIE_OK;
+}
+
+// Small per-pass control block on the device.
+struct Misc {
+  PlanHdr plan;
+  int32_t item_off[2];
+  int32_t q_cnt[1];
+  int32_t work;
+  int32_t near_cnt;
+  int32_t bad;
+  int32_t pad[2];
+};
+
+struct SolveBufs {
+  DBuf probs, ppos, lam0, sd, si, q_cnt_pass, item_off, ctrl, out, res, codes;
+  DBuf qpos[2], qlam[2], q_cnt[2], act[2], near[2];
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key;   // launch arguments the cached graph was captured with
+  std::vector<cudaEvent_t> ev;      // profiling events inside the graph (2 per round)
+  void release() {
+    for (DBuf* b : {&probs, &ppos, &lam0, &sd, &si, &q_cnt_pass, &item_off, &ctrl, &out, &res,
+                    &codes})
+      b->release();
+    for (int s = 0; s < 2; ++s)
+      for (DBuf* b : {&qpos[s], &qlam[s], &q_cnt[s], &act[s], &near[s]}) b->release();
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    ev.clear();
+  }
+};
+
+// Device control words of a solve: plan, counters, statistics.
+struct SolveCtrl {
+  PlanHdr plan;
+  int32_t work;
+  int32_t round;
+  int32_t act_cnt[2];
+  int32_t near_cnt[2];
+  int32_t bad;
+  int32_t pad;
+  unsigned long long stat_queries;
+  double stat_pairs;
+};
+
+int device_sm_count(int dev) {
+  int n = 0;
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+// Persistent grid size of a kernel: resident CTAs per SM times SMs.
+struct GridCache {
+  std::mutex mu;
+  std::vector<std::pair<const void*, int>> entries;
+};
+GridCache g_grids;
+
+int persistent_grid(const KernelRef& k, int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_grids.mu);
+    for (auto& e : g_grids.entries)
+      if (e.first == k.fn) return e.second;
+  }
+  if (k.smem > 48 * 1024)
+    cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.nt, k.smem);
+  if (per_sm < 1) per_sm = 1;
+  const int g = per_sm * device_sm_count(dev);
+  std::lock_guard<std::mutex> lk(g_grids.mu);
+  g_grids.entries.push_back({k.fn, g});
+  return g;
+}
+
+}  // namespace
+
+struct dbie_ctx {
+  int device = 0;
+  int32_t nx = 0, ny = 0;
+  double x0 = 0, y0 = 0, hx = 1, hy = 1, dA = 1;
+  int64_t npix = 0;
+  int32_t ntiles = 0;
+  int sm_count = 1;
+  DBuf t32, t64, prob, err, misc;
+  DBuf st_in, st_out, st_aux;     // host-memory staging
+  DBuf qpos, qlam, near_list, out, ptiles;
+  SolveBufs sb;
+  int cfg[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // tuned launch config per variant / tied
+  int vjp_cfg = 0;
+  cudaStream_t cap_stream = nullptr;  // stream used only to capture graphs
+  int32_t* pinned = nullptr;          // pinned host words for polling
+  bool profiling = false;
+  dbie_stats stats{};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;  // eval/vjp launches to time
+  std::vector<double> pending_pairs;
+  std::vector<cudaEvent_t> free_events;
+};
+
+namespace {
+
+dbie_options resolved(const dbie_ctx* c, const dbie_options* o) {
+  dbie_options r;
+  dbie_default_options(&r);
+  if (o) r = *o;
+  if (!(r.simplex_step > 0)) r.simplex_step = 1.0 / (std::max(c->nx, c->ny) * c->hx);
+  if (!(r.g_scale > 0)) r.g_scale = c->hx / 6.0;
+  if (r.near_z < 0) r.near_z = 2.0 * c->hx;
+  return r;
+}
+
+dbie_status check_opts(const dbie_options& o) {
+  if (!(o.tol >= 0) || !std::isfinite(o.tol)) return fail(DBIE_EINVAL, "tol must be >= 0");
+  if (o.max_iter < 0) return fail(DBIE_EINVAL, "max_iter must be >= 0");
+  if (o.lambda_mode != DBIE_LAMBDA_PER_COMPONENT && o.lambda_mode != DBIE_LAMBDA_TIED)
+    return fail(DBIE_EINVAL, "lambda_mode must be DBIE_LAMBDA_PER_COMPONENT or DBIE_LAMBDA_TIED");
+  if (o.precision != DBIE_PREC_MIXED && o.precision != DBIE_PREC_FP64)
+    return fail(DBIE_EINVAL, "precision must be DBIE_PREC_MIXED or DBIE_PREC_FP64");
+  if (!std::isfinite(o.simplex_step) || !std::isfinite(o.w_g) || !std::isfinite(o.g_scale) ||
+      !std::isfinite(o.near_z) || !std::isfinite(o.eps_f) || !std::isfinite(o.eps_g))
+    return fail(DBIE_EINVAL, "options must be finite");
+  return DBIE_OK;
+}
+
+dbie_status check_mem(int32_t mem_kind) {
+  if (mem_kind != DBIE_MEM_HOST && mem_kind != DBIE_MEM_DEVICE)
+    return fail(DBIE_EINVAL, "mem_kind must be DBIE_MEM_HOST or DBIE_MEM_DEVICE");
+  return DBIE_OK;
+}
+
+dbie_status host_points_ok(const float* xyz, int64_t n) {
+  for (int64_t i = 0; i < n; ++i) {
+    const float x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) || !(z > 0.f))
+      return fail(DBIE_EINVAL, "point " + std::to_string(i) + " is not finite or has z <= 0");
+  }
+  return DBIE_OK;
+}
+
+dbie_status host_finite(const float* a, int64_t n, const char* what) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return fail(DBIE_EINVAL, std::string(what) + " has a non-finite value");
+  return DBIE_OK;
+}
+dbie_status host_finite(const double* a, int64_t n, const char* what) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return fail(DBIE_EINVAL, std::string(what) + " has a non-finite value");
+  return DBIE_OK;
+}
+
+// Reads and clears the device error word (synchronises the stream).
+dbie_status check_device_error(dbie_ctx* c, cudaStream_t s) {
+  CUDA_TRY(cudaStreamSynchronize(s));
+  unsigned e = 0;
+  CUDA_TRY(cudaMemcpy(&e, c->err.p, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (e) {
+    CUDA_TRY(cudaMemset(c->err.p, 0, sizeof(unsigned)));
+    char buf[128];
+    std::snprintf(buf, sizeof buf, "a bounded device wait gave up (error word 0x%x)", e);
+    return fail(DBIE_ETIMEOUT, buf);
+  }
+  return DBIE_OK;
+}
+
+cudaEvent_t take_event(dbie_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void resolve_pending(dbie_ctx* c) {
+  for (size_t i = 0; i < c->pending.size(); ++i) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(c->pending[i].second) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, c->pending[i].first, c->pending[i].second) == cudaSuccess) {
+      c->stats.kernel_ms += ms;
+      c->stats.launches += 1;
+      c->stats.pair_evals += c->pending_pairs[i];
+    } else {
+      (void)cudaGetLastError();
+    }
+    c->free_events.push_back(c->pending[i].first);
+    c->free_events.push_back(c->pending[i].second);
+  }
+  c->pending.clear();
+  c->pending_pairs.clear();
+}
+
+dbie_status launch_kernel(const KernelRef& k, int grid, void* args, cudaStream_t s) {
+  void* argv[1] = {args};
+  CUDA_TRY(cudaLaunchKernel(k.fn, dim3(grid), dim3(k.nt), argv, k.smem, s));
+  return DBIE_OK;
+}
+
+int var_of(bool grad, bool dlam) {
+  return grad ? (dlam ? VAR_OBJL : VAR_OBJ) : (dlam ? VAR_VL : VAR_V);
+}
+
+KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64) {
+  return fp64 ? g1_ref_f64(var, tied) : g1_ref_f32(var, tied, c->cfg[var][tied ? 1 : 0]);
+}
+
+// One pair-sum pass over n queries of this context (single problem): pack, plan, sweep,
+// near-field correction.  Results are in c->out as item chunks described by c->misc.
+dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, int64_t n,
+                        const float* d_xyz, const float* d_lamf, const double* d_lamd,
+                        cudaStream_t s) {
+  Misc* m = c->misc.as<Misc>();
+  DBIE_TRY(ensure(c->qpos, sizeof(float4) * n));
+  DBIE_TRY(ensure(c->qlam, sizeof(Lam4) * n));
+  const bool near_on = !fp64 && o.near_z > 0;
+  if (near_on) DBIE_TRY(ensure(c->near_list, sizeof(int32_t) * n));
+  CUDA_TRY(cudaMemsetAsync(&m->near_cnt, 0, sizeof(int32_t), s));
+  launch_pack_eval(n, d_xyz, d_lamf, d_lamd, c->qpos.as<float4>(), c->qlam.as<Lam4>(),
+                   c->near_list.as<int32_t>(), &m->near_cnt, near_on ? 1 : 0, o.near_z, s);
+  const KernelRef k = g1_ref(c, var, false, fp64);
+  const int grid = persistent_grid(k, c->device);
+  const int64_t nblk = (n + k.qper - 1) / k.qper;
+  const int64_t target = 2LL * grid;
+  int64_t nsplit = 1;
+  if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, c->ntiles);
+  const int64_t nitems = nblk * nsplit;
+  if (nitems > INT32_MAX / 2) return fail(DBIE_EINVAL, "too many points for one call");
+  const int nsum = 3 * nsum_per_comp(var);
+  DBIE_TRY(ensure(c->out, sizeof(double) * nitems * nsum * k.qper));
+  launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit, k.qper,
+                     (int)n, s);
+  G1Args a{};
+  a.probs = c->prob.as<ProbDesc>();
+  a.nprob = 1;
+  a.plan = &m->plan;
+  a.item_off = m->item_off;
+  a.q_cnt = m->q_cnt;
+  a.work = &m->work;
+  a.qpos = c->qpos.as<float4>();
+  a.qlam = c->qlam.as<Lam4>();
+  a.out = c->out.as<double>();
+  a.err = c->err.as<unsigned>();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->profiling) {
+    e0 = take_event(c);
+    e1 = take_event(c);
+    CUDA_TRY(cudaEventRecord(e0, s));
+  }
+  DBIE_TRY(launch_kernel(k, grid, &a, s));
+  if (c->profiling) {
+    CUDA_TRY(cudaEventRecord(e1, s));
+    c->pending.push_back({e0, e1});
+    c->pending_pairs.push_back((double)n * (double)c->npix);
+  }
+  if (near_on)
+    launch_nearfield(var, false, c->prob.as<ProbDesc>(), c->near_list.as<int32_t>(), &m->near_cnt,
+                     c->qpos.as<float4>(), c->qlam.as<Lam4>(), &m->plan, m->item_off,
+                     c->out.as<double>(), 2 * c->sm_count, s);
+  CUDA_TRY(cudaGetLastError());
+  return DBIE_OK;
+}
+
+struct Staging {  // host-memory calls: where each argument lives on the device
+  size_t off = 0;
+  char* base = nullptr;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+// =====================================================================================
+extern "C" {
+
+const char* dbie_last_error(void) { return g_err.c_str(); }
+
+const char* dbie_version(void) { return "dbie-gb300 0.1 (sm_103a)"; }
+
+void dbie_default_options(dbie_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof *o);
+  o->eps_f = 1e-3;
+  o->eps_g = 1e-4;
+  o->tol = 1e-6;
+  o->max_iter = 50;
+  o->lambda_mode = DBIE_LAMBDA_PER_COMPONENT;
+  o->simplex_step = 0.0;
+  o->w_g = 1.0;
+  o->g_scale = 0.0;
+  o->precision = DBIE_PREC_MIXED;
+  o->near_z = -1.0;
+}
+
+void dbie_destroy(dbie_ctx* c) {
+  if (!c) return;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
+                  &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles})
+    b->release();
+  c->sb.release();
+  for (auto& pr : c->pending) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  for (cudaEvent_t e : c->free_events) cudaEventDestroy(e);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  cudaSetDevice(prev);
+  delete c;
+}
+
+static dbie_status stage_boundary(dbie_ctx* c, const float* Bx, const float* By, const float* Bz,
+                                  int32_t mem_kind, cudaStream_t s) {
+  const float* src[3] = {Bx, By, Bz};
+  const int64_t npix = c->npix;
+  if (mem_kind == DBIE_MEM_HOST) {
+    for (int p = 0; p < 3; ++p) DBIE_TRY(host_finite(src[p], npix, "magnetogram"));
+    DBIE_TRY(ensure(c->st_in, 3 * align256(sizeof(float) * npix)));
+    Staging st{0, c->st_in.as<char>()};
+    float* d[3];
+    for (int p = 0; p < 3; ++p) {
+      d[p] = st.take<float>(npix);
+      CUDA_TRY(cudaMemcpyAsync(d[p], src[p], sizeof(float) * npix, cudaMemcpyHostToDevice, s));
+    }
+    launch_stage_boundary(d[0], d[1], d[2], c->nx, c->ny, c->x0, c->y0, c->hx, c->hy,
+                          c->dA / TWO_PI, c->ntiles, c->t32.as<float>(), c->t64.as<double>(), s);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(s));   // staging buffer may be reused by the next call
+  } else {
+    Misc* m = c->misc.as<Misc>();
+    CUDA_TRY(cudaMemsetAsync(&m->bad, 0, sizeof(int32_t), s));
+    for (int p = 0; p < 3; ++p) launch_count_bad(src[p], npix, 0, &m->bad, s);
+    int32_t bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, &m->bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return fail(DBIE_EINVAL, "magnetogram has a non-finite value");
+    launch_stage_boundary(Bx, By, Bz, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy, c->dA / TWO_PI,
+                          c->ntiles, c->t32.as<float>(), c->t64.as<double>(), s);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return DBIE_OK;
+}
+
+dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, double y0, double hx,
+                        double hy, double pixel_area, const float* Bx, const float* By,
+                        const float* Bz, int32_t mem_kind, void* stream) {
+  if (!out) return fail(DBIE_EINVAL, "out is NULL");
+  *out = nullptr;
+  DBIE_TRY(check_mem(mem_kind));
+  if (nx < 1 || ny < 1) return fail(DBIE_EINVAL, "nx and ny must be >= 1");
+  if ((int64_t)nx * ny > (int64_t)1 << 30) return fail(DBIE_EINVAL, "magnetogram too large");
+  if (!(hx > 0) || !(hy > 0) || !std::isfinite(hx) || !std::isfinite(hy))
+    return fail(DBIE_EINVAL, "hx and hy must be finite and > 0");
+  if (!(pixel_area > 0) || !std::isfinite(pixel_area))
+    return fail(DBIE_EINVAL, "pixel_area must be finite and > 0");
+  if (!std::isfinite(x0) || !std::isfinite(y0)) return fail(DBIE_EINVAL, "x0, y0 must be finite");
+  if (!Bx || !By || !Bz) return fail(DBIE_EINVAL, "Bx, By, Bz must not be NULL");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  dbie_ctx* c = new dbie_ctx();
+  cudaGetDevice(&c->device);
+  c->sm_count = device_sm_count(c->device);
+  c->nx = nx; c->ny = ny; c->x0 = x0; c->y0 = y0; c->hx = hx; c->hy = hy; c->dA = pixel_area;
+  c->npix = (int64_t)nx * ny;
+  c->ntiles = (int32_t)((c->npix + TILE - 1) / TILE);
+  auto bail = [&](dbie_status st) { std::string m = g_err; dbie_destroy(c); g_err = m; return st; };
+  dbie_status st;
+  if ((st = ensure(c->t32, sizeof(float) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->t64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->prob, sizeof(ProbDesc))) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->err, sizeof(unsigned))) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->misc, sizeof(Misc))) != DBIE_OK) return bail(st);
+  if (cudaMemsetAsync(c->err.p, 0, sizeof(unsigned), s) != cudaSuccess ||
+      cudaMemsetAsync(c->misc.p, 0, sizeof(Misc), s) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaHostAlloc((void**)&c->pinned, 64, cudaHostAllocDefault) != cudaSuccess)
+    return bail(fail(DBIE_ECUDA, "context set-up failed"));
+  ProbDesc pd{};
+  pd.tiles32 = c->t32.as<float>();
+  pd.tiles64 = c->t64.as<double>();
+  pd.ntiles = c->ntiles;
+  pd.nx = nx; pd.ny = ny;
+  pd.x0 = x0; pd.y0 = y0; pd.hx = hx; pd.hy = hy;
+  pd.step = 0.0; pd.g_scale = 0.0; pd.near_z = 0.0;
+  pd.q_off = 0; pd.pt_off = 0; pd.npts = 0;
+  if (cudaMemcpyAsync(c->prob.p, &pd, sizeof pd, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return bail(fail(DBIE_ECUDA, "copy of the problem descriptor failed"));
+  if ((st = stage_boundary(c, Bx, By, Bz, mem_kind, s)) != DBIE_OK) return bail(st);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(DBIE_ECUDA, "create: sync failed"));
+  *out = c;
+  return DBIE_OK;
+}
+
+dbie_status dbie_set_boundary(dbie_ctx* c, const float* Bx, const float* By, const float* Bz,
+                              int32_t mem_kind, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  if (!Bx || !By || !Bz) return fail(DBIE_EINVAL, "Bx, By, Bz must not be NULL");
+  CUDA_TRY(cudaSetDevice(c->device));
+  return stage_boundary(c, Bx, By, Bz, mem_kind, static_cast<cudaStream_t>(stream));
+}
+
+dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lambda,
+                      const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
+                      double* dBdlam, double* fgphi, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (n > ((int64_t)1 << 31) - 1) return fail(DBIE_EINVAL, "n too large");
+  if (n > 0 && (!xyz || !lambda || !B))
+    return fail(DBIE_EINVAL, "xyz, lambda and B must not be NULL");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  if (n == 0) return DBIE_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const int var = var_of(gradB || fgphi, dBdlam != nullptr);
+  const float* d_xyz = xyz;
+  const float* d_lam = lambda;
+  double *dB = B, *dG = gradB, *dL = dBdlam, *dF = fgphi;
+  if (mem_kind == DBIE_MEM_HOST) {
+    DBIE_TRY(host_points_ok(xyz, n));
+    DBIE_TRY(host_finite(lambda, 3 * n, "lambda"));
+    DBIE_TRY(ensure(c->st_in, 2 * align256(sizeof(float) * 3 * n)));
+    DBIE_TRY(ensure(c->st_out, 4 * align256(sizeof(double) * 9 * n)));
+    Staging si{0, c->st_in.as<char>()}, so{0, c->st_out.as<char>()};
+    float* t_xyz = si.take<float>(3 * n);
+    float* t_lam = si.take<float>(3 * n);
+    CUDA_TRY(cudaMemcpyAsync(t_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(t_lam, lambda, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    d_xyz = t_xyz;
+    d_lam = t_lam;
+    dB = so.take<double>(3 * n);
+    dG = gradB ? so.take<double>(9 * n) : nullptr;
+    dL = dBdlam ? so.take<double>(3 * n) : nullptr;
+    dF = fgphi ? so.take<double>(3 * n) : nullptr;
+  }
+  DBIE_TRY(pass_single(c, var, fp64, o, n, d_xyz, d_lam, nullptr, s));
+  Misc* m = c->misc.as<Misc>();
+  launch_finalize_eval(var, n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
+                       c->qlam.as<Lam4>(), o.g_scale, o.w_g, dB, dG, dL, nullptr, dF, s);
+  CUDA_TRY(cudaGetLastError());
+  if (mem_kind == DBIE_MEM_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(B, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (gradB) CUDA_TRY(cudaMemcpyAsync(gradB, dG, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, s));
+    if (dBdlam) CUDA_TRY(cudaMemcpyAsync(dBdlam, dL, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (fgphi) CUDA_TRY(cudaMemcpyAsync(fgphi, dF, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
+dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
+                     const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
+                     double* glam, int32_t accumulate, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (n > ((int64_t)1 << 31) - 1) return fail(DBIE_EINVAL, "n too large");
+  if (!gB0) return fail(DBIE_EINVAL, "gB0 must not be NULL");
+  if (n > 0 && (!xyz || !lambda || !gB)) return fail(DBIE_EINVAL, "xyz, lambda, gB must not be NULL");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const int64_t npix = c->npix;
+  const float* d_xyz = xyz;
+  const double *d_lam = lambda, *d_gB = gB;
+  double *d_gB0 = gB0, *d_glam = glam;
+  if (mem_kind == DBIE_MEM_HOST) {
+    if (n > 0) {
+      DBIE_TRY(host_points_ok(xyz, n));
+      DBIE_TRY(host_finite(lambda, 3 * n, "lambda"));
+      DBIE_TRY(host_finite(gB, 3 * n, "gB"));
+    }
+    DBIE_TRY(ensure(c->st_in, align256(sizeof(float) * 3 * n) + 2 * align256(sizeof(double) * 3 * n)));
+    DBIE_TRY(ensure(c->st_out, align256(sizeof(double) * 3 * npix) + align256(sizeof(double) * 3 * n)));
+    Staging si{0, c->st_in.as<char>()}, so{0, c->st_out.as<char>()};
+    float* t_xyz = si.take<float>(3 * n);
+    double* t_lam = si.take<double>(3 * n);
+    double* t_gB = si.take<double>(3 * n);
+    if (n > 0) {
+      CUDA_TRY(cudaMemcpyAsync(t_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(t_lam, lambda, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(t_gB, gB, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    }
+    d_xyz = t_xyz; d_lam = t_lam; d_gB = t_gB;
+    d_gB0 = so.take<double>(3 * npix);
+    d_glam = glam ? so.take<double>(3 * n) : nullptr;
+    if (accumulate)
+      CUDA_TRY(cudaMemcpyAsync(d_gB0, gB0, sizeof(double) * 3 * npix, cudaMemcpyHostToDevice, s));
+  }
+  if (n == 0) {
+    if (!accumulate) CUDA_TRY(cudaMemsetAsync(d_gB0, 0, sizeof(double) * 3 * npix, s));
+  } else {
+    // Adjoint sweep: pixels in registers, point tiles through shared memory.
+    const int nptiles = (int)((n + TILE - 1) / TILE);
+    DBIE_TRY(ensure(c->ptiles, (size_t)nptiles * VJP_NFIELD * TILE * (fp64 ? 8 : 4)));
+    launch_pack_vjp(n, d_xyz, d_lam, d_gB, 0, nptiles, c->ptiles.as<float>(),
+                    c->ptiles.as<double>(), fp64 ? 1 : 0, s);
+    const KernelRef k = vjp_ref(fp64, false, c->vjp_cfg);
+    const int grid = persistent_grid(k, c->device);
+    const int64_t nblk = (npix + k.qper - 1) / k.qper;
+    const int64_t target = 2LL * grid;
+    int64_t nsplit = 1;
+    if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, nptiles);
+    const int64_t nitems = nblk * nsplit;
+    DBIE_TRY(ensure(c->out, sizeof(double) * nitems * 3 * k.qper));
+    Misc* m = c->misc.as<Misc>();
+    launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit,
+                       k.qper, (int)npix, s);
+    VjpArgs a{};
+    a.ptiles32 = c->ptiles.as<float>();
+    a.ptiles64 = c->ptiles.as<double>();
+    a.nptiles = nptiles;
+    a.npix = (int32_t)npix;
+    a.btiles32 = c->t32.as<float>();
+    a.btiles64 = c->t64.as<double>();
+    a.plan = &m->plan;
+    a.work = &m->work;
+    a.out = c->out.as<double>();
+    a.err = c->err.as<unsigned>();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+      e0 = take_event(c);
+      e1 = take_event(c);
+      CUDA_TRY(cudaEventRecord(e0, s));
+    }
+    DBIE_TRY(launch_kernel(k, grid, &a, s));
+    if (c->profiling) {
+      CUDA_TRY(cudaEventRecord(e1, s));
+      c->pending.push_back({e0, e1});
+      c->pending_pairs.push_back((double)n * (double)npix);
+    }
+    launch_finalize_vjp(npix, &m->plan, c->out.as<double>(), c->dA / TWO_PI, d_gB0,
+                        accumulate ? 1 : 0, s);
+    CUDA_TRY(cudaGetLastError());
+    if (d_glam) {
+      // dL/dlambda_p = gB_p * z lambda_p Sl_p, from a value + dB/dlambda pass.
+      DBIE_TRY(pass_single(c, VAR_VL, fp64, o, n, d_xyz, nullptr, d_lam, s));
+      launch_finalize_eval(VAR_VL, n, &m->plan, m->item_off, c->out.as<double>(),
+                           c->qpos.as<float4>(), c->qlam.as<Lam4>(), o.g_scale, o.w_g, nullptr,
+                           nullptr, d_glam, d_gB, nullptr, s);
+      CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (mem_kind == DBIE_MEM_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(gB0, d_gB0, sizeof(double) * 3 * npix, cudaMemcpyDeviceToHost, s));
+    if (glam && n > 0)
+      CUDA_TRY(cudaMemcpyAsync(glam, d_glam, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
+// -------------------------------------------------------------------------- solve ----
+static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_t* n,
+                              const float* const* xyz, const dbie_options* opt,
+                              const double* const* lam_init, int32_t mem_kind,
+                              const dbie_solve_out* out, cudaStream_t s) {
+  dbie_ctx* c = ctxs[0];
+  CUDA_TRY(cudaSetDevice(c->device));
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const bool tied = o.lambda_mode == DBIE_LAMBDA_TIED;
+  const int dim = tied ? 1 : 3;
+  // Per-problem offsets.
+  std::vector<int64_t> pt_off(nprob + 1, 0);
+  for (int p = 0; p < nprob; ++p) pt_off[p + 1] = pt_off[p] + n[p];
+  const int64_t N = pt_off[nprob];
+  if (N == 0) return DBIE_OK;
+  if (N > ((int64_t)1 << 31) / 4 - 1) return fail(DBIE_EINVAL, "too many points for one solve");
+  const int64_t Qcap = (int64_t)(dim + 1) * N;
+  SolveBufs& b = c->sb;
+  int codes_stride = 0;
+  for (int p = 0; p < nprob; ++p)
+    if (out[p].codes) codes_stride = std::max(codes_stride, (int)out[p].codes_stride);
+  codes_stride = std::min(codes_stride, std::max(o.max_iter, 1));
+
+  const KernelRef k = g1_ref(c, VAR_OBJ, tied, fp64);
+  const int grid = persistent_grid(k, c->device);
+  const int target = 2 * grid;
+  const int64_t items_cap = std::max<int64_t>((Qcap + k.qper - 1) / k.qper + nprob, 2LL * target) + 1;
+
+  DBIE_TRY(ensure(b.probs, sizeof(ProbDesc) * nprob));
+  DBIE_TRY(ensure(b.ppos, sizeof(float4) * N));
+  DBIE_TRY(ensure(b.sd, sizeof(double) * D_NFIELDS * N));
+  DBIE_TRY(ensure(b.si, sizeof(int32_t) * I_NFIELDS * N));
+  DBIE_TRY(ensure(b.q_cnt_pass, sizeof(int32_t) * nprob));
+  DBIE_TRY(ensure(b.item_off, sizeof(int32_t) * (nprob + 1)));
+  DBIE_TRY(ensure(b.ctrl, sizeof(SolveCtrl)));
+  DBIE_TRY(ensure(b.out, sizeof(double) * items_cap * 12 * k.qper));
+  DBIE_TRY(ensure(b.res, align256(sizeof(double) * 8 * N) + align256(sizeof(int32_t) * 3 * N)));
+  if (codes_stride) DBIE_TRY(ensure(b.codes, (size_t)codes_stride * N));
+  for (int sd = 0; sd < 2; ++sd) {
+    DBIE_TRY(ensure(b.qpos[sd], sizeof(float4) * Qcap));
+    DBIE_TRY(ensure(b.qlam[sd], sizeof(Lam4) * Qcap));
+    DBIE_TRY(ensure(b.q_cnt[sd], sizeof(int32_t) * nprob));
+    DBIE_TRY(ensure(b.act[sd], sizeof(int32_t) * N));
+    if (!fp64) DBIE_TRY(ensure(b.near[sd], sizeof(int32_t) * Qcap));
+  }
+  bool any_init = false;
+  for (int p = 0; p < nprob; ++p) any_init |= (lam_init && lam_init[p]);
+  if (any_init) DBIE_TRY(ensure(b.lam0, sizeof(double) * 3 * N));
+
+  // Problems and points.
+  std::vector<ProbDesc> pds(nprob);
+  for (int p = 0; p < nprob; ++p) {
+    dbie_ctx* cp = ctxs[p];
+    ProbDesc& pd = pds[p];
+    pd = ProbDesc{};
+    pd.tiles32 = cp->t32.as<float>();
+    pd.tiles64 = cp->t64.as<double>();
+    pd.ntiles = cp->ntiles;
+    pd.nx = cp->nx; pd.ny = cp->ny;
+    pd.x0 = cp->x0; pd.y0 = cp->y0; pd.hx = cp->hx; pd.hy = cp->hy;
+    const dbie_options op = resolved(cp, opt);   // size- and spacing-dependent defaults
+    pd.step = op.simplex_step;
+    pd.g_scale = op.g_scale;
+    pd.near_z = (!fp64 && op.near_z > 0) ? op.near_z : 0.0;
+    pd.q_off = (int64_t)(dim + 1) * pt_off[p];
+    pd.pt_off = pt_off[p];
+    pd.npts = n[p];
+  }
+  CUDA_TRY(cudaMemcpyAsync(b.probs.p, pds.data(), sizeof(ProbDesc) * nprob, cudaMemcpyHostToDevice, s));
+  SolveCtrl* ctrl = b.ctrl.as<SolveCtrl>();
+  CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(SolveCtrl), s));
+  for (int p = 0; p < nprob; ++p) {
+    if (n[p] == 0) continue;
+    const float* src = xyz[p];
+    const float* dsrc = src;
+    if (mem_kind == DBIE_MEM_HOST) {
+      DBIE_TRY(host_points_ok(src, n[p]));
+      DBIE_TRY(ensure(c->st_in, sizeof(float) * 3 * n[p]));
+      CUDA_TRY(cudaMemcpyAsync(c->st_in.p, src, sizeof(float) * 3 * n[p], cudaMemcpyHostToDevice, s));
+      dsrc = c->st_in.as<float>();
+    } else {
+      launch_count_bad(src, n[p], 1, &ctrl->bad, s);
+    }
+    launch_pack_points(n[p], dsrc, p, b.ppos.as<float4>() + pt_off[p], s);
+    if (any_init) {
+      double* dst = b.lam0.as<double>() + 3 * pt_off[p];
+      if (lam_init[p]) {
+        if (mem_kind == DBIE_MEM_HOST) DBIE_TRY(host_finite(lam_init[p], 3 * n[p], "lambda_init"));
+        CUDA_TRY(cudaMemcpyAsync(dst, lam_init[p], sizeof(double) * 3 * n[p],
+                                 mem_kind == DBIE_MEM_HOST ? cudaMemcpyHostToDevice
+                                                           : cudaMemcpyDeviceToDevice, s));
+      } else {
+        CUDA_TRY(cudaMemsetAsync(dst, 0, sizeof(double) * 3 * n[p], s));
+      }
+    }
+    if (mem_kind == DBIE_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(s));  // staging reuse
+  }
+  if (mem_kind == DBIE_MEM_DEVICE) {
+    CUDA_TRY(cudaMemcpyAsync(c->pinned, &ctrl->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->pinned[0]) return fail(DBIE_EINVAL, "a point is not finite or has z <= 0");
+  }
+  for (int sd = 0; sd < 2; ++sd) CUDA_TRY(cudaMemsetAsync(b.q_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
+  if (codes_stride) CUDA_TRY(cudaMemsetAsync(b.codes.p, 0, (size_t)codes_stride * N, s));
+
+  // Kernel arguments.
+  char* rb = b.res.as<char>();
+  double* res_B = reinterpret_cast<double*>(rb);
+  double* res_lam = res_B + 3 * N;
+  double* res_f = res_lam + 3 * N;
+  double* res_g = res_f + N;
+  int32_t* res_i = reinterpret_cast<int32_t*>(rb + align256(sizeof(double) * 8 * N));
+  SolveArgs sa[2];
+  bool near_on = false;
+  for (int p = 0; p < nprob; ++p) near_on |= pds[p].near_z > 0;
+  for (int cur = 0; cur < 2; ++cur) {
+    SolveArgs& a = sa[cur];
+    a = SolveArgs{};
+    a.probs = b.probs.as<ProbDesc>();
+    a.nprob = nprob;
+    a.N = N;
+    a.ppos = b.ppos.as<float4>();
+    a.sd = b.sd.as<double>();
+    a.si = b.si.as<int32_t>();
+    const int nx_ = cur ^ 1;
+    a.cur = RoundBuf{b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(), b.q_cnt[cur].as<int32_t>(),
+                     b.act[cur].as<int32_t>(), &ctrl->act_cnt[cur], b.near[cur].as<int32_t>(),
+                     &ctrl->near_cnt[cur]};
+    a.nxt = RoundBuf{b.qpos[nx_].as<float4>(), b.qlam[nx_].as<Lam4>(), b.q_cnt[nx_].as<int32_t>(),
+                     b.act[nx_].as<int32_t>(), &ctrl->act_cnt[nx_], b.near[nx_].as<int32_t>(),
+                     &ctrl->near_cnt[nx_]};
+    a.out = b.out.as<double>();
+    a.plan = &ctrl->plan;
+    a.item_off = b.item_off.as<int32_t>();
+    a.o = SolveOpts{o.eps_f, o.eps_g, o.tol, o.w_g, o.max_iter, dim, near_on ? 1 : 0, 0};
+    a.res_B = res_B;
+    a.res_lam = res_lam;
+    a.res_f = res_f;
+    a.res_g = res_g;
+    a.res_iters = res_i;
+    a.res_status = res_i + N;
+    a.res_nfev = res_i + 2 * N;
+    a.codes = codes_stride ? b.codes.as<char>() : nullptr;
+    a.codes_stride = codes_stride;
+    a.err = c->err.as<unsigned>();
+  }
+  // Initial simplex and its queries go to side 0.
+  SolveArgs a0 = sa[1];  // "next" of the side-1 round is side 0
+  const int nm_grid = (int)std::min<int64_t>((N + 127) / 128, 8LL * c->sm_count);
+  launch_solve_init(a0, any_init ? b.lam0.as<double>() : nullptr,
+                    (int)std::min<int64_t>((N + 255) / 256, 8LL * c->sm_count), s);
+  CUDA_TRY(cudaGetLastError());
+
+  // One simplex round = plan, pair sums (objective variant), near-field correction, step.
+  constexpr int K = 4;  // rounds per graph launch (even: the ping-pong side returns to 0)
+  auto record_rounds = [&](cudaStream_t cs) -> dbie_status {
+    for (int r = 0; r < K; ++r) {
+      const int cur = r & 1;
+      PlanArgs pa{};
+      pa.probs = b.probs.as<ProbDesc>();
+      pa.nprob = nprob;
+      pa.qper = k.qper;
+      pa.target_items = target;
+      pa.nsplit_cap = 1 << 20;
+      pa.q_cnt_cur = b.q_cnt[cur].as<int32_t>();
+      pa.q_cnt_pass = b.q_cnt_pass.as<int32_t>();
+      pa.item_off = b.item_off.as<int32_t>();
+      pa.plan = &ctrl->plan;
+      pa.work = &ctrl->work;
+      pa.q_cnt_nxt = b.q_cnt[cur ^ 1].as<int32_t>();
+      pa.act_cnt_nxt = &ctrl->act_cnt[cur ^ 1];
+      pa.near_cnt_nxt = &ctrl->near_cnt[cur ^ 1];
+      pa.round_ctr = &ctrl->round;
+      pa.stat_queries = &ctrl->stat_queries;
+      pa.stat_pairs = &ctrl->stat_pairs;
+      launch_plan_round(pa, cs);
+      G1Args ga{};
+      ga.probs = b.probs.as<ProbDesc>();
+      ga.nprob = nprob;
+      ga.plan = &ctrl->plan;
+      ga.item_off = b.item_off.as<int32_t>();
+      ga.q_cnt = b.q_cnt_pass.as<int32_t>();
+      ga.work = &ctrl->work;
+      ga.qpos = b.qpos[cur].as<float4>();
+      ga.qlam = b.qlam[cur].as<Lam4>();
+      ga.out = b.out.as<double>();
+      ga.err = c->err.as<unsigned>();
+      // External event records become event-record nodes of the graph (plain records inside a
+      // capture only order work and are never timestamped).
+      if (c->profiling) CUDA_TRY(cudaEventRecordWithFlags(b.ev[2 * r], cs, cudaEventRecordExternal));
+      DBIE_TRY(launch_kernel(k, grid, &ga, cs));
+      if (c->profiling)
+        CUDA_TRY(cudaEventRecordWithFlags(b.ev[2 * r + 1], cs, cudaEventRecordExternal));
+      if (near_on)
+        launch_nearfield(VAR_OBJ, tied, b.probs.as<ProbDesc>(), b.near[cur].as<int32_t>(),
+                         &ctrl->near_cnt[cur], b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(),
+                         &ctrl->plan, b.item_off.as<int32_t>(), b.out.as<double>(),
+                         2 * c->sm_count, cs);
+      launch_nm_step(sa[cur], nm_grid, cs);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return DBIE_OK;
+  };
+  if (c->profiling && b.ev.size() != 2 * K) {
+    for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
+    b.ev.assign(2 * K, nullptr);
+    for (auto& e : b.ev) CUDA_TRY(cudaEventCreate(&e));
+  }
+  // Capture (or reuse) the graph of K rounds; the key is every launch argument.
+  std::vector<unsigned char> key(sizeof sa + sizeof(KernelRef) + 3 * sizeof(int));
+  {
+    unsigned char* kp = key.data();
+    std::memcpy(kp, sa, sizeof sa);
+    std::memcpy(kp + sizeof sa, &k, sizeof k);
+    const int extra[3] = {grid, nm_grid, c->profiling ? 1 : 0};
+    std::memcpy(kp + sizeof sa + sizeof k, extra, sizeof extra);
+  }
+  if (!b.exec || b.key != key) {
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+    b.exec = nullptr;
+    CUDA_TRY(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    dbie_status st = record_rounds(c->cap_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &graph);
+    if (st != DBIE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    if (ce != cudaSuccess) return fail(DBIE_ECUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    ce = cudaGraphInstantiate(&b.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(DBIE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+    b.key = key;
+  }
+  const int max_launches = (3 * o.max_iter + 8) / K + 2;
+  int launches = 0;
+  for (;;) {
+    CUDA_TRY(cudaGraphLaunch(b.exec, s));
+    CUDA_TRY(cudaMemcpyAsync(c->pinned, &ctrl->act_cnt[0], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    ++launches;
+    if (c->profiling) {
+      for (int r = 0; r < K; ++r) {
+        float ms = 0.f;
+        const cudaError_t te = cudaEventElapsedTime(&ms, b.ev[2 * r], b.ev[2 * r + 1]);
+        if (te == cudaSuccess) {
+          c->stats.kernel_ms += ms;
+          c->stats.objective_ms += ms;
+          c->stats.launches += 1;
+        } else {
+          (void)cudaGetLastError();  // timing unavailable: not an error of the solve
+          if (std::getenv("DBIE_DEBUG"))
+            std::fprintf(stderr, "dbie: graph event timing failed: %s\n", cudaGetErrorString(te));
+        }
+      }
+    }
+    DBIE_TRY(check_device_error(c, s));
+    if (c->pinned[0] == 0) break;
+    if (launches >= max_launches) return fail(DBIE_EINTERNAL, "simplex rounds did not terminate");
+  }
+  // Statistics and outputs.
+  SolveCtrl hc;
+  CUDA_TRY(cudaMemcpy(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost));
+  c->stats.rounds += hc.round;
+  c->stats.queries += (int64_t)hc.stat_queries;
+  if (c->profiling) {
+    c->stats.pair_evals += hc.stat_pairs;
+    c->stats.objective_pairs += hc.stat_pairs;
+  }
+  const cudaMemcpyKind kind = mem_kind == DBIE_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  for (int p = 0; p < nprob; ++p) {
+    const int64_t np = n[p], off = pt_off[p];
+    if (np == 0) continue;
+    const dbie_solve_out& so = out[p];
+    CUDA_TRY(cudaMemcpyAsync(so.B, res_B + 3 * off, sizeof(double) * 3 * np, kind, s));
+    CUDA_TRY(cudaMemcpyAsync(so.lambda, res_lam + 3 * off, sizeof(double) * 3 * np, kind, s));
+    if (so.f) CUDA_TRY(cudaMemcpyAsync(so.f, res_f + off, sizeof(double) * np, kind, s));
+    if (so.g) CUDA_TRY(cudaMemcpyAsync(so.g, res_g + off, sizeof(double) * np, kind, s));
+    if (so.iters) CUDA_TRY(cudaMemcpyAsync(so.iters, res_i + off, sizeof(int32_t) * np, kind, s));
+    if (so.status) CUDA_TRY(cudaMemcpyAsync(so.status, res_i + N + off, sizeof(int32_t) * np, kind, s));
+    if (so.nfev) CUDA_TRY(cudaMemcpyAsync(so.nfev, res_i + 2 * N + off, sizeof(int32_t) * np, kind, s));
+    if (so.codes && so.codes_stride > 0) {
+      const int w = std::min<int>(so.codes_stride, codes_stride);
+      if (mem_kind == DBIE_MEM_HOST) std::memset(so.codes, 0, (size_t)so.codes_stride * np);
+      else CUDA_TRY(cudaMemsetAsync(so.codes, 0, (size_t)so.codes_stride * np, s));
+      if (w > 0)
+        CUDA_TRY(cudaMemcpy2DAsync(so.codes, so.codes_stride, b.codes.as<char>() + off * codes_stride,
+                                   codes_stride, w, np, kind, s));
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return DBIE_OK;
+}
+
+dbie_status dbie_solve(dbie_ctx* c, int64_t n, const float* xyz, const dbie_options* opt,
+                       const double* lambda_init, int32_t mem_kind, const dbie_solve_out* out,
+                       void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (!out) return fail(DBIE_EINVAL, "out must not be NULL");
+  if (n > 0 && (!xyz || !out->B || !out->lambda))
+    return fail(DBIE_EINVAL, "xyz, out->B and out->lambda are required");
+  const double* li[1] = {lambda_init};
+  return solve_impl(1, &c, &n, &xyz, opt, li, mem_kind, out, static_cast<cudaStream_t>(stream));
+}
+
+dbie_status dbie_solve_batched(int32_t nprob, dbie_ctx* const* ctxs, const int64_t* n,
+                               const float* const* xyz, const dbie_options* opt,
+                               const double* const* lambda_init, int32_t mem_kind,
+                               const dbie_solve_out* out, void* stream) {
+  if (nprob < 1) return fail(DBIE_EINVAL, "nprob must be >= 1");
+  if (!ctxs || !n || !xyz || !out) return fail(DBIE_EINVAL, "ctxs, n, xyz, out must not be NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  for (int p = 0; p < nprob; ++p) {
+    if (!ctxs[p]) return fail(DBIE_EINVAL, "ctxs[" + std::to_string(p) + "] is NULL");
+    if (ctxs[p]->device != ctxs[0]->device) return fail(DBIE_EINVAL, "contexts on different devices");
+    if (n[p] < 0) return fail(DBIE_EINVAL, "n[" + std::to_string(p) + "] < 0");
+    if (n[p] > 0 && !xyz[p]) return fail(DBIE_EINVAL, "xyz[" + std::to_string(p) + "] is NULL");
+    if (n[p] > 0 && (!out[p].B || !out[p].lambda))
+      return fail(DBIE_EINVAL, "out[p].B and out[p].lambda are required");
+  }
+  return solve_impl(nprob, ctxs, n, xyz, opt, lambda_init, mem_kind, out,
+                    static_cast<cudaStream_t>(stream));
+}
+
+dbie_status dbie_set_profiling(dbie_ctx* c, int32_t enable) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  c->profiling = enable != 0;
+  return DBIE_OK;
+}
+
+dbie_status dbie_get_stats(dbie_ctx* c, dbie_stats* st, int32_t reset) {
+  if (!c || !st) return fail(DBIE_EINVAL, "ctx and stats must not be NULL");
+  CUDA_TRY(cudaSetDevice(c->device));
+  resolve_pending(c);
+  *st = c->stats;
+  if (reset) c->stats = dbie_stats{};
+  return DBIE_OK;
+}
+
+dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  (void)stream;
+  return DBIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,317 @@
+// dbie_internal.cuh -- device-side building blocks of the DBIE library (sm_103a).
+//
+// Layout of the boundary on the device ("tile-blocked SoA"): pixels are grouped in tiles of
+// TILE consecutive row-major pixels; a tile stores TILE x, then TILE y, then TILE values of
+// b_p = B_p0 * dA / (2 pi) for p = x, y, z.  One tile is one contiguous block that a single
+// cp.async.bulk copy moves into shared memory.  The last tile is padded with b = 0 pixels,
+// which add exactly zero to every sum.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dbie {
+
+constexpr int TILE = 256;            // pixels (or points, for the adjoint) per tile
+constexpr int NFIELD = 5;            // x, y, bx, by, bz
+constexpr int VJP_NFIELD = 9;        // x, y, z^2, lx, ly, lz, wx, wy, wz
+constexpr int NEAR_W = 8;            // near-field window half width (pixels): 17 x 17 window
+constexpr double TWO_PI = 6.283185307179586476925286766559;
+
+// Error word bits (set with atomicOr, read by the host after synchronising).
+constexpr unsigned ERR_TIMEOUT_FULL = 1u;
+constexpr unsigned ERR_TIMEOUT_EMPTY = 2u;
+constexpr unsigned ERR_TIMEOUT_DRAIN = 4u;
+constexpr unsigned ERR_BAD_PLAN = 8u;
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
+
+// Pair-sum variants: which per-component sums are accumulated (Sect. 2.1 / Eq. 13):
+//   S0 = sum phi b, S1 = sum psi b, Sx = sum psi (x_i - x_k) b, Sy = sum psi (y_i - y_k) b,
+//   Sl = sum cos(lambda r) b / r, with phi = u / r^3, u = lambda r sin(lambda r) + cos(lambda r),
+//   psi = phi'(r) / r = (lambda^2 cos(lambda r) - 3 u / r^2) / r^3.
+// Then B_p = z S0, dB_p/dx = z Sx, dB_p/dy = z Sy, dB_p/dz = S0 + z^2 S1, dB_p/dlambda = z lambda Sl.
+enum Variant { VAR_V = 0, VAR_VL = 1, VAR_OBJ = 2, VAR_OBJL = 3 };
+__host__ __device__ constexpr int nsum_per_comp(int var) {
+  return var == VAR_V ? 1 : var == VAR_VL ? 2 : var == VAR_OBJ ? 4 : 5;
+}
+__host__ __device__ constexpr bool has_grad(int var) { return var == VAR_OBJ || var == VAR_OBJL; }
+__host__ __device__ constexpr bool has_dlam(int var) { return var == VAR_VL || var == VAR_OBJL; }
+// index of the Sl sum within a component's block
+__host__ __device__ constexpr int idx_sl(int var) { return var == VAR_VL ? 1 : 4; }
+
+// Lambda triple of a query (FP64; the mixed form rounds it to FP32 when loading).
+struct __align__(32) Lam4 {
+  double x, y, z, w;
+};
+__host__ __device__ inline Lam4 make_lam4(double x, double y, double z) { return Lam4{x, y, z, 0.0}; }
+
+// ------------------------------------------------------------------ problem and plan ----
+struct ProbDesc {
+  const float* tiles32;     // tile-blocked float boundary
+  const double* tiles64;    // tile-blocked double boundary
+  int32_t ntiles;
+  int32_t nx, ny;
+  int32_t pad0;
+  double x0, y0, hx, hy;
+  double step;              // initial simplex edge of this problem's lambda search
+  double g_scale;           // Delta V / Delta sigma of Eq. 9 for this problem
+  double near_z;            // FP64 near field for z <= near_z (0: off)
+  int64_t q_off;            // first query slot of this problem
+  int64_t pt_off;           // first global point index
+  int64_t npts;
+};
+
+// Launch plan of one pair-sum pass, written on the device (solve rounds) or by a one-thread
+// kernel (single evaluations), so that kernels can be captured in CUDA graphs.
+struct PlanHdr {
+  int32_t nitems;           // work items = sum over problems of blocks * nsplit
+  int32_t nsplit;           // tile-range splits (same for all problems of the pass)
+  int32_t qper;             // queries per item (CTA size * points per thread)
+  int32_t pad0;
+};
+
+struct G1Args {
+  const ProbDesc* probs;
+  int32_t nprob;
+  int32_t pad0;
+  const PlanHdr* plan;
+  const int32_t* item_off;  // [nprob + 1] prefix of items per problem
+  const int32_t* q_cnt;     // [nprob] queries per problem in this pass
+  int32_t* work;            // dynamic item counter (zero before the launch)
+  const float4* qpos;       // [slot] x, y, z, problem index (int bits)
+  const Lam4* qlam;         // [slot] lambda_x, lambda_y, lambda_z
+  double* out;              // per work item a chunk of nsum * qper partial sums (see out_index)
+  unsigned* err;
+};
+
+// Position of partial sum s of the query with local index j (within its problem) for split
+// `sp`: work item = item_off[problem] + (j / qper) * nsplit + sp owns a dense chunk of
+// nsum * qper values, so the buffer size is bounded by the number of items, not by nsplit.
+__host__ __device__ inline int64_t out_index(const PlanHdr& h, const int32_t* item_off, int pidx,
+                                             int64_t j, int sp, int s, int nsum) {
+  const int64_t blk = j / h.qper;
+  const int64_t r = j - blk * h.qper;
+  const int64_t item = (int64_t)item_off[pidx] + blk * h.nsplit + sp;
+  return (item * nsum + s) * h.qper + r;
+}
+
+// Point tiles for the adjoint: per tile TILE x, y, z^2, lambda_x, lambda_y, lambda_z and the
+// weights w_p = gB_p * z (padding points carry w = 0).
+struct VjpArgs {
+  const float* ptiles32;    // tile-blocked point records (mixed form)
+  const double* ptiles64;   // (FP64 form)
+  int32_t nptiles;
+  int32_t npix;             // real pixels
+  const float* btiles32;    // boundary tiles (pixel coordinates)
+  const double* btiles64;
+  const PlanHdr* plan;      // nitems = pixel blocks * nsplit
+  int32_t* work;
+  double* out;              // per item (pixel block, split): 3 * qper partial sums
+  unsigned* err;
+};
+
+// ------------------------------------------------------------------ PTX helpers ----
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait on an mbarrier phase: gives up after WAIT_LIMIT_NS and sets `code` in *err.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned* err,
+                                                  unsigned code) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > WAIT_LIMIT_NS) {
+      atomicOr(err, code);
+      return false;
+    }
+  }
+}
+// TMA bulk copy global -> shared (non-tensor, non-multicast), completion counted on `bar`.
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void* src, uint32_t bytes,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// MUFU approximations (PTX sin/cos/rsqrt .approx); argument in radians.
+__device__ __forceinline__ float sin_mufu(float x) {
+  float y;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float cos_mufu(float x) {
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_mufu(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------------ per-pair terms ----
+// A query (evaluation point and its lambda) held in registers.
+template <typename Real, bool TIED>
+struct Query {
+  Real x, y, z2;
+  Real l[TIED ? 1 : 3];
+  Real l2[TIED ? 1 : 3];
+};
+
+template <typename Real, bool TIED>
+__device__ __forceinline__ Query<Real, TIED> make_query(float4 pos, Lam4 lam) {
+  Query<Real, TIED> q;
+  if constexpr (sizeof(Real) == 4) {
+    q.x = pos.x;
+    q.y = pos.y;
+    q.z2 = __fmul_rn(pos.z, pos.z);
+    const float l0 = (float)lam.x, l1 = (float)lam.y, l2 = (float)lam.z;
+    q.l[0] = l0;
+    q.l2[0] = __fmul_rn(l0, l0);
+    if constexpr (!TIED) {
+      q.l[1] = l1; q.l2[1] = __fmul_rn(l1, l1);
+      q.l[2] = l2; q.l2[2] = __fmul_rn(l2, l2);
+    }
+  } else {
+    q.x = (double)pos.x;
+    q.y = (double)pos.y;
+    q.z2 = (double)pos.z * (double)pos.z;
+    q.l[0] = lam.x;
+    q.l2[0] = lam.x * lam.x;
+    if constexpr (!TIED) {
+      q.l[1] = lam.y; q.l2[1] = lam.y * lam.y;
+      q.l[2] = lam.z; q.l2[2] = lam.z * lam.z;
+    }
+  }
+  return q;
+}
+
+// Per-pair contributions (before they are added to the running sums):
+//   t0[p] = phi b_p, t1[p] = psi b_p (its products with dx, dy give Sx, Sy), tl[p] = cos(lr) b_p / r.
+// FP32 form: every operation has an explicit rounding so that the near-field kernel, which
+// re-evaluates these terms to replace them by FP64 ones, reproduces them bit for bit.
+template <int VAR, bool TIED>
+struct Terms32 {
+  float dx, dy;
+  float t0[3];
+  float t1[has_grad(VAR) ? 3 : 1];
+  float tl[has_dlam(VAR) ? 3 : 1];
+};
+
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float px, float py,
+                                             const float b[3], Terms32<VAR, TIED>& t) {
+  t.dx = __fsub_rn(q.x, px);
+  t.dy = __fsub_rn(q.y, py);
+  const float r2 = __fmaf_rn(t.dx, t.dx, __fmaf_rn(t.dy, t.dy, q.z2));
+  const float ri = rsqrt_mufu(r2);
+  const float r = __fmul_rn(r2, ri);
+  const float ri2 = __fmul_rn(ri, ri);
+  const float ri3 = __fmul_rn(ri2, ri);
+  if constexpr (TIED) {
+    const float th = __fmul_rn(q.l[0], r);
+    const float s = sin_mufu(th), c = cos_mufu(th);
+    const float u = __fmaf_rn(th, s, c);
+    float w = 0.f, cr = 0.f;
+    if constexpr (has_grad(VAR)) w = __fmaf_rn(-u, __fmul_rn(3.f, ri2), __fmul_rn(q.l2[0], c));
+    if constexpr (has_dlam(VAR)) cr = __fmul_rn(c, ri);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const float rb = __fmul_rn(ri3, b[p]);
+      t.t0[p] = __fmul_rn(u, rb);
+      if constexpr (has_grad(VAR)) t.t1[p] = __fmul_rn(w, rb);
+      if constexpr (has_dlam(VAR)) t.tl[p] = __fmul_rn(cr, b[p]);
+    }
+  } else {
+    float ri2x3 = 0.f;
+    if constexpr (has_grad(VAR)) ri2x3 = __fmul_rn(3.f, ri2);
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      const float th = __fmul_rn(q.l[p], r);
+      const float s = sin_mufu(th), c = cos_mufu(th);
+      const float u = __fmaf_rn(th, s, c);
+      const float rb = __fmul_rn(ri3, b[p]);
+      t.t0[p] = __fmul_rn(u, rb);
+      if constexpr (has_grad(VAR)) {
+        const float w = __fmaf_rn(-u, ri2x3, __fmul_rn(q.l2[p], c));
+        t.t1[p] = __fmul_rn(w, rb);
+      }
+      if constexpr (has_dlam(VAR)) t.tl[p] = __fmul_rn(__fmul_rn(c, ri), b[p]);
+    }
+  }
+}
+
+// FP64 terms (used by the FP64 form and by the near-field correction).
+template <int VAR, bool TIED>
+struct Terms64 {
+  double dx, dy;
+  double t0[3];
+  double t1[has_grad(VAR) ? 3 : 1];
+  double tl[has_dlam(VAR) ? 3 : 1];
+};
+
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, double px, double py,
+                                             const double b[3], Terms64<VAR, TIED>& t) {
+  t.dx = q.x - px;
+  t.dy = q.y - py;
+  const double r2 = t.dx * t.dx + t.dy * t.dy + q.z2;
+  const double ri = rsqrt(r2);
+  const double r = r2 * ri;
+  const double ri2 = ri * ri;
+  const double ri3 = ri2 * ri;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int lp = TIED ? 0 : p;
+    double s, c;
+    const double th = q.l[lp] * r;
+    sincos(th, &s, &c);
+    const double u = th * s + c;
+    const double rb = ri3 * b[p];
+    t.t0[p] = u * rb;
+    if constexpr (has_grad(VAR)) t.t1[p] = (q.l2[lp] * c - 3.0 * u * ri2) * rb;
+    if constexpr (has_dlam(VAR)) t.tl[p] = c * ri * b[p];
+  }
+}
+
+// Address of field f (0..4) of pixel k in a tile-blocked boundary.
+template <typename Real>
+__device__ __forceinline__ const Real* tile_field(const Real* tiles, int64_t k, int f) {
+  return tiles + (k / TILE) * (int64_t)(NFIELD * TILE) + f * TILE + (k % TILE);
+}
+
+}  // namespace dbie

@@ -1,0 +1,60 @@
+// kernels.h -- host-side interface to the device kernels (launch wrappers and kernel lookup).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "solve.cuh"
+
+namespace dbie {
+
+// Launch configurations of the pair-sum kernels: points (or pixels) per thread and CTA size.
+constexpr int NCFG = 3;
+constexpr int NSTAGE = 3;
+struct LaunchCfg { int p, nt; };
+__host__ __device__ constexpr LaunchCfg cfg_of(int c) {
+  return c == 0 ? LaunchCfg{1, 128} : c == 1 ? LaunchCfg{2, 128} : LaunchCfg{1, 256};
+}
+
+struct KernelRef {
+  const void* fn;     // __global__ function
+  int nt;             // threads per CTA
+  int qper;           // queries (or pixels) per CTA = nt * points per thread
+  size_t smem;        // dynamic shared memory bytes
+};
+
+KernelRef g1_ref_f32(int var, bool tied, int cfg);   // pairsum_f32_*.cu
+KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
+KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
+
+// aux.cu
+void launch_stage_boundary(const float* Bx, const float* By, const float* Bz, int nx, int ny,
+                           double x0, double y0, double hx, double hy, double scale,
+                           int ntiles, float* t32, double* t64, cudaStream_t s);
+void launch_pack_eval(int64_t n, const float* xyz, const float* lam_f, const double* lam_d,
+                      float4* qpos, Lam4* qlam, int32_t* near_list, int32_t* near_cnt,
+                      int near_on, double near_z, cudaStream_t s);
+void launch_plan_single(PlanHdr* plan, int32_t* item_off, int32_t* q_cnt, int32_t* work,
+                        int nitems, int nsplit, int qper, int qcount, cudaStream_t s);
+void launch_nearfield(int var, bool tied, const ProbDesc* probs, const int32_t* near_list,
+                      const int32_t* near_cnt, const float4* qpos, const Lam4* qlam,
+                      const PlanHdr* plan, const int32_t* item_off, double* out, int grid,
+                      cudaStream_t s);
+void launch_pack_vjp(int64_t n, const float* xyz, const double* lam, const double* gB, int tied,
+                     int nptiles, float* p32, double* p64, int fp64, cudaStream_t s);
+void launch_finalize_vjp(int64_t npix, const PlanHdr* plan, const double* out, double scale,
+                         double* gB0, int accumulate, cudaStream_t s);
+
+void launch_count_bad(const float* a, int64_t n, int mode, int32_t* cnt, cudaStream_t s);
+void launch_pack_points(int64_t n, const float* xyz, int pidx, float4* ppos, cudaStream_t s);
+
+// solve.cu
+void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                          const double* out, const float4* qpos, const Lam4* qlam, double g_scale,
+                          double w_g, double* B, double* gradB, double* dBdl,
+                          const double* gB_for_glam, double* fgphi, cudaStream_t s);
+void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);
+void launch_plan_round(const PlanArgs& a, cudaStream_t s);
+void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s);
+
+}  // namespace dbie

@@ -1,0 +1,439 @@
+// pairsum.cuh -- the DBIE pair-sum kernels, N-body style.
+//
+// g1_kernel: Eq. 6 / Eq. 16 and the fixed-lambda derivatives of Eq. 13.  Each CTA holds a
+//   block of queries (evaluation point + lambda triple) in registers and streams boundary tiles
+//   through shared memory.
+// vjp_kernel: the transpose of Eq. 16 (dL/dB0 = A^T gB): each CTA holds a block of pixels in
+//   registers and streams tiles of points (with their lambda and upstream gradient), recomputing
+//   a_ik instead of storing the point-by-pixel matrix.
+//
+//  * Work: persistent CTAs take items (problem, register block, tile range) from a device
+//    counter, so many magnetograms of uneven size share one launch and small sets can be split
+//    over tile ranges; each item writes FP64 partial sums for its split.
+//  * Staging: one elected thread moves each tile with one cp.async.bulk (TMA bulk copy, no
+//    multicast) into an NSTAGE-deep ring of shared-memory buffers guarded by mbarriers (full:
+//    transaction bytes; empty: one arrival per warp).  Every wait is bounded in time.
+//  * Arithmetic (mixed form): FP32 pair terms (rsqrt, sin, cos on the SFU), plain FP32 sums
+//    over SUB elements, folded by an error-free two-sum into float-float accumulators and
+//    converted to FP64 at the end of the item.  FP64 form: the same sweep in double precision.
+#pragma once
+#include "dbie_internal.cuh"
+
+namespace dbie {
+
+constexpr int SUB = 32;  // elements summed in plain FP32 before a compensated fold
+
+// Ring of NSTAGE shared-memory tile buffers filled by TMA bulk copies.  Thread 0 issues; all
+// warps consume.  `issued` / `consumed` count tiles over the CTA's lifetime, which fixes the
+// mbarrier phase parity of every wait.
+template <typename Elem, int NSTAGE, int NWARP>
+struct TileRing {
+  Elem* buf;
+  uint64_t* full;
+  uint64_t* empty;
+  volatile int* abort_flag;
+  unsigned* err;
+  uint32_t tile_elems;
+  uint32_t issued, consumed;
+
+  __device__ void init_barriers() {  // thread 0, before the first __syncthreads
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), NWARP);
+    }
+    fence_mbar_init();
+  }
+  // Thread 0: copy tile `src` into the next stage (waits until that stage is released).
+  __device__ bool issue(const Elem* src) {
+    const uint32_t st = issued % NSTAGE;
+    if (issued >= NSTAGE &&
+        !mbar_wait_bounded(smem_addr(&empty[st]), ((issued / NSTAGE) - 1) & 1, err,
+                           ERR_TIMEOUT_EMPTY)) {
+      *abort_flag = 1;
+      return false;
+    }
+    const uint32_t bytes = tile_elems * (uint32_t)sizeof(Elem);
+    mbar_arrive_expect_tx(smem_addr(&full[st]), bytes);
+    tma_load_1d(smem_addr(buf + st * tile_elems), src, bytes, smem_addr(&full[st]));
+    ++issued;
+    return true;
+  }
+  // All threads: wait for the next tile; warp-uniform result (nullptr on timeout).
+  __device__ const Elem* wait_next() {
+    const uint32_t st = consumed % NSTAGE;
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(smem_addr(&full[st]),
+                                                               (consumed / NSTAGE) & 1, err,
+                                                               ERR_TIMEOUT_FULL));
+    if (!ok) {
+      *abort_flag = 1;
+      return nullptr;
+    }
+    return buf + st * tile_elems;
+  }
+  // All threads: release the tile just consumed (one arrival per warp).
+  __device__ void release(int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(smem_addr(&empty[consumed % NSTAGE]));
+    ++consumed;
+  }
+  // Thread 0 at the end: wait for copies still in flight before shared memory goes away.
+  __device__ void drain() {
+    for (uint32_t u = consumed; u < issued; ++u)
+      mbar_wait_bounded(smem_addr(&full[u % NSTAGE]), (u / NSTAGE) & 1, err, ERR_TIMEOUT_DRAIN);
+  }
+};
+
+// Streams tiles [t0, t1) of `tiles` through the ring, calling body(tile_ptr) for each.  The
+// producer keeps NSTAGE - 1 tiles ahead and refills the stage released one tile earlier, so the
+// issuing thread rarely waits for a slow warp.
+template <typename Elem, int NSTAGE, int NWARP, typename Body>
+__device__ __forceinline__ void sweep_tiles(TileRing<Elem, NSTAGE, NWARP>& ring, const Elem* tiles,
+                                            int t0, int t1, int tid, Body&& body) {
+  const int ntl = t1 - t0;
+  if (tid == 0)
+    for (int s = 0; s < NSTAGE && s < ntl; ++s)
+      if (!ring.issue(tiles + (int64_t)(t0 + s) * ring.tile_elems)) break;
+  for (int t = 0; t < ntl; ++t) {
+    const Elem* tp = ring.wait_next();
+    if (tp == nullptr) break;
+    body(tp);
+    ring.release(tid & 31);
+    if (tid == 0 && t >= 1 && (t - 1) + NSTAGE < ntl && !*ring.abort_flag)
+      ring.issue(tiles + (int64_t)(t0 + t - 1 + NSTAGE) * ring.tile_elems);
+    if (__any_sync(0xffffffffu, *ring.abort_flag != 0)) break;
+  }
+}
+
+template <int VAR, bool TIED, int NS>
+__device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED>& t) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    acc[p * NS + 0] = __fadd_rn(acc[p * NS + 0], t.t0[p]);
+    if constexpr (has_grad(VAR)) {
+      acc[p * NS + 1] = __fadd_rn(acc[p * NS + 1], t.t1[p]);
+      acc[p * NS + 2] = __fmaf_rn(t.t1[p], t.dx, acc[p * NS + 2]);
+      acc[p * NS + 3] = __fmaf_rn(t.t1[p], t.dy, acc[p * NS + 3]);
+    }
+    if constexpr (has_dlam(VAR))
+      acc[p * NS + idx_sl(VAR)] = __fadd_rn(acc[p * NS + idx_sl(VAR)], t.tl[p]);
+  }
+}
+
+template <int VAR, bool TIED, int NS>
+__device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIED>& t) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    acc[p * NS + 0] += t.t0[p];
+    if constexpr (has_grad(VAR)) {
+      acc[p * NS + 1] += t.t1[p];
+      acc[p * NS + 2] += t.t1[p] * t.dx;
+      acc[p * NS + 3] += t.t1[p] * t.dy;
+    }
+    if constexpr (has_dlam(VAR)) acc[p * NS + idx_sl(VAR)] += t.tl[p];
+  }
+}
+
+// Error-free fold of a plain FP32 partial sum into a float-float accumulator (two-sum).
+__device__ __forceinline__ void fold2(float& hi, float& lo, float& a) {
+  const float s = __fadd_rn(hi, a);
+  const float bp = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(a, bp));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+  a = 0.f;
+}
+
+// Locate the problem owning work item `it` (item_off is a prefix array of length nprob + 1).
+__device__ __forceinline__ int find_problem(const int32_t* item_off, int nprob, int it) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(item_off + mid) <= it) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------- g1 ----
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
+__global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
+  constexpr int NS = nsum_per_comp(VAR);
+  constexpr int NSUM = 3 * NS;
+  constexpr int Q = NT * P;
+  constexpr int NWARP = NT / 32;
+  constexpr bool F32 = sizeof(Real) == 4;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
+  __shared__ int s_item;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x;
+  TileRing<Real, NSTAGE, NWARP> ring{reinterpret_cast<Real*>(smem_raw), full_bar, empty_bar,
+                                     &s_abort, a.err, (uint32_t)(NFIELD * TILE), 0u, 0u};
+  if (tid == 0) {
+    ring.init_barriers();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const PlanHdr plan = *a.plan;
+
+  for (;;) {
+    // Thread 0 alone decides whether to stop, so the decision is uniform across the CTA.
+    if (tid == 0) s_item = s_abort ? plan.nitems : atomicAdd(a.work, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();  // every thread has read s_item before it can be overwritten
+    if (it >= plan.nitems) break;
+
+    const int pidx = find_problem(a.item_off, a.nprob, it);
+    const ProbDesc& pd = a.probs[pidx];
+    const int local = it - __ldg(a.item_off + pidx);
+    const int blk = local / plan.nsplit;
+    const int sp = local - blk * plan.nsplit;
+    const int qtotal = __ldg(a.q_cnt + pidx);
+    const int t0 = (int)(((int64_t)sp * pd.ntiles) / plan.nsplit);
+    const int t1 = (int)(((int64_t)(sp + 1) * pd.ntiles) / plan.nsplit);
+    const Real* tiles = F32 ? reinterpret_cast<const Real*>(pd.tiles32)
+                            : reinterpret_cast<const Real*>(pd.tiles64);
+
+    Query<Real, TIED> q[P];
+    bool valid[P];
+    int64_t slot[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int j = blk * Q + tid + u * NT;
+      valid[u] = j < qtotal;
+      slot[u] = pd.q_off + j;
+      float4 pos = make_float4(0.f, 0.f, 1.f, 0.f);
+      Lam4 lam = make_lam4(0.0, 0.0, 0.0);
+      if (valid[u]) {
+        pos = a.qpos[slot[u]];
+        lam = a.qlam[slot[u]];
+      }
+      q[u] = make_query<Real, TIED>(pos, lam);
+    }
+
+    Real acc[P][NSUM];
+    float hi[F32 ? P : 1][F32 ? NSUM : 1], lo[F32 ? P : 1][F32 ? NSUM : 1];
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+#pragma unroll
+      for (int s = 0; s < NSUM; ++s) {
+        acc[u][s] = Real(0);
+        if constexpr (F32) {
+          hi[u][s] = 0.f;
+          lo[u][s] = 0.f;
+        }
+      }
+
+    sweep_tiles(ring, tiles, t0, t1, tid, [&](const Real* sx) {
+      if constexpr (F32) {
+#pragma unroll 1
+        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+#pragma unroll
+          for (int k = k0; k < k0 + SUB; k += 4) {
+            const float4 X = *reinterpret_cast<const float4*>(sx + k);
+            const float4 Y = *reinterpret_cast<const float4*>(sx + TILE + k);
+            const float4 BX = *reinterpret_cast<const float4*>(sx + 2 * TILE + k);
+            const float4 BY = *reinterpret_cast<const float4*>(sx + 3 * TILE + k);
+            const float4 BZ = *reinterpret_cast<const float4*>(sx + 4 * TILE + k);
+            const float px[4] = {X.x, X.y, X.z, X.w};
+            const float py[4] = {Y.x, Y.y, Y.z, Y.w};
+            const float bx[4] = {BX.x, BX.y, BX.z, BX.w};
+            const float by[4] = {BY.x, BY.y, BY.z, BY.w};
+            const float bz[4] = {BZ.x, BZ.y, BZ.z, BZ.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float b[3] = {bx[e], by[e], bz[e]};
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                Terms32<VAR, TIED> tm;
+                pair_terms32<VAR, TIED>(q[u], px[e], py[e], b, tm);
+                accumulate32<VAR, TIED, NS>(acc[u], tm);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int s = 0; s < NSUM; ++s) fold2(hi[u][s], lo[u][s], acc[u][s]);
+        }
+      } else {
+#pragma unroll 2
+        for (int k = 0; k < TILE; ++k) {
+          const double b[3] = {sx[2 * TILE + k], sx[3 * TILE + k], sx[4 * TILE + k]};
+          const double px = sx[k], py = sx[TILE + k];
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            Terms64<VAR, TIED> tm;
+            pair_terms64<VAR, TIED>(q[u], px, py, b, tm);
+            accumulate64<VAR, TIED, NS>(acc[u], tm);
+          }
+        }
+      }
+    });
+
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      if (!valid[u]) continue;
+#pragma unroll
+      for (int s = 0; s < NSUM; ++s) {
+        double v;
+        if constexpr (F32) v = (double)hi[u][s] + (double)lo[u][s];
+        else v = (double)acc[u][s];
+        a.out[((int64_t)it * NSUM + s) * Q + (tid + u * NT)] = v;
+      }
+    }
+  }
+  if (tid == 0) ring.drain();
+}
+
+// --------------------------------------------------------------------------- vjp ----
+
+
+template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+__global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
+  constexpr int Q = NT * P;
+  constexpr int NWARP = NT / 32;
+  constexpr bool F32 = sizeof(Real) == 4;
+  constexpr int NL = TIED ? 1 : 3;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
+  __shared__ int s_item;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x;
+  TileRing<Real, NSTAGE, NWARP> ring{reinterpret_cast<Real*>(smem_raw), full_bar, empty_bar,
+                                     &s_abort, a.err, (uint32_t)(VJP_NFIELD * TILE), 0u, 0u};
+  if (tid == 0) {
+    ring.init_barriers();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const PlanHdr plan = *a.plan;
+  const Real* ptiles = F32 ? reinterpret_cast<const Real*>(a.ptiles32)
+                           : reinterpret_cast<const Real*>(a.ptiles64);
+  const Real* btiles = F32 ? reinterpret_cast<const Real*>(a.btiles32)
+                           : reinterpret_cast<const Real*>(a.btiles64);
+
+  for (;;) {
+    if (tid == 0) s_item = s_abort ? plan.nitems : atomicAdd(a.work, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= plan.nitems) break;
+    const int blk = it / plan.nsplit;
+    const int sp = it - blk * plan.nsplit;
+    const int t0 = (int)(((int64_t)sp * a.nptiles) / plan.nsplit);
+    const int t1 = (int)(((int64_t)(sp + 1) * a.nptiles) / plan.nsplit);
+
+    Real px[P], py[P];
+    bool valid[P];
+    int kpix[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      kpix[u] = blk * Q + tid + u * NT;
+      valid[u] = kpix[u] < a.npix;
+      const int k = valid[u] ? kpix[u] : 0;
+      px[u] = *tile_field(btiles, k, 0);
+      py[u] = *tile_field(btiles, k, 1);
+    }
+    Real acc[P][3];
+    float hi[F32 ? P : 1][3], lo[F32 ? P : 1][3];
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        acc[u][p] = Real(0);
+        if constexpr (F32) {
+          hi[u][p] = 0.f;
+          lo[u][p] = 0.f;
+        }
+      }
+
+    sweep_tiles(ring, ptiles, t0, t1, tid, [&](const Real* sx) {
+      const Real* X = sx;
+      const Real* Y = sx + TILE;
+      const Real* Z2 = sx + 2 * TILE;
+      const Real* L = sx + 3 * TILE;
+      const Real* W = sx + 6 * TILE;
+      if constexpr (F32) {
+#pragma unroll 1
+        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+#pragma unroll 4
+          for (int k = k0; k < k0 + SUB; ++k) {
+            const float xi = X[k], yi = Y[k], z2 = Z2[k];
+            float lam[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) lam[l] = L[l * TILE + k];
+            const float w[3] = {W[k], W[TILE + k], W[2 * TILE + k]};
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+              const float dx = __fsub_rn(px[u], xi), dy = __fsub_rn(py[u], yi);
+              const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, z2));
+              const float ri = rsqrt_mufu(r2);
+              const float r = __fmul_rn(r2, ri);
+              const float ri3 = __fmul_rn(__fmul_rn(ri, ri), ri);
+              if constexpr (TIED) {
+                const float th = __fmul_rn(lam[0], r);
+                const float phi = __fmul_rn(__fmaf_rn(th, sin_mufu(th), cos_mufu(th)), ri3);
+#pragma unroll
+                for (int p = 0; p < 3; ++p) acc[u][p] = __fmaf_rn(phi, w[p], acc[u][p]);
+              } else {
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                  const float th = __fmul_rn(lam[p], r);
+                  const float phi = __fmul_rn(__fmaf_rn(th, sin_mufu(th), cos_mufu(th)), ri3);
+                  acc[u][p] = __fmaf_rn(phi, w[p], acc[u][p]);
+                }
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) fold2(hi[u][p], lo[u][p], acc[u][p]);
+        }
+      } else {
+#pragma unroll 2
+        for (int k = 0; k < TILE; ++k) {
+          const double xi = X[k], yi = Y[k], z2 = Z2[k];
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            const double dx = px[u] - xi, dy = py[u] - yi;
+            const double r2 = dx * dx + dy * dy + z2;
+            const double ri = rsqrt(r2);
+            const double r = r2 * ri;
+            const double ri3 = ri * ri * ri;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+              double s, c;
+              const double th = L[(TIED ? 0 : p) * TILE + k] * r;
+              sincos(th, &s, &c);
+              acc[u][p] += (th * s + c) * ri3 * W[p * TILE + k];
+            }
+          }
+        }
+      }
+    });
+
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      if (!valid[u]) continue;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        double v;
+        if constexpr (F32) v = (double)hi[u][p] + (double)lo[u][p];
+        else v = (double)acc[u][p];
+        a.out[((int64_t)it * 3 + p) * Q + (tid + u * NT)] = v;
+      }
+    }
+  }
+  if (tid == 0) ring.drain();
+}
+
+}  // namespace dbie

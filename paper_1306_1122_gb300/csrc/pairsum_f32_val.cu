@@ -1,0 +1,9 @@
+// Pair-sum kernels, FP32 form: value variants (B; B and dB/dlambda).
+#include "pairsum_inst.cuh"
+
+namespace dbie {
+KernelRef g1_ref_f32_val(int var, bool tied, int cfg) {
+  if (var == VAR_V) return tied ? g1_ref_cfg<float, VAR_V, true>(cfg) : g1_ref_cfg<float, VAR_V, false>(cfg);
+  return tied ? g1_ref_cfg<float, VAR_VL, true>(cfg) : g1_ref_cfg<float, VAR_VL, false>(cfg);
+}
+}  // namespace dbie

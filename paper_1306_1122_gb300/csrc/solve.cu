@@ -1,0 +1,461 @@
+// solve.cu -- per-point objective and the on-device Downhill Simplex search for lambda.
+//
+// Compiled with -fmad=false: the simplex arithmetic and the objective are evaluated with
+// separately rounded operations, as written.
+//
+//  * objective: B_p = z S0_p, dB_p/dx = z Sx_p, dB_p/dy = z Sy_p, dB_p/dz = S0_p + z^2 S1_p
+//    (the fixed-lambda derivatives of Eq. 13), J = curl B (Eq. 14), f = |J x B| / (|J||B|)
+//    (Eq. 8), g = |div B| dV/dSigma / |B| (Eq. 9), Phi = f + w_g g.
+//  * simplex (Sect. 2.1; Nelder & Mead 1965, reflection 1, expansion 2, contraction 1/2,
+//    shrink 1/2, outside/inside contraction as in Lagarias et al. 1998): one thread per active
+//    point advances a state machine by one step per round; every round evaluates all pending
+//    trial points of all active points in one pair-sum pass.
+#include "kernels.h"
+#include "solve.cuh"
+
+namespace dbie {
+
+struct Eval {
+  double B[3];
+  double f, g, phi;
+};
+
+__device__ __forceinline__ void objective(const double B[3], const double G[9], double g_scale,
+                                          double w_g, double& f, double& g, double& phi) {
+  const double Jx = G[3 * 2 + 1] - G[3 * 1 + 2];
+  const double Jy = G[3 * 0 + 2] - G[3 * 2 + 0];
+  const double Jz = G[3 * 1 + 0] - G[3 * 0 + 1];
+  const double div = G[0] + G[4] + G[8];
+  const double cx = Jy * B[2] - Jz * B[1];
+  const double cy = Jz * B[0] - Jx * B[2];
+  const double cz = Jx * B[1] - Jy * B[0];
+  const double nJ = sqrt(Jx * Jx + Jy * Jy + Jz * Jz);
+  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  const double nC = sqrt(cx * cx + cy * cy + cz * cz);
+  f = (nJ * nB > 0.0) ? nC / (nJ * nB) : 0.0;
+  g = (nB > 0.0) ? fabs(div) * g_scale / nB : 0.0;
+  phi = f + w_g * g;
+}
+
+// Sum over the split partials of sum s of the query with local index j in problem pidx
+// (near-field corrections were already added to split 0).
+__device__ __forceinline__ double gather_sum(const double* out, const PlanHdr& h,
+                                             const int32_t* item_off, int pidx, int64_t j,
+                                             int nsum, int s) {
+  double v = 0.0;
+  for (int sp = 0; sp < h.nsplit; ++sp) v += out[out_index(h, item_off, pidx, j, sp, s, nsum)];
+  return v;
+}
+
+// B, gradient and objective from the 12 objective sums of one query.
+__device__ __forceinline__ void assemble_obj(const double S[12], double z, double g_scale,
+                                             double w_g, Eval& e, double G[9]) {
+  for (int p = 0; p < 3; ++p) {
+    const double S0 = S[p * 4 + 0], S1 = S[p * 4 + 1], Sx = S[p * 4 + 2], Sy = S[p * 4 + 3];
+    e.B[p] = z * S0;
+    G[3 * p + 0] = z * Sx;
+    G[3 * p + 1] = z * Sy;
+    G[3 * p + 2] = S0 + z * z * S1;
+  }
+  objective(e.B, G, g_scale, w_g, e.f, e.g, e.phi);
+}
+
+// ----------------------------------------------------------------- eval finalize ----
+template <int VAR>
+__global__ void finalize_eval_kernel(int64_t n, const PlanHdr* __restrict__ plan,
+                                     const int32_t* __restrict__ item_off,
+                                     const double* __restrict__ out,
+                                     const float4* __restrict__ qpos,
+                                     const Lam4* __restrict__ qlam, double g_scale, double w_g,
+                                     double* B, double* gradB, double* dBdl, const double* gB,
+                                     double* fgphi) {
+  constexpr int NS = nsum_per_comp(VAR);
+  constexpr int NSUM = 3 * NS;
+  const PlanHdr h = *plan;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pos = qpos[i];
+    const double z = (double)pos.z;
+    double S[NSUM];
+    for (int s = 0; s < NSUM; ++s) S[s] = gather_sum(out, h, item_off, 0, i, NSUM, s);
+    double Bv[3], G[9];
+    for (int p = 0; p < 3; ++p) {
+      Bv[p] = z * S[p * NS];
+      if (B) B[3 * i + p] = Bv[p];
+    }
+    if constexpr (has_grad(VAR)) {
+      for (int p = 0; p < 3; ++p) {
+        G[3 * p + 0] = z * S[p * NS + 2];
+        G[3 * p + 1] = z * S[p * NS + 3];
+        G[3 * p + 2] = S[p * NS] + z * z * S[p * NS + 1];
+      }
+      if (gradB)
+        for (int j = 0; j < 9; ++j) gradB[9 * i + j] = G[j];
+      if (fgphi) {
+        double f, g, phi;
+        objective(Bv, G, g_scale, w_g, f, g, phi);
+        fgphi[3 * i + 0] = f;
+        fgphi[3 * i + 1] = g;
+        fgphi[3 * i + 2] = phi;
+      }
+    }
+    if constexpr (has_dlam(VAR)) {
+      const Lam4 l = qlam[i];
+      const double lam[3] = {l.x, l.y, l.z};
+      for (int p = 0; p < 3; ++p) {
+        const double d = z * lam[p] * S[p * NS + idx_sl(VAR)];
+        if (gB) {
+          if (dBdl) dBdl[3 * i + p] = gB[3 * i + p] * d;
+        } else if (dBdl) {
+          dBdl[3 * i + p] = d;
+        }
+      }
+    }
+  }
+}
+
+void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                          const double* out, const float4* qpos, const Lam4* qlam, double g_scale,
+                          double w_g, double* B, double* gradB, double* dBdl, const double* gB,
+                          double* fgphi, cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+#define FIN(V)                                                                              \
+  finalize_eval_kernel<V><<<grid, 256, 0, s>>>(n, plan, item_off, out, qpos, qlam, g_scale, \
+                                               w_g, B, gradB, dBdl, gB, fgphi)
+  switch (var) {
+    case VAR_V: FIN(VAR_V); break;
+    case VAR_VL: FIN(VAR_VL); break;
+    case VAR_OBJ: FIN(VAR_OBJ); break;
+    default: FIN(VAR_OBJL); break;
+  }
+#undef FIN
+}
+
+// ------------------------------------------------------------------ simplex state ----
+struct Vert {
+  double l[3];
+  double B[3];
+  double f, g, phi;
+};
+
+__device__ __forceinline__ double& SD(const SolveArgs& a, int f, int64_t g) {
+  return a.sd[(int64_t)f * a.N + g];
+}
+__device__ __forceinline__ int32_t& SI(const SolveArgs& a, int f, int64_t g) {
+  return a.si[(int64_t)f * a.N + g];
+}
+
+__device__ __forceinline__ void load_vert(const SolveArgs& a, int64_t g, int v, Vert& x) {
+  for (int d = 0; d < 3; ++d) x.l[d] = SD(a, D_VL + v * 3 + d, g);
+  for (int p = 0; p < 3; ++p) x.B[p] = SD(a, D_VB + v * 3 + p, g);
+  x.f = SD(a, D_VF + v, g);
+  x.g = SD(a, D_VG + v, g);
+  x.phi = SD(a, D_VPHI + v, g);
+}
+__device__ __forceinline__ void store_vert(const SolveArgs& a, int64_t g, int v, const Vert& x) {
+  for (int d = 0; d < 3; ++d) SD(a, D_VL + v * 3 + d, g) = x.l[d];
+  for (int p = 0; p < 3; ++p) SD(a, D_VB + v * 3 + p, g) = x.B[p];
+  SD(a, D_VF + v, g) = x.f;
+  SD(a, D_VG + v, g) = x.g;
+  SD(a, D_VPHI + v, g) = x.phi;
+}
+
+// Objective of the k-th pending query of point g.
+__device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, int pidx,
+                                          int64_t slot, double z, Eval& e) {
+  const ProbDesc& pd = a.probs[pidx];
+  const int64_t j = slot - pd.q_off;
+  double S[12], G[9];
+  for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 12, s);
+  assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G);
+}
+
+// Queue k trial points (lambda rows) of point g for the next round.
+__device__ void emit(const SolveArgs& a, int64_t g, const float4& pos, int pidx, int k,
+                     const double (*lam)[3]) {
+  const ProbDesc& pd = a.probs[pidx];
+  const int base = atomicAdd(a.nxt.q_cnt + pidx, k);
+  const int64_t slot0 = pd.q_off + base;
+  for (int j = 0; j < k; ++j) {
+    a.nxt.qpos[slot0 + j] = pos;
+    if (a.o.dim == 1) a.nxt.qlam[slot0 + j] = make_lam4(lam[j][0], lam[j][0], lam[j][0]);
+    else a.nxt.qlam[slot0 + j] = make_lam4(lam[j][0], lam[j][1], lam[j][2]);
+  }
+  if (a.o.near_on && (double)pos.z <= pd.near_z) {
+    const int nb = atomicAdd(a.nxt.near_cnt, k);
+    for (int j = 0; j < k; ++j) a.nxt.near[nb + j] = (int32_t)(slot0 + j);
+  }
+  SI(a, I_QSLOT, g) = (int32_t)slot0;
+  a.nxt.act[atomicAdd(a.nxt.act_cnt, 1)] = (int32_t)g;
+}
+
+__global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ lam_init) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const int n = a.o.dim;
+    double lam[4][3];
+    for (int v = 0; v <= n; ++v)
+      for (int d = 0; d < 3; ++d) {
+        const double l0 = lam_init ? lam_init[3 * g + d] : 0.0;
+        lam[v][d] = (d < n) ? l0 + ((v == d + 1) ? a.probs[pidx].step : 0.0) : 0.0;
+      }
+    for (int v = 0; v <= n; ++v)
+      for (int d = 0; d < 3; ++d) SD(a, D_VL + v * 3 + d, g) = lam[v][d];
+    SI(a, I_STAGE, g) = ST_INIT;
+    SI(a, I_ITERS, g) = 0;
+    SI(a, I_NFEV, g) = 0;
+    SI(a, I_STATUS, g) = PT_RUNNING;
+    emit(a, g, pos, pidx, n + 1, lam);
+  }
+}
+
+void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s) {
+  solve_init_kernel<<<grid, 256, 0, s>>>(a, lam_init);
+}
+
+// Stable insertion sort of the n+1 vertices by Phi (ties keep their order).
+__device__ __forceinline__ void sort_verts(Vert* v, int n) {
+  for (int i = 1; i <= n; ++i)
+    for (int j = i; j > 0 && v[j].phi < v[j - 1].phi; --j) {
+      const Vert t = v[j];
+      v[j] = v[j - 1];
+      v[j - 1] = t;
+    }
+}
+
+__global__ void nm_step_kernel(const SolveArgs a) {
+  const double rho = 1.0, chi = 2.0, psi = 0.5, sigma = 0.5;
+  const int nact = *a.cur.act_cnt;
+  const int n = a.o.dim;
+  const PlanHdr h = *a.plan;
+  for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
+    const int64_t g = a.cur.act[ia];
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const double z = (double)pos.z;
+    const int64_t slot = SI(a, I_QSLOT, g);
+    int stage = SI(a, I_STAGE, g);
+    int iters = SI(a, I_ITERS, g);
+    int nfev = SI(a, I_NFEV, g);
+
+    Vert v[4];
+    for (int k = 0; k <= n; ++k) load_vert(a, g, k, v[k]);
+    bool to_check = false;  // an iteration (or the initialisation) completed: sort and test
+    char code = 0;
+
+    auto centroid = [&](double c[3]) {
+      for (int d = 0; d < n; ++d) {
+        double s = 0.0;
+        for (int k = 0; k < n; ++k) s += v[k].l[d];
+        c[d] = s / n;
+      }
+    };
+    auto trial = [&](double coef_c, double coef_w, double out[3]) {  // coef_c * c + coef_w * v[n]
+      double c[3];
+      centroid(c);
+      for (int d = 0; d < 3; ++d) out[d] = (d < n) ? coef_c * c[d] + coef_w * v[n].l[d] : 0.0;
+    };
+    auto accept_last = [&](const double l[3], const Eval& e) {
+      for (int d = 0; d < 3; ++d) v[n].l[d] = l[d];
+      for (int p = 0; p < 3; ++p) v[n].B[p] = e.B[p];
+      v[n].f = e.f;
+      v[n].g = e.g;
+      v[n].phi = e.phi;
+    };
+    auto emit_one = [&](const double l[3], int st) {
+      double rows[1][3] = {{l[0], l[1], l[2]}};
+      for (int d = 0; d < 3; ++d) SD(a, D_TL + d, g) = l[d];
+      stage = st;
+      emit(a, g, pos, pidx, 1, rows);
+    };
+    auto start_shrink = [&]() {
+      double rows[3][3];
+      for (int k = 1; k <= n; ++k) {
+        for (int d = 0; d < 3; ++d)
+          v[k].l[d] = (d < n) ? v[0].l[d] + sigma * (v[k].l[d] - v[0].l[d]) : 0.0;
+        for (int d = 0; d < 3; ++d) rows[k - 1][d] = v[k].l[d];
+      }
+      stage = ST_SHRINK;
+      emit(a, g, pos, pidx, n, rows);
+    };
+
+    if (stage == ST_INIT) {
+      for (int k = 0; k <= n; ++k) {
+        Eval e;
+        read_eval(a, h, pidx, slot + k, z, e);
+        for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
+        v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
+      }
+      nfev += n + 1;
+      to_check = true;
+    } else if (stage == ST_REFLECT) {
+      Eval e;
+      read_eval(a, h, pidx, slot, z, e);
+      nfev += 1;
+      double lr[3];
+      for (int d = 0; d < 3; ++d) lr[d] = SD(a, D_TL + d, g);
+      if (e.phi < v[0].phi) {
+        for (int d = 0; d < 3; ++d) SD(a, D_RL + d, g) = lr[d];
+        for (int p = 0; p < 3; ++p) SD(a, D_RB + p, g) = e.B[p];
+        SD(a, D_RF, g) = e.f; SD(a, D_RG, g) = e.g; SD(a, D_RPHI, g) = e.phi;
+        double xe[3];
+        trial(1.0 + rho * chi, -(rho * chi), xe);
+        emit_one(xe, ST_EXPAND);
+      } else if (e.phi < v[n - 1].phi) {
+        accept_last(lr, e);
+        code = 'R';
+        to_check = true;
+      } else if (e.phi < v[n].phi) {
+        SD(a, D_RPHI, g) = e.phi;
+        double xc[3];
+        trial(1.0 + psi * rho, -(psi * rho), xc);
+        emit_one(xc, ST_OCONTRACT);
+      } else {
+        double xc[3];
+        trial(1.0 - psi, psi, xc);
+        emit_one(xc, ST_ICONTRACT);
+      }
+    } else if (stage == ST_EXPAND) {
+      Eval e;
+      read_eval(a, h, pidx, slot, z, e);
+      nfev += 1;
+      const double phr = SD(a, D_RPHI, g);
+      double l[3];
+      if (e.phi < phr) {
+        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_TL + d, g);
+        accept_last(l, e);
+        code = 'E';
+      } else {
+        Eval r;
+        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_RL + d, g);
+        for (int p = 0; p < 3; ++p) r.B[p] = SD(a, D_RB + p, g);
+        r.f = SD(a, D_RF, g); r.g = SD(a, D_RG, g); r.phi = phr;
+        accept_last(l, r);
+        code = 'R';
+      }
+      to_check = true;
+    } else if (stage == ST_OCONTRACT || stage == ST_ICONTRACT) {
+      Eval e;
+      read_eval(a, h, pidx, slot, z, e);
+      nfev += 1;
+      const bool ok = (stage == ST_OCONTRACT) ? (e.phi <= SD(a, D_RPHI, g)) : (e.phi < v[n].phi);
+      if (ok) {
+        double l[3];
+        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_TL + d, g);
+        accept_last(l, e);
+        code = (stage == ST_OCONTRACT) ? 'O' : 'I';
+        to_check = true;
+      } else {
+        start_shrink();
+      }
+    } else if (stage == ST_SHRINK) {
+      for (int k = 1; k <= n; ++k) {
+        Eval e;
+        read_eval(a, h, pidx, slot + (k - 1), z, e);
+        for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
+        v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
+      }
+      nfev += n;
+      code = 'S';
+      to_check = true;
+    }
+
+    if (code && a.codes && iters >= 1 && iters <= a.codes_stride)
+      a.codes[g * a.codes_stride + (iters - 1)] = code;
+
+    if (to_check) {
+      sort_verts(v, n);
+      int fin = -1;
+      if (v[0].f <= a.o.eps_f && v[0].g <= a.o.eps_g) fin = PT_CONVERGED;
+      else if (v[n].phi - v[0].phi <= a.o.tol) fin = PT_CONVERGED;
+      else if (iters >= a.o.max_iter) fin = PT_MAXITER;
+      if (fin >= 0) {
+        for (int p = 0; p < 3; ++p) {
+          a.res_B[3 * g + p] = v[0].B[p];
+          a.res_lam[3 * g + p] = fabs(n == 1 ? v[0].l[0] : v[0].l[p]);
+        }
+        a.res_f[g] = v[0].f;
+        a.res_g[g] = v[0].g;
+        a.res_iters[g] = iters;
+        a.res_status[g] = fin;
+        a.res_nfev[g] = nfev;
+        stage = ST_DONE;
+        SI(a, I_STATUS, g) = fin;
+      } else {
+        iters += 1;
+        double xr[3];
+        trial(1.0 + rho, -rho, xr);
+        emit_one(xr, ST_REFLECT);
+      }
+    }
+    for (int k = 0; k <= n; ++k) store_vert(a, g, k, v[k]);
+    SI(a, I_STAGE, g) = stage;
+    SI(a, I_ITERS, g) = iters;
+    SI(a, I_NFEV, g) = nfev;
+  }
+}
+
+void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s) {
+  nm_step_kernel<<<grid, 128, 0, s>>>(a);
+}
+
+// --------------------------------------------------------------- per-round plan ----
+__global__ void plan_round_kernel(const PlanArgs a) {
+  __shared__ long long s_blocks;
+  __shared__ int s_minTiles;
+  if (threadIdx.x == 0) {
+    s_blocks = 0;
+    s_minTiles = 1 << 30;
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) {
+    const int q = a.q_cnt_cur[p];
+    a.q_cnt_pass[p] = q;
+    if (q > 0) {
+      atomicAdd((unsigned long long*)&s_blocks, (unsigned long long)((q + a.qper - 1) / a.qper));
+      atomicMin(&s_minTiles, a.probs[p].ntiles);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long blocks = s_blocks;
+    int nsplit = 1;
+    if (blocks > 0 && blocks < a.target_items) {
+      nsplit = (int)((a.target_items + blocks - 1) / blocks);
+      if (nsplit > a.nsplit_cap) nsplit = a.nsplit_cap;
+      if (nsplit > s_minTiles) nsplit = s_minTiles;
+      if (nsplit < 1) nsplit = 1;
+    }
+    int acc = 0;
+    double pairs = 0.0;
+    unsigned long long queries = 0;
+    for (int p = 0; p < a.nprob; ++p) {
+      a.item_off[p] = acc;
+      const int q = a.q_cnt_pass[p];
+      acc += ((q + a.qper - 1) / a.qper) * nsplit;
+      pairs += (double)q * (double)(a.probs[p].nx) * (double)(a.probs[p].ny);
+      queries += (unsigned long long)q;
+    }
+    a.item_off[a.nprob] = acc;
+    PlanHdr h;
+    h.nitems = acc;
+    h.nsplit = nsplit;
+    h.qper = a.qper;
+    h.pad0 = 0;
+    *a.plan = h;
+    *a.work = 0;
+    *a.act_cnt_nxt = 0;
+    *a.near_cnt_nxt = 0;
+    *a.round_ctr += 1;
+    if (a.stat_queries) *a.stat_queries += queries;
+    if (a.stat_pairs) *a.stat_pairs += pairs;
+  }
+  for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) a.q_cnt_nxt[p] = 0;
+}
+
+void launch_plan_round(const PlanArgs& a, cudaStream_t s) { plan_round_kernel<<<1, 256, 0, s>>>(a); }
+
+}  // namespace dbie

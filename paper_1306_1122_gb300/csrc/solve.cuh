@@ -1,0 +1,89 @@
+// solve.cuh -- structures shared by the host driver and the lambda-search kernels.
+#pragma once
+#include "dbie_internal.cuh"
+
+namespace dbie {
+
+// Per-point simplex state, structure-of-arrays: field f of point g is at [f * N + g].
+enum DField {
+  D_VL = 0,      // vertex lambda: D_VL + v * 3 + d   (v = 0..3, d = 0..2)
+  D_VB = 12,     // vertex field B: D_VB + v * 3 + p
+  D_VF = 24,     // vertex f: D_VF + v
+  D_VG = 28,     // vertex g
+  D_VPHI = 32,   // vertex Phi
+  D_RL = 36,     // reflected point: lambda (3), B (3), f, g, Phi
+  D_RB = 39,
+  D_RF = 42,
+  D_RG = 43,
+  D_RPHI = 44,
+  D_TL = 45,     // pending single trial point lambda (3)
+  D_NFIELDS = 48
+};
+enum IField { I_STAGE = 0, I_ITERS = 1, I_NFEV = 2, I_STATUS = 3, I_QSLOT = 4, I_NFIELDS = 5 };
+enum PtStatus { PT_RUNNING = -1, PT_CONVERGED = 0, PT_MAXITER = 1 };
+enum Stage { ST_INIT = 0, ST_REFLECT = 1, ST_EXPAND = 2, ST_OCONTRACT = 3, ST_ICONTRACT = 4,
+             ST_SHRINK = 5, ST_DONE = 6 };
+
+struct SolveOpts {
+  double eps_f, eps_g, tol, w_g;
+  int32_t max_iter, dim, near_on, pad0;
+};
+
+// One ping-pong side of the per-round buffers.
+struct RoundBuf {
+  float4* qpos;        // query slots
+  Lam4* qlam;
+  int32_t* q_cnt;      // [nprob]
+  int32_t* act;        // active points
+  int32_t* act_cnt;    // [1]
+  int32_t* near;       // near-field query slots
+  int32_t* near_cnt;   // [1]
+};
+
+struct SolveArgs {
+  const ProbDesc* probs;
+  int32_t nprob;
+  int32_t pad0;
+  int64_t N;                 // total points
+  const float4* ppos;        // [N] x, y, z, problem (int bits)
+  double* sd;                // [D_NFIELDS * N]
+  int32_t* si;               // [I_NFIELDS * N]
+  RoundBuf cur, nxt;
+  const double* out;         // pair-sum partials of the current round (item chunks)
+  const PlanHdr* plan;       // plan of the current round
+  const int32_t* item_off;   // [nprob + 1]
+  SolveOpts o;
+  // final per-point results
+  double* res_B;             // [N * 3]
+  double* res_lam;           // [N * 3]
+  double* res_f;
+  double* res_g;
+  int32_t* res_iters;
+  int32_t* res_status;
+  int32_t* res_nfev;
+  char* codes;               // [N * codes_stride] or null
+  int32_t codes_stride;
+  int32_t pad1;
+  unsigned* err;
+};
+
+struct PlanArgs {
+  const ProbDesc* probs;
+  int32_t nprob;
+  int32_t qper;              // queries per item
+  int32_t target_items;
+  int32_t nsplit_cap;
+  const int32_t* q_cnt_cur;
+  int32_t* q_cnt_pass;       // copy of the current counts read by the pair-sum pass
+  int32_t* item_off;         // [nprob + 1]
+  PlanHdr* plan;
+  int32_t* work;
+  int32_t* q_cnt_nxt;        // zeroed
+  int32_t* act_cnt_nxt;
+  int32_t* near_cnt_nxt;
+  int32_t* round_ctr;        // incremented per round
+  unsigned long long* stat_queries;
+  double* stat_pairs;
+};
+
+}  // namespace dbie

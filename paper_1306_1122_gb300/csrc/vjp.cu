@@ -1,0 +1,23 @@
+// Adjoint (transpose of Eq. 16) kernels, FP32 and FP64 forms.
+#include "kernels.h"
+#include "pairsum.cuh"
+
+namespace dbie {
+
+template <typename Real, bool TIED, int CFG>
+KernelRef vjp_ref_t() {
+  constexpr LaunchCfg c = cfg_of(CFG);
+  return KernelRef{(const void*)&vjp_kernel<Real, TIED, c.p, c.nt, NSTAGE>, c.nt, c.p * c.nt,
+                   (size_t)NSTAGE * VJP_NFIELD * TILE * sizeof(Real)};
+}
+
+KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
+  if (fp64) return tied ? vjp_ref_t<double, true, 0>() : vjp_ref_t<double, false, 0>();
+  switch (cfg) {
+    case 1: return tied ? vjp_ref_t<float, true, 1>() : vjp_ref_t<float, false, 1>();
+    case 2: return tied ? vjp_ref_t<float, true, 2>() : vjp_ref_t<float, false, 2>();
+    default: return tied ? vjp_ref_t<float, true, 0>() : vjp_ref_t<float, false, 0>();
+  }
+}
+
+}  // namespace dbie

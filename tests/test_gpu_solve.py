@@ -1,0 +1,135 @@
+"""GPU parity of the on-device lambda search (dbie_solve, dbie_solve_batched) with the oracle.
+
+The simplex takes discrete decisions on Phi, and lambda is not unique (Sect. 2.1), so:
+  * FP64 GPU form: same step-code sequence as the oracle on >= 99 % of points, and there lambda
+    and B agree tightly;
+  * mixed form: B returned by the GPU equals the oracle's field at the GPU's own lambda* (gate of
+    tests/gates.py), f and g are consistent with that field, and the search quality matches the
+    oracle's statistically (most points take the oracle's step sequence)."""
+import numpy as np
+import pytest
+
+import oracle
+from gates import abs_scales, check_B, oracle_boundary
+from synth import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbie():
+    import paper_1306_1122_gb300 as d
+    return d
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = workloads.small_ll()
+    idx = np.random.default_rng(5).choice(len(w.points), 384, replace=False)
+    idx.sort()
+    return w, w.points[idx]
+
+
+def oracle_solve(mag, pts, lambda_mode=0, max_iter=50):
+    return oracle.solve(oracle_boundary(mag), pts.astype(np.float64),
+                        oracle.Options(lambda_mode=lambda_mode, max_iter=max_iter))
+
+
+def gpu_solve(dbie, mag, pts, precision, lambda_mode=0, max_iter=50):
+    f = dbie.DBIEField.from_magnetogram(mag)
+    r = f.solve(torch.from_numpy(pts), dbie.Options(precision=precision, lambda_mode=lambda_mode,
+                                                     max_iter=max_iter), codes=max_iter)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in r.items()}
+    out["codes"] = [bytes(row).rstrip(b"\0").decode() for row in out["codes"]]
+    f.close()
+    return out
+
+
+def lam_close(a, b, L):
+    return np.all(np.abs(a - b) <= 1e-4 * np.maximum(np.abs(b), 1.0 / L), axis=1)
+
+
+@pytest.mark.parametrize("lambda_mode", [0, 1])
+def test_fp64_solve_follows_oracle(dbie, small, lambda_mode):
+    w, pts = small
+    ref = oracle_solve(w.mag, pts, lambda_mode)
+    got = gpu_solve(dbie, w.mag, pts, 1, lambda_mode)
+    same = np.array([a == b for a, b in zip(got["codes"], ref["codes"])])
+    assert same.mean() >= 0.99, same.mean()
+    L = 32.0
+    assert lam_close(got["lam"][same], ref["lam"][same], L).all()
+    assert np.array_equal(got["iters"][same], ref["iters"][same])
+    assert np.array_equal(got["nfev"][same], ref["nfev"][same])
+    assert np.array_equal(got["status"][same], ref["status"][same])
+    rel = np.linalg.norm(got["B"] - ref["B"], axis=1) / np.linalg.norm(ref["B"], axis=1)
+    assert rel[same].max() < 1e-9
+    assert np.all(got["lam"] >= 0)
+
+
+def test_mixed_solve_field_and_objective_at_own_lambda(dbie, small):
+    w, pts = small
+    got = gpu_solve(dbie, w.mag, pts, 0)
+    bd = oracle_boundary(w.mag)
+    B, G, _ = oracle.field(bd, pts.astype(np.float64), got["lam"])
+    sB, _ = abs_scales(w.mag, pts, got["lam"])
+    rb = check_B(got["B"], B, sB)
+    assert rb["bad"].size == 0, rb
+    f, g, phi, _, _ = oracle.objective(B, G, g_scale=1.0 / 6.0)
+    # Phi = f + g at lambda*: the GPU's own value against the oracle's at the same lambda
+    dphi = np.abs((got["f"] + got["g"]) - phi)
+    assert np.median(dphi) < 1e-5 and np.percentile(dphi, 95) < 1e-3, (np.median(dphi),)
+    ref = oracle_solve(w.mag, pts)
+    same = np.array([a == b for a, b in zip(got["codes"], ref["codes"])])
+    # the oracle's own optimum is not better than the GPU's by more than the FP32 noise on most
+    # points (the search is local and Phi is evaluated in FP32 pair terms)
+    worse = (got["f"] + got["g"]) > ref["phi"] * (1 + 1e-4) + 1e-4
+    print(f"mixed solve: step sequences equal on {same.mean():.3f}, worse Phi on {worse.mean():.3f}")
+    assert same.mean() >= 0.5
+    assert worse.mean() <= 0.2
+    assert lam_close(got["lam"][same], ref["lam"][same], 32.0).mean() >= 0.9
+
+
+def test_batched_matches_individual(dbie):
+    rng = np.random.default_rng(9)
+    mags, pts = [], []
+    for k, (n, m) in enumerate([(24, 150), (40, 333), (17, 64)]):
+        w = workloads.active_region(n, n, 2, seed=100 + k, peak=(500, 1500), sigma=(3, 5))
+        mags.append(w)
+        pts.append(np.stack([rng.uniform(0, n - 1, m), rng.uniform(0, n - 1, m),
+                             rng.uniform(1, 10, m)], 1).astype(np.float32))
+    opt = dbie.Options(precision=1, max_iter=30)
+    fields = [dbie.DBIEField.from_magnetogram(m) for m in mags]
+    outs = dbie.solve_batched(fields, [torch.from_numpy(p) for p in pts], opt, codes=30)
+    torch.cuda.synchronize()
+    for f, p, o in zip(fields, pts, outs):
+        single = f.solve(torch.from_numpy(p), opt, codes=30)
+        torch.cuda.synchronize()
+        same = (o["codes"] == single["codes"]).all(dim=1).cpu().numpy()
+        assert same.mean() >= 0.99
+        d = (o["B"] - single["B"]).abs().max(dim=1).values.cpu().numpy()
+        s = single["B"].abs().max(dim=1).values.cpu().numpy()
+        assert np.all(d[same] <= 1e-9 * s[same])
+    for f in fields:
+        f.close()
+
+
+def test_solve_edge_cases(dbie, small):
+    w, pts = small
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    r0 = f.solve(torch.zeros((0, 3)))
+    assert r0["B"].shape == (0, 3)
+    # max_iter = 0: the best initial vertex, no iteration
+    r = f.solve(torch.from_numpy(pts[:7]), dbie.Options(max_iter=0, precision=1))
+    torch.cuda.synchronize()
+    assert (r["iters"] == 0).all() and (r["nfev"] == 4).all()
+    ref = oracle_solve(w.mag, pts[:7], max_iter=0)
+    assert np.allclose(r["lam"].cpu().numpy(), ref["lam"], rtol=0, atol=1e-15)
+    # one point, given initial lambda
+    r1 = f.solve(torch.from_numpy(pts[:1]), dbie.Options(precision=1, max_iter=5),
+                 lambda_init=torch.tensor([[0.05, -0.02, 0.01]], dtype=torch.float64))
+    ref1 = oracle.solve(oracle_boundary(w.mag), pts[:1].astype(np.float64),
+                        oracle.Options(max_iter=5), lam0=np.array([[0.05, -0.02, 0.01]]))
+    assert np.allclose(r1["lam"].cpu().numpy(), ref1["lam"], rtol=1e-9, atol=1e-12)
+    f.close()
