@@ -156,6 +156,28 @@ dbie_status dbie_vjp(dbie_ctx* ctx, int64_t n, const float* xyz, const double* l
                      const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
                      double* glam, int32_t accumulate, void* stream);
 
+/* Field evaluation that allocates no memory (no counterpart in the paper: an interface for
+ * callers that may not allocate device memory while they run -- code inside another framework's
+ * memory pool or arena, real-time loops that cannot take an allocation's implicit device
+ * synchronisation, plugin hosts that forbid allocations by third-party libraries).
+ *   Computes B (n, 3) float64 as dbie_eval does with opt = NULL (mixed precision, FP64 near field
+ *   for z <= 2 hx), for the magnetogram (nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz: device
+ *   float32, row-major (ny, nx)) at the points xyz (n, 3) device float32 with lambda (n, 3)
+ *   device float32.  No context is needed.  All pointers are device memory.
+ *   Limits: nx * ny <= 65536 and n <= 65536; larger sizes return DBIE_EINVAL.
+ *   Scratch: one fixed 16 MiB array in the library's device image; every GPU that loads the
+ *   library holds it until the process exits.  No cudaMalloc or cudaFree is made.
+ *   The first call on a device looks up that array's device address (cudaGetSymbolAddress) with
+ *   the device current; make that first call before any stream capture.
+ *   All calls share the array and it keeps the previous call's contents (the call clears what
+ *   must start at zero); calls that overlap on the GPU (other streams, other host threads) race.
+ *   Synchronises `stream` before returning.  Device inputs are not validated.  Error messages
+ *   go to stderr (dbie_last_error() is not updated by this function). */
+dbie_status dbie_eval_noalloc(int32_t nx, int32_t ny, double x0, double y0, double hx, double hy,
+                              double pixel_area, const float* Bx, const float* By,
+                              const float* Bz, int64_t n, const float* xyz, const float* lambda,
+                              double* B, void* stream);
+
 /* Turn CUDA-event timing of the pair-sum kernels on or off, and read or reset the counters. */
 dbie_status dbie_set_profiling(dbie_ctx* ctx, int32_t enable);
 dbie_status dbie_get_stats(dbie_ctx* ctx, dbie_stats* stats, int32_t reset);

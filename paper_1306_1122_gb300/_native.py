@@ -65,6 +65,7 @@ _SIGS = {
     "dbie_solve_batched": (_I32, [_I32, _P, _P, _P, ctypes.POINTER(dbie_options), _P, _I32,
                                   ctypes.POINTER(dbie_solve_out), _P]),
     "dbie_vjp": (_I32, [_P, _I64, _P, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _I32, _P]),
+    "dbie_eval_noalloc": (_I32, [_I32, _I32, _D, _D, _D, _D, _D, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "dbie_set_profiling": (_I32, [_P, _I32]),
     "dbie_get_stats": (_I32, [_P, ctypes.POINTER(dbie_stats), _I32]),
     "dbie_autotune": (_I32, [_P, _P]),
@@ -127,6 +128,15 @@ def dbie_solve_batched(nprob, ctxs, n, xyz, opt, lambda_init, mem_kind, outs, st
 def dbie_vjp(ctx, n, xyz, lam, gB, opt, mem_kind, gB0, glam, accumulate, stream):
     check(lib.dbie_vjp(ctx, n, xyz, lam, gB, None if opt is None else ctypes.byref(opt), mem_kind,
                        gB0, glam, accumulate, stream))
+
+
+def dbie_eval_noalloc(nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz, n, xyz, lam, B, stream):
+    """Evaluation that allocates nothing: all scratch lives in one fixed device array of the
+    library (for callers that may not allocate while they run).  Device pointers only."""
+    status = lib.dbie_eval_noalloc(nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz, n, xyz, lam, B,
+                                   stream)
+    if status != DBIE_OK:
+        raise DBIEError(status, "dbie_eval_noalloc failed (message on stderr)")
 
 
 def dbie_set_profiling(ctx, enable):

@@ -27,6 +27,7 @@ UNITS = {
     "pairsum_f32_obj.cu": [],
     "pairsum_f64.cu": [],
     "vjp.cu": [],
+    "noalloc.cu": [],
 }
 
 
