@@ -141,6 +141,8 @@ def run_ours(args):
     stream0 = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     h = N.dbie_create(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA, *(ptr(c) for c in B0_dev),
                       N.DBIE_MEM_DEVICE, stream0)
+    N.dbie_autotune(h, stream0)              # launch configuration per kernel (cached per device)
+    tuned = N.dbie_get_config(h)
     N.dbie_set_profiling(h, 1)
 
     def step(stats_out):
@@ -170,6 +172,7 @@ def run_ours(args):
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     hh = N.dbie_create(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA, P(m.Bx), P(m.By), P(m.Bz),
                        N.DBIE_MEM_HOST, None)
+    N.dbie_set_config(hh, tuned)
 
     def step_host(h2d, d2h):
         """Same step through the C ABI with host buffers (copies inside the calls)."""
@@ -269,7 +272,8 @@ def run_ours(args):
                    "fwd_bwd": "solve (Nelder-Mead, tol 1e-6, max 50 it) + adjoint + dL/dlambda",
                    "pairs_per_step": pairs_step, "simplex_rounds": rounds,
                    "objective_evals": q, "l2": "flushed before each step (256 MB write)",
-                   "parallelism": f"replicas x{world} (points are independent)"},
+                   "parallelism": f"replicas x{world} (points are independent)",
+                   "launch_configs": tuned},
         "solve_ms": step_ms,
         "roofline": {"bound": "alu", "pipe": "MUFU (rsqrt, sin, cos)",
                      "kernel": "g1_kernel<float, objective, per-component lambda>",

@@ -187,6 +187,13 @@ dbie_status dbie_get_stats(dbie_ctx* ctx, dbie_stats* stats, int32_t reset);
  * memory and in the file named by $DBIE_TUNE_CACHE when set.  Synchronises `stream`. */
 dbie_status dbie_autotune(dbie_ctx* ctx, void* stream);
 
+/* Launch configuration indices in use (after dbie_autotune): cfg_out[2 * variant + tied] for the
+ * pair-sum variants value, value+dlambda, objective, objective+dlambda (8 entries), then the
+ * adjoint kernel's (cfg_out[8]).  cfg_out must hold 9 int32. */
+dbie_status dbie_get_config(dbie_ctx* ctx, int32_t* cfg_out);
+/* Set the same 9 indices (each in [0, 6)); DBIE_EINVAL if one is out of range. */
+dbie_status dbie_set_config(dbie_ctx* ctx, const int32_t* cfg_in);
+
 /* Release the context and everything it owns.  NULL is a no-op. */
 void dbie_destroy(dbie_ctx* ctx);
 

@@ -69,6 +69,8 @@ _SIGS = {
     "dbie_set_profiling": (_I32, [_P, _I32]),
     "dbie_get_stats": (_I32, [_P, ctypes.POINTER(dbie_stats), _I32]),
     "dbie_autotune": (_I32, [_P, _P]),
+    "dbie_get_config": (_I32, [_P, _P]),
+    "dbie_set_config": (_I32, [_P, _P]),
     "dbie_destroy": (None, [_P]),
     "dbie_last_error": (ctypes.c_char_p, []),
     "dbie_version": (ctypes.c_char_p, []),
@@ -151,6 +153,17 @@ def dbie_get_stats(ctx, reset=False) -> dbie_stats:
 
 def dbie_autotune(ctx, stream):
     check(lib.dbie_autotune(ctx, stream))
+
+
+def dbie_get_config(ctx):
+    cfg = (_I32 * 9)()
+    check(lib.dbie_get_config(ctx, cfg))
+    return list(cfg)
+
+
+def dbie_set_config(ctx, cfg):
+    arr = (_I32 * 9)(*cfg)
+    check(lib.dbie_set_config(ctx, arr))
 
 
 def dbie_destroy(ctx):

@@ -271,7 +271,7 @@ KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64) {
 // near-field correction.  Results are in c->out as item chunks described by c->misc.
 dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, int64_t n,
                         const float* d_xyz, const float* d_lamf, const double* d_lamd,
-                        cudaStream_t s) {
+                        cudaStream_t s, bool tied = false) {
   Misc* m = c->misc.as<Misc>();
   DBIE_TRY(ensure(c->qpos, sizeof(float4) * n));
   DBIE_TRY(ensure(c->qlam, sizeof(Lam4) * n));
@@ -280,7 +280,7 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   CUDA_TRY(cudaMemsetAsync(&m->near_cnt, 0, sizeof(int32_t), s));
   launch_pack_eval(n, d_xyz, d_lamf, d_lamd, c->qpos.as<float4>(), c->qlam.as<Lam4>(),
                    c->near_list.as<int32_t>(), &m->near_cnt, near_on ? 1 : 0, o.near_z, s);
-  const KernelRef k = g1_ref(c, var, false, fp64);
+  const KernelRef k = g1_ref(c, var, tied, fp64);
   const int grid = persistent_grid(k, c->device);
   const int64_t nblk = (n + k.qper - 1) / k.qper;
   const int64_t target = 2LL * grid;
@@ -316,7 +316,7 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
     c->pending_pairs.push_back((double)n * (double)c->npix);
   }
   if (near_on)
-    launch_nearfield(var, false, c->prob.as<ProbDesc>(), c->near_list.as<int32_t>(), &m->near_cnt,
+    launch_nearfield(var, tied, c->prob.as<ProbDesc>(), c->near_list.as<int32_t>(), &m->near_cnt,
                      c->qpos.as<float4>(), c->qlam.as<Lam4>(), &m->plan, m->item_off,
                      c->out.as<double>(), 2 * c->sm_count, s);
   CUDA_TRY(cudaGetLastError());
@@ -336,6 +336,75 @@ struct Staging {  // host-memory calls: where each argument lives on the device
 };
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// ------------------------------------------------------------------------ autotuning ----
+// Chosen launch configuration per (device, kernel, variant, boundary size class), kept in memory
+// and, when $DBIE_TUNE_CACHE names a file, appended to it as "key cfg" lines.
+struct TuneCache {
+  std::mutex mu;
+  std::vector<std::pair<std::string, int>> entries;
+  bool loaded = false;
+};
+TuneCache g_tune;
+
+std::string tune_key(int dev, const char* kernel, int var, int tied, int64_t units) {
+  cudaDeviceProp p;
+  cudaGetDeviceProperties(&p, dev);
+  int bucket = 0;
+  while ((int64_t(1) << bucket) < units) ++bucket;
+  std::string name(p.name);
+  for (char& ch : name)
+    if (ch == ' ') ch = '_';
+  return name + "/" + kernel + "/v" + std::to_string(var) + "/t" + std::to_string(tied) + "/2^" +
+         std::to_string(bucket);
+}
+
+int tune_lookup(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  if (!g_tune.loaded) {
+    g_tune.loaded = true;
+    if (const char* path = std::getenv("DBIE_TUNE_CACHE")) {
+      if (FILE* f = std::fopen(path, "r")) {
+        char k[512];
+        int v;
+        while (std::fscanf(f, "%511s %d", k, &v) == 2)
+          if (v >= 0 && v < NCFG) g_tune.entries.push_back({k, v});
+        std::fclose(f);
+      }
+    }
+  }
+  for (auto it = g_tune.entries.rbegin(); it != g_tune.entries.rend(); ++it)
+    if (it->first == key) return it->second;
+  return -1;
+}
+
+void tune_store(const std::string& key, int cfg) {
+  std::lock_guard<std::mutex> lk(g_tune.mu);
+  g_tune.entries.push_back({key, cfg});
+  if (const char* path = std::getenv("DBIE_TUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d\n", key.c_str(), cfg);
+      std::fclose(f);
+    }
+  }
+}
+
+// Minimum over `reps` launches of the timed pair-sum kernel of fn() (profiling events).
+template <typename Fn>
+dbie_status time_min(dbie_ctx* c, int reps, Fn fn, double* best_ms) {
+  *best_ms = 1e30;
+  for (int r = 0; r < reps; ++r) {
+    c->pending.clear();
+    c->pending_pairs.clear();
+    const dbie_stats saved = c->stats;
+    c->stats = dbie_stats{};
+    DBIE_TRY(fn());
+    resolve_pending(c);
+    if (c->stats.launches > 0) *best_ms = std::min(*best_ms, c->stats.kernel_ms);
+    c->stats = saved;
+  }
+  return DBIE_OK;
+}
 
 }  // namespace
 
@@ -972,7 +1041,117 @@ dbie_status dbie_get_stats(dbie_ctx* c, dbie_stats* st, int32_t reset) {
 
 dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
   if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
-  (void)stream;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // Synthetic queries over the context's own boundary: points above the field of view at
+  // 1..16 pixels, lambda of the order of 1 / (box size); a fixed linear congruential sequence.
+  const int64_t n = std::min<int64_t>(131072, std::max<int64_t>(8192, 16LL * c->sm_count * 128));
+  std::vector<float> xyz(3 * n), lamf(3 * n);
+  std::vector<double> lamd(3 * n), gB(3 * n);
+  uint64_t st = 0x9E3779B97F4A7C15ull;
+  auto rnd = [&]() {
+    st = st * 6364136223846793005ull + 1442695040888963407ull;
+    return (double)(st >> 11) * (1.0 / 9007199254740992.0);
+  };
+  const double L = std::max(c->nx * c->hx, c->ny * c->hy);
+  for (int64_t i = 0; i < n; ++i) {
+    xyz[3 * i] = (float)(c->x0 + rnd() * (c->nx - 1) * c->hx);
+    xyz[3 * i + 1] = (float)(c->y0 + rnd() * (c->ny - 1) * c->hy);
+    xyz[3 * i + 2] = (float)(c->hx * (1.0 + 15.0 * rnd()));
+    for (int p = 0; p < 3; ++p) {
+      lamd[3 * i + p] = (rnd() - 0.5) * 4.0 / L;
+      lamf[3 * i + p] = (float)lamd[3 * i + p];
+      gB[3 * i + p] = rnd() - 0.5;
+    }
+  }
+  DBuf buf;
+  const size_t bytes = align256(12 * n) * 2 + align256(24 * n) * 2 + align256(24 * c->npix);
+  CUDA_TRY(cudaMalloc(&buf.p, bytes));
+  buf.cap = bytes;
+  Staging sg{0, buf.as<char>()};
+  float* d_xyz = sg.take<float>(3 * n);
+  float* d_lamf = sg.take<float>(3 * n);
+  double* d_lamd = sg.take<double>(3 * n);
+  double* d_gB = sg.take<double>(3 * n);
+  double* d_gB0 = sg.take<double>(3 * c->npix);
+  cudaError_t ce = cudaMemcpyAsync(d_xyz, xyz.data(), 12 * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_lamf, lamf.data(), 12 * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_lamd, lamd.data(), 24 * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_gB, gB.data(), 24 * n, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    buf.release();
+    return fail(DBIE_ECUDA, std::string("autotune staging: ") + cudaGetErrorString(ce));
+  }
+  dbie_options o;
+  dbie_default_options(&o);
+  o = resolved(c, &o);
+  const bool prof = c->profiling;
+  c->profiling = true;
+  dbie_status status = DBIE_OK;
+  const int pairs[5][2] = {{VAR_OBJ, 0}, {VAR_OBJ, 1}, {VAR_V, 0}, {VAR_VL, 0}, {VAR_OBJL, 0}};
+  for (const auto& vt : pairs) {
+    const int var = vt[0], tied = vt[1];
+    const std::string key = tune_key(c->device, "g1", var, tied, c->npix);
+    const int cached = tune_lookup(key);
+    if (cached >= 0) {
+      c->cfg[var][tied] = cached;
+      continue;
+    }
+    int best = 0;
+    double best_ms = 1e30;
+    for (int cfg = 0; cfg < NCFG && status == DBIE_OK; ++cfg) {
+      c->cfg[var][tied] = cfg;
+      double ms = 0;
+      status = time_min(c, 3, [&]() {
+        return pass_single(c, var, false, o, n, d_xyz, d_lamf, nullptr, s, tied != 0);
+      }, &ms);
+      if (ms < best_ms) { best_ms = ms; best = cfg; }
+    }
+    c->cfg[var][tied] = best;
+    if (status == DBIE_OK) tune_store(key, best);
+  }
+  {
+    const std::string key = tune_key(c->device, "vjp", 0, 0, c->npix);
+    const int cached = tune_lookup(key);
+    if (cached >= 0) {
+      c->vjp_cfg = cached;
+    } else {
+      int best = 0;
+      double best_ms = 1e30;
+      for (int cfg = 0; cfg < NCFG && status == DBIE_OK; ++cfg) {
+        c->vjp_cfg = cfg;
+        double ms = 0;
+        status = time_min(c, 3, [&]() {
+          return dbie_vjp(c, n, d_xyz, d_lamd, d_gB, &o, DBIE_MEM_DEVICE, d_gB0, nullptr, 0, s);
+        }, &ms);
+        if (ms < best_ms) { best_ms = ms; best = cfg; }
+      }
+      c->vjp_cfg = best;
+      if (status == DBIE_OK) tune_store(key, best);
+    }
+  }
+  c->profiling = prof;
+  cudaStreamSynchronize(s);
+  buf.release();
+  return status;
+}
+
+dbie_status dbie_set_config(dbie_ctx* c, const int32_t* cfg_in) {
+  if (!c || !cfg_in) return fail(DBIE_EINVAL, "ctx and cfg_in must not be NULL");
+  for (int i = 0; i < 9; ++i)
+    if (cfg_in[i] < 0 || cfg_in[i] >= NCFG) return fail(DBIE_EINVAL, "configuration index out of range");
+  for (int v = 0; v < 4; ++v)
+    for (int t = 0; t < 2; ++t) c->cfg[v][t] = cfg_in[2 * v + t];
+  c->vjp_cfg = cfg_in[8];
+  return DBIE_OK;
+}
+
+dbie_status dbie_get_config(dbie_ctx* c, int32_t* cfg_out) {
+  if (!c || !cfg_out) return fail(DBIE_EINVAL, "ctx and cfg_out must not be NULL");
+  for (int v = 0; v < 4; ++v)
+    for (int t = 0; t < 2; ++t) cfg_out[2 * v + t] = c->cfg[v][t];
+  cfg_out[8] = c->vjp_cfg;
   return DBIE_OK;
 }
 

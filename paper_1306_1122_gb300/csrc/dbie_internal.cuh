@@ -15,7 +15,7 @@ namespace dbie {
 constexpr int TILE = 256;            // pixels (or points, for the adjoint) per tile
 constexpr int NFIELD = 5;            // x, y, bx, by, bz
 constexpr int VJP_NFIELD = 9;        // x, y, z^2, lx, ly, lz, wx, wy, wz
-constexpr int NEAR_W = 8;            // near-field window half width (pixels): 17 x 17 window
+constexpr int NEAR_W = 3;            // near-field window half width (pixels): 7 x 7 window
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
 // Error word bits (set with atomicOr, read by the host after synchronising).
@@ -220,16 +220,20 @@ __device__ __forceinline__ Query<Real, TIED> make_query(float4 pos, Lam4 lam) {
   return q;
 }
 
-// Per-pair contributions (before they are added to the running sums):
-//   t0[p] = phi b_p, t1[p] = psi b_p (its products with dx, dy give Sx, Sy), tl[p] = cos(lr) b_p / r.
-// FP32 form: every operation has an explicit rounding so that the near-field kernel, which
-// re-evaluates these terms to replace them by FP64 ones, reproduces them bit for bit.
+// Per-pair factors of the FP32 form.  The running sums take them as
+//   S0 += u * rb (fused), S1 += t1, Sx += t1 * dx (fused), Sy += t1 * dy (fused),
+//   Sl += cr * b (fused),  with rb = b / r^3, t1 = psi b = (lambda^2 c - 3 u / r^2) rb, cr = c / r,
+// so the exact contribution of a pixel is a product of two rounded FP32 factors.  Every factor
+// is computed with an explicit rounding so that the near-field kernel, which replaces these
+// contributions by FP64 ones, reproduces them bit for bit (a product of two FP32 values is exact
+// in FP64).
 template <int VAR, bool TIED>
 struct Terms32 {
   float dx, dy;
-  float t0[3];
+  float u[TIED ? 1 : 3];
+  float rb[3];
   float t1[has_grad(VAR) ? 3 : 1];
-  float tl[has_dlam(VAR) ? 3 : 1];
+  float cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
 };
 
 template <int VAR, bool TIED>
@@ -242,36 +246,25 @@ __device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float 
   const float r = __fmul_rn(r2, ri);
   const float ri2 = __fmul_rn(ri, ri);
   const float ri3 = __fmul_rn(ri2, ri);
-  if constexpr (TIED) {
-    const float th = __fmul_rn(q.l[0], r);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) t.rb[p] = __fmul_rn(ri3, b[p]);
+  float ri2x3 = 0.f;
+  if constexpr (has_grad(VAR)) ri2x3 = __fmul_rn(3.f, ri2);
+#pragma unroll
+  for (int p = 0; p < (TIED ? 1 : 3); ++p) {
+    const float th = __fmul_rn(q.l[p], r);
     const float s = sin_mufu(th), c = cos_mufu(th);
-    const float u = __fmaf_rn(th, s, c);
-    float w = 0.f, cr = 0.f;
-    if constexpr (has_grad(VAR)) w = __fmaf_rn(-u, __fmul_rn(3.f, ri2), __fmul_rn(q.l2[0], c));
-    if constexpr (has_dlam(VAR)) cr = __fmul_rn(c, ri);
+    t.u[p] = __fmaf_rn(th, s, c);
+    if constexpr (has_grad(VAR)) {
+      const float w = __fmaf_rn(-t.u[p], ri2x3, __fmul_rn(q.l2[p], c));
+      if constexpr (TIED) {
 #pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const float rb = __fmul_rn(ri3, b[p]);
-      t.t0[p] = __fmul_rn(u, rb);
-      if constexpr (has_grad(VAR)) t.t1[p] = __fmul_rn(w, rb);
-      if constexpr (has_dlam(VAR)) t.tl[p] = __fmul_rn(cr, b[p]);
-    }
-  } else {
-    float ri2x3 = 0.f;
-    if constexpr (has_grad(VAR)) ri2x3 = __fmul_rn(3.f, ri2);
-#pragma unroll
-    for (int p = 0; p < 3; ++p) {
-      const float th = __fmul_rn(q.l[p], r);
-      const float s = sin_mufu(th), c = cos_mufu(th);
-      const float u = __fmaf_rn(th, s, c);
-      const float rb = __fmul_rn(ri3, b[p]);
-      t.t0[p] = __fmul_rn(u, rb);
-      if constexpr (has_grad(VAR)) {
-        const float w = __fmaf_rn(-u, ri2x3, __fmul_rn(q.l2[p], c));
-        t.t1[p] = __fmul_rn(w, rb);
+        for (int pp = 0; pp < 3; ++pp) t.t1[pp] = __fmul_rn(w, t.rb[pp]);
+      } else {
+        t.t1[p] = __fmul_rn(w, t.rb[p]);
       }
-      if constexpr (has_dlam(VAR)) t.tl[p] = __fmul_rn(__fmul_rn(c, ri), b[p]);
     }
+    if constexpr (has_dlam(VAR)) t.cr[p] = __fmul_rn(c, ri);
   }
 }
 

@@ -8,12 +8,18 @@
 
 namespace dbie {
 
-// Launch configurations of the pair-sum kernels: points (or pixels) per thread and CTA size.
-constexpr int NCFG = 3;
+// Launch configurations of the pair-sum kernels: points (or pixels) per thread, CTA size, and a
+// minimum number of resident CTAs per SM (a register cap; 1 = none).  The autotuner picks one.
+constexpr int NCFG = 6;
 constexpr int NSTAGE = 3;
-struct LaunchCfg { int p, nt; };
+struct LaunchCfg { int p, nt, minb; };
 __host__ __device__ constexpr LaunchCfg cfg_of(int c) {
-  return c == 0 ? LaunchCfg{1, 128} : c == 1 ? LaunchCfg{2, 128} : LaunchCfg{1, 256};
+  return c == 0 ? LaunchCfg{1, 128, 1}
+       : c == 1 ? LaunchCfg{2, 128, 1}
+       : c == 2 ? LaunchCfg{1, 256, 1}
+       : c == 3 ? LaunchCfg{1, 128, 6}
+       : c == 4 ? LaunchCfg{1, 64, 1}
+                : LaunchCfg{2, 128, 4};
 }
 
 struct KernelRef {

@@ -105,17 +105,19 @@ __device__ __forceinline__ void sweep_tiles(TileRing<Elem, NSTAGE, NWARP>& ring,
 }
 
 template <int VAR, bool TIED, int NS>
-__device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED>& t) {
+__device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED>& t,
+                                             const float b[3]) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    acc[p * NS + 0] = __fadd_rn(acc[p * NS + 0], t.t0[p]);
+    const int lp = TIED ? 0 : p;
+    acc[p * NS + 0] = __fmaf_rn(t.u[lp], t.rb[p], acc[p * NS + 0]);
     if constexpr (has_grad(VAR)) {
       acc[p * NS + 1] = __fadd_rn(acc[p * NS + 1], t.t1[p]);
       acc[p * NS + 2] = __fmaf_rn(t.t1[p], t.dx, acc[p * NS + 2]);
       acc[p * NS + 3] = __fmaf_rn(t.t1[p], t.dy, acc[p * NS + 3]);
     }
     if constexpr (has_dlam(VAR))
-      acc[p * NS + idx_sl(VAR)] = __fadd_rn(acc[p * NS + idx_sl(VAR)], t.tl[p]);
+      acc[p * NS + idx_sl(VAR)] = __fmaf_rn(t.cr[lp], b[p], acc[p * NS + idx_sl(VAR)]);
   }
 }
 
@@ -156,7 +158,7 @@ __device__ __forceinline__ int find_problem(const int32_t* item_off, int nprob, 
 
 // ---------------------------------------------------------------------------- g1 ----
 template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
-__global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
+__device__ __forceinline__ void g1_body(const G1Args& a) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
   constexpr int Q = NT * P;
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
               for (int u = 0; u < P; ++u) {
                 Terms32<VAR, TIED> tm;
                 pair_terms32<VAR, TIED>(q[u], px[e], py[e], b, tm);
-                accumulate32<VAR, TIED, NS>(acc[u], tm);
+                accumulate32<VAR, TIED, NS>(acc[u], tm, b);
               }
             }
           }
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
 
 
 template <typename Real, bool TIED, int P, int NT, int NSTAGE>
-__global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
+__device__ __forceinline__ void vjp_body(const VjpArgs& a) {
   constexpr int Q = NT * P;
   constexpr int NWARP = NT / 32;
   constexpr bool F32 = sizeof(Real) == 4;
@@ -434,6 +436,25 @@ __global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
     }
   }
   if (tid == 0) ring.drain();
+}
+
+// Kernel entry points.  MINB > 1 caps registers so that MINB CTAs fit on an SM; MINB = 1 leaves
+// the register allocation to the compiler (a plain __launch_bounds__(NT)).
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
+__global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
+  g1_body<Real, VAR, TIED, P, NT, NSTAGE>(a);
+}
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) g1_kernel_mb(const G1Args a) {
+  g1_body<Real, VAR, TIED, P, NT, NSTAGE>(a);
+}
+template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+__global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
+  vjp_body<Real, TIED, P, NT, NSTAGE>(a);
+}
+template <typename Real, bool TIED, int P, int NT, int NSTAGE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) vjp_kernel_mb(const VjpArgs a) {
+  vjp_body<Real, TIED, P, NT, NSTAGE>(a);
 }
 
 }  // namespace dbie

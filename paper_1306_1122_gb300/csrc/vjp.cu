@@ -7,7 +7,10 @@ namespace dbie {
 template <typename Real, bool TIED, int CFG>
 KernelRef vjp_ref_t() {
   constexpr LaunchCfg c = cfg_of(CFG);
-  return KernelRef{(const void*)&vjp_kernel<Real, TIED, c.p, c.nt, NSTAGE>, c.nt, c.p * c.nt,
+  const void* fn;
+  if constexpr (c.minb > 1) fn = (const void*)&vjp_kernel_mb<Real, TIED, c.p, c.nt, NSTAGE, c.minb>;
+  else fn = (const void*)&vjp_kernel<Real, TIED, c.p, c.nt, NSTAGE>;
+  return KernelRef{fn, c.nt, c.p * c.nt,
                    (size_t)NSTAGE * VJP_NFIELD * TILE * sizeof(Real)};
 }
 
@@ -16,6 +19,9 @@ KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
   switch (cfg) {
     case 1: return tied ? vjp_ref_t<float, true, 1>() : vjp_ref_t<float, false, 1>();
     case 2: return tied ? vjp_ref_t<float, true, 2>() : vjp_ref_t<float, false, 2>();
+    case 3: return tied ? vjp_ref_t<float, true, 3>() : vjp_ref_t<float, false, 3>();
+    case 4: return tied ? vjp_ref_t<float, true, 4>() : vjp_ref_t<float, false, 4>();
+    case 5: return tied ? vjp_ref_t<float, true, 5>() : vjp_ref_t<float, false, 5>();
     default: return tied ? vjp_ref_t<float, true, 0>() : vjp_ref_t<float, false, 0>();
   }
 }

@@ -158,6 +158,14 @@ class DBIEField:
                    _ptr(gl), int(acc), _stream())
         return gB0, gl
 
+    def autotune(self):
+        """Time every launch configuration on this boundary and keep the fastest (cached)."""
+        N.dbie_autotune(self._h, _stream())
+        return N.dbie_get_config(self._h)
+
+    def set_config(self, cfg):
+        N.dbie_set_config(self._h, cfg)
+
     def set_profiling(self, on=True):
         N.dbie_set_profiling(self._h, on)
 

@@ -185,3 +185,44 @@ def test_invalid_points_rejected_and_context_survives(dbie):
     empty = f.eval(torch.zeros((0, 3)), torch.zeros((0, 3)))
     assert empty["B"].shape == (0, 3)
     f.close()
+
+
+@pytest.mark.parametrize("cfg", range(6))
+def test_every_launch_configuration(dbie, cfg):
+    """Each launch configuration the autotuner may pick gives the same sums (FP32 form: within
+    the gate; the item split differs between configurations)."""
+    mag = random_mag(70, 45, 50 + cfg)
+    xyz, lam = random_points(mag, 700, 60 + cfg)
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_config([cfg] * 9)
+    r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True, dlam=True)
+    gB = np.random.default_rng(cfg).normal(0, 1, (700, 3))
+    gB0, _ = f.vjp(torch.from_numpy(xyz), torch.from_numpy(lam.astype(np.float64)),
+                   torch.from_numpy(gB), glam=False)
+    torch.cuda.synchronize()
+    bd = oracle_boundary(mag)
+    B, G, _ = oracle.field(bd, xyz.astype(np.float64), lam.astype(np.float64))
+    sB, sG = abs_scales(mag, xyz, lam)
+    rb = check_B(r["B"].cpu().numpy(), B, sB)
+    assert rb["bad"].size == 0, rb
+    assert check_grad(r["gradB"].cpu().numpy(), G, sG[:, :, None])["ok"]
+    ref0 = oracle.vjp(bd, xyz.astype(np.float64), lam.astype(np.float64), gB)
+    assert np.linalg.norm(gB0.cpu().numpy() - ref0) / np.linalg.norm(ref0) < 1e-5
+    # the solve's objective kernels of this configuration, both lambda modes: the field the
+    # search returns equals the oracle's at the returned lambda
+    for mode in (0, 1):
+        s = f.solve(torch.from_numpy(xyz[:200]), dbie.Options(lambda_mode=mode, max_iter=4))
+        torch.cuda.synchronize()
+        ls = s["lam"].cpu().numpy()
+        Bs, _, _ = oracle.field(bd, xyz[:200].astype(np.float64), ls)
+        sBs, _ = abs_scales(mag, xyz[:200], ls)
+        assert check_B(s["B"].cpu().numpy(), Bs, sBs)["bad"].size == 0, (cfg, mode)
+    f.close()
+
+
+def test_autotune_picks_valid_configs(dbie):
+    mag = random_mag(64, 64, 70)
+    f = dbie.DBIEField.from_magnetogram(mag)
+    cfg = f.autotune()
+    assert len(cfg) == 9 and all(0 <= c < 6 for c in cfg)
+    f.close()
