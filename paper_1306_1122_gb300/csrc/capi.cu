@@ -748,10 +748,18 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   if (any_init) DBIE_TRY(ensure(b.lam0, sizeof(double) * 3 * N));
 
   // Problems and points.
+  // Descriptor slot of each problem: largest (points x pixels) first, so that the dynamic item
+  // queue hands out the longest work first and the round ends evenly (LPT order).
+  std::vector<int> order(nprob), slot_of(nprob);
+  for (int p = 0; p < nprob; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
+    return (double)n[a] * ctxs[a]->npix > (double)n[b2] * ctxs[b2]->npix;
+  });
+  for (int q = 0; q < nprob; ++q) slot_of[order[q]] = q;
   std::vector<ProbDesc> pds(nprob);
   for (int p = 0; p < nprob; ++p) {
     dbie_ctx* cp = ctxs[p];
-    ProbDesc& pd = pds[p];
+    ProbDesc& pd = pds[slot_of[p]];
     pd = ProbDesc{};
     pd.tiles32 = cp->t32.as<float>();
     pd.tiles64 = cp->t64.as<double>();
@@ -781,7 +789,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     } else {
       launch_count_bad(src, n[p], 1, &ctrl->bad, s);
     }
-    launch_pack_points(n[p], dsrc, p, b.ppos.as<float4>() + pt_off[p], s);
+    launch_pack_points(n[p], dsrc, slot_of[p], b.ppos.as<float4>() + pt_off[p], s);
     if (any_init) {
       double* dst = b.lam0.as<double>() + 3 * pt_off[p];
       if (lam_init[p]) {
@@ -812,7 +820,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   int32_t* res_i = reinterpret_cast<int32_t*>(rb + align256(sizeof(double) * 8 * N));
   SolveArgs sa[2];
   bool near_on = false;
-  for (int p = 0; p < nprob; ++p) near_on |= pds[p].near_z > 0;
+  for (int q = 0; q < nprob; ++q) near_on |= pds[q].near_z > 0;
   for (int cur = 0; cur < 2; ++cur) {
     SolveArgs& a = sa[cur];
     a = SolveArgs{};

@@ -19,7 +19,7 @@ __host__ __device__ constexpr LaunchCfg cfg_of(int c) {
        : c == 2 ? LaunchCfg{1, 256, 1}
        : c == 3 ? LaunchCfg{1, 128, 6}
        : c == 4 ? LaunchCfg{1, 64, 1}
-                : LaunchCfg{2, 128, 4};
+                : LaunchCfg{1, 128, 7};
 }
 
 struct KernelRef {

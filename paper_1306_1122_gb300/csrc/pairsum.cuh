@@ -14,8 +14,8 @@
 //    multicast) into an NSTAGE-deep ring of shared-memory buffers guarded by mbarriers (full:
 //    transaction bytes; empty: one arrival per warp).  Every wait is bounded in time.
 //  * Arithmetic (mixed form): FP32 pair terms (rsqrt, sin, cos on the SFU), plain FP32 sums
-//    over SUB elements, folded by an error-free two-sum into float-float accumulators and
-//    converted to FP64 at the end of the item.  FP64 form: the same sweep in double precision.
+//    over SUB elements, folded by an error-free two-sum (its error carried into the next
+//    block) and converted to FP64 at the end of the item.  FP64 form: the same sweep in double precision.
 #pragma once
 #include "dbie_internal.cuh"
 
@@ -135,14 +135,15 @@ __device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIE
   }
 }
 
-// Error-free fold of a plain FP32 partial sum into a float-float accumulator (two-sum).
-__device__ __forceinline__ void fold2(float& hi, float& lo, float& a) {
+// Fold a plain FP32 block sum `a` into the running sum `hi` with an error-free two-sum; the
+// rounding error of the fold becomes the starting value of the next block's sum (so it is not
+// lost), and hi + a is the compensated total at any time.
+__device__ __forceinline__ void fold2(float& hi, float& a) {
   const float s = __fadd_rn(hi, a);
   const float bp = __fsub_rn(s, hi);
   const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(a, bp));
   hi = s;
-  lo = __fadd_rn(lo, e);
-  a = 0.f;
+  a = e;
 }
 
 // Locate the problem owning work item `it` (item_off is a prefix array of length nprob + 1).
@@ -218,16 +219,13 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
     }
 
     Real acc[P][NSUM];
-    float hi[F32 ? P : 1][F32 ? NSUM : 1], lo[F32 ? P : 1][F32 ? NSUM : 1];
+    float hi[F32 ? P : 1][F32 ? NSUM : 1];
 #pragma unroll
     for (int u = 0; u < P; ++u)
 #pragma unroll
       for (int s = 0; s < NSUM; ++s) {
         acc[u][s] = Real(0);
-        if constexpr (F32) {
-          hi[u][s] = 0.f;
-          lo[u][s] = 0.f;
-        }
+        if constexpr (F32) hi[u][s] = 0.f;
       }
 
     sweep_tiles(ring, tiles, t0, t1, tid, [&](const Real* sx) {
@@ -260,7 +258,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
           for (int u = 0; u < P; ++u)
 #pragma unroll
-            for (int s = 0; s < NSUM; ++s) fold2(hi[u][s], lo[u][s], acc[u][s]);
+            for (int s = 0; s < NSUM; ++s) fold2(hi[u][s], acc[u][s]);
         }
       } else {
 #pragma unroll 2
@@ -283,7 +281,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
       for (int s = 0; s < NSUM; ++s) {
         double v;
-        if constexpr (F32) v = (double)hi[u][s] + (double)lo[u][s];
+        if constexpr (F32) v = (double)hi[u][s] + (double)acc[u][s];
         else v = (double)acc[u][s];
         a.out[((int64_t)it * NSUM + s) * Q + (tid + u * NT)] = v;
       }
@@ -345,16 +343,13 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
       py[u] = *tile_field(btiles, k, 1);
     }
     Real acc[P][3];
-    float hi[F32 ? P : 1][3], lo[F32 ? P : 1][3];
+    float hi[F32 ? P : 1][3];
 #pragma unroll
     for (int u = 0; u < P; ++u)
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         acc[u][p] = Real(0);
-        if constexpr (F32) {
-          hi[u][p] = 0.f;
-          lo[u][p] = 0.f;
-        }
+        if constexpr (F32) hi[u][p] = 0.f;
       }
 
     sweep_tiles(ring, ptiles, t0, t1, tid, [&](const Real* sx) {
@@ -398,7 +393,7 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
 #pragma unroll
           for (int u = 0; u < P; ++u)
 #pragma unroll
-            for (int p = 0; p < 3; ++p) fold2(hi[u][p], lo[u][p], acc[u][p]);
+            for (int p = 0; p < 3; ++p) fold2(hi[u][p], acc[u][p]);
         }
       } else {
 #pragma unroll 2
@@ -429,7 +424,7 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         double v;
-        if constexpr (F32) v = (double)hi[u][p] + (double)lo[u][p];
+        if constexpr (F32) v = (double)hi[u][p] + (double)acc[u][p];
         else v = (double)acc[u][p];
         a.out[((int64_t)it * 3 + p) * Q + (tid + u * NT)] = v;
       }
