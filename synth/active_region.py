@@ -104,33 +104,35 @@ def monopole_field(m: Magnetogram, pts):
 
 def trace_samples(m: Magnetogram, nsamples: int, seed: int, step: float = 0.5,
                   zmin: float = 1.0, zmax: float = 128.0, seed_thresh: float = 200.0,
-                  max_steps: int = 4000) -> np.ndarray:
-    """Field-line samples: RK4 traces through the monopole potential field, seeded at pixels with
-    |Bz| > seed_thresh, keeping samples with zmin <= z <= zmax inside the field of view."""
+                  max_steps: int = 4000, stride: int = 4, batch: int = 4096) -> np.ndarray:
+    """Field-line samples: RK4 traces (step `step` px) through the monopole potential field,
+    seeded at pixels with |Bz| > seed_thresh, each line followed until it leaves the box
+    zmin <= z <= zmax inside the field of view; every `stride`-th point along the lines is a
+    candidate and nsamples of them are drawn uniformly."""
     rng = np.random.default_rng(seed)
     cand = np.argwhere(np.abs(m.Bz) > seed_thresh)
-    out = []
-    have = 0
-    batch = 4096
+    pool, have = [], 0
     while have < nsamples:
         pick = cand[rng.integers(0, len(cand), batch)]
         p = np.stack([pick[:, 1] + rng.uniform(-0.5, 0.5, batch),
                       pick[:, 0] + rng.uniform(-0.5, 0.5, batch), np.full(batch, zmin)], axis=1)
         sgn = np.sign(m.Bz[pick[:, 0], pick[:, 1]]).astype(np.float64)[:, None]
         alive = np.ones(batch, bool)
-        for _ in range(max_steps):
-            def v(q):
-                b = monopole_field(m, q)
-                return sgn * b / np.maximum(np.linalg.norm(b, axis=1, keepdims=True), 1e-30)
+
+        def v(q):
+            b = monopole_field(m, q)
+            return sgn * b / np.maximum(np.linalg.norm(b, axis=1, keepdims=True), 1e-30)
+
+        for it in range(max_steps):
             k1 = v(p); k2 = v(p + 0.5 * step * k1); k3 = v(p + 0.5 * step * k2); k4 = v(p + step * k3)
             p = p + step / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-            inside = ((p[:, 2] >= zmin) & (p[:, 2] <= zmax) & (p[:, 0] >= 0) & (p[:, 0] <= m.nx - 1)
+            alive &= ((p[:, 2] >= zmin) & (p[:, 2] <= zmax) & (p[:, 0] >= 0) & (p[:, 0] <= m.nx - 1)
                       & (p[:, 1] >= 0) & (p[:, 1] <= m.ny - 1))
-            alive &= inside
             if not alive.any():
                 break
-            out.append(p[alive].copy())
-            have += int(alive.sum())
-            if have >= nsamples:
-                break
-    return np.concatenate(out)[:nsamples].astype(np.float32)
+            if it % stride == 0:
+                pool.append(p[alive].copy())
+                have += int(alive.sum())
+    allp = np.concatenate(pool)
+    idx = rng.choice(len(allp), nsamples, replace=False)
+    return allp[np.sort(idx)].astype(np.float32)
