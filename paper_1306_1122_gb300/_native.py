@@ -9,7 +9,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libdbie.so")
+# DBIE_LIBRARY may name another build of the same library (e.g. one compiled with other kernel
+# knobs); by default the in-tree libdbie.so is loaded.
+LIB_PATH = os.environ.get("DBIE_LIBRARY") or os.path.join(_PKG, "libdbie.so")
 
 DBIE_OK, DBIE_EINVAL, DBIE_ENOMEM, DBIE_ECUDA, DBIE_ETIMEOUT, DBIE_EINTERNAL = range(6)
 DBIE_MEM_HOST, DBIE_MEM_DEVICE = 0, 1

@@ -46,7 +46,14 @@ def _sources_mtime() -> float:
     return m
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          extra: list[str] | None = None, lib: str | None = None) -> str:
+    """Compile every translation unit and link libdbie.so.  `extra` adds nvcc flags (e.g.
+    -D knobs of the pair-sum kernel) and `lib` redirects the output (with its own object dir)."""
+    global LIB, BUILD
+    if lib is not None:
+        LIB, BUILD = lib, lib + ".objs"
+    extra = list(extra or [])
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
         return LIB
     nvcc = _nvcc()
@@ -54,7 +61,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(unit):
         obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
-        cmd = [nvcc, *ARCH, *COMMON, *UNITS[unit], "-c", os.path.join(CSRC, unit), "-o", obj]
+        cmd = [nvcc, *ARCH, *COMMON, *extra, *UNITS[unit], "-c", os.path.join(CSRC, unit), "-o",
+               obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {unit}:\n{r.stderr}")

@@ -236,27 +236,40 @@ struct Terms32 {
   float cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
 };
 
+// Geometry of one pair: dx, dy, r, 1/r^2 (times 3) and 1/r^3 (SFU rsqrt).
+struct Geom32 {
+  float dx, dy, r, ri, ri2x3, ri3;
+};
+
+template <bool TIED>
+__device__ __forceinline__ Geom32 pair_geom32(const Query<float, TIED>& q, float px, float py) {
+  Geom32 g;
+  g.dx = __fsub_rn(q.x, px);
+  g.dy = __fsub_rn(q.y, py);
+  const float r2 = __fmaf_rn(g.dx, g.dx, __fmaf_rn(g.dy, g.dy, q.z2));
+  g.ri = rsqrt_mufu(r2);
+  g.r = __fmul_rn(r2, g.ri);
+  const float ri2 = __fmul_rn(g.ri, g.ri);
+  g.ri3 = __fmul_rn(ri2, g.ri);
+  g.ri2x3 = __fmul_rn(3.f, ri2);
+  return g;
+}
+
+// Angular part: sin, cos of lambda r (SFU) and the factors of the sums.
 template <int VAR, bool TIED>
-__device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float px, float py,
-                                             const float b[3], Terms32<VAR, TIED>& t) {
-  t.dx = __fsub_rn(q.x, px);
-  t.dy = __fsub_rn(q.y, py);
-  const float r2 = __fmaf_rn(t.dx, t.dx, __fmaf_rn(t.dy, t.dy, q.z2));
-  const float ri = rsqrt_mufu(r2);
-  const float r = __fmul_rn(r2, ri);
-  const float ri2 = __fmul_rn(ri, ri);
-  const float ri3 = __fmul_rn(ri2, ri);
+__device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, const Geom32& g,
+                                               const float b[3], Terms32<VAR, TIED>& t) {
+  t.dx = g.dx;
+  t.dy = g.dy;
 #pragma unroll
-  for (int p = 0; p < 3; ++p) t.rb[p] = __fmul_rn(ri3, b[p]);
-  float ri2x3 = 0.f;
-  if constexpr (has_grad(VAR)) ri2x3 = __fmul_rn(3.f, ri2);
+  for (int p = 0; p < 3; ++p) t.rb[p] = __fmul_rn(g.ri3, b[p]);
 #pragma unroll
   for (int p = 0; p < (TIED ? 1 : 3); ++p) {
-    const float th = __fmul_rn(q.l[p], r);
+    const float th = __fmul_rn(q.l[p], g.r);
     const float s = sin_mufu(th), c = cos_mufu(th);
     t.u[p] = __fmaf_rn(th, s, c);
     if constexpr (has_grad(VAR)) {
-      const float w = __fmaf_rn(-t.u[p], ri2x3, __fmul_rn(q.l2[p], c));
+      const float w = __fmaf_rn(-t.u[p], g.ri2x3, __fmul_rn(q.l2[p], c));
       if constexpr (TIED) {
 #pragma unroll
         for (int pp = 0; pp < 3; ++pp) t.t1[pp] = __fmul_rn(w, t.rb[pp]);
@@ -264,8 +277,14 @@ __device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float 
         t.t1[p] = __fmul_rn(w, t.rb[p]);
       }
     }
-    if constexpr (has_dlam(VAR)) t.cr[p] = __fmul_rn(c, ri);
+    if constexpr (has_dlam(VAR)) t.cr[p] = __fmul_rn(c, g.ri);
   }
+}
+
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float px, float py,
+                                             const float b[3], Terms32<VAR, TIED>& t) {
+  pair_angular32<VAR, TIED>(q, pair_geom32<TIED>(q, px, py), b, t);
 }
 
 // FP64 terms (used by the FP64 form and by the near-field correction).

@@ -21,7 +21,17 @@
 
 namespace dbie {
 
-constexpr int SUB = 32;  // elements summed in plain FP32 before a compensated fold
+#ifndef DBIE_FOLD_PIXELS
+#define DBIE_FOLD_PIXELS 32
+#endif
+#ifndef DBIE_STAGED
+#define DBIE_STAGED 0
+#endif
+#ifndef DBIE_GROUP_UNROLL
+#define DBIE_GROUP_UNROLL 8
+#endif
+constexpr int SUB = DBIE_FOLD_PIXELS;  // elements summed in plain FP32 before a compensated fold
+constexpr int GROUP_UNROLL = DBIE_GROUP_UNROLL;  // 4-pixel groups unrolled within a block
 
 // Ring of NSTAGE shared-memory tile buffers filled by TMA bulk copies.  Thread 0 issues; all
 // warps consume.  `issued` / `consumed` count tiles over the CTA's lifetime, which fixes the
@@ -232,7 +242,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
       if constexpr (F32) {
 #pragma unroll 1
         for (int k0 = 0; k0 < TILE; k0 += SUB) {
-#pragma unroll
+#pragma unroll GROUP_UNROLL
           for (int k = k0; k < k0 + SUB; k += 4) {
             const float4 X = *reinterpret_cast<const float4*>(sx + k);
             const float4 Y = *reinterpret_cast<const float4*>(sx + TILE + k);
@@ -244,6 +254,24 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
             const float bx[4] = {BX.x, BX.y, BX.z, BX.w};
             const float by[4] = {BY.x, BY.y, BY.z, BY.w};
             const float bz[4] = {BZ.x, BZ.y, BZ.z, BZ.w};
+#if DBIE_STAGED
+            // Geometry (one SFU rsqrt per pair) of the whole group first, then the angular part.
+            Geom32 gm[4][P];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+#pragma unroll
+              for (int u = 0; u < P; ++u) gm[e][u] = pair_geom32<TIED>(q[u], px[e], py[e]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const float b[3] = {bx[e], by[e], bz[e]};
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                Terms32<VAR, TIED> tm;
+                pair_angular32<VAR, TIED>(q[u], gm[e][u], b, tm);
+                accumulate32<VAR, TIED, NS>(acc[u], tm, b);
+              }
+            }
+#else
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float b[3] = {bx[e], by[e], bz[e]};
@@ -254,6 +282,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
                 accumulate32<VAR, TIED, NS>(acc[u], tm, b);
               }
             }
+#endif
           }
 #pragma unroll
           for (int u = 0; u < P; ++u)
