@@ -60,7 +60,7 @@ class _Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("lambda_mode", ctypes.c_int32),
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("deriv", ctypes.c_int32),
-                ("fd_delta", ctypes.c_double)]
+                ("fd_delta", ctypes.c_double), ("method", ctypes.c_int32)]
 
 
 class _NMResult(ctypes.Structure):
@@ -70,6 +70,8 @@ class _NMResult(ctypes.Structure):
 
 FUN = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
                        ctypes.POINTER(ctypes.c_int32))
+FUN_GRAD = ctypes.CFUNCTYPE(ctypes.c_double, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double),
+                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32))
 
 
 def _load():
@@ -87,6 +89,12 @@ def _load():
             lib.orc_vjp.argtypes = [P, ctypes.c_int64, P, P, P, P, ctypes.c_int32]
             lib.orc_nelder_mead_sim.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_int32,
                                                 FUN, P, P, P, ctypes.c_int32]
+            lib.orc_bfgs.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_int32, FUN_GRAD, P, P]
+            lib.orc_objective_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double,
+                                               ctypes.c_double, P, P, ctypes.c_int32]
+            lib.orc_field_dl.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
+                                         P, P, P, P]
             _lib = lib
     return _lib
 
@@ -145,6 +153,7 @@ class Options:
     g_scale: float = 0.0        # 0 -> hx / 6 (cubic cell: dV / dSigma = h^3 / 6 h^2)
     deriv: int = 0
     fd_delta: float = 0.0       # 0 -> 1e-3 * hx (one thousandth of a pixel, Sect. 2.1)
+    method: int = 0             # 0: Downhill Simplex (the paper), 1: quasi-Newton (BFGS)
 
     def resolved(self, grid: Grid) -> "Options":
         o = Options(**self.__dict__)
@@ -159,7 +168,7 @@ class Options:
     def c(self, grid: Grid) -> _Options:
         o = self.resolved(grid)
         return _Options(o.eps_f, o.eps_g, o.tol, o.max_iter, o.lambda_mode, o.simplex_step,
-                        o.w_g, o.g_scale, o.deriv, o.fd_delta)
+                        o.w_g, o.g_scale, o.deriv, o.fd_delta, o.method)
 
 
 def _threads(nthreads):
@@ -176,6 +185,53 @@ def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthrea
     lib.orc_eval_many(bd.ref, n, _ptr(xyz), _ptr(lam), deriv, fd_delta, _ptr(B), _ptr(G), _ptr(dl),
                       _threads(nthreads))
     return B, G, dl
+
+
+def field_dl(bd: Boundary, xyz, lam):
+    """B, G as field(), dB/dlambda (n,3) and dGdl (n,3,3) = d^2 B_p / (dx_j dlambda_p)."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    n = xyz.shape[0]
+    B = np.zeros((n, 3)); G = np.zeros((n, 9)); dl = np.zeros((n, 3)); dG = np.zeros((n, 9))
+    for i in range(n):
+        lib.orc_field_dl(bd.ref, xyz[i, 0], xyz[i, 1], xyz[i, 2], _ptr(lam[i]),
+                         B[i].ctypes.data_as(ctypes.c_void_p), G[i].ctypes.data_as(ctypes.c_void_p),
+                         dl[i].ctypes.data_as(ctypes.c_void_p), dG[i].ctypes.data_as(ctypes.c_void_p))
+    return B, G.reshape(n, 3, 3), dl, dG.reshape(n, 3, 3)
+
+
+def objective_grad(bd: Boundary, xyz, lam, g_scale: float, w_g: float = 1.0, nthreads=None):
+    """f, g, Phi (n,) and dPhi/dlambda (n,3) at given lambda (n,3)."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    n = xyz.shape[0]
+    fgp = np.zeros((n, 3)); dphi = np.zeros((n, 3))
+    lib.orc_objective_many(bd.ref, n, _ptr(xyz), _ptr(lam), g_scale, w_g, _ptr(fgp), _ptr(dphi),
+                           _threads(nthreads))
+    return fgp[:, 0], fgp[:, 1], fgp[:, 2], dphi
+
+
+def bfgs(fun_grad, x0, step: float, tol: float, max_iter: int):
+    """The oracle's quasi-Newton search on a Python objective: fun_grad(x) -> (value, grad, flag)."""
+    lib = _load()
+    x0 = _f64(x0)
+    n = x0.shape[0]
+
+    def cb(_ctx, xp, gp, flagp):
+        v, g, fl = fun_grad(np.array([xp[d] for d in range(n)]))
+        for d in range(n):
+            gp[d] = float(g[d])
+        flagp[0] = int(fl)
+        return float(v)
+
+    cfun = FUN_GRAD(cb)
+    res = _NMResult()
+    x3 = np.zeros(3); x3[:n] = x0
+    lib.orc_bfgs(n, _ptr(x3), step, tol, max_iter, cfun, None, ctypes.byref(res))
+    return dict(x=np.array(res.x[:n]), fx=res.fx, iters=res.iters, nfev=res.nfev,
+                status=res.status)
 
 
 def objective(B, G, g_scale: float, w_g: float = 1.0):

@@ -89,6 +89,43 @@ void orc_field(const orc_boundary* bd, double xi, double yi, double zi, const do
   }
 }
 
+/* The lambda-derivatives of the weight's spatial derivatives, term by term:
+ *   d/dlam (da/dx_i) = z (x_i - x_k) dpsi/dlam w,  d/dlam (da/dy_i) = z (y_i - y_k) dpsi/dlam w,
+ *   d/dlam (da/dz_i) = (dphi/dlam + z^2 dpsi/dlam) w,
+ *   dphi/dlam = lambda cos(lambda r) / r,
+ *   dpsi/dlam = (2 lambda cos(lambda r) - lambda^2 r sin(lambda r) - 3 lambda cos(lambda r)) / r^3
+ * (the last from differentiating psi = (lambda^2 cos(lambda r) - 3 u / r^2) / r^3 with
+ * du/dlam = lambda r^2 cos(lambda r)). */
+void orc_field_dl(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                  double B[3], double G[9], double dBdl[3], double dGdl[9]) {
+  orc_field(bd, xi, yi, zi, lam, B, G, dBdl);
+  for (int p = 0; p < 3; ++p) {
+    const float* B0 = comp_ptr(bd, p);
+    const double l = lam[p];
+    nsum sx = {0, 0}, sy = {0, 0}, sz = {0, 0};
+    for (int j = 0; j < bd->ny; ++j) {
+      const double yk = bd->y0 + j * bd->hy;
+      for (int i = 0; i < bd->nx; ++i) {
+        const double xk = bd->x0 + i * bd->hx;
+        const double b0 = (double)B0[(int64_t)j * bd->nx + i];
+        const double dx = xi - xk, dy = yi - yk;
+        const double r = sqrt(dx * dx + dy * dy + zi * zi);
+        const double lr = l * r;
+        const double r3 = r * r * r;
+        const double dphi = l * cos(lr) / r;
+        const double dpsi = (2.0 * l * cos(lr) - l * l * r * sin(lr) - 3.0 * l * cos(lr)) / r3;
+        const double w = bd->dA / TWO_PI;
+        nsum_add(&sx, zi * dx * dpsi * w * b0);
+        nsum_add(&sy, zi * dy * dpsi * w * b0);
+        nsum_add(&sz, (dphi + zi * zi * dpsi) * w * b0);
+      }
+    }
+    dGdl[3 * p + 0] = nsum_get(&sx);
+    dGdl[3 * p + 1] = nsum_get(&sy);
+    dGdl[3 * p + 2] = nsum_get(&sz);
+  }
+}
+
 /* Eq. 13 read literally: first-order forward differences of B with lambda held at its value at r_i. */
 void orc_field_fd(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
                   double delta, double B[3], double G[9]) {
@@ -123,6 +160,129 @@ void orc_objective(const double B[3], const double G[9], double g_scale, double 
   if (phi) *phi = fv + w_g * gv;
   if (J) { J[0] = Jx; J[1] = Jy; J[2] = Jz; }
   if (D) *D = div;
+}
+
+/* Gradient of Phi = f + w_g g with respect to lambda_q: lambda_q moves B_q (by dBdl[q]) and row q
+ * of the gradient matrix (by dGdl[q][.]); the derivatives of |J x B|, |J|, |B| and |div B| follow
+ * by the chain rule.  At |J x B| = 0 or |div B| = 0 (kinks of f and g) the one-sided part is 0. */
+void orc_objective_grad(const double B[3], const double G[9], const double dBdl[3],
+                        const double dGdl[9], double g_scale, double w_g, double* f, double* g,
+                        double* phi, double dphi[3]) {
+  double J[3], D;
+  orc_objective(B, G, g_scale, w_g, f, g, phi, J, &D);
+  const double C[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                       J[0] * B[1] - J[1] * B[0]};
+  const double nJ = sqrt(J[0] * J[0] + J[1] * J[1] + J[2] * J[2]);
+  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  const double nC = sqrt(C[0] * C[0] + C[1] * C[1] + C[2] * C[2]);
+  for (int q = 0; q < 3; ++q) {
+    double dB[3] = {0, 0, 0}, dG[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    dB[q] = dBdl[q];
+    for (int j = 0; j < 3; ++j) dG[3 * q + j] = dGdl[3 * q + j];
+    const double dJ[3] = {dG[3 * 2 + 1] - dG[3 * 1 + 2], dG[3 * 0 + 2] - dG[3 * 2 + 0],
+                          dG[3 * 1 + 0] - dG[3 * 0 + 1]};
+    const double dD = dG[0] + dG[4] + dG[8];
+    /* dC = dJ x B + J x dB */
+    const double dC[3] = {dJ[1] * B[2] - dJ[2] * B[1] + J[1] * dB[2] - J[2] * dB[1],
+                          dJ[2] * B[0] - dJ[0] * B[2] + J[2] * dB[0] - J[0] * dB[2],
+                          dJ[0] * B[1] - dJ[1] * B[0] + J[0] * dB[1] - J[1] * dB[0]};
+    double df = 0.0, dg = 0.0;
+    if (nJ * nB > 0.0) {
+      const double JdJ = J[0] * dJ[0] + J[1] * dJ[1] + J[2] * dJ[2];
+      const double BdB = B[0] * dB[0] + B[1] * dB[1] + B[2] * dB[2];
+      const double CdC = C[0] * dC[0] + C[1] * dC[1] + C[2] * dC[2];
+      df = (nC > 0.0 ? CdC / (nC * nJ * nB) : 0.0) - (*f) * (JdJ / (nJ * nJ) + BdB / (nB * nB));
+    }
+    if (nB > 0.0) {
+      const double BdB = B[0] * dB[0] + B[1] * dB[1] + B[2] * dB[2];
+      const double sgn = D > 0.0 ? 1.0 : (D < 0.0 ? -1.0 : 0.0);
+      dg = g_scale * (sgn * dD / nB - fabs(D) * BdB / (nB * nB * nB));
+    }
+    dphi[q] = df + w_g * dg;
+  }
+}
+
+/* ---------------------------------------------------------------------- quasi-Newton ---- */
+
+void orc_bfgs(int32_t n, const double x0[3], double step, double tol, int32_t max_iter,
+              orc_fun_grad fun, void* ctx, orc_nm_result* res) {
+  double x[3] = {0, 0, 0}, gr[3] = {0, 0, 0}, H[9], xt[3] = {0, 0, 0}, gt[3] = {0, 0, 0};
+  double d[3] = {0, 0, 0};
+  int32_t flag = 0, flagt = 0, nfev = 0, iters = 0, status = 0;
+  for (int i = 0; i < n; ++i) x[i] = x0[i];
+  double F = fun(ctx, x, gr, &flag);
+  nfev++;
+  double gn = 0.0;
+  for (int i = 0; i < n; ++i) gn += gr[i] * gr[i];
+  gn = sqrt(gn);
+  for (int i = 0; i < 9; ++i) H[i] = 0.0;
+  if (gn > 0.0)
+    for (int i = 0; i < n; ++i) H[3 * i + i] = step / gn;
+  for (;;) {
+    if (flag) { status = 0; break; }
+    if (!(gn > 0.0)) { status = 0; break; }
+    if (iters >= max_iter) { status = 1; break; }
+    double gd = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < n; ++j) s += H[3 * i + j] * gr[j];
+      d[i] = -s;
+    }
+    for (int i = 0; i < n; ++i) gd += gr[i] * d[i];
+    if (!(gd < 0.0)) {  /* not a descent direction: restart from the scaled gradient */
+      for (int i = 0; i < 9; ++i) H[i] = 0.0;
+      for (int i = 0; i < n; ++i) H[3 * i + i] = step / gn;
+      gd = 0.0;
+      for (int i = 0; i < n; ++i) { d[i] = -(H[3 * i + i] * gr[i]); gd += gr[i] * d[i]; }
+    }
+    double a = 1.0, Ft = 0.0;
+    int accepted = 0;
+    for (int ls = 0; ls <= 30; ++ls) {
+      for (int i = 0; i < n; ++i) xt[i] = x[i] + a * d[i];
+      Ft = fun(ctx, xt, gt, &flagt);
+      nfev++;
+      if (Ft <= F + 1e-4 * a * gd) { accepted = 1; break; }
+      a = 0.5 * a;
+    }
+    if (!accepted) { status = 0; break; }
+    iters++;
+    double s[3] = {0, 0, 0}, y[3] = {0, 0, 0}, sy = 0.0, ss = 0.0, yy = 0.0;
+    for (int i = 0; i < n; ++i) {
+      s[i] = xt[i] - x[i];
+      y[i] = gt[i] - gr[i];
+      sy += s[i] * y[i];
+      ss += s[i] * s[i];
+      yy += y[i] * y[i];
+    }
+    if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
+      const double rho = 1.0 / sy;
+      double Hy[3] = {0, 0, 0}, yHy = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double t = 0.0;
+        for (int j = 0; j < n; ++j) t += H[3 * i + j] * y[j];
+        Hy[i] = t;
+      }
+      for (int i = 0; i < n; ++i) yHy += y[i] * Hy[i];
+      const double c2 = rho * rho * yHy + rho;
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j)
+          H[3 * i + j] = H[3 * i + j] - rho * (s[i] * Hy[j] + Hy[i] * s[j]) + c2 * s[i] * s[j];
+    }
+    const double dec = F - Ft;
+    for (int i = 0; i < n; ++i) { x[i] = xt[i]; gr[i] = gt[i]; }
+    F = Ft;
+    flag = flagt;
+    gn = 0.0;
+    for (int i = 0; i < n; ++i) gn += gr[i] * gr[i];
+    gn = sqrt(gn);
+    if (dec <= tol) { status = 0; break; }
+  }
+  for (int i = 0; i < 3; ++i) res->x[i] = i < n ? x[i] : 0.0;
+  res->fx = F;
+  res->iters = iters;
+  res->nfev = nfev;
+  res->status = status;
+  res->ncodes = 0;
 }
 
 /* ---------------------------------------------------------------- Downhill Simplex ---- */
@@ -257,6 +417,35 @@ static double dbie_phi(void* ctx, const double* x, int32_t* flag) {
   return phi;
 }
 
+/* Phi and its lambda-gradient at point pc (tied mode: the sum over the three components). */
+static double dbie_phi_grad(void* ctx, const double* x, double* grad, int32_t* flag) {
+  const dbie_point_ctx* pc = (const dbie_point_ctx*)ctx;
+  double lam[3], B[3], G[9], dBdl[3], dGdl[9], f, g, phi, dphi[3];
+  expand_lambda(pc->opt, x, lam);
+  orc_field_dl(pc->bd, pc->x, pc->y, pc->z, lam, B, G, dBdl, dGdl);
+  orc_objective_grad(B, G, dBdl, dGdl, pc->opt->g_scale, pc->opt->w_g, &f, &g, &phi, dphi);
+  if (pc->opt->lambda_mode == 1) grad[0] = dphi[0] + dphi[1] + dphi[2];
+  else { grad[0] = dphi[0]; grad[1] = dphi[1]; grad[2] = dphi[2]; }
+  *flag = (f <= pc->opt->eps_f && g <= pc->opt->eps_g) ? 1 : 0;
+  return phi;
+}
+
+void orc_objective_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                        double g_scale, double w_g, double* fgphi, double* dphi,
+                        int32_t nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    double B[3], G[9], dBdl[3], dGdl[9], f, g, phi;
+    orc_field_dl(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, B, G, dBdl, dGdl);
+    orc_objective_grad(B, G, dBdl, dGdl, g_scale, w_g, &f, &g, &phi, dphi + 3 * i);
+    fgphi[3 * i] = f;
+    fgphi[3 * i + 1] = g;
+    fgphi[3 * i + 2] = phi;
+  }
+}
+
 void orc_eval_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                    int32_t deriv, double fd_delta, double* B, double* G, double* dBdl,
                    int32_t nthreads) {
@@ -289,8 +478,11 @@ void orc_solve_many(const orc_boundary* bd, int64_t n, const double* xyz, const 
     double x0[3] = {0, 0, 0};
     if (lam0) for (int d = 0; d < dim; ++d) x0[d] = lam0[3 * i + d];
     orc_nm_result r;
-    orc_nelder_mead(dim, x0, opt->simplex_step, opt->tol, opt->max_iter, dbie_phi, &pc, &r,
-                    codes ? codes + i * (int64_t)codes_stride : NULL, codes ? codes_stride : 0);
+    if (opt->method == 1)
+      orc_bfgs(dim, x0, opt->simplex_step, opt->tol, opt->max_iter, dbie_phi_grad, &pc, &r);
+    else
+      orc_nelder_mead(dim, x0, opt->simplex_step, opt->tol, opt->max_iter, dbie_phi, &pc, &r,
+                      codes ? codes + i * (int64_t)codes_stride : NULL, codes ? codes_stride : 0);
     /* The kernel depends on lambda^2 only, so |lambda| is reported (Sect. 2.1: lambda is not unique). */
     double lb[3];
     expand_lambda(opt, r.x, lb);

@@ -35,6 +35,7 @@ typedef struct {
   double g_scale;        /* Delta V_i / Delta sigma_i of Eq. 9 */
   int32_t deriv;         /* 0: analytic derivative at fixed lambda, 1: forward difference */
   double fd_delta;       /* difference step for deriv = 1 */
+  int32_t method;        /* 0: Downhill Simplex (the paper), 1: quasi-Newton (orc_bfgs) */
 } orc_options;
 
 /* Field and its derivatives at one point for a given lambda triple:
@@ -47,9 +48,20 @@ void orc_field(const orc_boundary* bd, double xi, double yi, double zi, const do
 void orc_field_fd(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
                   double delta, double B[3], double G[9]);
 
+/* As orc_field, plus the lambda-derivatives of the spatial derivatives:
+ *   dGdl[p][j] = d^2 B_p / (d x_j d lambda_p). */
+void orc_field_dl(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                  double B[3], double G[9], double dBdl[3], double dGdl[9]);
+
 /* Force-freeness f (Eq. 8), divergence measure g (Eq. 9), J = curl B (Eq. 14), D = div B. */
 void orc_objective(const double B[3], const double G[9], double g_scale, double w_g,
                    double* f, double* g, double* phi, double J[3], double* D);
+
+/* Phi = f + w_g g and its gradient with respect to (lambda_x, lambda_y, lambda_z), by the chain
+ * rule through B and its spatial derivatives (lambda_p moves only component p). */
+void orc_objective_grad(const double B[3], const double G[9], const double dBdl[3],
+                        const double dGdl[9], double g_scale, double w_g, double* f, double* g,
+                        double* phi, double dphi[3]);
 
 /* Generic Downhill Simplex in n dimensions (n <= 3).  fun(ctx, x, &flag) returns the
  * objective and sets flag != 0 when the point meets the problem's own stopping test. */
@@ -68,7 +80,21 @@ void orc_nelder_mead(int32_t n, const double x0[3], double step, double tol, int
 void orc_nelder_mead_sim(int32_t n, const double* sim, double tol, int32_t max_iter,
                          orc_fun fun, void* ctx, orc_nm_result* res, char* codes, int32_t codes_cap);
 
+/* Quasi-Newton (BFGS, Armijo backtracking) search for lambda at one point; not in the paper:
+ * an alternative to the Downhill Simplex that uses the exact gradient of Phi.
+ *   x_{k+1} = x_k + a d_k, d_k = -H_k grad Phi, a = 1, 1/2, 1/4, ... until
+ *   Phi(x_k + a d_k) <= Phi(x_k) + 1e-4 a grad . d_k (at most 30 halvings), then the BFGS update
+ *   of the inverse Hessian H (skipped unless s.y > 1e-12 |s||y|).  H_0 = I step / |grad Phi_0|
+ *   (first step of length `step` along -grad), reset the same way when d is not a descent
+ *   direction.  Stops on Eq. 12, on a decrease below tol, on grad = 0, when the line search
+ *   fails, or after max_iter accepted steps. */
+typedef double (*orc_fun_grad)(void* ctx, const double* x, double* grad, int32_t* flag);
+void orc_bfgs(int32_t n, const double x0[3], double step, double tol, int32_t max_iter,
+              orc_fun_grad fun, void* ctx, orc_nm_result* res);
+
 /* Batched entry points over n points (OpenMP over points when nthreads > 1). */
+void orc_objective_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                        double g_scale, double w_g, double* fgphi, double* dphi, int32_t nthreads);
 void orc_eval_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                    int32_t deriv, double fd_delta, double* B, double* G, double* dBdl,
                    int32_t nthreads);

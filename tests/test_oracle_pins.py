@@ -303,3 +303,63 @@ def test_solve_improves_objective_and_reports_abs_lambda(oracle_lib):
     assert np.all(res["lam"] >= 0)
     assert all(set(c) <= set("REOIS") for c in res["codes"])
     assert np.all((res["status"] == 0) | (res["iters"] == opt.max_iter))
+
+
+def test_lambda_gradient_of_objective_matches_central_differences(oracle_lib):
+    """dPhi/dlambda (chain rule through B, its gradient, J and div B) equals central differences
+    of the oracle's own Phi, and the second derivatives d^2B/(dx dlambda) equal differences of G."""
+    bd = _random_boundary(11)
+    pts = np.array([[0.3, -0.7, 1.5], [2.0, 1.0, 4.0], [-3.1, 2.2, 2.9], [4.4, -1.0, 6.0]])
+    lam = np.array([[0.11, -0.23, 0.37], [0.02, 0.5, 0.05], [0.8, 0.1, -0.2], [0.3, 0.3, 0.3]])
+    gs = 1.0 / 6.0
+    f, g, phi, dphi = oracle.objective_grad(bd, pts, lam, gs)
+    B, G, dl, dG = oracle.field_dl(bd, pts, lam)
+    h = 1e-5
+    for q in range(3):
+        e = np.zeros(3); e[q] = h
+        _, _, pp, _ = oracle.objective_grad(bd, pts, lam + e, gs)
+        _, _, pm, _ = oracle.objective_grad(bd, pts, lam - e, gs)
+        assert np.allclose((pp - pm) / (2 * h), dphi[:, q], rtol=1e-5, atol=1e-7), q
+        _, Gp, _ = oracle.field(bd, pts, lam + e)
+        _, Gm, _ = oracle.field(bd, pts, lam - e)
+        fd = (Gp - Gm)[:, q, :] / (2 * h)
+        assert np.allclose(fd, dG[:, q, :], rtol=1e-6, atol=1e-8 * np.abs(dG).max()), q
+
+
+@pytest.mark.parametrize("name", ["quadratic", "rosen3"])
+def test_bfgs_reaches_minimum_and_decreases(oracle_lib, name):
+    """The oracle's quasi-Newton search: monotone decrease (Armijo) and the known minimum of a
+    convex quadratic (exactly) and of Rosenbrock's function (to tolerance)."""
+    A = np.array([1.0, 3.0, 0.5])
+    c = np.array([0.3, -0.2, 0.7])
+    vals = []
+
+    def quad(x):
+        vals.append(float(np.sum(A * (x - c) ** 2) + 0.1))
+        return vals[-1], 2 * A * (x - c), 0
+
+    def rosen(x):
+        v = float(sum(100 * (x[1:] - x[:-1] ** 2) ** 2 + (1 - x[:-1]) ** 2))
+        gr = np.zeros(3)
+        gr[:-1] += -400 * x[:-1] * (x[1:] - x[:-1] ** 2) - 2 * (1 - x[:-1])
+        gr[1:] += 200 * (x[1:] - x[:-1] ** 2)
+        vals.append(v)
+        return v, gr, 0
+
+    fun = quad if name == "quadratic" else rosen
+    r = oracle.bfgs(fun, np.zeros(3), step=0.25, tol=1e-14, max_iter=500)
+    target = c if name == "quadratic" else np.ones(3)
+    assert np.allclose(r["x"], target, atol=1e-5), r
+    assert r["status"] == 0 and r["nfev"] == len(vals)
+
+
+def test_bfgs_solve_improves_on_start(oracle_lib):
+    """method = 1 on points of the small Low & Lou case: Phi never above Phi at the start."""
+    from synth import workloads
+    w = workloads.small_ll()
+    m = w.mag
+    bd = oracle.Boundary(oracle.Grid(m.nx, m.ny), m.Bx, m.By, m.Bz)
+    pts = w.points[[3, 400, 1200]].astype(np.float64)
+    r = oracle.solve(bd, pts, oracle.Options(method=1, max_iter=20))
+    _, _, phi0, _ = oracle.objective_grad(bd, pts, np.zeros((3, 3)), 1.0 / 6.0)
+    assert np.all(r["phi"] <= phi0 + 1e-15)
