@@ -299,6 +299,7 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_form"] = fp64_compare(w, args.fp64_points, dev)
+        line["quasi_newton"] = method_compare(w, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if world > 1:
@@ -346,6 +347,34 @@ def fp64_compare(w, npts, dev):
                                                 "max": float(rel.max())},
             "same_step_sequence_frac": float(same.mean()),
             "lambda_rel_err_where_same": float(lam_rel[same].max()) if same.any() else None}
+
+
+def method_compare(w, dev):
+    """The paper's Downhill Simplex against the gradient-based quasi-Newton search (not in the
+    paper) on all points of the workload, mixed precision: solve time, objective evaluations and
+    the final Phi = f + g."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    pts = torch.from_numpy(w.points).to(dev)
+    f = dbie.DBIEField.from_magnetogram(w.mag, device=dev)
+    f.autotune()
+    out = {}
+    for name, method in (("simplex", 0), ("quasi_newton", 1)):
+        opt = dbie.Options(method=method)
+        f.solve(pts[:256], opt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = f.solve(pts, opt)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        phi = (r["f"] + r["g"]).cpu().numpy()
+        out[name] = {"solve_s": dt, "evals_mean": float(r["nfev"].float().mean()),
+                     "phi_median": float(np.median(phi)), "phi_mean": float(phi.mean()),
+                     "f_median": float(r["f"].median()), "g_median": float(r["g"].median())}
+    f.close()
+    out["speedup"] = out["simplex"]["solve_s"] / out["quasi_newton"]["solve_s"]
+    return out
 
 
 # --------------------------------------------------------------------- oracle (CPU) ----

@@ -58,6 +58,8 @@ enum { DBIE_PREC_MIXED = 0, DBIE_PREC_FP64 = 1 };
 enum { DBIE_LAMBDA_PER_COMPONENT = 0, DBIE_LAMBDA_TIED = 1 };
 /* Per-point result status of dbie_solve. */
 enum { DBIE_PT_CONVERGED = 0, DBIE_PT_MAXITER = 1 };
+/* Lambda search method of dbie_solve. */
+enum { DBIE_METHOD_SIMPLEX = 0, DBIE_METHOD_QUASI_NEWTON = 1 };
 
 /* Options of the lambda search (Sect. 2.1, Eqs. 8-12) and of the arithmetic.
  * Fill with dbie_default_options() and override fields. */
@@ -72,7 +74,12 @@ typedef struct {
   double g_scale;      /* Delta V_i / Delta sigma_i of Eq. 9; <= 0 selects hx / 6 */
   int32_t precision;   /* DBIE_PREC_MIXED (FP32 pair terms, compensated sums, FP64 near field
                           and FP64 reductions) or DBIE_PREC_FP64 (FP64 throughout) */
-  int32_t reserved0;
+  int32_t method;      /* DBIE_METHOD_SIMPLEX (the paper's Downhill Simplex, default) or
+                          DBIE_METHOD_QUASI_NEWTON (BFGS with Armijo backtracking on the exact
+                          gradient dPhi/dlambda; not in the paper).  For the quasi-Newton method
+                          max_iter counts accepted steps, tol bounds the decrease of Phi per step,
+                          and the search starts at lambda_init + simplex_step (1, 1, 1) (Phi is even
+                          in every lambda_p, so lambda_init = 0 itself is a stationary point). */
   double near_z;       /* mixed precision: points with z <= near_z get their near-field pixels
                           (a 17 x 17 window) summed in FP64; < 0 selects 2 * hx, 0 disables */
 } dbie_options;
@@ -128,6 +135,14 @@ dbie_status dbie_set_boundary(dbie_ctx* ctx, const float* Bx, const float* By, c
 dbie_status dbie_eval(dbie_ctx* ctx, int64_t n, const float* xyz, const float* lambda,
                       const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
                       double* dBdlam, double* fgphi, void* stream);
+
+/* f (Eq. 8), g (Eq. 9), Phi = f + w_g g (fgphi, (n, 3)) and the exact gradient dPhi/dlambda_p
+ * (dphi, (n, 3); lambda_p moves component p of B and its spatial derivatives) at n points for
+ * given lambda (n, 3) float32.  Either output may be NULL, not both.  Not in the paper: the
+ * gradient used by the quasi-Newton search, exposed for callers' own optimisers. */
+dbie_status dbie_objective(dbie_ctx* ctx, int64_t n, const float* xyz, const float* lambda,
+                           const dbie_options* opt, int32_t mem_kind, double* fgphi, double* dphi,
+                           void* stream);
 
 /* Solve for lambda point by point (Sect. 2.1): Nelder-Mead on Phi(lambda) = f + w_g g from the
  * simplex lambda_init + simplex_step * e_j (lambda_init (n, 3) float64, NULL = 0), stopping on
@@ -188,10 +203,10 @@ dbie_status dbie_get_stats(dbie_ctx* ctx, dbie_stats* stats, int32_t reset);
 dbie_status dbie_autotune(dbie_ctx* ctx, void* stream);
 
 /* Launch configuration indices in use (after dbie_autotune): cfg_out[2 * variant + tied] for the
- * pair-sum variants value, value+dlambda, objective, objective+dlambda (8 entries), then the
- * adjoint kernel's (cfg_out[8]).  cfg_out must hold 9 int32. */
+ * pair-sum variants value, value+dlambda, objective, objective+dlambda, objective+gradient
+ * (10 entries), then the adjoint kernel's (cfg_out[10]).  cfg_out must hold 11 int32. */
 dbie_status dbie_get_config(dbie_ctx* ctx, int32_t* cfg_out);
-/* Set the same 9 indices (each in [0, 6)); DBIE_EINVAL if one is out of range. */
+/* Set the same 11 indices (each in [0, 6)); DBIE_EINVAL if one is out of range. */
 dbie_status dbie_set_config(dbie_ctx* ctx, const int32_t* cfg_in);
 
 /* Release the context and everything it owns.  NULL is a no-op. */

@@ -478,8 +478,12 @@ void orc_solve_many(const orc_boundary* bd, int64_t n, const double* xyz, const 
     double x0[3] = {0, 0, 0};
     if (lam0) for (int d = 0; d < dim; ++d) x0[d] = lam0[3 * i + d];
     orc_nm_result r;
-    if (opt->method == 1)
+    if (opt->method == 1) {
+      /* Phi is even in every lambda_p, so lambda = 0 is a stationary point: the gradient search
+       * starts one step away from it along (1, 1, 1). */
+      for (int d = 0; d < dim; ++d) x0[d] += opt->simplex_step;
       orc_bfgs(dim, x0, opt->simplex_step, opt->tol, opt->max_iter, dbie_phi_grad, &pc, &r);
+    }
     else
       orc_nelder_mead(dim, x0, opt->simplex_step, opt->tol, opt->max_iter, dbie_phi, &pc, &r,
                       codes ? codes + i * (int64_t)codes_stride : NULL, codes ? codes_stride : 0);

@@ -35,7 +35,9 @@ typedef struct {
   double g_scale;        /* Delta V_i / Delta sigma_i of Eq. 9 */
   int32_t deriv;         /* 0: analytic derivative at fixed lambda, 1: forward difference */
   double fd_delta;       /* difference step for deriv = 1 */
-  int32_t method;        /* 0: Downhill Simplex (the paper), 1: quasi-Newton (orc_bfgs) */
+  int32_t method;        /* 0: Downhill Simplex (the paper), 1: quasi-Newton (orc_bfgs) from
+                            lambda_init + simplex_step (1, 1, 1): Phi is even in each lambda_p,
+                            so lambda = 0 itself is a stationary point */
 } orc_options;
 
 /* Field and its derivatives at one point for a given lambda triple:

@@ -18,6 +18,7 @@ DBIE_MEM_HOST, DBIE_MEM_DEVICE = 0, 1
 DBIE_PREC_MIXED, DBIE_PREC_FP64 = 0, 1
 DBIE_LAMBDA_PER_COMPONENT, DBIE_LAMBDA_TIED = 0, 1
 DBIE_PT_CONVERGED, DBIE_PT_MAXITER = 0, 1
+DBIE_METHOD_SIMPLEX, DBIE_METHOD_QUASI_NEWTON = 0, 1
 STATUS_NAMES = {0: "DBIE_OK", 1: "DBIE_EINVAL", 2: "DBIE_ENOMEM", 3: "DBIE_ECUDA",
                 4: "DBIE_ETIMEOUT", 5: "DBIE_EINTERNAL"}
 
@@ -27,7 +28,7 @@ class dbie_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("lambda_mode", ctypes.c_int32),
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("near_z", ctypes.c_double)]
+                ("method", ctypes.c_int32), ("near_z", ctypes.c_double)]
 
 
 class dbie_solve_out(ctypes.Structure):
@@ -62,6 +63,7 @@ _SIGS = {
     "dbie_create": (_I32, [ctypes.POINTER(_P), _I32, _I32, _D, _D, _D, _D, _D, _P, _P, _P, _I32, _P]),
     "dbie_set_boundary": (_I32, [_P, _P, _P, _P, _I32, _P]),
     "dbie_eval": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P, _P, _P]),
+    "dbie_objective": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P]),
     "dbie_solve": (_I32, [_P, _I64, _P, ctypes.POINTER(dbie_options), _P, _I32,
                           ctypes.POINTER(dbie_solve_out), _P]),
     "dbie_solve_batched": (_I32, [_I32, _P, _P, _P, ctypes.POINTER(dbie_options), _P, _I32,
@@ -112,6 +114,11 @@ def dbie_eval(ctx, n, xyz, lam, opt, mem_kind, B, gradB, dBdlam, fgphi, stream):
                         gradB, dBdlam, fgphi, stream))
 
 
+def dbie_objective(ctx, n, xyz, lam, opt, mem_kind, fgphi, dphi, stream):
+    check(lib.dbie_objective(ctx, n, xyz, lam, None if opt is None else ctypes.byref(opt),
+                             mem_kind, fgphi, dphi, stream))
+
+
 def dbie_solve(ctx, n, xyz, opt, lambda_init, mem_kind, out: dbie_solve_out, stream):
     check(lib.dbie_solve(ctx, n, xyz, None if opt is None else ctypes.byref(opt), lambda_init,
                          mem_kind, ctypes.byref(out), stream))
@@ -157,14 +164,17 @@ def dbie_autotune(ctx, stream):
     check(lib.dbie_autotune(ctx, stream))
 
 
+NCONFIG = 11   # pair-sum variants x {per-component, tied} + adjoint
+
+
 def dbie_get_config(ctx):
-    cfg = (_I32 * 9)()
+    cfg = (_I32 * NCONFIG)()
     check(lib.dbie_get_config(ctx, cfg))
     return list(cfg)
 
 
 def dbie_set_config(ctx, cfg):
-    arr = (_I32 * 9)(*cfg)
+    arr = (_I32 * NCONFIG)(*cfg)
     check(lib.dbie_set_config(ctx, arr))
 
 

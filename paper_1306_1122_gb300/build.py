@@ -25,6 +25,7 @@ UNITS = {
     "solve.cu": ["-fmad=false"],
     "pairsum_f32_val.cu": [],
     "pairsum_f32_obj.cu": [],
+    "pairsum_f32_newton.cu": [],
     "pairsum_f64.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],

@@ -149,6 +149,10 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
           }
           if constexpr (has_dlam(VAR))
             c[p * NS + idx_sl(VAR)] += t64.tl[p] - (double)t32.cr[lp] * (double)b32[p];
+          if constexpr (has_newton(VAR)) {
+            c[p * NS + IDX_TX] += t64.t0[p] * t64.dx - (double)t32.t0[p] * (double)t32.dx;
+            c[p * NS + IDX_TY] += t64.t0[p] * t64.dy - (double)t32.t0[p] * (double)t32.dy;
+          }
         }
       }
     }
@@ -174,14 +178,16 @@ void launch_nearfield(int var, bool tied, const ProbDesc* probs, const int32_t* 
       case VAR_V: NF(VAR_V, true); break;
       case VAR_VL: NF(VAR_VL, true); break;
       case VAR_OBJ: NF(VAR_OBJ, true); break;
-      default: NF(VAR_OBJL, true); break;
+      case VAR_OBJL: NF(VAR_OBJL, true); break;
+      default: NF(VAR_OBJN, true); break;
     }
   } else {
     switch (var) {
       case VAR_V: NF(VAR_V, false); break;
       case VAR_VL: NF(VAR_VL, false); break;
       case VAR_OBJ: NF(VAR_OBJ, false); break;
-      default: NF(VAR_OBJL, false); break;
+      case VAR_OBJL: NF(VAR_OBJL, false); break;
+      default: NF(VAR_OBJN, false); break;
     }
   }
 #undef NF

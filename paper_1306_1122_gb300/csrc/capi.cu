@@ -148,7 +148,7 @@ struct dbie_ctx {
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
   SolveBufs sb;
-  int cfg[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};   // tuned launch config per variant / tied
+  int cfg[NVAR][2] = {};   // tuned launch configuration per variant / tied
   int vjp_cfg = 0;
   cudaStream_t cap_stream = nullptr;  // stream used only to capture graphs
   int32_t* pinned = nullptr;          // pinned host words for polling
@@ -178,6 +178,8 @@ dbie_status check_opts(const dbie_options& o) {
     return fail(DBIE_EINVAL, "lambda_mode must be DBIE_LAMBDA_PER_COMPONENT or DBIE_LAMBDA_TIED");
   if (o.precision != DBIE_PREC_MIXED && o.precision != DBIE_PREC_FP64)
     return fail(DBIE_EINVAL, "precision must be DBIE_PREC_MIXED or DBIE_PREC_FP64");
+  if (o.method != DBIE_METHOD_SIMPLEX && o.method != DBIE_METHOD_QUASI_NEWTON)
+    return fail(DBIE_EINVAL, "method must be DBIE_METHOD_SIMPLEX or DBIE_METHOD_QUASI_NEWTON");
   if (!std::isfinite(o.simplex_step) || !std::isfinite(o.w_g) || !std::isfinite(o.g_scale) ||
       !std::isfinite(o.near_z) || !std::isfinite(o.eps_f) || !std::isfinite(o.eps_g))
     return fail(DBIE_EINVAL, "options must be finite");
@@ -592,6 +594,52 @@ dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lam
   return DBIE_OK;
 }
 
+dbie_status dbie_objective(dbie_ctx* c, int64_t n, const float* xyz, const float* lambda,
+                           const dbie_options* opt, int32_t mem_kind, double* fgphi, double* dphi,
+                           void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (n > ((int64_t)1 << 31) - 1) return fail(DBIE_EINVAL, "n too large");
+  if (!fgphi && !dphi) return fail(DBIE_EINVAL, "fgphi and dphi are both NULL");
+  if (n > 0 && (!xyz || !lambda)) return fail(DBIE_EINVAL, "xyz and lambda must not be NULL");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  if (n == 0) return DBIE_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const float* d_xyz = xyz;
+  const float* d_lam = lambda;
+  double *dF = fgphi, *dD = dphi;
+  if (mem_kind == DBIE_MEM_HOST) {
+    DBIE_TRY(host_points_ok(xyz, n));
+    DBIE_TRY(host_finite(lambda, 3 * n, "lambda"));
+    DBIE_TRY(ensure(c->st_in, 2 * align256(sizeof(float) * 3 * n)));
+    DBIE_TRY(ensure(c->st_out, 2 * align256(sizeof(double) * 3 * n)));
+    Staging si{0, c->st_in.as<char>()}, so{0, c->st_out.as<char>()};
+    float* t_xyz = si.take<float>(3 * n);
+    float* t_lam = si.take<float>(3 * n);
+    CUDA_TRY(cudaMemcpyAsync(t_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(t_lam, lambda, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+    d_xyz = t_xyz;
+    d_lam = t_lam;
+    dF = fgphi ? so.take<double>(3 * n) : nullptr;
+    dD = dphi ? so.take<double>(3 * n) : nullptr;
+  }
+  DBIE_TRY(pass_single(c, VAR_OBJN, fp64, o, n, d_xyz, d_lam, nullptr, s));
+  Misc* m = c->misc.as<Misc>();
+  launch_finalize_objective(n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
+                            c->qlam.as<Lam4>(), o.g_scale, o.w_g, dF, dD, nullptr, s);
+  CUDA_TRY(cudaGetLastError());
+  if (mem_kind == DBIE_MEM_HOST) {
+    if (fgphi) CUDA_TRY(cudaMemcpyAsync(fgphi, dF, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (dphi) CUDA_TRY(cudaMemcpyAsync(dphi, dD, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
 dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
                      const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
                      double* glam, int32_t accumulate, void* stream) {
@@ -721,7 +769,10 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (out[p].codes) codes_stride = std::max(codes_stride, (int)out[p].codes_stride);
   codes_stride = std::min(codes_stride, std::max(o.max_iter, 1));
 
-  const KernelRef k = g1_ref(c, VAR_OBJ, tied, fp64);
+  const bool qn = o.method == DBIE_METHOD_QUASI_NEWTON;
+  const int var = qn ? VAR_OBJN : VAR_OBJ;            // quasi-Newton needs the gradient sums
+  const int nsum = 3 * nsum_per_comp(var);
+  const KernelRef k = g1_ref(c, var, tied, fp64);
   const int grid = persistent_grid(k, c->device);
   const int target = 2 * grid;
   const int64_t items_cap = std::max<int64_t>((Qcap + k.qper - 1) / k.qper + nprob, 2LL * target) + 1;
@@ -733,7 +784,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   DBIE_TRY(ensure(b.q_cnt_pass, sizeof(int32_t) * nprob));
   DBIE_TRY(ensure(b.item_off, sizeof(int32_t) * (nprob + 1)));
   DBIE_TRY(ensure(b.ctrl, sizeof(SolveCtrl)));
-  DBIE_TRY(ensure(b.out, sizeof(double) * items_cap * 12 * k.qper));
+  DBIE_TRY(ensure(b.out, sizeof(double) * items_cap * nsum * k.qper));
   DBIE_TRY(ensure(b.res, align256(sizeof(double) * 8 * N) + align256(sizeof(int32_t) * 3 * N)));
   if (codes_stride) DBIE_TRY(ensure(b.codes, (size_t)codes_stride * N));
   for (int sd = 0; sd < 2; ++sd) {
@@ -855,7 +906,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   // Initial simplex and its queries go to side 0.
   SolveArgs a0 = sa[1];  // "next" of the side-1 round is side 0
   const int nm_grid = (int)std::min<int64_t>((N + 127) / 128, 8LL * c->sm_count);
-  launch_solve_init(a0, any_init ? b.lam0.as<double>() : nullptr,
+  (qn ? launch_bfgs_init : launch_solve_init)(a0, any_init ? b.lam0.as<double>() : nullptr,
                     (int)std::min<int64_t>((N + 255) / 256, 8LL * c->sm_count), s);
   CUDA_TRY(cudaGetLastError());
 
@@ -900,11 +951,11 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       if (c->profiling)
         CUDA_TRY(cudaEventRecordWithFlags(b.ev[2 * r + 1], cs, cudaEventRecordExternal));
       if (near_on)
-        launch_nearfield(VAR_OBJ, tied, b.probs.as<ProbDesc>(), b.near[cur].as<int32_t>(),
+        launch_nearfield(var, tied, b.probs.as<ProbDesc>(), b.near[cur].as<int32_t>(),
                          &ctrl->near_cnt[cur], b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(),
                          &ctrl->plan, b.item_off.as<int32_t>(), b.out.as<double>(),
                          2 * c->sm_count, cs);
-      launch_nm_step(sa[cur], nm_grid, cs);
+      (qn ? launch_bfgs_step : launch_nm_step)(sa[cur], nm_grid, cs);
     }
     CUDA_TRY(cudaGetLastError());
     return DBIE_OK;
@@ -920,7 +971,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     unsigned char* kp = key.data();
     std::memcpy(kp, sa, sizeof sa);
     std::memcpy(kp + sizeof sa, &k, sizeof k);
-    const int extra[3] = {grid, nm_grid, c->profiling ? 1 : 0};
+    const int extra[3] = {grid, nm_grid, (c->profiling ? 1 : 0) | (qn ? 2 : 0)};
     std::memcpy(kp + sizeof sa + sizeof k, extra, sizeof extra);
   }
   if (!b.exec || b.key != key) {
@@ -1097,7 +1148,8 @@ dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
   const bool prof = c->profiling;
   c->profiling = true;
   dbie_status status = DBIE_OK;
-  const int pairs[5][2] = {{VAR_OBJ, 0}, {VAR_OBJ, 1}, {VAR_V, 0}, {VAR_VL, 0}, {VAR_OBJL, 0}};
+  const int pairs[7][2] = {{VAR_OBJ, 0},  {VAR_OBJ, 1}, {VAR_V, 0},   {VAR_VL, 0},
+                           {VAR_OBJL, 0}, {VAR_OBJN, 0}, {VAR_OBJN, 1}};
   for (const auto& vt : pairs) {
     const int var = vt[0], tied = vt[1];
     const std::string key = tune_key(c->device, "g1", var, tied, c->npix);
@@ -1147,19 +1199,19 @@ dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
 
 dbie_status dbie_set_config(dbie_ctx* c, const int32_t* cfg_in) {
   if (!c || !cfg_in) return fail(DBIE_EINVAL, "ctx and cfg_in must not be NULL");
-  for (int i = 0; i < 9; ++i)
+  for (int i = 0; i < 2 * NVAR + 1; ++i)
     if (cfg_in[i] < 0 || cfg_in[i] >= NCFG) return fail(DBIE_EINVAL, "configuration index out of range");
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < NVAR; ++v)
     for (int t = 0; t < 2; ++t) c->cfg[v][t] = cfg_in[2 * v + t];
-  c->vjp_cfg = cfg_in[8];
+  c->vjp_cfg = cfg_in[2 * NVAR];
   return DBIE_OK;
 }
 
 dbie_status dbie_get_config(dbie_ctx* c, int32_t* cfg_out) {
   if (!c || !cfg_out) return fail(DBIE_EINVAL, "ctx and cfg_out must not be NULL");
-  for (int v = 0; v < 4; ++v)
+  for (int v = 0; v < NVAR; ++v)
     for (int t = 0; t < 2; ++t) cfg_out[2 * v + t] = c->cfg[v][t];
-  cfg_out[8] = c->vjp_cfg;
+  cfg_out[2 * NVAR] = c->vjp_cfg;
   return DBIE_OK;
 }
 

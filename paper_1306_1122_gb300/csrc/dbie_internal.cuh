@@ -30,12 +30,23 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 //   Sl = sum cos(lambda r) b / r, with phi = u / r^3, u = lambda r sin(lambda r) + cos(lambda r),
 //   psi = phi'(r) / r = (lambda^2 cos(lambda r) - 3 u / r^2) / r^3.
 // Then B_p = z S0, dB_p/dx = z Sx, dB_p/dy = z Sy, dB_p/dz = S0 + z^2 S1, dB_p/dlambda = z lambda Sl.
-enum Variant { VAR_V = 0, VAR_VL = 1, VAR_OBJ = 2, VAR_OBJL = 3 };
+// VAR_OBJN adds Tx = sum phi (x_i - x_k) b and Ty = sum phi (y_i - y_k) b, which with S_lambda
+// give the exact lambda-derivatives of the objective sums: dS0/dlambda = lambda Sl,
+// dS1/dlambda = -lambda S0, dSx/dlambda = -lambda Tx, dSy/dlambda = -lambda Ty.
+enum Variant { VAR_V = 0, VAR_VL = 1, VAR_OBJ = 2, VAR_OBJL = 3, VAR_OBJN = 4 };
+constexpr int NVAR = 5;
 __host__ __device__ constexpr int nsum_per_comp(int var) {
-  return var == VAR_V ? 1 : var == VAR_VL ? 2 : var == VAR_OBJ ? 4 : 5;
+  return var == VAR_V ? 1 : var == VAR_VL ? 2 : var == VAR_OBJ ? 4 : var == VAR_OBJL ? 5 : 7;
 }
-__host__ __device__ constexpr bool has_grad(int var) { return var == VAR_OBJ || var == VAR_OBJL; }
-__host__ __device__ constexpr bool has_dlam(int var) { return var == VAR_VL || var == VAR_OBJL; }
+__host__ __device__ constexpr bool has_grad(int var) {
+  return var == VAR_OBJ || var == VAR_OBJL || var == VAR_OBJN;
+}
+__host__ __device__ constexpr bool has_dlam(int var) {
+  return var == VAR_VL || var == VAR_OBJL || var == VAR_OBJN;
+}
+__host__ __device__ constexpr bool has_newton(int var) { return var == VAR_OBJN; }
+// indices of Tx, Ty within a component's block (VAR_OBJN)
+constexpr int IDX_TX = 5, IDX_TY = 6;
 // index of the Sl sum within a component's block
 __host__ __device__ constexpr int idx_sl(int var) { return var == VAR_VL ? 1 : 4; }
 
@@ -234,6 +245,7 @@ struct Terms32 {
   float rb[3];
   float t1[has_grad(VAR) ? 3 : 1];
   float cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
+  float t0[has_newton(VAR) ? 3 : 1];  // phi b = u rb (rounded), the factor of Tx and Ty
 };
 
 // Geometry of one pair: dx, dy, r, 1/r^2 (times 3) and 1/r^3 (SFU rsqrt).
@@ -268,6 +280,14 @@ __device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, cons
     const float th = __fmul_rn(q.l[p], g.r);
     const float s = sin_mufu(th), c = cos_mufu(th);
     t.u[p] = __fmaf_rn(th, s, c);
+    if constexpr (has_newton(VAR)) {
+      if constexpr (TIED) {
+#pragma unroll
+        for (int pp = 0; pp < 3; ++pp) t.t0[pp] = __fmul_rn(t.u[0], t.rb[pp]);
+      } else {
+        t.t0[p] = __fmul_rn(t.u[p], t.rb[p]);
+      }
+    }
     if constexpr (has_grad(VAR)) {
       const float w = __fmaf_rn(-t.u[p], g.ri2x3, __fmul_rn(q.l2[p], c));
       if constexpr (TIED) {
@@ -295,6 +315,7 @@ struct Terms64 {
   double t1[has_grad(VAR) ? 3 : 1];
   double tl[has_dlam(VAR) ? 3 : 1];
 };
+// (Tx and Ty of the FP64 form are t0 * dx and t0 * dy.)
 
 template <int VAR, bool TIED>
 __device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, double px, double py,

@@ -59,6 +59,12 @@ void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t
                           const double* out, const float4* qpos, const Lam4* qlam, double g_scale,
                           double w_g, double* B, double* gradB, double* dBdl,
                           const double* gB_for_glam, double* fgphi, cudaStream_t s);
+void launch_finalize_objective(int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                               const double* out, const float4* qpos, const Lam4* qlam,
+                               double g_scale, double w_g, double* fgphi, double* dphi, double* B,
+                               cudaStream_t s);
+void launch_bfgs_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);
+void launch_bfgs_step(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);
 void launch_plan_round(const PlanArgs& a, cudaStream_t s);
 void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s);

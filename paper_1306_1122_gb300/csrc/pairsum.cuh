@@ -128,6 +128,10 @@ __device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED
     }
     if constexpr (has_dlam(VAR))
       acc[p * NS + idx_sl(VAR)] = __fmaf_rn(t.cr[lp], b[p], acc[p * NS + idx_sl(VAR)]);
+    if constexpr (has_newton(VAR)) {
+      acc[p * NS + IDX_TX] = __fmaf_rn(t.t0[p], t.dx, acc[p * NS + IDX_TX]);
+      acc[p * NS + IDX_TY] = __fmaf_rn(t.t0[p], t.dy, acc[p * NS + IDX_TY]);
+    }
   }
 }
 
@@ -142,6 +146,10 @@ __device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIE
       acc[p * NS + 3] += t.t1[p] * t.dy;
     }
     if constexpr (has_dlam(VAR)) acc[p * NS + idx_sl(VAR)] += t.tl[p];
+    if constexpr (has_newton(VAR)) {
+      acc[p * NS + IDX_TX] += t.t0[p] * t.dx;
+      acc[p * NS + IDX_TY] += t.t0[p] * t.dy;
+    }
   }
 }
 

@@ -1,0 +1,8 @@
+// Pair-sum kernels, FP32 form: objective variant with the lambda-derivative sums (Sl, Tx, Ty).
+#include "pairsum_inst.cuh"
+
+namespace dbie {
+KernelRef g1_ref_f32_newton(bool tied, int cfg) {
+  return tied ? g1_ref_cfg<float, VAR_OBJN, true>(cfg) : g1_ref_cfg<float, VAR_OBJN, false>(cfg);
+}
+}  // namespace dbie

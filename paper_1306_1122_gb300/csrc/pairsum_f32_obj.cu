@@ -3,12 +3,14 @@
 
 namespace dbie {
 KernelRef g1_ref_f32_val(int var, bool tied, int cfg);
+KernelRef g1_ref_f32_newton(bool tied, int cfg);
 
 KernelRef g1_ref_f32(int var, bool tied, int cfg) {
   if (var == VAR_OBJ)
     return tied ? g1_ref_cfg<float, VAR_OBJ, true>(cfg) : g1_ref_cfg<float, VAR_OBJ, false>(cfg);
   if (var == VAR_OBJL)
     return tied ? g1_ref_cfg<float, VAR_OBJL, true>(cfg) : g1_ref_cfg<float, VAR_OBJL, false>(cfg);
+  if (var == VAR_OBJN) return g1_ref_f32_newton(tied, cfg);
   return g1_ref_f32_val(var, tied, cfg);
 }
 }  // namespace dbie

@@ -459,3 +459,288 @@ __global__ void plan_round_kernel(const PlanArgs a) {
 void launch_plan_round(const PlanArgs& a, cudaStream_t s) { plan_round_kernel<<<1, 256, 0, s>>>(a); }
 
 }  // namespace dbie
+
+// ======================================================= objective gradient, quasi-Newton ----
+namespace dbie {
+
+// Phi and dPhi/dlambda_q from the 21 sums of VAR_OBJN (per component: S0, S1, Sx, Sy, Sl, Tx, Ty).
+// lambda_q moves only component q: dB_q = z lambda Sl, d(dB_q/dx) = -z lambda Tx,
+// d(dB_q/dy) = -z lambda Ty, d(dB_q/dz) = lambda Sl - z^2 lambda S0; the rest is the chain rule
+// through J = curl B, div B and the norms (kinks of f and g contribute 0).
+__device__ void objective_grad(const double* S, double z, const double lam[3], double g_scale,
+                               double w_g, Eval& e, double dphi[3]) {
+  double G[9], dBdl[3], dGdl[9];
+  for (int p = 0; p < 3; ++p) {
+    const double* s = S + 7 * p;
+    e.B[p] = z * s[0];
+    G[3 * p + 0] = z * s[2];
+    G[3 * p + 1] = z * s[3];
+    G[3 * p + 2] = s[0] + z * z * s[1];
+    dBdl[p] = z * lam[p] * s[4];
+    dGdl[3 * p + 0] = -(z * lam[p] * s[5]);
+    dGdl[3 * p + 1] = -(z * lam[p] * s[6]);
+    dGdl[3 * p + 2] = lam[p] * s[4] - z * z * lam[p] * s[0];
+  }
+  objective(e.B, G, g_scale, w_g, e.f, e.g, e.phi);
+  const double* B = e.B;
+  const double J[3] = {G[3 * 2 + 1] - G[3 * 1 + 2], G[3 * 0 + 2] - G[3 * 2 + 0],
+                       G[3 * 1 + 0] - G[3 * 0 + 1]};
+  const double D = G[0] + G[4] + G[8];
+  const double C[3] = {J[1] * B[2] - J[2] * B[1], J[2] * B[0] - J[0] * B[2],
+                       J[0] * B[1] - J[1] * B[0]};
+  const double nJ = sqrt(J[0] * J[0] + J[1] * J[1] + J[2] * J[2]);
+  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  const double nC = sqrt(C[0] * C[0] + C[1] * C[1] + C[2] * C[2]);
+  for (int q = 0; q < 3; ++q) {
+    double dB[3] = {0, 0, 0}, dG[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    dB[q] = dBdl[q];
+    for (int j = 0; j < 3; ++j) dG[3 * q + j] = dGdl[3 * q + j];
+    const double dJ[3] = {dG[3 * 2 + 1] - dG[3 * 1 + 2], dG[3 * 0 + 2] - dG[3 * 2 + 0],
+                          dG[3 * 1 + 0] - dG[3 * 0 + 1]};
+    const double dD = dG[0] + dG[4] + dG[8];
+    const double dC[3] = {dJ[1] * B[2] - dJ[2] * B[1] + J[1] * dB[2] - J[2] * dB[1],
+                          dJ[2] * B[0] - dJ[0] * B[2] + J[2] * dB[0] - J[0] * dB[2],
+                          dJ[0] * B[1] - dJ[1] * B[0] + J[0] * dB[1] - J[1] * dB[0]};
+    double df = 0.0, dg = 0.0;
+    if (nJ * nB > 0.0) {
+      const double JdJ = J[0] * dJ[0] + J[1] * dJ[1] + J[2] * dJ[2];
+      const double BdB = B[0] * dB[0] + B[1] * dB[1] + B[2] * dB[2];
+      const double CdC = C[0] * dC[0] + C[1] * dC[1] + C[2] * dC[2];
+      df = (nC > 0.0 ? CdC / (nC * nJ * nB) : 0.0) - e.f * (JdJ / (nJ * nJ) + BdB / (nB * nB));
+    }
+    if (nB > 0.0) {
+      const double BdB = B[0] * dB[0] + B[1] * dB[1] + B[2] * dB[2];
+      const double sgn = D > 0.0 ? 1.0 : (D < 0.0 ? -1.0 : 0.0);
+      dg = g_scale * (sgn * dD / nB - fabs(D) * BdB / (nB * nB * nB));
+    }
+    dphi[q] = df + w_g * dg;
+  }
+}
+
+__global__ void finalize_objective_kernel(int64_t n, const PlanHdr* __restrict__ plan,
+                                          const int32_t* __restrict__ item_off,
+                                          const double* __restrict__ out,
+                                          const float4* __restrict__ qpos,
+                                          const Lam4* __restrict__ qlam, double g_scale,
+                                          double w_g, double* fgphi, double* dphi, double* B) {
+  const PlanHdr h = *plan;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double S[21];
+    for (int s = 0; s < 21; ++s) S[s] = gather_sum(out, h, item_off, 0, i, 21, s);
+    const Lam4 l = qlam[i];
+    const double lam[3] = {l.x, l.y, l.z};
+    Eval e;
+    double dp[3];
+    objective_grad(S, (double)qpos[i].z, lam, g_scale, w_g, e, dp);
+    if (fgphi) {
+      fgphi[3 * i] = e.f;
+      fgphi[3 * i + 1] = e.g;
+      fgphi[3 * i + 2] = e.phi;
+    }
+    if (dphi)
+      for (int q = 0; q < 3; ++q) dphi[3 * i + q] = dp[q];
+    if (B)
+      for (int p = 0; p < 3; ++p) B[3 * i + p] = e.B[p];
+  }
+}
+
+void launch_finalize_objective(int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                               const double* out, const float4* qpos, const Lam4* qlam,
+                               double g_scale, double w_g, double* fgphi, double* dphi, double* B,
+                               cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  finalize_objective_kernel<<<grid, 256, 0, s>>>(n, plan, item_off, out, qpos, qlam, g_scale,
+                                                 w_g, fgphi, dphi, B);
+}
+
+// ----------------------------------------------------------------------- quasi-Newton ----
+// Same algorithm, same order of operations as the oracle's orc_bfgs (this file is compiled
+// without FMA contraction): one line-search trial per point per round.
+
+__global__ void bfgs_init_kernel(const SolveArgs a, const double* __restrict__ lam_init) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const int n = a.o.dim;
+    // Phi is even in every lambda_p, so lambda = 0 is a stationary point: start one step away
+    // from the initial lambda along (1, 1, 1).
+    double x[1][3];
+    for (int d = 0; d < 3; ++d) {
+      x[0][d] = d < n ? (lam_init ? lam_init[3 * g + d] : 0.0) + a.probs[pidx].step : 0.0;
+      SD(a, B_X + d, g) = x[0][d];
+    }
+    SI(a, I_STAGE, g) = ST_BF_INIT;
+    SI(a, I_ITERS, g) = 0;
+    SI(a, I_NFEV, g) = 0;
+    SI(a, I_STATUS, g) = PT_RUNNING;
+    emit(a, g, pos, pidx, 1, x);
+  }
+}
+
+void launch_bfgs_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s) {
+  bfgs_init_kernel<<<grid, 256, 0, s>>>(a, lam_init);
+}
+
+__global__ void bfgs_step_kernel(const SolveArgs a) {
+  const int nact = *a.cur.act_cnt;
+  const int n = a.o.dim;
+  const PlanHdr h = *a.plan;
+  for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
+    const int64_t g = a.cur.act[ia];
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const ProbDesc& pd = a.probs[pidx];
+    const double z = (double)pos.z;
+    const int stage = SI(a, I_STAGE, g);
+    int iters = SI(a, I_ITERS, g);
+    int nfev = SI(a, I_NFEV, g) + 1;
+    double x[3], gr[3], H[9], dv[3], B[3];
+    for (int i = 0; i < 3; ++i) {
+      x[i] = SD(a, B_X + i, g);
+      gr[i] = SD(a, B_GR + i, g);
+      dv[i] = SD(a, B_D + i, g);
+      B[i] = SD(a, B_B + i, g);
+    }
+    for (int i = 0; i < 9; ++i) H[i] = SD(a, B_H + i, g);
+    double F = SD(a, B_PHI, g), fv = SD(a, B_F, g), gv = SD(a, B_G, g);
+    double alpha = SD(a, B_ALPHA, g), gd = SD(a, B_GD, g), gn = SD(a, B_GN, g);
+
+    // the pending trial's objective and gradient
+    double xt[3] = {0, 0, 0};
+    if (stage == ST_BF_INIT) {
+      for (int i = 0; i < n; ++i) xt[i] = x[i];
+    } else {
+      for (int i = 0; i < n; ++i) xt[i] = x[i] + alpha * dv[i];
+    }
+    const double lamt[3] = {xt[0], n == 1 ? xt[0] : xt[1], n == 1 ? xt[0] : xt[2]};
+    double S[21];
+    const int64_t j = (int64_t)SI(a, I_QSLOT, g) - pd.q_off;
+    for (int s = 0; s < 21; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 21, s);
+    Eval e;
+    double dp[3], gt[3] = {0, 0, 0};
+    objective_grad(S, z, lamt, pd.g_scale, a.o.w_g, e, dp);
+    if (n == 1) gt[0] = dp[0] + dp[1] + dp[2];
+    else { gt[0] = dp[0]; gt[1] = dp[1]; gt[2] = dp[2]; }
+    const bool flagt = e.f <= a.o.eps_f && e.g <= a.o.eps_g;
+
+    int fin = -1;  // final status, or -1 to continue
+    bool flag = false;
+    bool need_dir = false;
+    if (stage == ST_BF_INIT) {
+      for (int i = 0; i < 3; ++i) { gr[i] = gt[i]; B[i] = e.B[i]; }
+      F = e.phi; fv = e.f; gv = e.g; flag = flagt;
+      gn = 0.0;
+      for (int i = 0; i < n; ++i) gn += gr[i] * gr[i];
+      gn = sqrt(gn);
+      for (int i = 0; i < 9; ++i) H[i] = 0.0;
+      if (gn > 0.0)
+        for (int i = 0; i < n; ++i) H[3 * i + i] = pd.step / gn;
+      need_dir = true;
+    } else if (e.phi <= F + 1e-4 * alpha * gd) {  // Armijo: accept the trial
+      iters += 1;
+      double sv[3] = {0, 0, 0}, yv[3] = {0, 0, 0}, sy = 0.0, ss = 0.0, yy = 0.0;
+      for (int i = 0; i < n; ++i) {
+        sv[i] = xt[i] - x[i];
+        yv[i] = gt[i] - gr[i];
+        sy += sv[i] * yv[i];
+        ss += sv[i] * sv[i];
+        yy += yv[i] * yv[i];
+      }
+      if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
+        const double rho = 1.0 / sy;
+        double Hy[3] = {0, 0, 0}, yHy = 0.0;
+        for (int i = 0; i < n; ++i) {
+          double t = 0.0;
+          for (int k = 0; k < n; ++k) t += H[3 * i + k] * yv[k];
+          Hy[i] = t;
+        }
+        for (int i = 0; i < n; ++i) yHy += yv[i] * Hy[i];
+        const double c2 = rho * rho * yHy + rho;
+        for (int i = 0; i < n; ++i)
+          for (int k = 0; k < n; ++k)
+            H[3 * i + k] = H[3 * i + k] - rho * (sv[i] * Hy[k] + Hy[i] * sv[k]) + c2 * sv[i] * sv[k];
+      }
+      const double dec = F - e.phi;
+      for (int i = 0; i < n; ++i) { x[i] = xt[i]; gr[i] = gt[i]; }
+      for (int i = 0; i < 3; ++i) B[i] = e.B[i];
+      F = e.phi; fv = e.f; gv = e.g; flag = flagt;
+      gn = 0.0;
+      for (int i = 0; i < n; ++i) gn += gr[i] * gr[i];
+      gn = sqrt(gn);
+      if (dec <= a.o.tol) fin = PT_CONVERGED;
+      else need_dir = true;
+    } else {  // reject: halve the step (at most 31 trials per line search)
+      alpha = 0.5 * alpha;
+      if (alpha < 9.313225746154785e-10) fin = PT_CONVERGED;  // 2^-30
+      else {
+        double row[1][3] = {{0, 0, 0}};
+        for (int i = 0; i < n; ++i) row[0][i] = x[i] + alpha * dv[i];
+        SD(a, B_ALPHA, g) = alpha;
+        SI(a, I_NFEV, g) = nfev;
+        emit(a, g, pos, pidx, 1, row);
+        continue;
+      }
+    }
+    if (need_dir) {
+      if (flag) fin = PT_CONVERGED;
+      else if (!(gn > 0.0)) fin = PT_CONVERGED;
+      else if (iters >= a.o.max_iter) fin = PT_MAXITER;
+      else {
+        for (int i = 0; i < n; ++i) {
+          double s = 0.0;
+          for (int k = 0; k < n; ++k) s += H[3 * i + k] * gr[k];
+          dv[i] = -s;
+        }
+        gd = 0.0;
+        for (int i = 0; i < n; ++i) gd += gr[i] * dv[i];
+        if (!(gd < 0.0)) {
+          for (int i = 0; i < 9; ++i) H[i] = 0.0;
+          for (int i = 0; i < n; ++i) H[3 * i + i] = pd.step / gn;
+          gd = 0.0;
+          for (int i = 0; i < n; ++i) { dv[i] = -(H[3 * i + i] * gr[i]); gd += gr[i] * dv[i]; }
+        }
+        alpha = 1.0;
+        double row[1][3] = {{0, 0, 0}};
+        for (int i = 0; i < n; ++i) row[0][i] = x[i] + alpha * dv[i];
+        emit(a, g, pos, pidx, 1, row);
+      }
+    }
+    if (fin >= 0) {
+      for (int p = 0; p < 3; ++p) {
+        a.res_B[3 * g + p] = B[p];
+        a.res_lam[3 * g + p] = fabs(n == 1 ? x[0] : x[p]);
+      }
+      a.res_f[g] = fv;
+      a.res_g[g] = gv;
+      a.res_iters[g] = iters;
+      a.res_status[g] = fin;
+      a.res_nfev[g] = nfev;
+      SI(a, I_STATUS, g) = fin;
+    }
+    for (int i = 0; i < 3; ++i) {
+      SD(a, B_X + i, g) = x[i];
+      SD(a, B_GR + i, g) = gr[i];
+      SD(a, B_D + i, g) = dv[i];
+      SD(a, B_B + i, g) = B[i];
+    }
+    for (int i = 0; i < 9; ++i) SD(a, B_H + i, g) = H[i];
+    SD(a, B_PHI, g) = F;
+    SD(a, B_F, g) = fv;
+    SD(a, B_G, g) = gv;
+    SD(a, B_ALPHA, g) = alpha;
+    SD(a, B_GD, g) = gd;
+    SD(a, B_GN, g) = gn;
+    SI(a, I_STAGE, g) = fin >= 0 ? ST_DONE : ST_BF_LS;
+    SI(a, I_ITERS, g) = iters;
+    SI(a, I_NFEV, g) = nfev;
+  }
+}
+
+void launch_bfgs_step(const SolveArgs& a, int grid, cudaStream_t s) {
+  bfgs_step_kernel<<<grid, 128, 0, s>>>(a);
+}
+
+}  // namespace dbie

@@ -19,10 +19,16 @@ enum DField {
   D_TL = 45,     // pending single trial point lambda (3)
   D_NFIELDS = 48
 };
+// Quasi-Newton state (same arrays, other meaning): x, grad Phi, inverse Hessian H (3 x 3),
+// direction d, B, f, g, Phi at x, line-search step alpha, grad . d, |grad|.
+enum BField {
+  B_X = 0, B_GR = 3, B_H = 6, B_D = 15, B_B = 18, B_F = 21, B_G = 22, B_PHI = 23, B_ALPHA = 24,
+  B_GD = 25, B_GN = 26
+};
 enum IField { I_STAGE = 0, I_ITERS = 1, I_NFEV = 2, I_STATUS = 3, I_QSLOT = 4, I_NFIELDS = 5 };
 enum PtStatus { PT_RUNNING = -1, PT_CONVERGED = 0, PT_MAXITER = 1 };
 enum Stage { ST_INIT = 0, ST_REFLECT = 1, ST_EXPAND = 2, ST_OCONTRACT = 3, ST_ICONTRACT = 4,
-             ST_SHRINK = 5, ST_DONE = 6 };
+             ST_SHRINK = 5, ST_DONE = 6, ST_BF_INIT = 10, ST_BF_LS = 11 };
 
 struct SolveOpts {
   double eps_f, eps_g, tol, w_g;

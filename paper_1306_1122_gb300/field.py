@@ -32,6 +32,7 @@ class Options:
     w_g: float = 1.0
     g_scale: float = 0.0
     precision: int = N.DBIE_PREC_MIXED
+    method: int = N.DBIE_METHOD_SIMPLEX
     near_z: float = -1.0
 
     def c(self) -> N.dbie_options:
@@ -116,6 +117,17 @@ class DBIEField:
         if objective:
             out["f"], out["g"], out["phi"] = F[:, 0], F[:, 1], F[:, 2]
         return out
+
+    def objective(self, xyz, lam, options: Options | None = None):
+        """f, g, Phi and dPhi/dlambda (n, 3) at fixed lambda."""
+        xyz = _dev_f32(xyz, self.device).reshape(-1, 3)
+        lam = _dev_f32(lam, self.device).reshape(-1, 3)
+        n = xyz.shape[0]
+        F = torch.empty((n, 3), device=self.device, dtype=torch.float64)
+        D = torch.empty((n, 3), device=self.device, dtype=torch.float64)
+        N.dbie_objective(self._h, n, _ptr(xyz), _ptr(lam), None if options is None else options.c(),
+                         N.DBIE_MEM_DEVICE, _ptr(F), _ptr(D), _stream())
+        return dict(f=F[:, 0], g=F[:, 1], phi=F[:, 2], dphi=D)
 
     def _solve_out(self, n, codes):
         kw = dict(device=self.device)

@@ -361,5 +361,7 @@ def test_bfgs_solve_improves_on_start(oracle_lib):
     bd = oracle.Boundary(oracle.Grid(m.nx, m.ny), m.Bx, m.By, m.Bz)
     pts = w.points[[3, 400, 1200]].astype(np.float64)
     r = oracle.solve(bd, pts, oracle.Options(method=1, max_iter=20))
-    _, _, phi0, _ = oracle.objective_grad(bd, pts, np.zeros((3, 3)), 1.0 / 6.0)
-    assert np.all(r["phi"] <= phi0 + 1e-15)
+    s = 1.0 / 32.0   # the search starts at lambda = s (1, 1, 1), off the stationary point 0
+    _, _, phi0, grad0 = oracle.objective_grad(bd, pts, np.full((3, 3), s), 1.0 / 6.0)
+    assert np.all(np.abs(grad0) > 0)
+    assert np.all(r["phi"] <= phi0 + 1e-15) and np.all(r["nfev"] > 3)
