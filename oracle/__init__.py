@@ -95,6 +95,14 @@ def _load():
                                                ctypes.c_double, P, P, ctypes.c_int32]
             lib.orc_field_dl.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
                                          P, P, P, P]
+            lib.orc_hessian_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, P, P, P, P,
+                                             ctypes.c_int32]
+            lib.orc_implicit_vjp.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int32,
+                                             ctypes.c_double, ctypes.c_double, P, P, P,
+                                             ctypes.c_int32]
+            lib.orc_noise_var.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_double, P,
+                                          ctypes.c_int32]
             _lib = lib
     return _lib
 
@@ -281,6 +289,55 @@ def vjp(bd: Boundary, xyz, lam, gB, nthreads=None):
     out = np.zeros((g.ny * g.nx, 3))
     lib.orc_vjp(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), _ptr(out), _threads(nthreads))
     return out.reshape(g.ny, g.nx, 3)
+
+
+def hessian(bd: Boundary, xyz, lam, g_scale: float, w_g: float = 1.0, lambda_mode: int = 0,
+            nthreads=None):
+    """Phi (n,), dPhi/dlambda (n,3), the lambda-Hessian (n,3,3) and dB_p/dlambda_p (n,3), all by
+    hyper-dual arithmetic through the quadrature.  Tied mode: entry 0 (and H[:,0,0]) only."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    n = xyz.shape[0]
+    phi = np.zeros(n); grad = np.zeros((n, 3)); H = np.zeros((n, 9)); dl = np.zeros((n, 3))
+    lib.orc_hessian_many(bd.ref, n, _ptr(xyz), _ptr(lam), lambda_mode, g_scale, w_g, _ptr(phi),
+                         _ptr(grad), _ptr(H), _ptr(dl), _threads(nthreads))
+    return phi, grad, H.reshape(n, 3, 3), dl
+
+
+def implicit_vjp(bd: Boundary, xyz, lam, gB, g_scale: float, w_g: float = 1.0,
+                 lambda_mode: int = 0, nthreads=None):
+    """dL/dB0 (ny, nx, 3) through the lambda search (lambda* a stationary point of Phi), the
+    adjoint vectors v = H^-1 dL/dlambda (n, 3) and flags (n,) = 1 where H is not positive
+    definite."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    gB = _f64(gB).reshape(-1, 3)
+    n = xyz.shape[0]
+    g = bd.grid
+    out = np.zeros((g.ny * g.nx, 3)); v = np.zeros((n, 3)); flags = np.zeros(n, np.int32)
+    lib.orc_implicit_vjp(bd.ref, n, _ptr(xyz), _ptr(lam), _ptr(gB), lambda_mode, g_scale, w_g,
+                         _ptr(out), _ptr(v), _ptr(flags), _threads(nthreads))
+    return out.reshape(g.ny, g.nx, 3), v, flags
+
+
+def noise_var(bd: Boundary, xyz, lam, sigma=None, sigma0: float = 1.0, nthreads=None):
+    """Var B_p (n, 3) at fixed lambda for independent pixel noise: sigma = None (sigma0 on every
+    pixel) or three (ny, nx) arrays of standard deviations (entries may be None)."""
+    lib = _load()
+    xyz = _f64(xyz).reshape(-1, 3)
+    lam = _f64(lam).reshape(-1, 3)
+    n = xyz.shape[0]
+    g = bd.grid
+    sig = [None, None, None] if sigma is None else list(sigma)
+    keep = [None if a is None else np.ascontiguousarray(np.asarray(a, np.float32).reshape(g.ny, g.nx))
+            for a in sig]
+    var = np.zeros((n, 3))
+    lib.orc_noise_var(bd.ref, n, _ptr(xyz), _ptr(lam),
+                      *[None if a is None else _ptr(a) for a in keep], sigma0, _ptr(var),
+                      _threads(nthreads))
+    return var
 
 
 def nelder_mead(fun, sim0, tol: float, max_iter: int, codes_cap: int = 256):

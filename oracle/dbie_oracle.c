@@ -527,3 +527,277 @@ void orc_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double*
     }
   }
 }
+
+/* ------------------------------------------------------ second order: hyper-dual numbers ---- */
+/* x = v + a e1 + b e2 + c e1 e2 with e1^2 = e2^2 = 0 (hyper-dual numbers, Fike & Alonso 2011).
+ * A function evaluated at x0 + s1 e1 + s2 e2 returns its value, its derivatives along s1 (a) and
+ * s2 (b) and the second derivative s1^T Hess s2 (c), exactly and without a difference step. */
+typedef struct { double v, a, b, c; } hd;
+
+static hd hd_k(double v) { hd r = {v, 0.0, 0.0, 0.0}; return r; }
+static hd hd_add(hd x, hd y) { hd r = {x.v + y.v, x.a + y.a, x.b + y.b, x.c + y.c}; return r; }
+static hd hd_sub(hd x, hd y) { hd r = {x.v - y.v, x.a - y.a, x.b - y.b, x.c - y.c}; return r; }
+static hd hd_scl(hd x, double s) { hd r = {x.v * s, x.a * s, x.b * s, x.c * s}; return r; }
+static hd hd_mul(hd x, hd y) {
+  hd r = {x.v * y.v, x.v * y.a + x.a * y.v, x.v * y.b + x.b * y.v,
+          x.v * y.c + x.a * y.b + x.b * y.a + x.c * y.v};
+  return r;
+}
+/* phi(x) for a scalar function with phi = g0, phi' = g1, phi'' = g2 at x.v. */
+static hd hd_chain(hd x, double g0, double g1, double g2) {
+  hd r = {g0, g1 * x.a, g1 * x.b, g1 * x.c + g2 * x.a * x.b};
+  return r;
+}
+static hd hd_sin(hd x) { return hd_chain(x, sin(x.v), cos(x.v), -sin(x.v)); }
+static hd hd_cos(hd x) { return hd_chain(x, cos(x.v), -sin(x.v), -cos(x.v)); }
+static hd hd_inv(hd x) {
+  const double i = 1.0 / x.v;
+  return hd_chain(x, i, -i * i, 2.0 * i * i * i);
+}
+static hd hd_div(hd x, hd y) { return hd_mul(x, hd_inv(y)); }
+static hd hd_abs(hd x) { return x.v < 0.0 ? hd_scl(x, -1.0) : x; }
+/* |x| of a 3-vector; at |x| = 0 (a kink) the derivative parts are taken as 0. */
+static hd hd_norm3(const hd x[3]) {
+  const hd q = hd_add(hd_add(hd_mul(x[0], x[0]), hd_mul(x[1], x[1])), hd_mul(x[2], x[2]));
+  if (!(q.v > 0.0)) return hd_k(0.0);
+  const double s = sqrt(q.v);
+  return hd_chain(q, s, 0.5 / s, -0.25 / (s * q.v));
+}
+
+typedef struct { nsum v, a, b, c; } hsum;
+static void hsum_add(hsum* s, hd x) {
+  nsum_add(&s->v, x.v);
+  nsum_add(&s->a, x.a);
+  nsum_add(&s->b, x.b);
+  nsum_add(&s->c, x.c);
+}
+static hd hsum_get(const hsum* s) {
+  hd r = {nsum_get(&s->v), nsum_get(&s->a), nsum_get(&s->b), nsum_get(&s->c)};
+  return r;
+}
+
+/* The weight a_ik of Eq. 16 and its spatial derivatives at fixed lambda (the terms of orc_field)
+ * for one pixel, with lambda a hyper-dual number: w4 = {a, da/dx_i, da/dy_i, da/dz_i}.
+ * dx = x_i - x_k, dy = y_i - y_k, w = dA / 2 pi. */
+static void weights_hd(double dx, double dy, double zi, hd l, double w, hd w4[4]) {
+  const double r = sqrt(dx * dx + dy * dy + zi * zi);
+  const double r3 = r * r * r;
+  const hd lr = hd_scl(l, r);
+  const hd s = hd_sin(lr), c = hd_cos(lr);
+  const hd u = hd_add(hd_mul(lr, s), c);
+  const hd dudr = hd_scl(hd_mul(hd_mul(l, l), c), r);
+  const hd psi = hd_scl(hd_sub(hd_scl(dudr, 1.0 / r3), hd_scl(u, 3.0 / (r3 * r))), 1.0 / r);
+  w4[0] = hd_scl(u, zi / r3 * w);
+  w4[1] = hd_scl(psi, zi * dx * w);
+  w4[2] = hd_scl(psi, zi * dy * w);
+  w4[3] = hd_scl(hd_add(hd_scl(u, 1.0 / r3), hd_scl(psi, zi * zi)), w);
+}
+
+/* B_p and row p of the gradient matrix (Eq. 16 and Eq. 13 at fixed lambda), each component at
+ * its own hyper-dual lambda_p. */
+static void field_hd(const orc_boundary* bd, double xi, double yi, double zi, const hd lam[3],
+                     hd B[3], hd G[9]) {
+  const double w = bd->dA / TWO_PI;
+  for (int p = 0; p < 3; ++p) {
+    const float* B0 = comp_ptr(bd, p);
+    hsum s[4];
+    memset(s, 0, sizeof s);
+    for (int j = 0; j < bd->ny; ++j) {
+      const double yk = bd->y0 + j * bd->hy;
+      for (int i = 0; i < bd->nx; ++i) {
+        const double xk = bd->x0 + i * bd->hx;
+        const double b0 = (double)B0[(int64_t)j * bd->nx + i];
+        hd w4[4];
+        weights_hd(xi - xk, yi - yk, zi, lam[p], w, w4);
+        for (int q = 0; q < 4; ++q) hsum_add(&s[q], hd_scl(w4[q], b0));
+      }
+    }
+    B[p] = hsum_get(&s[0]);
+    for (int j = 0; j < 3; ++j) G[3 * p + j] = hsum_get(&s[1 + j]);
+  }
+}
+
+/* Eq. 14, Eq. 8 and Eq. 9 in hyper-dual arithmetic, Phi = f + w_g g, with the degenerate cases of
+ * orc_objective (f = 0 when |J||B| = 0, g = 0 when |B| = 0). */
+static hd objective_hd(const hd B[3], const hd G[9], double g_scale, double w_g) {
+  const hd J[3] = {hd_sub(G[3 * 2 + 1], G[3 * 1 + 2]), hd_sub(G[3 * 0 + 2], G[3 * 2 + 0]),
+                   hd_sub(G[3 * 1 + 0], G[3 * 0 + 1])};
+  const hd D = hd_add(hd_add(G[0], G[4]), G[8]);
+  const hd C[3] = {hd_sub(hd_mul(J[1], B[2]), hd_mul(J[2], B[1])),
+                   hd_sub(hd_mul(J[2], B[0]), hd_mul(J[0], B[2])),
+                   hd_sub(hd_mul(J[0], B[1]), hd_mul(J[1], B[0]))};
+  const hd nJ = hd_norm3(J), nB = hd_norm3(B), nC = hd_norm3(C);
+  const hd f = (nJ.v * nB.v > 0.0) ? hd_div(nC, hd_mul(nJ, nB)) : hd_k(0.0);
+  const hd g = (nB.v > 0.0) ? hd_scl(hd_div(hd_abs(D), nB), g_scale) : hd_k(0.0);
+  return hd_add(f, hd_scl(g, w_g));
+}
+
+void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                 int32_t lambda_mode, double g_scale, double w_g, double* phi, double grad[3],
+                 double H[9], double dBdl[3]) {
+  hd lh[3], B[3], G[9];
+  for (int q = 0; q < 9; ++q) H[q] = 0.0;
+  for (int q = 0; q < 3; ++q) grad[q] = dBdl[q] = 0.0;
+  if (lambda_mode == 1) {
+    for (int p = 0; p < 3; ++p) { lh[p].v = lam[p]; lh[p].a = 1.0; lh[p].b = 1.0; lh[p].c = 0.0; }
+    field_hd(bd, xi, yi, zi, lh, B, G);
+    const hd ph = objective_hd(B, G, g_scale, w_g);
+    *phi = ph.v;
+    grad[0] = ph.a;
+    H[0] = ph.c;
+    for (int p = 0; p < 3; ++p) dBdl[p] = B[p].a;
+    return;
+  }
+  for (int j = 0; j < 3; ++j)
+    for (int k = j; k < 3; ++k) {
+      for (int p = 0; p < 3; ++p) {
+        lh[p].v = lam[p];
+        lh[p].a = p == j ? 1.0 : 0.0;
+        lh[p].b = p == k ? 1.0 : 0.0;
+        lh[p].c = 0.0;
+      }
+      field_hd(bd, xi, yi, zi, lh, B, G);
+      const hd ph = objective_hd(B, G, g_scale, w_g);
+      H[3 * j + k] = H[3 * k + j] = ph.c;
+      if (j == k) {
+        grad[j] = ph.a;
+        dBdl[j] = B[j].a;
+        *phi = ph.v;
+      }
+    }
+}
+
+void orc_hessian_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      int32_t lambda_mode, double g_scale, double w_g, double* phi, double* grad,
+                      double* H, double* dBdl, int32_t nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i)
+    orc_hessian(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, lambda_mode, g_scale,
+                w_g, phi + i, grad + 3 * i, H + 9 * i, dBdl + 3 * i);
+}
+
+/* Solve H v = r for a symmetric m x m matrix (m <= 3) by Cholesky; returns 0 when H is not
+ * positive definite (a pivot <= 0). */
+static int chol_solve(int m, const double* H, const double* r, double* v) {
+  double L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, y[3] = {0, 0, 0};
+  for (int j = 0; j < m; ++j) {
+    double d = H[3 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[3 * j + k] * L[3 * j + k];
+    if (!(d > 0.0)) return 0;
+    L[3 * j + j] = sqrt(d);
+    for (int i = j + 1; i < m; ++i) {
+      double e = H[3 * i + j];
+      for (int k = 0; k < j; ++k) e -= L[3 * i + k] * L[3 * j + k];
+      L[3 * i + j] = e / L[3 * j + j];
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double e = r[i];
+    for (int k = 0; k < i; ++k) e -= L[3 * i + k] * y[k];
+    y[i] = e / L[3 * i + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double e = y[i];
+    for (int k = i + 1; k < m; ++k) e -= L[3 * k + i] * v[k];
+    v[i] = e / L[3 * i + i];
+  }
+  return 1;
+}
+
+void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      const double* gB, int32_t lambda_mode, double g_scale, double w_g,
+                      double* gB0, double* v_out, int32_t* flags, int32_t nthreads) {
+  const int m = lambda_mode == 1 ? 1 : 3;
+  const double w = bd->dA / TWO_PI;
+  double* vp = (double*)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
+  hd* q = (hd*)calloc((size_t)(n > 0 ? n : 1) * 12, sizeof(hd));
+  int32_t* fl = (int32_t*)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+  /* per point: H, dL/dlambda, v = H^-1 dL/dlambda, and B, grad B moving along v (e1) */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    const double xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
+    double phi, grad[3], H[9], dBdl[3], gl[3] = {0, 0, 0}, v[3] = {0, 0, 0};
+    orc_hessian(bd, xi, yi, zi, lam + 3 * i, lambda_mode, g_scale, w_g, &phi, grad, H, dBdl);
+    if (lambda_mode == 1) gl[0] = gB[3 * i] * dBdl[0] + gB[3 * i + 1] * dBdl[1] + gB[3 * i + 2] * dBdl[2];
+    else for (int p = 0; p < 3; ++p) gl[p] = gB[3 * i + p] * dBdl[p];
+    if (!chol_solve(m, H, gl, v)) { fl[i] = 1; v[0] = v[1] = v[2] = 0.0; }
+    for (int p = 0; p < 3; ++p) vp[3 * i + p] = lambda_mode == 1 ? v[0] : v[p];
+    hd lh[3], B[3], G[9];
+    for (int p = 0; p < 3; ++p) { lh[p] = hd_k(lam[3 * i + p]); lh[p].a = vp[3 * i + p]; }
+    field_hd(bd, xi, yi, zi, lh, B, G);
+    for (int p = 0; p < 3; ++p) q[12 * i + p] = B[p];
+    for (int e = 0; e < 9; ++e) q[12 * i + 3 + e] = G[e];
+    if (v_out) for (int p = 0; p < 3; ++p) v_out[3 * i + p] = vp[3 * i + p];
+    if (flags) flags[i] = fl[i];
+  }
+  /* per pixel and component: the fixed-lambda adjoint minus d/dB0_pk of v . grad_lambda Phi,
+   * the latter as the e1 e2 part of Phi with e2 seeded on the pixel's weights */
+  const int64_t nb = (int64_t)bd->nx * bd->ny;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t k = 0; k < nb; ++k) {
+    const int i_ = (int)(k % bd->nx), j_ = (int)(k / bd->nx);
+    const double xk = bd->x0 + i_ * bd->hx, yk = bd->y0 + j_ * bd->hy;
+    for (int p = 0; p < 3; ++p) {
+      nsum s = {0, 0};
+      for (int64_t i = 0; i < n; ++i) {
+        hd l = hd_k(lam[3 * i + p]);
+        l.a = vp[3 * i + p];
+        hd w4[4];
+        weights_hd(xyz[3 * i] - xk, xyz[3 * i + 1] - yk, xyz[3 * i + 2], l, w, w4);
+        double t = gB[3 * i + p] * w4[0].v;
+        if (!fl[i]) {
+          hd B[3], G[9];
+          for (int e = 0; e < 3; ++e) B[e] = q[12 * i + e];
+          for (int e = 0; e < 9; ++e) G[e] = q[12 * i + 3 + e];
+          B[p].b = w4[0].v;
+          B[p].c = w4[0].a;
+          for (int j = 0; j < 3; ++j) {
+            G[3 * p + j].b = w4[1 + j].v;
+            G[3 * p + j].c = w4[1 + j].a;
+          }
+          t -= objective_hd(B, G, g_scale, w_g).c;
+        }
+        nsum_add(&s, t);
+      }
+      gB0[3 * k + p] = nsum_get(&s);
+    }
+  }
+  free(vp);
+  free(q);
+  free(fl);
+}
+
+void orc_noise_var(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                   const float* sx, const float* sy, const float* sz, double sigma0, double* var,
+                   int32_t nthreads) {
+  const float* sg[3] = {sx, sy, sz};
+  const double w = bd->dA / TWO_PI;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i) {
+    const double xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
+    for (int p = 0; p < 3; ++p) {
+      nsum s = {0, 0};
+      for (int j = 0; j < bd->ny; ++j) {
+        const double yk = bd->y0 + j * bd->hy;
+        for (int ii = 0; ii < bd->nx; ++ii) {
+          const double xk = bd->x0 + ii * bd->hx;
+          const double dx = xi - xk, dy = yi - yk;
+          const double r = sqrt(dx * dx + dy * dy + zi * zi);
+          const double lr = lam[3 * i + p] * r;
+          const double a = zi * (lr * sin(lr) + cos(lr)) / (r * r * r) * w;
+          const double sd = sg[p] ? (double)sg[p][(int64_t)j * bd->nx + ii] : sigma0;
+          nsum_add(&s, a * a * sd * sd);
+        }
+      }
+      var[3 * i + p] = nsum_get(&s);
+    }
+  }
+}

@@ -94,6 +94,36 @@ typedef double (*orc_fun_grad)(void* ctx, const double* x, double* grad, int32_t
 void orc_bfgs(int32_t n, const double x0[3], double step, double tol, int32_t max_iter,
               orc_fun_grad fun, void* ctx, orc_nm_result* res);
 
+/* Second order, by hyper-dual numbers through the whole quadrature (no difference step; not in
+ * the paper).  At one point and lambda: Phi, its gradient grad[q] = dPhi/dlambda_q, the Hessian
+ * H[3q+r] = d^2 Phi / dlambda_q dlambda_r and dBdl[p] = dB_p/dlambda_p.  lambda_mode = 1 (one
+ * shared lambda): grad[0], H[0] and dBdl[p] = dB_p/dlambda are the derivatives along the shared
+ * lambda, the other entries 0. */
+void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                 int32_t lambda_mode, double g_scale, double w_g, double* phi, double grad[3],
+                 double H[9], double dBdl[3]);
+void orc_hessian_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      int32_t lambda_mode, double g_scale, double w_g, double* phi, double* grad,
+                      double* H, double* dBdl, int32_t nthreads);
+
+/* Gradient of L(B) with respect to the magnetogram THROUGH the lambda search: lambda* is taken as
+ * a stationary point of Phi (grad_lambda Phi = 0), so d(lambda*) / dB0 = -H^-1 d(grad_lambda Phi) / dB0
+ * and, for gB = dL/dB (n, 3),
+ *   gB0[k][p] = sum_i gB_pi a_ik(lambda_pi) - d/dB0_pk sum_i v_i . grad_lambda Phi_i,
+ *   v_i = H_i^-1 dL/dlambda_i,  dL/dlambda_p = gB_p dB_p/dlambda_p (summed over p when tied).
+ * v_out (n, 3, nullable) gets v per component; flags (n, nullable) is 1 where H is not positive
+ * definite (that point keeps only the fixed-lambda term). */
+void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      const double* gB, int32_t lambda_mode, double g_scale, double w_g,
+                      double* gB0, double* v_out, int32_t* flags, int32_t nthreads);
+
+/* Noise propagation at fixed lambda: with independent zero-mean noise of standard deviation
+ * s_p[k] on pixel k of component p (sx, sy, sz are (ny, nx); a NULL array means sigma0), B is
+ * linear in B0 (Eq. 16), so Var B_p(r_i) = sum_k a_ik(lambda_pi)^2 s_p[k]^2.  var is (n, 3). */
+void orc_noise_var(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                   const float* sx, const float* sy, const float* sz, double sigma0, double* var,
+                   int32_t nthreads);
+
 /* Batched entry points over n points (OpenMP over points when nthreads > 1). */
 void orc_objective_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                         double g_scale, double w_g, double* fgphi, double* dphi, int32_t nthreads);
