@@ -81,7 +81,7 @@ typedef struct {
                           and the search starts at lambda_init + simplex_step (1, 1, 1) (Phi is even
                           in every lambda_p, so lambda_init = 0 itself is a stationary point). */
   double near_z;       /* mixed precision: points with z <= near_z get their near-field pixels
-                          (a 17 x 17 window) summed in FP64; < 0 selects 2 * hx, 0 disables */
+                          (a 7 x 7 window) summed in FP64; < 0 selects 2 * hx, 0 disables */
 } dbie_options;
 
 /* Per-point outputs of dbie_solve; every pointer may be NULL except B and lambda. */
@@ -171,6 +171,43 @@ dbie_status dbie_vjp(dbie_ctx* ctx, int64_t n, const float* xyz, const double* l
                      const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
                      double* glam, int32_t accumulate, void* stream);
 
+/* Second order at fixed lambda (n, 3) float64 (not in the paper): Phi = f + w_g g (phi, (n)),
+ * its gradient dPhi/dlambda (grad, (n, 3)) and its Hessian d2Phi / dlambda_q dlambda_r (hess,
+ * (n, 9), row-major 3 x 3), from one pass of ten pair sums per component (the objective sums, their
+ * first lambda-derivatives and the second-derivative sums sum sin(lambda r) b,
+ * sum cos(lambda r) (x_i - x_k) b / r and the same in y).  With lambda_mode = DBIE_LAMBDA_TIED,
+ * lambda_x is the shared lambda and grad[0], hess[0] are the derivatives along it (other entries
+ * 0).  Any of phi, grad, hess may be NULL, not all. */
+dbie_status dbie_hessian(dbie_ctx* ctx, int64_t n, const float* xyz, const double* lambda,
+                         const dbie_options* opt, int32_t mem_kind, double* phi, double* grad,
+                         double* hess, void* stream);
+
+/* Gradient of a loss L(B) with respect to the magnetogram THROUGH the lambda search (not in the
+ * paper).  lambda (n, 3) float64 is taken as a stationary point of Phi (the result of dbie_solve),
+ * so by implicit differentiation of grad_lambda Phi(lambda*; B0) = 0,
+ *   gB0[k][p] = sum_i gB_pi a_ik(lambda_pi)  -  d/dB0_pk sum_i v_i . grad_lambda Phi_i,
+ *   v_i = H_i^-1 dL/dlambda_i,  dL/dlambda_p = gB_p dB_p/dlambda_p (summed over p when tied),
+ * H_i the lambda-Hessian of dbie_hessian.  The second term is a transposed pair sum of seven kernel
+ * functions per component (no n x N matrix is stored).  gB (n, 3) float64 = dL/dB; gB0
+ * ((ny*nx), 3) float64 (accumulate != 0 adds to it); v (n, 3) and flags (n) int32 may be NULL:
+ * flags[i] = 1 where H_i is not positive definite (Cholesky fails), and that point contributes
+ * only its fixed-lambda term (v_i = 0).  Points the search stopped early (Eq. 12 threshold or
+ * max_iter) are not exactly stationary; the formula is applied to them as they are. */
+dbie_status dbie_vjp_implicit(dbie_ctx* ctx, int64_t n, const float* xyz, const double* lambda,
+                              const double* gB, const dbie_options* opt, int32_t mem_kind,
+                              double* gB0, double* v, int32_t* flags, int32_t accumulate,
+                              void* stream);
+
+/* Noise propagation at fixed lambda (n, 3) float64 (not in the paper): with independent
+ * zero-mean noise of standard deviation sigma_p on pixel k of component p, B is linear in B0
+ * (Eq. 16), so var[i][p] = Var B_p(r_i) = sum_k a_ik(lambda_pi)^2 sigma_p[k]^2.  sigma_x, sigma_y,
+ * sigma_z: (ny, nx) float32 maps (where mem_kind says), each may be NULL for the constant sigma0.
+ * var (n, 3) float64.  Mixed precision sums the positive FP32 terms without a near field. */
+dbie_status dbie_noise_var(dbie_ctx* ctx, int64_t n, const float* xyz, const double* lambda,
+                           const float* sigma_x, const float* sigma_y, const float* sigma_z,
+                           double sigma0, const dbie_options* opt, int32_t mem_kind, double* var,
+                           void* stream);
+
 /* Field evaluation that allocates no memory (no counterpart in the paper: an interface for
  * callers that may not allocate device memory while they run -- code inside another framework's
  * memory pool or arena, real-time loops that cannot take an allocation's implicit device
@@ -203,10 +240,11 @@ dbie_status dbie_get_stats(dbie_ctx* ctx, dbie_stats* stats, int32_t reset);
 dbie_status dbie_autotune(dbie_ctx* ctx, void* stream);
 
 /* Launch configuration indices in use (after dbie_autotune): cfg_out[2 * variant + tied] for the
- * pair-sum variants value, value+dlambda, objective, objective+dlambda, objective+gradient
- * (10 entries), then the adjoint kernel's (cfg_out[10]).  cfg_out must hold 11 int32. */
+ * pair-sum variants value, value+dlambda, objective, objective+dlambda, objective+gradient,
+ * objective+Hessian and noise variance (14 entries), then the adjoint kernel's (cfg_out[14]).
+ * cfg_out must hold 15 int32. */
 dbie_status dbie_get_config(dbie_ctx* ctx, int32_t* cfg_out);
-/* Set the same 11 indices (each in [0, 6)); DBIE_EINVAL if one is out of range. */
+/* Set the same 15 indices (each in [0, 6)); DBIE_EINVAL if one is out of range. */
 dbie_status dbie_set_config(dbie_ctx* ctx, const int32_t* cfg_in);
 
 /* Release the context and everything it owns.  NULL is a no-op. */

@@ -69,6 +69,11 @@ _SIGS = {
     "dbie_solve_batched": (_I32, [_I32, _P, _P, _P, ctypes.POINTER(dbie_options), _P, _I32,
                                   ctypes.POINTER(dbie_solve_out), _P]),
     "dbie_vjp": (_I32, [_P, _I64, _P, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _I32, _P]),
+    "dbie_hessian": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P, _P]),
+    "dbie_vjp_implicit": (_I32, [_P, _I64, _P, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P,
+                                 _P, _I32, _P]),
+    "dbie_noise_var": (_I32, [_P, _I64, _P, _P, _P, _P, _P, _D, ctypes.POINTER(dbie_options),
+                              _I32, _P, _P]),
     "dbie_eval_noalloc": (_I32, [_I32, _I32, _D, _D, _D, _D, _D, _P, _P, _P, _I64, _P, _P, _P, _P]),
     "dbie_set_profiling": (_I32, [_P, _I32]),
     "dbie_get_stats": (_I32, [_P, ctypes.POINTER(dbie_stats), _I32]),
@@ -141,6 +146,22 @@ def dbie_vjp(ctx, n, xyz, lam, gB, opt, mem_kind, gB0, glam, accumulate, stream)
                        gB0, glam, accumulate, stream))
 
 
+def dbie_hessian(ctx, n, xyz, lam, opt, mem_kind, phi, grad, hess, stream):
+    check(lib.dbie_hessian(ctx, n, xyz, lam, None if opt is None else ctypes.byref(opt), mem_kind,
+                           phi, grad, hess, stream))
+
+
+def dbie_vjp_implicit(ctx, n, xyz, lam, gB, opt, mem_kind, gB0, v, flags, accumulate, stream):
+    check(lib.dbie_vjp_implicit(ctx, n, xyz, lam, gB, None if opt is None else ctypes.byref(opt),
+                                mem_kind, gB0, v, flags, accumulate, stream))
+
+
+def dbie_noise_var(ctx, n, xyz, lam, sigma_x, sigma_y, sigma_z, sigma0, opt, mem_kind, var,
+                   stream):
+    check(lib.dbie_noise_var(ctx, n, xyz, lam, sigma_x, sigma_y, sigma_z, sigma0,
+                             None if opt is None else ctypes.byref(opt), mem_kind, var, stream))
+
+
 def dbie_eval_noalloc(nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz, n, xyz, lam, B, stream):
     """Evaluation that allocates nothing: all scratch lives in one fixed device array of the
     library (for callers that may not allocate while they run).  Device pointers only."""
@@ -164,7 +185,7 @@ def dbie_autotune(ctx, stream):
     check(lib.dbie_autotune(ctx, stream))
 
 
-NCONFIG = 11   # pair-sum variants x {per-component, tied} + adjoint
+NCONFIG = 15   # seven pair-sum variants x {per-component, tied} + adjoint
 
 
 def dbie_get_config(ctx):

@@ -23,9 +23,12 @@ UNITS = {
     "capi.cu": [],
     "aux.cu": [],
     "solve.cu": ["-fmad=false"],
+    "second_order.cu": ["-fmad=false"],
     "pairsum_f32_val.cu": [],
     "pairsum_f32_obj.cu": [],
     "pairsum_f32_newton.cu": [],
+    "pairsum_f32_hess.cu": [],
+    "pairsum_f32_nv.cu": [],
     "pairsum_f64.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],

@@ -153,6 +153,11 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
             c[p * NS + IDX_TX] += t64.t0[p] * t64.dx - (double)t32.t0[p] * (double)t32.dx;
             c[p * NS + IDX_TY] += t64.t0[p] * t64.dy - (double)t32.t0[p] * (double)t32.dy;
           }
+          if constexpr (has_hess(VAR)) {
+            c[p * NS + IDX_Q] += t64.tq[p] - (double)t32.sn[lp] * (double)b32[p];
+            c[p * NS + IDX_UX] += t64.tl[p] * t64.dx - (double)t32.tl[p] * (double)t32.dx;
+            c[p * NS + IDX_UY] += t64.tl[p] * t64.dy - (double)t32.tl[p] * (double)t32.dy;
+          }
         }
       }
     }
@@ -179,7 +184,9 @@ void launch_nearfield(int var, bool tied, const ProbDesc* probs, const int32_t* 
       case VAR_VL: NF(VAR_VL, true); break;
       case VAR_OBJ: NF(VAR_OBJ, true); break;
       case VAR_OBJL: NF(VAR_OBJL, true); break;
-      default: NF(VAR_OBJN, true); break;
+      case VAR_OBJN: NF(VAR_OBJN, true); break;
+      case VAR_HESS: NF(VAR_HESS, true); break;
+      default: break;  // VAR_NV: sums of positive terms, no near-field correction
     }
   } else {
     switch (var) {
@@ -187,7 +194,9 @@ void launch_nearfield(int var, bool tied, const ProbDesc* probs, const int32_t* 
       case VAR_VL: NF(VAR_VL, false); break;
       case VAR_OBJ: NF(VAR_OBJ, false); break;
       case VAR_OBJL: NF(VAR_OBJL, false); break;
-      default: NF(VAR_OBJN, false); break;
+      case VAR_OBJN: NF(VAR_OBJN, false); break;
+      case VAR_HESS: NF(VAR_HESS, false); break;
+      default: break;
     }
   }
 #undef NF

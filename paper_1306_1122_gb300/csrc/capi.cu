@@ -147,6 +147,7 @@ struct dbie_ctx {
   DBuf t32, t64, prob, err, misc;
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
+  DBuf tv32, tv64, probv;         // noise-variance tiles and their problem descriptor
   SolveBufs sb;
   int cfg[NVAR][2] = {};   // tuned launch configuration per variant / tied
   int vjp_cfg = 0;
@@ -277,7 +278,8 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   Misc* m = c->misc.as<Misc>();
   DBIE_TRY(ensure(c->qpos, sizeof(float4) * n));
   DBIE_TRY(ensure(c->qlam, sizeof(Lam4) * n));
-  const bool near_on = !fp64 && o.near_z > 0;
+  // (the noise variance sums positive terms: FP32 is accurate there without a near field)
+  const bool near_on = !fp64 && o.near_z > 0 && var != VAR_NV;
   if (near_on) DBIE_TRY(ensure(c->near_list, sizeof(int32_t) * n));
   CUDA_TRY(cudaMemsetAsync(&m->near_cnt, 0, sizeof(int32_t), s));
   launch_pack_eval(n, d_xyz, d_lamf, d_lamd, c->qpos.as<float4>(), c->qlam.as<Lam4>(),
@@ -295,7 +297,7 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit, k.qper,
                      (int)n, s);
   G1Args a{};
-  a.probs = c->prob.as<ProbDesc>();
+  a.probs = var == VAR_NV ? c->probv.as<ProbDesc>() : c->prob.as<ProbDesc>();
   a.nprob = 1;
   a.plan = &m->plan;
   a.item_off = m->item_off;
@@ -439,7 +441,8 @@ void dbie_destroy(dbie_ctx* c) {
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
-                  &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles})
+                  &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
+                  &c->tv64, &c->probv})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -482,6 +485,28 @@ static dbie_status stage_boundary(dbie_ctx* c, const float* Bx, const float* By,
                           c->ntiles, c->t32.as<float>(), c->t64.as<double>(), s);
     CUDA_TRY(cudaGetLastError());
   }
+  return DBIE_OK;
+}
+
+// Variance tiles for the noise propagation (device sigma arrays or NULL = sigma0).
+static dbie_status stage_variance(dbie_ctx* c, const float* sx, const float* sy, const float* sz,
+                                  double sigma0, cudaStream_t s) {
+  if (!c->probv.p) {
+    DBIE_TRY(ensure(c->tv32, sizeof(float) * NFIELD * TILE * (size_t)c->ntiles));
+    DBIE_TRY(ensure(c->tv64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles));
+    DBIE_TRY(ensure(c->probv, sizeof(ProbDesc)));
+    ProbDesc pd{};
+    pd.tiles32 = c->tv32.as<float>();
+    pd.tiles64 = c->tv64.as<double>();
+    pd.ntiles = c->ntiles;
+    pd.nx = c->nx; pd.ny = c->ny;
+    pd.x0 = c->x0; pd.y0 = c->y0; pd.hx = c->hx; pd.hy = c->hy;
+    CUDA_TRY(cudaMemcpyAsync(c->probv.p, &pd, sizeof pd, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));   // pd is a host temporary
+  }
+  launch_stage_variance(sx, sy, sz, sigma0, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy,
+                        c->dA / TWO_PI, c->ntiles, c->tv32.as<float>(), c->tv64.as<double>(), s);
+  CUDA_TRY(cudaGetLastError());
   return DBIE_OK;
 }
 
@@ -744,6 +769,242 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
   return DBIE_OK;
 }
 
+// ------------------------------------------------------------------ second order ----
+// Common argument checks and host staging of (xyz, lambda[, gB]) for the second-order calls.
+struct PtArgs {
+  const float* xyz = nullptr;
+  const double* lam = nullptr;
+  const double* gB = nullptr;
+};
+static dbie_status stage_points(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
+                                const double* gB, int32_t mem_kind, size_t out_bytes,
+                                cudaStream_t s, PtArgs& d, Staging& so) {
+  d.xyz = xyz;
+  d.lam = lambda;
+  d.gB = gB;
+  if (mem_kind != DBIE_MEM_HOST) return DBIE_OK;
+  DBIE_TRY(host_points_ok(xyz, n));
+  DBIE_TRY(host_finite(lambda, 3 * n, "lambda"));
+  if (gB) DBIE_TRY(host_finite(gB, 3 * n, "gB"));
+  DBIE_TRY(ensure(c->st_in, align256(sizeof(float) * 3 * n) + 2 * align256(sizeof(double) * 3 * n)));
+  DBIE_TRY(ensure(c->st_out, out_bytes));
+  Staging si{0, c->st_in.as<char>()};
+  so = Staging{0, c->st_out.as<char>()};
+  float* t_xyz = si.take<float>(3 * n);
+  double* t_lam = si.take<double>(3 * n);
+  CUDA_TRY(cudaMemcpyAsync(t_xyz, xyz, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(t_lam, lambda, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+  d.xyz = t_xyz;
+  d.lam = t_lam;
+  if (gB) {
+    double* t_gB = si.take<double>(3 * n);
+    CUDA_TRY(cudaMemcpyAsync(t_gB, gB, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    d.gB = t_gB;
+  }
+  return DBIE_OK;
+}
+
+static dbie_status check_n(int64_t n) {
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (n > ((int64_t)1 << 31) - 1) return fail(DBIE_EINVAL, "n too large");
+  return DBIE_OK;
+}
+
+dbie_status dbie_hessian(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
+                         const dbie_options* opt, int32_t mem_kind, double* phi, double* grad,
+                         double* hess, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  DBIE_TRY(check_n(n));
+  if (!phi && !grad && !hess) return fail(DBIE_EINVAL, "phi, grad and hess are all NULL");
+  if (n > 0 && (!xyz || !lambda)) return fail(DBIE_EINVAL, "xyz and lambda must not be NULL");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  if (n == 0) return DBIE_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const bool tied = o.lambda_mode == DBIE_LAMBDA_TIED;
+  PtArgs d;
+  Staging so;
+  DBIE_TRY(stage_points(c, n, xyz, lambda, nullptr, mem_kind,
+                        align256(sizeof(double) * n) + align256(sizeof(double) * 3 * n) +
+                            align256(sizeof(double) * 9 * n),
+                        s, d, so));
+  double *dP = phi, *dG = grad, *dH = hess;
+  if (mem_kind == DBIE_MEM_HOST) {
+    dP = phi ? so.take<double>(n) : nullptr;
+    dG = grad ? so.take<double>(3 * n) : nullptr;
+    dH = hess ? so.take<double>(9 * n) : nullptr;
+  }
+  DBIE_TRY(pass_single(c, VAR_HESS, fp64, o, n, d.xyz, nullptr, d.lam, s, tied));
+  Misc* m = c->misc.as<Misc>();
+  launch_finalize_hessian(n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
+                          c->qlam.as<Lam4>(), tied ? 1 : 3, o.g_scale, o.w_g, dP, dG, dH, s);
+  CUDA_TRY(cudaGetLastError());
+  if (mem_kind == DBIE_MEM_HOST) {
+    if (phi) CUDA_TRY(cudaMemcpyAsync(phi, dP, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (grad) CUDA_TRY(cudaMemcpyAsync(grad, dG, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (hess) CUDA_TRY(cudaMemcpyAsync(hess, dH, sizeof(double) * 9 * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
+dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
+                              const double* gB, const dbie_options* opt, int32_t mem_kind,
+                              double* gB0, double* v, int32_t* flags, int32_t accumulate,
+                              void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  DBIE_TRY(check_n(n));
+  if (!gB0) return fail(DBIE_EINVAL, "gB0 must not be NULL");
+  if (n > 0 && (!xyz || !lambda || !gB)) return fail(DBIE_EINVAL, "xyz, lambda, gB must not be NULL");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const bool tied = o.lambda_mode == DBIE_LAMBDA_TIED;
+  const int64_t npix = c->npix;
+  PtArgs d;
+  Staging so;
+  DBIE_TRY(stage_points(c, n, xyz, lambda, gB, mem_kind,
+                        align256(sizeof(double) * 3 * npix) + align256(sizeof(double) * 3 * n) +
+                            align256(sizeof(int32_t) * n),
+                        s, d, so));
+  double *d_gB0 = gB0, *d_v = v;
+  int32_t* d_fl = flags;
+  if (mem_kind == DBIE_MEM_HOST) {
+    d_gB0 = so.take<double>(3 * npix);
+    d_v = v ? so.take<double>(3 * n) : nullptr;
+    d_fl = flags ? so.take<int32_t>(n) : nullptr;
+    if (accumulate)
+      CUDA_TRY(cudaMemcpyAsync(d_gB0, gB0, sizeof(double) * 3 * npix, cudaMemcpyHostToDevice, s));
+  }
+  if (n == 0) {
+    if (!accumulate) CUDA_TRY(cudaMemsetAsync(d_gB0, 0, sizeof(double) * 3 * npix, s));
+  } else {
+    // 1. Hessian pass at lambda (ten sums per component) -> 2. per-point H, v and the adjoint
+    // weights, written as point records -> 3. seven-weight adjoint sweep over the pixels.
+    DBIE_TRY(pass_single(c, VAR_HESS, fp64, o, n, d.xyz, nullptr, d.lam, s, tied));
+    Misc* m = c->misc.as<Misc>();
+    const int nptiles = (int)((n + TILE - 1) / TILE);
+    DBIE_TRY(ensure(c->ptiles, (size_t)nptiles * VJP7_NFIELD * TILE * (fp64 ? 8 : 4)));
+    launch_implicit_weights(n, nptiles, &m->plan, m->item_off, c->out.as<double>(),
+                            c->qpos.as<float4>(), c->qlam.as<Lam4>(), d.gB, tied ? 1 : 3,
+                            o.g_scale, o.w_g, c->ptiles.as<float>(), c->ptiles.as<double>(),
+                            fp64 ? 1 : 0, d_v, d_fl, s);
+    CUDA_TRY(cudaGetLastError());
+    const KernelRef k = vjp7_ref(fp64, tied);
+    const int grid = persistent_grid(k, c->device);
+    const int64_t nblk = (npix + k.qper - 1) / k.qper;
+    const int64_t target = 2LL * grid;
+    int64_t nsplit = 1;
+    if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, nptiles);
+    const int64_t nitems = nblk * nsplit;
+    // (the Hessian pass's partial sums were consumed by the weights kernel above; the stream
+    // orders the reuse of c->out and of the plan block)
+    DBIE_TRY(ensure(c->out, sizeof(double) * nitems * 3 * k.qper));
+    launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit,
+                       k.qper, (int)npix, s);
+    VjpArgs a{};
+    a.ptiles32 = c->ptiles.as<float>();
+    a.ptiles64 = c->ptiles.as<double>();
+    a.nptiles = nptiles;
+    a.npix = (int32_t)npix;
+    a.btiles32 = c->t32.as<float>();
+    a.btiles64 = c->t64.as<double>();
+    a.plan = &m->plan;
+    a.work = &m->work;
+    a.out = c->out.as<double>();
+    a.err = c->err.as<unsigned>();
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+      e0 = take_event(c);
+      e1 = take_event(c);
+      CUDA_TRY(cudaEventRecord(e0, s));
+    }
+    DBIE_TRY(launch_kernel(k, grid, &a, s));
+    if (c->profiling) {
+      CUDA_TRY(cudaEventRecord(e1, s));
+      c->pending.push_back({e0, e1});
+      c->pending_pairs.push_back((double)n * (double)npix);
+    }
+    launch_finalize_vjp(npix, &m->plan, c->out.as<double>(), c->dA / TWO_PI, d_gB0,
+                        accumulate ? 1 : 0, s);
+    CUDA_TRY(cudaGetLastError());
+  }
+  if (mem_kind == DBIE_MEM_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(gB0, d_gB0, sizeof(double) * 3 * npix, cudaMemcpyDeviceToHost, s));
+    if (v && n > 0) CUDA_TRY(cudaMemcpyAsync(v, d_v, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    if (flags && n > 0)
+      CUDA_TRY(cudaMemcpyAsync(flags, d_fl, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
+dbie_status dbie_noise_var(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
+                           const float* sigma_x, const float* sigma_y, const float* sigma_z,
+                           double sigma0, const dbie_options* opt, int32_t mem_kind, double* var,
+                           void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  DBIE_TRY(check_mem(mem_kind));
+  DBIE_TRY(check_n(n));
+  if (n > 0 && (!xyz || !lambda || !var))
+    return fail(DBIE_EINVAL, "xyz, lambda and var must not be NULL");
+  if (!std::isfinite(sigma0)) return fail(DBIE_EINVAL, "sigma0 must be finite");
+  const dbie_options o = resolved(c, opt);
+  DBIE_TRY(check_opts(o));
+  if (n == 0) return DBIE_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const float* sg[3] = {sigma_x, sigma_y, sigma_z};
+  const float* d_sg[3] = {sigma_x, sigma_y, sigma_z};
+  const int64_t npix = c->npix;
+  if (mem_kind == DBIE_MEM_HOST) {
+    for (int p = 0; p < 3; ++p)
+      if (sg[p]) DBIE_TRY(host_finite(sg[p], npix, "sigma"));
+    DBIE_TRY(ensure(c->st_aux, 3 * align256(sizeof(float) * npix)));
+    Staging sa{0, c->st_aux.as<char>()};
+    for (int p = 0; p < 3; ++p) {
+      float* t = sa.take<float>(npix);
+      if (sg[p]) {
+        CUDA_TRY(cudaMemcpyAsync(t, sg[p], sizeof(float) * npix, cudaMemcpyHostToDevice, s));
+        d_sg[p] = t;
+      }
+    }
+  }
+  if (mem_kind == DBIE_MEM_DEVICE) {
+    Misc* m = c->misc.as<Misc>();
+    CUDA_TRY(cudaMemsetAsync(&m->bad, 0, sizeof(int32_t), s));
+    for (int p = 0; p < 3; ++p)
+      if (sg[p]) launch_count_bad(sg[p], npix, 0, &m->bad, s);
+    int32_t bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, &m->bad, sizeof bad, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (bad) return fail(DBIE_EINVAL, "sigma has a non-finite value");
+  }
+  DBIE_TRY(stage_variance(c, d_sg[0], d_sg[1], d_sg[2], sigma0, s));
+  PtArgs d;
+  Staging so;
+  DBIE_TRY(stage_points(c, n, xyz, lambda, nullptr, mem_kind, align256(sizeof(double) * 3 * n), s,
+                        d, so));
+  double* d_var = mem_kind == DBIE_MEM_HOST ? so.take<double>(3 * n) : var;
+  DBIE_TRY(pass_single(c, VAR_NV, fp64, o, n, d.xyz, nullptr, d.lam, s,
+                       o.lambda_mode == DBIE_LAMBDA_TIED));
+  Misc* m = c->misc.as<Misc>();
+  launch_finalize_nv(n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(), d_var, s);
+  CUDA_TRY(cudaGetLastError());
+  if (mem_kind == DBIE_MEM_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(var, d_var, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    DBIE_TRY(check_device_error(c, s));
+  }
+  return DBIE_OK;
+}
+
 // -------------------------------------------------------------------------- solve ----
 static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_t* n,
                               const float* const* xyz, const dbie_options* opt,
@@ -991,7 +1252,10 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (ce != cudaSuccess) return fail(DBIE_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
     b.key = key;
   }
-  const int max_launches = (3 * o.max_iter + 8) / K + 2;
+  // Rounds a point can take: the simplex spends at most 3 per iteration; the quasi-Newton search
+  // at most 31 line-search trials (alpha = 1 ... 2^-30) per accepted step.
+  const int max_rounds = (qn ? 31 : 3) * o.max_iter + 8;
+  const int max_launches = max_rounds / K + 2;
   int launches = 0;
   for (;;) {
     CUDA_TRY(cudaGraphLaunch(b.exec, s));
@@ -1015,7 +1279,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     }
     DBIE_TRY(check_device_error(c, s));
     if (c->pinned[0] == 0) break;
-    if (launches >= max_launches) return fail(DBIE_EINTERNAL, "simplex rounds did not terminate");
+    if (launches >= max_launches) return fail(DBIE_EINTERNAL, "lambda-search rounds did not terminate");
   }
   // Statistics and outputs.
   SolveCtrl hc;
@@ -1148,9 +1412,12 @@ dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
   const bool prof = c->profiling;
   c->profiling = true;
   dbie_status status = DBIE_OK;
-  const int pairs[7][2] = {{VAR_OBJ, 0},  {VAR_OBJ, 1}, {VAR_V, 0},   {VAR_VL, 0},
-                           {VAR_OBJL, 0}, {VAR_OBJN, 0}, {VAR_OBJN, 1}};
+  const int pairs[9][2] = {{VAR_OBJ, 0},  {VAR_OBJ, 1},  {VAR_V, 0},    {VAR_VL, 0},
+                           {VAR_OBJL, 0}, {VAR_OBJN, 0}, {VAR_OBJN, 1}, {VAR_HESS, 0},
+                           {VAR_NV, 0}};
+  status = stage_variance(c, nullptr, nullptr, nullptr, 1.0, s);
   for (const auto& vt : pairs) {
+    if (status != DBIE_OK) break;
     const int var = vt[0], tied = vt[1];
     const std::string key = tune_key(c->device, "g1", var, tied, c->npix);
     const int cached = tune_lookup(key);

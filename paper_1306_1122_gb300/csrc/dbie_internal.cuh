@@ -15,6 +15,8 @@ namespace dbie {
 constexpr int TILE = 256;            // pixels (or points, for the adjoint) per tile
 constexpr int NFIELD = 5;            // x, y, bx, by, bz
 constexpr int VJP_NFIELD = 9;        // x, y, z^2, lx, ly, lz, wx, wy, wz
+constexpr int VJP7_NW = 7;           // weights per component of the general adjoint (see VjpArgs)
+constexpr int VJP7_NFIELD = 6 + 3 * VJP7_NW;   // x, y, z^2, lx, ly, lz, 21 weights
 constexpr int NEAR_W = 3;            // near-field window half width (pixels): 7 x 7 window
 constexpr double TWO_PI = 6.283185307179586476925286766559;
 
@@ -33,20 +35,31 @@ constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;   // 2 s per wait
 // VAR_OBJN adds Tx = sum phi (x_i - x_k) b and Ty = sum phi (y_i - y_k) b, which with S_lambda
 // give the exact lambda-derivatives of the objective sums: dS0/dlambda = lambda Sl,
 // dS1/dlambda = -lambda S0, dSx/dlambda = -lambda Tx, dSy/dlambda = -lambda Ty.
-enum Variant { VAR_V = 0, VAR_VL = 1, VAR_OBJ = 2, VAR_OBJL = 3, VAR_OBJN = 4 };
-constexpr int NVAR = 5;
+// VAR_HESS adds Q = sum sin(lambda r) b, Ux = sum cos(lambda r) (x_i - x_k) b / r and Uy, the
+// second derivatives: dSl/dlambda = -Q, dTx/dlambda = lambda Ux, dTy/dlambda = lambda Uy.
+// VAR_NV (noise variance) sums phi^2 s over a boundary whose "b" fields hold
+// s = sigma^2 (dA / 2 pi)^2, so that Var B_p = z^2 S0 (B is linear in B0, Eq. 16).
+enum Variant {
+  VAR_V = 0, VAR_VL = 1, VAR_OBJ = 2, VAR_OBJL = 3, VAR_OBJN = 4, VAR_HESS = 5, VAR_NV = 6
+};
+constexpr int NVAR = 7;
 __host__ __device__ constexpr int nsum_per_comp(int var) {
-  return var == VAR_V ? 1 : var == VAR_VL ? 2 : var == VAR_OBJ ? 4 : var == VAR_OBJL ? 5 : 7;
+  return var == VAR_V ? 1 : var == VAR_VL ? 2 : var == VAR_OBJ ? 4 : var == VAR_OBJL ? 5
+       : var == VAR_OBJN ? 7 : var == VAR_HESS ? 10 : 1;
 }
 __host__ __device__ constexpr bool has_grad(int var) {
-  return var == VAR_OBJ || var == VAR_OBJL || var == VAR_OBJN;
+  return var == VAR_OBJ || var == VAR_OBJL || var == VAR_OBJN || var == VAR_HESS;
 }
 __host__ __device__ constexpr bool has_dlam(int var) {
-  return var == VAR_VL || var == VAR_OBJL || var == VAR_OBJN;
+  return var == VAR_VL || var == VAR_OBJL || var == VAR_OBJN || var == VAR_HESS;
 }
-__host__ __device__ constexpr bool has_newton(int var) { return var == VAR_OBJN; }
-// indices of Tx, Ty within a component's block (VAR_OBJN)
-constexpr int IDX_TX = 5, IDX_TY = 6;
+__host__ __device__ constexpr bool has_newton(int var) {
+  return var == VAR_OBJN || var == VAR_HESS;
+}
+__host__ __device__ constexpr bool has_hess(int var) { return var == VAR_HESS; }
+__host__ __device__ constexpr bool is_nv(int var) { return var == VAR_NV; }
+// indices of Tx, Ty (VAR_OBJN, VAR_HESS) and of Q, Ux, Uy (VAR_HESS) within a component's block
+constexpr int IDX_TX = 5, IDX_TY = 6, IDX_Q = 7, IDX_UX = 8, IDX_UY = 9;
 // index of the Sl sum within a component's block
 __host__ __device__ constexpr int idx_sl(int var) { return var == VAR_VL ? 1 : 4; }
 
@@ -245,7 +258,10 @@ struct Terms32 {
   float rb[3];
   float t1[has_grad(VAR) ? 3 : 1];
   float cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
-  float t0[has_newton(VAR) ? 3 : 1];  // phi b = u rb (rounded), the factor of Tx and Ty
+  float t0[has_newton(VAR) || is_nv(VAR) ? 3 : 1];  // phi b = u rb (rounded): Tx, Ty; phi s (NV)
+  float sn[has_hess(VAR) ? (TIED ? 1 : 3) : 1];      // sin(lambda r), the factor of Q
+  float tl[has_hess(VAR) ? 3 : 1];                   // cos(lambda r) b / r (rounded): Ux, Uy
+  float ph[is_nv(VAR) ? (TIED ? 1 : 3) : 1];         // phi = u / r^3 (rounded)
 };
 
 // Geometry of one pair: dx, dy, r, 1/r^2 (times 3) and 1/r^3 (SFU rsqrt).
@@ -280,7 +296,9 @@ __device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, cons
     const float th = __fmul_rn(q.l[p], g.r);
     const float s = sin_mufu(th), c = cos_mufu(th);
     t.u[p] = __fmaf_rn(th, s, c);
-    if constexpr (has_newton(VAR)) {
+    if constexpr (is_nv(VAR)) t.ph[p] = __fmul_rn(t.u[p], g.ri3);
+    if constexpr (has_hess(VAR)) t.sn[p] = s;
+    if constexpr (has_newton(VAR) || is_nv(VAR)) {
       if constexpr (TIED) {
 #pragma unroll
         for (int pp = 0; pp < 3; ++pp) t.t0[pp] = __fmul_rn(t.u[0], t.rb[pp]);
@@ -298,6 +316,14 @@ __device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, cons
       }
     }
     if constexpr (has_dlam(VAR)) t.cr[p] = __fmul_rn(c, g.ri);
+    if constexpr (has_hess(VAR)) {
+      if constexpr (TIED) {
+#pragma unroll
+        for (int pp = 0; pp < 3; ++pp) t.tl[pp] = __fmul_rn(t.cr[0], b[pp]);
+      } else {
+        t.tl[p] = __fmul_rn(t.cr[p], b[p]);
+      }
+    }
   }
 }
 
@@ -314,6 +340,8 @@ struct Terms64 {
   double t0[3];
   double t1[has_grad(VAR) ? 3 : 1];
   double tl[has_dlam(VAR) ? 3 : 1];
+  double tq[has_hess(VAR) ? 3 : 1];   // sin(lambda r) b
+  double ph[is_nv(VAR) ? 3 : 1];      // phi
 };
 // (Tx and Ty of the FP64 form are t0 * dx and t0 * dy.)
 
@@ -338,6 +366,8 @@ __device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, doubl
     t.t0[p] = u * rb;
     if constexpr (has_grad(VAR)) t.t1[p] = (q.l2[lp] * c - 3.0 * u * ri2) * rb;
     if constexpr (has_dlam(VAR)) t.tl[p] = c * ri * b[p];
+    if constexpr (has_hess(VAR)) t.tq[p] = s * b[p];
+    if constexpr (is_nv(VAR)) t.ph[p] = u * ri3;
   }
 }
 

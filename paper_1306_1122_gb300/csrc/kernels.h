@@ -32,6 +32,7 @@ struct KernelRef {
 KernelRef g1_ref_f32(int var, bool tied, int cfg);   // pairsum_f32_*.cu
 KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
 KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
+KernelRef vjp7_ref(bool fp64, bool tied);            // vjp.cu (seven-weight adjoint)
 
 // aux.cu
 void launch_stage_boundary(const float* Bx, const float* By, const float* Bz, int nx, int ny,
@@ -63,6 +64,22 @@ void launch_finalize_objective(int64_t n, const PlanHdr* plan, const int32_t* it
                                const double* out, const float4* qpos, const Lam4* qlam,
                                double g_scale, double w_g, double* fgphi, double* dphi, double* B,
                                cudaStream_t s);
+// second_order.cu
+void launch_finalize_hessian(int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                             const double* out, const float4* qpos, const Lam4* qlam, int dim,
+                             double g_scale, double w_g, double* phi, double* grad, double* hess,
+                             cudaStream_t s);
+void launch_implicit_weights(int64_t n, int nptiles, const PlanHdr* plan, const int32_t* item_off,
+                             const double* out, const float4* qpos, const Lam4* qlam,
+                             const double* gB, int dim, double g_scale, double w_g, float* p32,
+                             double* p64, int fp64, double* v_out, int32_t* flags,
+                             cudaStream_t s);
+void launch_finalize_nv(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,
+                        const float4* qpos, double* var, cudaStream_t s);
+void launch_stage_variance(const float* sx, const float* sy, const float* sz, double sigma0,
+                           int nx, int ny, double x0, double y0, double hx, double hy, double w,
+                           int ntiles, float* t32, double* t64, cudaStream_t s);
+
 void launch_bfgs_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);
 void launch_bfgs_step(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);

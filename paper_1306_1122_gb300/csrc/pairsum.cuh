@@ -120,7 +120,8 @@ __device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int lp = TIED ? 0 : p;
-    acc[p * NS + 0] = __fmaf_rn(t.u[lp], t.rb[p], acc[p * NS + 0]);
+    if constexpr (is_nv(VAR)) acc[p * NS + 0] = __fmaf_rn(t.ph[lp], t.t0[p], acc[p * NS + 0]);
+    else acc[p * NS + 0] = __fmaf_rn(t.u[lp], t.rb[p], acc[p * NS + 0]);
     if constexpr (has_grad(VAR)) {
       acc[p * NS + 1] = __fadd_rn(acc[p * NS + 1], t.t1[p]);
       acc[p * NS + 2] = __fmaf_rn(t.t1[p], t.dx, acc[p * NS + 2]);
@@ -132,6 +133,11 @@ __device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED
       acc[p * NS + IDX_TX] = __fmaf_rn(t.t0[p], t.dx, acc[p * NS + IDX_TX]);
       acc[p * NS + IDX_TY] = __fmaf_rn(t.t0[p], t.dy, acc[p * NS + IDX_TY]);
     }
+    if constexpr (has_hess(VAR)) {
+      acc[p * NS + IDX_Q] = __fmaf_rn(t.sn[lp], b[p], acc[p * NS + IDX_Q]);
+      acc[p * NS + IDX_UX] = __fmaf_rn(t.tl[p], t.dx, acc[p * NS + IDX_UX]);
+      acc[p * NS + IDX_UY] = __fmaf_rn(t.tl[p], t.dy, acc[p * NS + IDX_UY]);
+    }
   }
 }
 
@@ -139,7 +145,8 @@ template <int VAR, bool TIED, int NS>
 __device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIED>& t) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
-    acc[p * NS + 0] += t.t0[p];
+    if constexpr (is_nv(VAR)) acc[p * NS + 0] += t.ph[p] * t.t0[p];
+    else acc[p * NS + 0] += t.t0[p];
     if constexpr (has_grad(VAR)) {
       acc[p * NS + 1] += t.t1[p];
       acc[p * NS + 2] += t.t1[p] * t.dx;
@@ -149,6 +156,11 @@ __device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIE
     if constexpr (has_newton(VAR)) {
       acc[p * NS + IDX_TX] += t.t0[p] * t.dx;
       acc[p * NS + IDX_TY] += t.t0[p] * t.dy;
+    }
+    if constexpr (has_hess(VAR)) {
+      acc[p * NS + IDX_Q] += t.tq[p];
+      acc[p * NS + IDX_UX] += t.tl[p] * t.dx;
+      acc[p * NS + IDX_UY] += t.tl[p] * t.dy;
     }
   }
 }
@@ -470,6 +482,176 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
   if (tid == 0) ring.drain();
 }
 
+// ------------------------------------------------------------------- general adjoint ----
+// Transposed sum with seven kernel functions per component (the adjoint of the 12 objective sums
+// and their lambda-derivatives, used by the gradient through the lambda search):
+//   out_pk = sum_i [ phi (W0 + W5 dx + W6 dy) + psi (W1 + W2 dx + W3 dy) + W4 cos(lambda r) / r ],
+// phi = u / r^3, psi = (lambda^2 cos(lambda r) - 3 u / r^2) / r^3, dx = x_i - x_k, dy = y_i - y_k,
+// with the seven weights W_m of point i and component p in its record (VJP7_NFIELD fields:
+// x, y, z^2, lambda_x, lambda_y, lambda_z, then W[p * 7 + m]).
+template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+__device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
+  constexpr int Q = NT * P;
+  constexpr int NWARP = NT / 32;
+  constexpr bool F32 = sizeof(Real) == 4;
+  constexpr int NL = TIED ? 1 : 3;
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[NSTAGE];
+  __shared__ __align__(8) uint64_t empty_bar[NSTAGE];
+  __shared__ int s_item;
+  __shared__ volatile int s_abort;
+
+  const int tid = threadIdx.x;
+  TileRing<Real, NSTAGE, NWARP> ring{reinterpret_cast<Real*>(smem_raw), full_bar, empty_bar,
+                                     &s_abort, a.err, (uint32_t)(VJP7_NFIELD * TILE), 0u, 0u};
+  if (tid == 0) {
+    ring.init_barriers();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const PlanHdr plan = *a.plan;
+  const Real* ptiles = F32 ? reinterpret_cast<const Real*>(a.ptiles32)
+                           : reinterpret_cast<const Real*>(a.ptiles64);
+  const Real* btiles = F32 ? reinterpret_cast<const Real*>(a.btiles32)
+                           : reinterpret_cast<const Real*>(a.btiles64);
+
+  for (;;) {
+    if (tid == 0) s_item = s_abort ? plan.nitems : atomicAdd(a.work, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= plan.nitems) break;
+    const int blk = it / plan.nsplit;
+    const int sp = it - blk * plan.nsplit;
+    const int t0 = (int)(((int64_t)sp * a.nptiles) / plan.nsplit);
+    const int t1 = (int)(((int64_t)(sp + 1) * a.nptiles) / plan.nsplit);
+
+    Real px[P], py[P];
+    bool valid[P];
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int kp = blk * Q + tid + u * NT;
+      valid[u] = kp < a.npix;
+      const int k = valid[u] ? kp : 0;
+      px[u] = *tile_field(btiles, k, 0);
+      py[u] = *tile_field(btiles, k, 1);
+    }
+    Real acc[P][3];
+    float hi[F32 ? P : 1][3];
+#pragma unroll
+    for (int u = 0; u < P; ++u)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        acc[u][p] = Real(0);
+        if constexpr (F32) hi[u][p] = 0.f;
+      }
+
+    sweep_tiles(ring, ptiles, t0, t1, tid, [&](const Real* sx) {
+      const Real* X = sx;
+      const Real* Y = sx + TILE;
+      const Real* Z2 = sx + 2 * TILE;
+      const Real* L = sx + 3 * TILE;
+      const Real* W = sx + 6 * TILE;
+      if constexpr (F32) {
+#pragma unroll 1
+        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+#pragma unroll 2
+          for (int k = k0; k < k0 + SUB; ++k) {
+            const float xi = X[k], yi = Y[k], z2 = Z2[k];
+            float lam[NL], lam2[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+              lam[l] = L[l * TILE + k];
+              lam2[l] = __fmul_rn(lam[l], lam[l]);
+            }
+#pragma unroll
+            for (int u = 0; u < P; ++u) {
+              const float dx = __fsub_rn(xi, px[u]), dy = __fsub_rn(yi, py[u]);
+              const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, z2));
+              const float ri = rsqrt_mufu(r2);
+              const float r = __fmul_rn(r2, ri);
+              const float ri2 = __fmul_rn(ri, ri);
+              const float ri3 = __fmul_rn(ri2, ri);
+              const float ri2x3 = __fmul_rn(3.f, ri2);
+              float ph[NL], ps[NL], cr[NL];
+#pragma unroll
+              for (int l = 0; l < NL; ++l) {
+                const float th = __fmul_rn(lam[l], r);
+                const float sn = sin_mufu(th), c = cos_mufu(th);
+                const float uu = __fmaf_rn(th, sn, c);
+                ph[l] = __fmul_rn(uu, ri3);
+                ps[l] = __fmul_rn(__fmaf_rn(-uu, ri2x3, __fmul_rn(lam2[l], c)), ri3);
+                cr[l] = __fmul_rn(c, ri);
+              }
+#pragma unroll
+              for (int p = 0; p < 3; ++p) {
+                const int l = TIED ? 0 : p;
+                const float* w = W + p * VJP7_NW * TILE + k;
+                const float aph = __fmaf_rn(w[6 * TILE], dy, __fmaf_rn(w[5 * TILE], dx, w[0]));
+                const float aps = __fmaf_rn(w[3 * TILE], dy, __fmaf_rn(w[2 * TILE], dx, w[TILE]));
+                acc[u][p] = __fmaf_rn(ph[l], aph,
+                                      __fmaf_rn(ps[l], aps, __fmaf_rn(w[4 * TILE], cr[l], acc[u][p])));
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int p = 0; p < 3; ++p) fold2(hi[u][p], acc[u][p]);
+        }
+      } else {
+#pragma unroll 1
+        for (int k = 0; k < TILE; ++k) {
+          const double xi = X[k], yi = Y[k], z2 = Z2[k];
+#pragma unroll
+          for (int u = 0; u < P; ++u) {
+            const double dx = xi - px[u], dy = yi - py[u];
+            const double r2 = dx * dx + dy * dy + z2;
+            const double ri = rsqrt(r2);
+            const double r = r2 * ri;
+            const double ri2 = ri * ri;
+            const double ri3 = ri2 * ri;
+            double ph[NL], ps[NL], cr[NL];
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+              const double lm = L[l * TILE + k];
+              double sn, c;
+              const double th = lm * r;
+              sincos(th, &sn, &c);
+              const double uu = th * sn + c;
+              ph[l] = uu * ri3;
+              ps[l] = (lm * lm * c - 3.0 * uu * ri2) * ri3;
+              cr[l] = c * ri;
+            }
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+              const int l = TIED ? 0 : p;
+              const double* w = W + p * VJP7_NW * TILE + k;
+              acc[u][p] += ph[l] * (w[0] + w[5 * TILE] * dx + w[6 * TILE] * dy) +
+                           ps[l] * (w[TILE] + w[2 * TILE] * dx + w[3 * TILE] * dy) +
+                           w[4 * TILE] * cr[l];
+            }
+          }
+        }
+      }
+    });
+
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      if (!valid[u]) continue;
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        double v;
+        if constexpr (F32) v = (double)hi[u][p] + (double)acc[u][p];
+        else v = (double)acc[u][p];
+        a.out[((int64_t)it * 3 + p) * Q + (tid + u * NT)] = v;
+      }
+    }
+  }
+  if (tid == 0) ring.drain();
+}
+
 // Kernel entry points.  MINB > 1 caps registers so that MINB CTAs fit on an SM; MINB = 1 leaves
 // the register allocation to the compiler (a plain __launch_bounds__(NT)).
 template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
@@ -487,6 +669,10 @@ __global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
 template <typename Real, bool TIED, int P, int NT, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(NT, MINB) vjp_kernel_mb(const VjpArgs a) {
   vjp_body<Real, TIED, P, NT, NSTAGE>(a);
+}
+template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+__global__ void __launch_bounds__(NT) vjp7_kernel(const VjpArgs a) {
+  vjp7_body<Real, TIED, P, NT, NSTAGE>(a);
 }
 
 }  // namespace dbie

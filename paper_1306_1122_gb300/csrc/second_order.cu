@@ -1,0 +1,373 @@
+// second_order.cu -- lambda-Hessian of the objective, the gradient of a loss through the lambda
+// search, and the noise variance of B (none of them in the paper).
+//
+// Compiled with -fmad=false: every operation is rounded as written.
+//
+// From the ten sums of the Hessian pass (per component p, lambda = lambda_p):
+//   q       : B = z S0, Gx = z Sx, Gy = z Sy, Gz = S0 + z^2 S1            (Eq. 16, Eq. 13)
+//   dq/dl   : z l Sl, -z l Tx, -z l Ty, l Sl - z^2 l S0
+//   d2q/dl2 : z (Sl - l Q), -z (Tx + l^2 Ux), -z (Ty + l^2 Uy), (Sl - l Q) - z^2 (S0 + l^2 Sl)
+// (dS0/dl = l Sl, dS1/dl = -l S0, dSx/dl = -l Tx, dSl/dl = -Q, dTx/dl = l Ux).  Phi = f + w_g g
+// (Eq. 8, 9, 14) is evaluated on hyper-dual numbers v + a e1 + b e2 + c e1 e2 (e1^2 = e2^2 = 0;
+// Fike & Alonso 2011), which carry first and second derivatives exactly: seeding a and b with
+// dq/dl_j and dq/dl_k (and c with d2q/dl_j^2 when j = k) gives H_jk in c.
+//
+// Gradient through the search: lambda* is a stationary point, grad_l Phi(lambda*; B0) = 0, so
+// d(lambda*)/dB0 = -H^-1 d(grad_l Phi)/dB0 and
+//   dL/dB0 = A^T gB - d/dB0 [v . grad_l Phi],  v = H^-1 dL/dl,  dL/dl_p = gB_p dB_p/dl_p.
+// The second term is a transposed sum over points of seven kernel functions per component with
+// per-point weights (vjp7_kernel); the weights come from Phi's derivatives with respect to the
+// twelve q (hyper-dual again: seed a with the change of q along v, b with one q at a time).
+#include "kernels.h"
+#include "solve.cuh"
+
+namespace dbie {
+
+namespace {
+
+struct HD {
+  double v, a, b, c;
+};
+__device__ __forceinline__ HD hd_k(double v) { return HD{v, 0.0, 0.0, 0.0}; }
+__device__ __forceinline__ HD operator+(HD x, HD y) {
+  return HD{x.v + y.v, x.a + y.a, x.b + y.b, x.c + y.c};
+}
+__device__ __forceinline__ HD operator-(HD x, HD y) {
+  return HD{x.v - y.v, x.a - y.a, x.b - y.b, x.c - y.c};
+}
+__device__ __forceinline__ HD operator*(HD x, HD y) {
+  return HD{x.v * y.v, x.v * y.a + x.a * y.v, x.v * y.b + x.b * y.v,
+            x.v * y.c + x.a * y.b + x.b * y.a + x.c * y.v};
+}
+__device__ __forceinline__ HD scale(HD x, double s) { return HD{x.v * s, x.a * s, x.b * s, x.c * s}; }
+// g(x) with g(x.v) = g0, g'(x.v) = g1, g''(x.v) = g2
+__device__ __forceinline__ HD lift(HD x, double g0, double g1, double g2) {
+  return HD{g0, g1 * x.a, g1 * x.b, g1 * x.c + g2 * x.a * x.b};
+}
+__device__ __forceinline__ HD recip(HD x) {
+  const double r = 1.0 / x.v;
+  return lift(x, r, -(r * r), 2.0 * r * r * r);
+}
+// Euclidean norm of a 3-vector; derivative parts 0 at the kink |x| = 0.
+__device__ __forceinline__ HD norm3(HD x0, HD x1, HD x2) {
+  const HD s = x0 * x0 + x1 * x1 + x2 * x2;
+  if (!(s.v > 0.0)) return hd_k(0.0);
+  const double r = sqrt(s.v);
+  return lift(s, r, 0.5 / r, -0.25 / (r * s.v));
+}
+
+// Phi = f + w_g g of Eq. 8, 9 (J = curl B, Eq. 14) on hyper-dual B (3) and G (9, G[3p+j] =
+// dB_p/dx_j); f = 0 when |J||B| = 0, g = 0 when |B| = 0.
+__device__ HD objective_hd(const HD* B, const HD* G, double g_scale, double w_g) {
+  const HD Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
+  const HD D = G[0] + G[4] + G[8];
+  const HD Cx = Jy * B[2] - Jz * B[1];
+  const HD Cy = Jz * B[0] - Jx * B[2];
+  const HD Cz = Jx * B[1] - Jy * B[0];
+  const HD nJ = norm3(Jx, Jy, Jz), nB = norm3(B[0], B[1], B[2]), nC = norm3(Cx, Cy, Cz);
+  HD phi = hd_k(0.0);
+  if (nJ.v * nB.v > 0.0) phi = nC * recip(nJ * nB);
+  if (nB.v > 0.0) {
+    const HD aD = D.v < 0.0 ? scale(D, -1.0) : D;
+    phi = phi + scale(aD * recip(nB), g_scale * w_g);
+  }
+  return phi;
+}
+
+// q (value), dq/dlambda_p and d2q/dlambda_p^2 of one query from its 30 Hessian-pass sums;
+// q index: 0..2 B_p, 3 + 3p + j dB_p/dx_j.
+__device__ void q_derivs(const double* S, double z, const double lam[3], double q[12],
+                         double d1[12], double d2[12]) {
+  for (int p = 0; p < 3; ++p) {
+    const double* s = S + 10 * p;
+    const double l = lam[p], l2 = l * l;
+    const double S0 = s[0], S1 = s[1], Sx = s[2], Sy = s[3], Sl = s[4], Tx = s[5], Ty = s[6];
+    const double Qs = s[7], Ux = s[8], Uy = s[9];
+    q[p] = z * S0;
+    q[3 + 3 * p] = z * Sx;
+    q[4 + 3 * p] = z * Sy;
+    q[5 + 3 * p] = S0 + z * z * S1;
+    d1[p] = z * l * Sl;
+    d1[3 + 3 * p] = -(z * l * Tx);
+    d1[4 + 3 * p] = -(z * l * Ty);
+    d1[5 + 3 * p] = l * Sl - z * z * l * S0;
+    const double e = Sl - l * Qs;   // d2S0/dl2 = Sl + l dSl/dl
+    d2[p] = z * e;
+    d2[3 + 3 * p] = -(z * (Tx + l2 * Ux));
+    d2[4 + 3 * p] = -(z * (Ty + l2 * Uy));
+    d2[5 + 3 * p] = e - z * z * (S0 + l2 * Sl);
+  }
+}
+
+__device__ __forceinline__ int comp_of(int m) { return m < 3 ? m : (m - 3) / 3; }
+
+// Phi, its gradient and its Hessian in lambda (dim 3: per component; dim 1: one shared lambda,
+// entry 0 only).
+__device__ void hessian_of(const double q[12], const double d1[12], const double d2[12], int dim,
+                           double g_scale, double w_g, double& phi, double grad[3], double H[9]) {
+  HD B[3], G[9];
+  for (int i = 0; i < 9; ++i) H[i] = 0.0;
+  grad[0] = grad[1] = grad[2] = 0.0;
+  for (int j = 0; j < dim; ++j)
+    for (int k = j; k < dim; ++k) {
+      for (int m = 0; m < 12; ++m) {
+        const int p = comp_of(m);
+        const bool sj = dim == 1 || p == j, sk = dim == 1 || p == k;
+        HD x = hd_k(q[m]);
+        x.a = sj ? d1[m] : 0.0;
+        x.b = sk ? d1[m] : 0.0;
+        x.c = (sj && sk) ? d2[m] : 0.0;
+        if (m < 3) B[m] = x;
+        else G[m - 3] = x;
+      }
+      const HD ph = objective_hd(B, G, g_scale, w_g);
+      H[3 * j + k] = ph.c;
+      H[3 * k + j] = ph.c;
+      if (j == k) {
+        grad[j] = ph.a;
+        phi = ph.v;
+      }
+    }
+}
+
+// Cholesky solve of H v = r (m <= 3); false when H is not positive definite.
+__device__ bool chol3(int m, const double* H, const double* r, double* v) {
+  double L[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, y[3] = {0, 0, 0};
+  for (int j = 0; j < m; ++j) {
+    double d = H[3 * j + j];
+    for (int k = 0; k < j; ++k) d -= L[3 * j + k] * L[3 * j + k];
+    if (!(d > 0.0)) return false;
+    L[3 * j + j] = sqrt(d);
+    for (int i = j + 1; i < m; ++i) {
+      double e = H[3 * i + j];
+      for (int k = 0; k < j; ++k) e -= L[3 * i + k] * L[3 * j + k];
+      L[3 * i + j] = e / L[3 * j + j];
+    }
+  }
+  for (int i = 0; i < m; ++i) {
+    double e = r[i];
+    for (int k = 0; k < i; ++k) e -= L[3 * i + k] * y[k];
+    y[i] = e / L[3 * i + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double e = y[i];
+    for (int k = i + 1; k < m; ++k) e -= L[3 * k + i] * v[k];
+    v[i] = e / L[3 * i + i];
+  }
+  return true;
+}
+
+__device__ __forceinline__ double gsum(const double* out, const PlanHdr& h,
+                                       const int32_t* item_off, int64_t j, int nsum, int s) {
+  double v = 0.0;
+  for (int sp = 0; sp < h.nsplit; ++sp) v += out[out_index(h, item_off, 0, j, sp, s, nsum)];
+  return v;
+}
+
+__global__ void finalize_hessian_kernel(int64_t n, const PlanHdr* __restrict__ plan,
+                                        const int32_t* __restrict__ item_off,
+                                        const double* __restrict__ out,
+                                        const float4* __restrict__ qpos,
+                                        const Lam4* __restrict__ qlam, int dim, double g_scale,
+                                        double w_g, double* phi_out, double* grad_out,
+                                        double* hess_out) {
+  constexpr int NSUM = 3 * nsum_per_comp(VAR_HESS);
+  const PlanHdr h = *plan;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double S[NSUM];
+    for (int s = 0; s < NSUM; ++s) S[s] = gsum(out, h, item_off, i, NSUM, s);
+    const Lam4 l = qlam[i];
+    // one shared lambda: lambda_x for every component, as the tied pair-sum pass used
+    const double lam[3] = {l.x, dim == 1 ? l.x : l.y, dim == 1 ? l.x : l.z};
+    double q[12], d1[12], d2[12], phi = 0.0, grad[3], H[9];
+    q_derivs(S, (double)qpos[i].z, lam, q, d1, d2);
+    hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
+    if (phi_out) phi_out[i] = phi;
+    if (grad_out)
+      for (int j = 0; j < 3; ++j) grad_out[3 * i + j] = grad[j];
+    if (hess_out)
+      for (int j = 0; j < 9; ++j) hess_out[9 * i + j] = H[j];
+  }
+}
+
+// Per point: H, v = H^-1 dL/dlambda and the 21 adjoint weights, written as the point's record of
+// the seven-weight adjoint sweep (plus padding records up to the tile multiple).
+__global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* __restrict__ plan,
+                                        const int32_t* __restrict__ item_off,
+                                        const double* __restrict__ out,
+                                        const float4* __restrict__ qpos,
+                                        const Lam4* __restrict__ qlam,
+                                        const double* __restrict__ gB, int dim, double g_scale,
+                                        double w_g, float* p32, double* p64, int fp64,
+                                        double* v_out, int32_t* flags) {
+  constexpr int NSUM = 3 * nsum_per_comp(VAR_HESS);
+  const PlanHdr h = *plan;
+  const int64_t total = (int64_t)nptiles * TILE;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0.0, y = 0.0, z = 1.0, lam[3] = {0.0, 0.0, 0.0}, W[21];
+    float zf = 1.f;
+    for (int m = 0; m < 21; ++m) W[m] = 0.0;
+    if (i < n) {
+      const float4 pos = qpos[i];
+      x = pos.x;
+      y = pos.y;
+      zf = pos.z;
+      z = zf;
+      const Lam4 l = qlam[i];
+      lam[0] = l.x;
+      lam[1] = dim == 1 ? l.x : l.y;
+      lam[2] = dim == 1 ? l.x : l.z;
+      double S[NSUM];
+      for (int s = 0; s < NSUM; ++s) S[s] = gsum(out, h, item_off, i, NSUM, s);
+      double q[12], d1[12], d2[12], phi = 0.0, grad[3], H[9];
+      q_derivs(S, z, lam, q, d1, d2);
+      hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
+      const double g[3] = {gB[3 * i], gB[3 * i + 1], gB[3 * i + 2]};
+      double gl[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
+      if (dim == 1) gl[0] = g[0] * d1[0] + g[1] * d1[1] + g[2] * d1[2];
+      else for (int p = 0; p < 3; ++p) gl[p] = g[p] * d1[p];
+      const bool pd = chol3(dim, H, gl, v);
+      if (!pd) v[0] = v[1] = v[2] = 0.0;
+      double vp[3];
+      for (int p = 0; p < 3; ++p) vp[p] = dim == 1 ? v[0] : v[p];
+      if (v_out)
+        for (int p = 0; p < 3; ++p) v_out[3 * i + p] = vp[p];
+      if (flags) flags[i] = pd ? 0 : 1;
+      // Phi's first derivatives dPhi/dq (b part) and w = (d2 Phi / dq dq) . (dq along v) (c part)
+      double Fq[12], wq[12];
+      for (int m = 0; m < 12; ++m) {
+        Fq[m] = 0.0;
+        wq[m] = 0.0;
+      }
+      if (pd) {
+        HD B[3], G[9];
+        for (int mm = 0; mm < 12; ++mm) {
+          for (int m = 0; m < 12; ++m) {
+            HD xq = hd_k(q[m]);
+            xq.a = vp[comp_of(m)] * d1[m];
+            xq.b = m == mm ? 1.0 : 0.0;
+            if (m < 3) B[m] = xq;
+            else G[m - 3] = xq;
+          }
+          const HD ph = objective_hd(B, G, g_scale, w_g);
+          Fq[mm] = ph.b;
+          wq[mm] = ph.c;
+        }
+      }
+      for (int p = 0; p < 3; ++p) {
+        const double lp = lam[p], vl = vp[p] * lp;
+        const double wB = wq[p], wx = wq[3 + 3 * p], wy = wq[4 + 3 * p], wz = wq[5 + 3 * p];
+        const double FB = Fq[p], Fx = Fq[3 + 3 * p], Fy = Fq[4 + 3 * p], Fz = Fq[5 + 3 * p];
+        double* w = W + 7 * p;
+        w[0] = g[p] * z - (z * wB + wz - vl * z * z * Fz);   // phi
+        w[1] = -(z * z * wz);                                 // psi
+        w[2] = -(z * wx);                                     // psi dx
+        w[3] = -(z * wy);                                     // psi dy
+        w[4] = -(vl * (z * FB + Fz));                         // cos(lambda r) / r
+        w[5] = vl * z * Fx;                                   // phi dx
+        w[6] = vl * z * Fy;                                   // phi dy
+      }
+    }
+    const int64_t base = (i / TILE) * (int64_t)(VJP7_NFIELD * TILE) + (i % TILE);
+    if (fp64) {
+      p64[base] = x;
+      p64[base + TILE] = y;
+      p64[base + 2 * TILE] = z * z;
+      for (int p = 0; p < 3; ++p) p64[base + (3 + p) * TILE] = lam[p];
+      for (int m = 0; m < 21; ++m) p64[base + (6 + m) * TILE] = W[m];
+    } else {
+      p32[base] = (float)x;
+      p32[base + TILE] = (float)y;
+      p32[base + 2 * TILE] = __fmul_rn(zf, zf);
+      for (int p = 0; p < 3; ++p) p32[base + (3 + p) * TILE] = (float)lam[p];
+      for (int m = 0; m < 21; ++m) p32[base + (6 + m) * TILE] = (float)W[m];
+    }
+  }
+}
+
+__global__ void finalize_nv_kernel(int64_t n, const PlanHdr* __restrict__ plan,
+                                   const int32_t* __restrict__ item_off,
+                                   const double* __restrict__ out,
+                                   const float4* __restrict__ qpos, double* var) {
+  const PlanHdr h = *plan;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double z = (double)qpos[i].z;
+    for (int p = 0; p < 3; ++p) var[3 * i + p] = z * z * gsum(out, h, item_off, i, 3, p);
+  }
+}
+
+// Variance tiles: positions as the boundary's, and s_p = (sigma_p (dA / 2 pi))^2 (sigma_p from
+// the array, or sigma0 where the array is NULL); padding pixels carry s = 0.
+__global__ void stage_variance_kernel(const float* __restrict__ sx, const float* __restrict__ sy,
+                                      const float* __restrict__ sz, double sigma0, int nx, int ny,
+                                      double x0, double y0, double hx, double hy, double w,
+                                      int ntiles, float* __restrict__ t32,
+                                      double* __restrict__ t64) {
+  const int64_t npix = (int64_t)nx * ny;
+  const int64_t total = (int64_t)ntiles * TILE;
+  const float* sg[3] = {sx, sy, sz};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const bool real = k < npix;
+    const int64_t kk = real ? k : npix - 1;
+    const int i = (int)(kk % nx), j = (int)(kk / nx);
+    const double x = x0 + i * hx, y = y0 + j * hy;
+    const int64_t base = (k / TILE) * (int64_t)(NFIELD * TILE) + (k % TILE);
+    t64[base] = x;
+    t64[base + TILE] = y;
+    t32[base] = (float)x;
+    t32[base + TILE] = (float)y;
+    for (int p = 0; p < 3; ++p) {
+      const double sd = real ? (sg[p] ? (double)sg[p][kk] : sigma0) * w : 0.0;
+      t64[base + (2 + p) * TILE] = sd * sd;
+      t32[base + (2 + p) * TILE] = (float)(sd * sd);
+    }
+  }
+}
+
+int grid_for(int64_t n, int cap) {
+  const int64_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g < cap ? g : cap));
+}
+
+}  // namespace
+
+void launch_finalize_hessian(int64_t n, const PlanHdr* plan, const int32_t* item_off,
+                             const double* out, const float4* qpos, const Lam4* qlam, int dim,
+                             double g_scale, double w_g, double* phi, double* grad, double* hess,
+                             cudaStream_t s) {
+  if (n <= 0) return;
+  finalize_hessian_kernel<<<grid_for(n, 4096), 256, 0, s>>>(n, plan, item_off, out, qpos, qlam,
+                                                            dim, g_scale, w_g, phi, grad, hess);
+}
+
+void launch_implicit_weights(int64_t n, int nptiles, const PlanHdr* plan, const int32_t* item_off,
+                             const double* out, const float4* qpos, const Lam4* qlam,
+                             const double* gB, int dim, double g_scale, double w_g, float* p32,
+                             double* p64, int fp64, double* v_out, int32_t* flags,
+                             cudaStream_t s) {
+  const int64_t total = (int64_t)nptiles * TILE;
+  if (total <= 0) return;
+  implicit_weights_kernel<<<grid_for(total, 4096), 128, 0, s>>>(
+      n, nptiles, plan, item_off, out, qpos, qlam, gB, dim, g_scale, w_g, p32, p64, fp64, v_out,
+      flags);
+}
+
+void launch_finalize_nv(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,
+                        const float4* qpos, double* var, cudaStream_t s) {
+  if (n <= 0) return;
+  finalize_nv_kernel<<<grid_for(n, 4096), 256, 0, s>>>(n, plan, item_off, out, qpos, var);
+}
+
+void launch_stage_variance(const float* sx, const float* sy, const float* sz, double sigma0,
+                           int nx, int ny, double x0, double y0, double hx, double hy, double w,
+                           int ntiles, float* t32, double* t64, cudaStream_t s) {
+  const int64_t total = (int64_t)ntiles * TILE;
+  stage_variance_kernel<<<grid_for(total, 8192), 256, 0, s>>>(sx, sy, sz, sigma0, nx, ny, x0, y0,
+                                                              hx, hy, w, ntiles, t32, t64);
+}
+
+}  // namespace dbie

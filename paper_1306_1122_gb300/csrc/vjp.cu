@@ -26,4 +26,17 @@ KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
   }
 }
 
+// The seven-weight adjoint (gradient through the lambda search) runs once per call, after a
+// Hessian pass; it uses one launch shape (128 threads, one pixel per thread).
+template <typename Real, bool TIED>
+KernelRef vjp7_ref_t() {
+  return KernelRef{(const void*)&vjp7_kernel<Real, TIED, 1, 128, NSTAGE>, 128, 128,
+                   (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(Real)};
+}
+
+KernelRef vjp7_ref(bool fp64, bool tied) {
+  if (fp64) return tied ? vjp7_ref_t<double, true>() : vjp7_ref_t<double, false>();
+  return tied ? vjp7_ref_t<float, true>() : vjp7_ref_t<float, false>();
+}
+
 }  // namespace dbie

@@ -170,6 +170,50 @@ class DBIEField:
                    _ptr(gl), int(acc), _stream())
         return gB0, gl
 
+    def hessian(self, xyz, lam, options: Options | None = None):
+        """Phi (n,), dPhi/dlambda (n, 3) and the lambda-Hessian (n, 3, 3) at fixed lambda (tied
+        mode: the derivatives along the shared lambda in entry 0)."""
+        xyz = _dev_f32(xyz, self.device).reshape(-1, 3)
+        lam = _dev_f64(lam, self.device).reshape(-1, 3)
+        n = xyz.shape[0]
+        kw = dict(device=self.device, dtype=torch.float64)
+        P, G, H = torch.empty(n, **kw), torch.empty((n, 3), **kw), torch.empty((n, 3, 3), **kw)
+        N.dbie_hessian(self._h, n, _ptr(xyz), _ptr(lam), None if options is None else options.c(),
+                       N.DBIE_MEM_DEVICE, _ptr(P), _ptr(G), _ptr(H), _stream())
+        return dict(phi=P, grad=G, hess=H)
+
+    def vjp_implicit(self, xyz, lam, gB, options: Options | None = None, gB0=None):
+        """dL/dB0 (ny, nx, 3) through the lambda search at a stationary lambda (n, 3), plus the
+        adjoint vectors v = H^-1 dL/dlambda (n, 3) and flags (n,) (1: H not positive definite,
+        only the fixed-lambda term kept).  gB0 given: accumulated into it."""
+        xyz = _dev_f32(xyz, self.device).reshape(-1, 3)
+        lam = _dev_f64(lam, self.device).reshape(-1, 3)
+        gB = _dev_f64(gB, self.device).reshape(-1, 3)
+        n = xyz.shape[0]
+        acc = gB0 is not None
+        if gB0 is None:
+            gB0 = torch.empty((self.ny, self.nx, 3), device=self.device, dtype=torch.float64)
+        v = torch.empty((n, 3), device=self.device, dtype=torch.float64)
+        fl = torch.empty(n, device=self.device, dtype=torch.int32)
+        N.dbie_vjp_implicit(self._h, n, _ptr(xyz), _ptr(lam), _ptr(gB),
+                            None if options is None else options.c(), N.DBIE_MEM_DEVICE,
+                            _ptr(gB0), _ptr(v), _ptr(fl), int(acc), _stream())
+        return gB0, v, fl
+
+    def noise_var(self, xyz, lam, sigma=None, sigma0: float = 1.0, options: Options | None = None):
+        """Var B (n, 3) at fixed lambda for independent pixel noise: sigma None (sigma0 on every
+        pixel) or three (ny, nx) standard-deviation maps (entries may be None)."""
+        xyz = _dev_f32(xyz, self.device).reshape(-1, 3)
+        lam = _dev_f64(lam, self.device).reshape(-1, 3)
+        n = xyz.shape[0]
+        sg = [None, None, None] if sigma is None else [
+            None if a is None else _dev_f32(a, self.device).reshape(self.ny, self.nx) for a in sigma]
+        var = torch.empty((n, 3), device=self.device, dtype=torch.float64)
+        N.dbie_noise_var(self._h, n, _ptr(xyz), _ptr(lam), *(_ptr(a) for a in sg), float(sigma0),
+                         None if options is None else options.c(), N.DBIE_MEM_DEVICE, _ptr(var),
+                         _stream())
+        return var
+
     def autotune(self):
         """Time every launch configuration on this boundary and keep the fastest (cached)."""
         N.dbie_autotune(self._h, _stream())
@@ -232,3 +276,31 @@ class _DBIEFunction(torch.autograd.Function):
 def dbie_apply(field: DBIEField, B0, lam, xyz, options: Options | None = None):
     """Differentiable DBIE evaluation: B = A(lambda) B0 at the points xyz (Eq. 16)."""
     return _DBIEFunction.apply(B0, lam, field, xyz, options)
+
+
+class _DBIESolveFunction(torch.autograd.Function):
+    """B0 (ny, nx, 3) -> B (n, 3) at the searched lambda*(B0); backward through the search
+    (dbie_vjp_implicit: lambda* treated as a stationary point of Phi)."""
+
+    @staticmethod
+    def forward(ctx, B0, field: DBIEField, xyz, options):
+        field.set_boundary(B0[..., 0], B0[..., 1], B0[..., 2])
+        r = field.solve(xyz, options)
+        ctx.field, ctx.options = field, options
+        ctx.save_for_backward(xyz, r["lam"])
+        ctx.B0_dtype = B0.dtype
+        ctx.mark_non_differentiable(r["lam"])
+        return r["B"], r["lam"]
+
+    @staticmethod
+    def backward(ctx, gB, _glam):
+        xyz, lam = ctx.saved_tensors
+        gB0, _, _ = ctx.field.vjp_implicit(xyz, lam, gB.contiguous(), options=ctx.options)
+        return gB0.to(ctx.B0_dtype), None, None, None
+
+
+def dbie_solve_apply(field: DBIEField, B0, xyz, options: Options | None = None):
+    """Differentiable solve: (B, lambda*) with B = A(lambda*(B0)) B0 at the points xyz; the
+    gradient with respect to B0 includes the change of lambda* (implicit differentiation of the
+    lambda search's stationarity condition)."""
+    return _DBIESolveFunction.apply(B0, field, xyz, options)

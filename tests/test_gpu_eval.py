@@ -194,7 +194,7 @@ def test_every_launch_configuration(dbie, cfg):
     mag = random_mag(70, 45, 50 + cfg)
     xyz, lam = random_points(mag, 700, 60 + cfg)
     f = dbie.DBIEField.from_magnetogram(mag)
-    f.set_config([cfg] * 11)
+    f.set_config([cfg] * 15)
     r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True, dlam=True)
     gB = np.random.default_rng(cfg).normal(0, 1, (700, 3))
     gB0, _ = f.vjp(torch.from_numpy(xyz), torch.from_numpy(lam.astype(np.float64)),
