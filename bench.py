@@ -300,6 +300,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_form"] = fp64_compare(w, args.fp64_points, dev)
         line["quasi_newton"] = method_compare(w, dev)
+        line["backward_through_search"] = backward_compare(w, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if world > 1:
@@ -375,6 +376,43 @@ def method_compare(w, dev):
     f.close()
     out["speedup"] = out["simplex"]["solve_s"] / out["quasi_newton"]["solve_s"]
     return out
+
+
+def backward_compare(w, dev):
+    """Cost of the gradient through the lambda search (Hessian pass + seven-weight adjoint) next to
+    the fixed-lambda adjoint, and of the noise variance, on all points of the workload at the
+    simplex's lambda (mixed precision, tuned launch shapes, CUDA events, 3 repeats, minimum)."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    pts = torch.from_numpy(w.points).to(dev)
+    f = dbie.DBIEField.from_magnetogram(w.mag, device=dev)
+    f.autotune()
+    r = f.solve(pts)
+    gB = 2.0 * r["B"]
+    n, npix = len(w.points), w.mag.nx * w.mag.ny
+
+    def timed(fn):
+        fn()
+        best = 1e30
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        return best
+
+    t_fixed = timed(lambda: f.vjp(pts, r["lam"], gB, glam=False))
+    t_impl = timed(lambda: f.vjp_implicit(pts, r["lam"], gB))
+    t_nv = timed(lambda: f.noise_var(pts, r["lam"], sigma0=10.0))
+    _, _, fl = f.vjp_implicit(pts, r["lam"], gB)
+    f.close()
+    return {"points": n, "pixels": npix, "fixed_lambda_adjoint_ms": t_fixed,
+            "implicit_adjoint_ms": t_impl, "noise_variance_ms": t_nv,
+            "implicit_pair_evals_per_s": 2.0 * n * npix / (t_impl / 1e3),
+            "points_without_positive_definite_hessian": int(fl.sum().item())}
 
 
 # --------------------------------------------------------------------- oracle (CPU) ----

@@ -224,5 +224,5 @@ def test_autotune_picks_valid_configs(dbie):
     mag = random_mag(64, 64, 70)
     f = dbie.DBIEField.from_magnetogram(mag)
     cfg = f.autotune()
-    assert len(cfg) == 11 and all(0 <= c < 6 for c in cfg)
+    assert len(cfg) == 15 and all(0 <= c < 6 for c in cfg)
     f.close()
