@@ -60,7 +60,8 @@ class _Options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("lambda_mode", ctypes.c_int32),
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("deriv", ctypes.c_int32),
-                ("fd_delta", ctypes.c_double), ("method", ctypes.c_int32)]
+                ("fd_delta", ctypes.c_double), ("method", ctypes.c_int32),
+                ("quad_order", ctypes.c_int32)]
 
 
 class _NMResult(ctypes.Structure):
@@ -95,6 +96,12 @@ def _load():
                                                ctypes.c_double, P, P, ctypes.c_int32]
             lib.orc_field_dl.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
                                          P, P, P, P]
+            lib.orc_gauss_legendre.argtypes = [ctypes.c_int32, P, P]
+            lib.orc_node_weights_q9.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                                ctypes.c_double, ctypes.c_double, ctypes.c_int32, P]
+            lib.orc_eval_many_q9.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32, P, P, P,
+                                             ctypes.c_int32]
+            lib.orc_vjp_q9.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int32, P, ctypes.c_int32]
             lib.orc_hessian_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32,
                                              ctypes.c_double, ctypes.c_double, P, P, P, P,
                                              ctypes.c_int32]
@@ -162,6 +169,7 @@ class Options:
     deriv: int = 0
     fd_delta: float = 0.0       # 0 -> 1e-3 * hx (one thousandth of a pixel, Sect. 2.1)
     method: int = 0             # 0: Downhill Simplex (the paper), 1: quasi-Newton (BFGS)
+    quad_order: int = 0         # 0: midpoint rule (Eq. 16); g: nine-node elements, g x g Gauss (Eq. 15)
 
     def resolved(self, grid: Grid) -> "Options":
         o = Options(**self.__dict__)
@@ -175,24 +183,57 @@ class Options:
 
     def c(self, grid: Grid) -> _Options:
         o = self.resolved(grid)
+        if o.quad_order and o.method:
+            raise ValueError("the oracle's element rule (quad_order > 0) runs with the simplex only")
         return _Options(o.eps_f, o.eps_g, o.tol, o.max_iter, o.lambda_mode, o.simplex_step,
-                        o.w_g, o.g_scale, o.deriv, o.fd_delta, o.method)
+                        o.w_g, o.g_scale, o.deriv, o.fd_delta, o.method, o.quad_order)
 
 
 def _threads(nthreads):
     return int(nthreads) if nthreads else (os.cpu_count() or 1)
 
 
-def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthreads=None):
-    """B (n,3), G (n,3,3) with G[i,p,j] = dB_p/dx_j, and dB/dlambda (n,3) at given lambda (n,3)."""
+def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthreads=None,
+          quad_order: int = 0):
+    """B (n,3), G (n,3,3) with G[i,p,j] = dB_p/dx_j, and dB/dlambda (n,3) at given lambda (n,3).
+    quad_order 0: midpoint rule (Eq. 16); g >= 1: nine-node elements with g x g Gauss points
+    (Eq. 15; nx, ny odd)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     n = xyz.shape[0]
     B = np.zeros((n, 3)); G = np.zeros((n, 3, 3)); dl = np.zeros((n, 3))
-    lib.orc_eval_many(bd.ref, n, _ptr(xyz), _ptr(lam), deriv, fd_delta, _ptr(B), _ptr(G), _ptr(dl),
-                      _threads(nthreads))
+    if quad_order:
+        _check_q9(bd)
+        lib.orc_eval_many_q9(bd.ref, n, _ptr(xyz), _ptr(lam), quad_order, _ptr(B), _ptr(G),
+                             _ptr(dl), _threads(nthreads))
+    else:
+        lib.orc_eval_many(bd.ref, n, _ptr(xyz), _ptr(lam), deriv, fd_delta, _ptr(B), _ptr(G),
+                          _ptr(dl), _threads(nthreads))
     return B, G, dl
+
+
+def _check_q9(bd: Boundary):
+    if bd.grid.nx < 3 or bd.grid.ny < 3 or bd.grid.nx % 2 == 0 or bd.grid.ny % 2 == 0:
+        raise ValueError("nine-node elements need odd nx, ny >= 3")
+
+
+def gauss_legendre(m: int):
+    """The oracle's own Gauss-Legendre nodes and weights on [-1, 1]."""
+    lib = _load()
+    x = np.zeros(m); w = np.zeros(m)
+    lib.orc_gauss_legendre(m, _ptr(x), _ptr(w))
+    return x, w
+
+
+def node_weights_q9(bd: Boundary, point, lam: float, order: int):
+    """Per node (ny, nx, 5): a_ik, da/dx_i, da/dy_i, da/dz_i, da/dlambda of Eq. 15's elements."""
+    lib = _load()
+    _check_q9(bd)
+    out = np.zeros((bd.grid.ny * bd.grid.nx, 5))
+    lib.orc_node_weights_q9(bd.ref, float(point[0]), float(point[1]), float(point[2]), float(lam),
+                            order, _ptr(out))
+    return out.reshape(bd.grid.ny, bd.grid.nx, 5)
 
 
 def field_dl(bd: Boundary, xyz, lam):
@@ -279,15 +320,22 @@ def solve(bd: Boundary, xyz, opt: Options | None = None, lam0=None, nthreads=Non
                 codes=code_str)
 
 
-def vjp(bd: Boundary, xyz, lam, gB, nthreads=None):
-    """dL/dB0 (ny, nx, 3) for dL/dB = gB (n, 3) at fixed lambda: the transpose of Eq. 16."""
+def vjp(bd: Boundary, xyz, lam, gB, nthreads=None, quad_order: int = 0):
+    """dL/dB0 (ny, nx, 3) for dL/dB = gB (n, 3) at fixed lambda: the transpose of Eq. 16 (of the
+    element weights of Eq. 15 when quad_order > 0)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     gB = _f64(gB).reshape(-1, 3)
     g = bd.grid
     out = np.zeros((g.ny * g.nx, 3))
-    lib.orc_vjp(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), _ptr(out), _threads(nthreads))
+    if quad_order:
+        _check_q9(bd)
+        lib.orc_vjp_q9(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), quad_order, _ptr(out),
+                       _threads(nthreads))
+    else:
+        lib.orc_vjp(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), _ptr(out),
+                    _threads(nthreads))
     return out.reshape(g.ny, g.nx, 3)
 
 

@@ -403,7 +403,8 @@ static void expand_lambda(const orc_options* opt, const double* x, double lam[3]
 static void eval_point(const dbie_point_ctx* pc, const double lam[3], double B[3], double* f,
                        double* g, double* phi) {
   double G[9];
-  if (pc->opt->deriv == 1) orc_field_fd(pc->bd, pc->x, pc->y, pc->z, lam, pc->opt->fd_delta, B, G);
+  if (pc->opt->quad_order > 0) orc_field_q9(pc->bd, pc->x, pc->y, pc->z, lam, pc->opt->quad_order, B, G, NULL);
+  else if (pc->opt->deriv == 1) orc_field_fd(pc->bd, pc->x, pc->y, pc->z, lam, pc->opt->fd_delta, B, G);
   else orc_field(pc->bd, pc->x, pc->y, pc->z, lam, B, G, NULL);
   orc_objective(B, G, pc->opt->g_scale, pc->opt->w_g, f, g, phi, NULL, NULL);
 }
@@ -800,4 +801,142 @@ void orc_noise_var(const orc_boundary* bd, int64_t n, const double* xyz, const d
       var[3 * i + p] = nsum_get(&s);
     }
   }
+}
+
+/* ------------------------------------------------------ Eq. 15: nine-node elements ---- */
+
+void orc_gauss_legendre(int32_t m, double* x, double* w) {
+  /* Roots of the Legendre polynomial P_m by Newton's method from the Chebyshev-like guesses
+   * cos(pi (i + 3/4) / (m + 1/2)); P_m and P_m' by the three-term recurrence;
+   * w = 2 / ((1 - x^2) P_m'(x)^2). */
+  const double PI = 3.14159265358979323846;
+  for (int i = 0; i < m; ++i) {
+    double t = cos(PI * (i + 0.75) / (m + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= m; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = m * (t * p1 - p0) / (t * t - 1.0);
+      const double dt = p1 / dp;
+      t -= dt;
+      if (fabs(dt) < 1e-16) break;
+    }
+    {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= m; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = m * (t * p1 - p0) / (t * t - 1.0);
+    }
+    x[m - 1 - i] = t;   /* ascending order */
+    w[m - 1 - i] = 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+/* 1-D quadratic Lagrange polynomials on the nodes -1, 0, 1. */
+static double lagr2(int a, double t) {
+  return a == 0 ? 0.5 * t * (t - 1.0) : (a == 1 ? 1.0 - t * t : 0.5 * t * (t + 1.0));
+}
+
+void orc_node_weights_q9(const orc_boundary* bd, double xi, double yi, double zi, double lam,
+                         int32_t order, double* out) {
+  double gx[16], gw[16];
+  orc_gauss_legendre(order, gx, gw);
+  const int64_t np = (int64_t)bd->nx * bd->ny;
+  for (int64_t k = 0; k < 5 * np; ++k) out[k] = 0.0;
+  const int nex = (bd->nx - 1) / 2, ney = (bd->ny - 1) / 2;
+  const double jac = bd->hx * bd->hy;
+  for (int ey = 0; ey < ney; ++ey)
+    for (int ex = 0; ex < nex; ++ex) {
+      const double xc = bd->x0 + (2 * ex + 1) * bd->hx, yc = bd->y0 + (2 * ey + 1) * bd->hy;
+      /* integral over the element of K (and its derivatives) times each shape function */
+      for (int jb = 0; jb < 3; ++jb)
+        for (int ia = 0; ia < 3; ++ia) {
+          const int64_t node = (int64_t)(2 * ey + jb) * bd->nx + (2 * ex + ia);
+          for (int gb = 0; gb < order; ++gb)
+            for (int ga = 0; ga < order; ++ga) {
+              const double s = gx[ga], t = gx[gb];
+              const double xk = xc + s * bd->hx, yk = yc + t * bd->hy;
+              const double dx = xi - xk, dy = yi - yk;
+              const double r = sqrt(dx * dx + dy * dy + zi * zi);
+              const double lr = lam * r;
+              const double u = lr * sin(lr) + cos(lr);
+              const double dudr = lam * lam * r * cos(lr);
+              const double r3 = r * r * r;
+              const double psi = (dudr / r3 - 3.0 * u / (r3 * r)) / r;
+              const double c = lagr2(ia, s) * lagr2(jb, t) * gw[ga] * gw[gb] * jac / TWO_PI;
+              out[5 * node + 0] += zi * u / r3 * c;
+              out[5 * node + 1] += zi * dx * psi * c;
+              out[5 * node + 2] += zi * dy * psi * c;
+              out[5 * node + 3] += (u / r3 + zi * zi * psi) * c;
+              out[5 * node + 4] += zi * lam * cos(lr) / r * c;
+            }
+        }
+    }
+}
+
+void orc_field_q9(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                  int32_t order, double B[3], double G[9], double dBdl[3]) {
+  const int64_t np = (int64_t)bd->nx * bd->ny;
+  double* a = (double*)malloc(sizeof(double) * 5 * (size_t)np);
+  for (int p = 0; p < 3; ++p) {
+    const float* B0 = comp_ptr(bd, p);
+    orc_node_weights_q9(bd, xi, yi, zi, lam[p], order, a);
+    nsum s[5];
+    memset(s, 0, sizeof s);
+    for (int64_t k = 0; k < np; ++k)
+      for (int q = 0; q < 5; ++q) nsum_add(&s[q], a[5 * k + q] * (double)B0[k]);
+    B[p] = nsum_get(&s[0]);
+    if (G)
+      for (int j = 0; j < 3; ++j) G[3 * p + j] = nsum_get(&s[1 + j]);
+    if (dBdl) dBdl[p] = nsum_get(&s[4]);
+  }
+  free(a);
+}
+
+void orc_eval_many_q9(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      int32_t order, double* B, double* G, double* dBdl, int32_t nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i)
+    orc_field_q9(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, order, B + 3 * i,
+                 G ? G + 9 * i : NULL, dBdl ? dBdl + 3 * i : NULL);
+}
+
+void orc_vjp_q9(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                const double* gB, int32_t order, double* gB0, int32_t nthreads) {
+  const int64_t np = (int64_t)bd->nx * bd->ny;
+  /* a_ik for every point and component (n x 3 x np), then the transposed sums in point order */
+  double* A = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1) * 3 * (size_t)np);
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  {
+    double* a = (double*)malloc(sizeof(double) * 5 * (size_t)np);
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < n; ++i)
+      for (int p = 0; p < 3; ++p) {
+        orc_node_weights_q9(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam[3 * i + p], order, a);
+        for (int64_t k = 0; k < np; ++k) A[((size_t)i * 3 + p) * np + k] = a[5 * k];
+      }
+    free(a);
+  }
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t k = 0; k < np; ++k)
+    for (int p = 0; p < 3; ++p) {
+      nsum s = {0, 0};
+      for (int64_t i = 0; i < n; ++i) nsum_add(&s, gB[3 * i + p] * A[((size_t)i * 3 + p) * np + k]);
+      gB0[3 * k + p] = nsum_get(&s);
+    }
+  free(A);
 }

@@ -38,6 +38,9 @@ typedef struct {
   int32_t method;        /* 0: Downhill Simplex (the paper), 1: quasi-Newton (orc_bfgs) from
                             lambda_init + simplex_step (1, 1, 1): Phi is even in each lambda_p,
                             so lambda = 0 itself is a stationary point */
+  int32_t quad_order;    /* 0: midpoint rule at pixel centres (Eq. 16); g >= 1: nine-node
+                            elements with g x g Gauss points each (Eq. 15, orc_field_q9);
+                            the simplex only */
 } orc_options;
 
 /* Field and its derivatives at one point for a given lambda triple:
@@ -93,6 +96,26 @@ void orc_nelder_mead_sim(int32_t n, const double* sim, double tol, int32_t max_i
 typedef double (*orc_fun_grad)(void* ctx, const double* x, double* grad, int32_t* flag);
 void orc_bfgs(int32_t n, const double x0[3], double step, double tol, int32_t max_iter,
               orc_fun_grad fun, void* ctx, orc_nm_result* res);
+
+/* Eq. 15: the boundary as nine-node biquadratic elements.  Element (ex, ey) spans nodes
+ * 2ex..2ex+2 by 2ey..2ey+2 (nx, ny odd, >= 3), centred on node (2ex+1, 2ey+1) at (xc, yc); local
+ * coordinates xi = (x - xc) / hx, eta = (y - yc) / hy in [-1, 1]; shape functions
+ * N = L_a(xi) L_b(eta) with L_-1 = xi (xi - 1) / 2, L_0 = 1 - xi^2, L_+1 = xi (xi + 1) / 2;
+ * Jacobian hx hy; each element integral by order x order Gauss-Legendre points.  The weights a_ik
+ * of Eq. 16 then follow per node (orc_node_weights_q9) and B_i = sum_k a_ik B_k.  dA is not used.
+ * gauss_legendre: nodes x[m] and weights w[m] on [-1, 1] (Newton's method on P_m). */
+void orc_gauss_legendre(int32_t m, double* x, double* w);
+/* Per node k (row-major, npix entries each): a_ik and its derivatives at fixed lambda,
+ * out[5 k + 0..4] = {a, da/dx_i, da/dy_i, da/dz_i, da/dlambda}. */
+void orc_node_weights_q9(const orc_boundary* bd, double xi, double yi, double zi, double lam,
+                         int32_t order, double* out);
+void orc_field_q9(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                  int32_t order, double B[3], double G[9], double dBdl[3]);
+void orc_eval_many_q9(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                      int32_t order, double* B, double* G, double* dBdl, int32_t nthreads);
+/* Transpose with the element weights: gB0[k][p] = sum_i gB_pi a_ik(lambda_pi). */
+void orc_vjp_q9(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                const double* gB, int32_t order, double* gB0, int32_t nthreads);
 
 /* Second order, by hyper-dual numbers through the whole quadrature (no difference step; not in
  * the paper).  At one point and lambda: Phi, its gradient grad[q] = dPhi/dlambda_q, the Hessian
