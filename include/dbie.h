@@ -126,6 +126,20 @@ dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, doubl
 dbie_status dbie_set_boundary(dbie_ctx* ctx, const float* Bx, const float* By, const float* Bz,
                               int32_t mem_kind, void* stream);
 
+/* Quadrature of the boundary integral for every later call on this context:
+ *   order = 0: the midpoint rule at pixel centres, a_ik = K(r_ik) pixel_area (Eq. 16; default);
+ *   order = g (1..8): Eq. 15's nine-node biquadratic elements.  Element (ex, ey) spans pixel
+ *     centres 2ex..2ex+2 by 2ey..2ey+2 (nx, ny odd and >= 3: the nodes are the pixel centres and
+ *     the integration domain is the rectangle they span), shape functions are products of the
+ *     quadratic Lagrange polynomials on the element's local coordinates in [-1, 1], the Jacobian
+ *     is hx hy, and each element integral uses g x g Gauss-Legendre points (pixel_area is not
+ *     used).  The pair sums then run over the ((nx-1)/2 g) x ((ny-1)/2 g) Gauss points, each
+ *     carrying the interpolated field times its weights; adjoints are gathered back to the
+ *     nodes.  dbie_noise_var needs order 0.
+ * Restages the stored magnetogram; synchronises `stream`.  DBIE_EINVAL for an order outside
+ * 0..8 or even / too small nx, ny with order > 0. */
+dbie_status dbie_set_quadrature(dbie_ctx* ctx, int32_t order, void* stream);
+
 /* Evaluate Eq. 16 at n points for given lambda (n, 3) float32, and optionally
  *   gradB  (n, 9): gradB[9i + 3p + j] = d B_p / d x_j at fixed lambda (Eq. 13, delta -> 0),
  *   dBdlam (n, 3): d B_p / d lambda_p,

@@ -69,6 +69,7 @@ _SIGS = {
     "dbie_solve_batched": (_I32, [_I32, _P, _P, _P, ctypes.POINTER(dbie_options), _P, _I32,
                                   ctypes.POINTER(dbie_solve_out), _P]),
     "dbie_vjp": (_I32, [_P, _I64, _P, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _I32, _P]),
+    "dbie_set_quadrature": (_I32, [_P, _I32, _P]),
     "dbie_hessian": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P, _P]),
     "dbie_vjp_implicit": (_I32, [_P, _I64, _P, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P,
                                  _P, _I32, _P]),
@@ -144,6 +145,10 @@ def dbie_solve_batched(nprob, ctxs, n, xyz, opt, lambda_init, mem_kind, outs, st
 def dbie_vjp(ctx, n, xyz, lam, gB, opt, mem_kind, gB0, glam, accumulate, stream):
     check(lib.dbie_vjp(ctx, n, xyz, lam, gB, None if opt is None else ctypes.byref(opt), mem_kind,
                        gB0, glam, accumulate, stream))
+
+
+def dbie_set_quadrature(ctx, order, stream):
+    check(lib.dbie_set_quadrature(ctx, order, stream))
 
 
 def dbie_hessian(ctx, n, xyz, lam, opt, mem_kind, phi, grad, hess, stream):

@@ -29,6 +29,7 @@ UNITS = {
     "pairsum_f32_newton.cu": [],
     "pairsum_f32_hess.cu": [],
     "pairsum_f32_nv.cu": [],
+    "pairsum_f32_split.cu": [],
     "pairsum_f64.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],

@@ -41,6 +41,104 @@ void launch_stage_boundary(const float* Bx, const float* By, const float* Bz, in
                                              t32, t64);
 }
 
+// Quadratic Lagrange polynomials on the nodes -1, 0, +1 (index 0, 1, 2).
+__device__ __forceinline__ double lagrange3(int a, double t) {
+  return a == 0 ? 0.5 * t * (t - 1.0) : (a == 1 ? 1.0 - t * t : 0.5 * t * (t + 1.0));
+}
+
+// Eq. 15 staging: quadrature point k = J * qnx + I of element (I / g, J / g), Gauss indices
+// (I % g, J % g), at xc + xi hx, yc + eta hy, carrying the nine-node interpolant of B0 times the
+// Gauss weights, the Jacobian hx hy and 1 / (2 pi).  Padding points carry b = 0.  FP32 tiles
+// have NFIELD_SPLIT fields (positions as hi + lo float pairs), FP64 tiles NFIELD.
+__global__ void stage_q9_kernel(const float* __restrict__ B0, int nx, int ny, double x0, double y0,
+                                double hx, double hy, QuadInfo qi, int ntiles,
+                                float* __restrict__ t32, double* __restrict__ t64) {
+  const int g = qi.g;
+  const int qnx = (nx - 1) / 2 * g, qny = (ny - 1) / 2 * g;
+  const int64_t nq = (int64_t)qnx * qny;
+  const int64_t npix = (int64_t)nx * ny;
+  const int64_t total = (int64_t)ntiles * TILE;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const bool real = k < nq;
+    const int64_t kk = real ? k : nq - 1;
+    const int I = (int)(kk % qnx), J = (int)(kk / qnx);
+    const int ex = I / g, a = I % g, ey = J / g, b = J % g;
+    const double xi = qi.gx[a], eta = qi.gx[b];
+    const double x = x0 + (2 * ex + 1) * hx + xi * hx;
+    const double y = y0 + (2 * ey + 1) * hy + eta * hy;
+    const double w = qi.gw[a] * qi.gw[b] * hx * hy / TWO_PI;
+    double v[3] = {0.0, 0.0, 0.0};
+    if (real)
+      for (int jb = 0; jb < 3; ++jb)
+        for (int ia = 0; ia < 3; ++ia) {
+          const double sf = lagrange3(ia, xi) * lagrange3(jb, eta);
+          const int64_t node = (int64_t)(2 * ey + jb) * nx + (2 * ex + ia);
+          for (int p = 0; p < 3; ++p) v[p] += sf * (double)B0[p * npix + node];
+        }
+    const int64_t base = (k / TILE) * (int64_t)(NFIELD * TILE) + (k % TILE);
+    const int64_t base32 = (k / TILE) * (int64_t)(NFIELD_SPLIT * TILE) + (k % TILE);
+    t64[base] = x;
+    t64[base + TILE] = y;
+    const float xh = (float)x, yh = (float)y;
+    t32[base32] = xh;
+    t32[base32 + TILE] = yh;
+    t32[base32 + 5 * TILE] = (float)(x - (double)xh);
+    t32[base32 + 6 * TILE] = (float)(y - (double)yh);
+    for (int p = 0; p < 3; ++p) {
+      const double bv = real ? v[p] * w : 0.0;
+      t64[base + (2 + p) * TILE] = bv;
+      t32[base32 + (2 + p) * TILE] = (float)bv;
+    }
+  }
+}
+
+void launch_stage_q9(const float* B0, int nx, int ny, double x0, double y0, double hx, double hy,
+                     const QuadInfo& qi, int ntiles, float* t32, double* t64, cudaStream_t s) {
+  const int64_t total = (int64_t)ntiles * TILE;
+  const int grid = (int)((total + 255) / 256 < 8192 ? (total + 255) / 256 : 8192);
+  stage_q9_kernel<<<grid, 256, 0, s>>>(B0, nx, ny, x0, y0, hx, hy, qi, ntiles, t32, t64);
+}
+
+// Adjoint of the Eq. 15 staging: per node, the sum over the elements that hold it and over their
+// Gauss points of shape function x Gauss weights x hx hy / (2 pi) x the per-point adjoint T.
+__global__ void q9_gather_kernel(const double* __restrict__ T, int nx, int ny, double hx,
+                                 double hy, QuadInfo qi, double* gB0, int accumulate) {
+  const int g = qi.g;
+  const int nex = (nx - 1) / 2, ney = (ny - 1) / 2, qnx = nex * g;
+  const int64_t npix = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < npix;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k % nx), j = (int)(k / nx);
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int ey = (j - 1) / 2 - 1; ey <= j / 2; ++ey) {
+      if (ey < 0 || ey >= ney) continue;
+      const int jb = j - 2 * ey;
+      if (jb < 0 || jb > 2) continue;
+      for (int ex = (i - 1) / 2 - 1; ex <= i / 2; ++ex) {
+        if (ex < 0 || ex >= nex) continue;
+        const int ia = i - 2 * ex;
+        if (ia < 0 || ia > 2) continue;
+        for (int b = 0; b < g; ++b)
+          for (int a = 0; a < g; ++a) {
+            const double c = lagrange3(ia, qi.gx[a]) * lagrange3(jb, qi.gx[b]) * qi.gw[a] *
+                             qi.gw[b] * hx * hy / TWO_PI;
+            const int64_t q = (int64_t)(ey * g + b) * qnx + (ex * g + a);
+            for (int p = 0; p < 3; ++p) acc[p] += c * T[3 * q + p];
+          }
+      }
+    }
+    for (int p = 0; p < 3; ++p) gB0[3 * k + p] = accumulate ? gB0[3 * k + p] + acc[p] : acc[p];
+  }
+}
+
+void launch_q9_gather(const double* T, int nx, int ny, double hx, double hy, const QuadInfo& qi,
+                      double* gB0, int accumulate, cudaStream_t s) {
+  const int64_t npix = (int64_t)nx * ny;
+  const int grid = (int)((npix + 255) / 256 < 8192 ? (npix + 255) / 256 : 8192);
+  q9_gather_kernel<<<grid, 256, 0, s>>>(T, nx, ny, hx, hy, qi, gB0, accumulate);
+}
+
 // Queries of a single evaluation: one per point, lambda from float or double input.
 __global__ void pack_eval_kernel(int64_t n, const float* __restrict__ xyz,
                                  const float* __restrict__ lam_f, const double* __restrict__ lam_d,
@@ -91,6 +189,26 @@ void launch_plan_single(PlanHdr* plan, int32_t* item_off, int32_t* q_cnt, int32_
 // The FP32 terms are recomputed with the same explicitly rounded code (pair_terms32), so the
 // correction sum_k (t64 - t32) removes exactly what was added.  One warp per query; the
 // correction is added in place to the query's split-0 partial sums (run after the pair sums).
+// Index (along one axis) of the quadrature point nearest to coordinate x: the pixel for the
+// midpoint rule; for nine-node elements of width 2h with g Gauss points, element e and the
+// nearest abscissa a give e * g + a.
+__device__ __forceinline__ long near_index(double x, double x0, double h, int nq,
+                                           const ProbDesc& pd) {
+  if (pd.quad_g == 0) return lrint((x - x0) / h);
+  const int g = pd.quad_g;
+  const long ne = nq / g;
+  long e = (long)floor((x - x0) / (2.0 * h));
+  e = e < 0 ? 0 : (e > ne - 1 ? ne - 1 : e);
+  const double xi = (x - x0) / h - (double)(2 * e + 1);
+  int best = 0;
+  double bd = fabs(xi - pd.gx[0]);
+  for (int a = 1; a < g; ++a) {
+    const double d = fabs(xi - pd.gx[a]);
+    if (d < bd) { bd = d; best = a; }
+  }
+  return e * g + best;
+}
+
 template <int VAR, bool TIED>
 __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
                                  const int32_t* __restrict__ near_list,
@@ -100,7 +218,6 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
                                  const int32_t* __restrict__ item_off, double* __restrict__ out) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
-  constexpr int WW = 2 * NEAR_W + 1;
   const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int cnt = *near_cnt;
@@ -112,28 +229,36 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
     const ProbDesc& pd = probs[pidx];
     const Query<float, TIED> q32 = make_query<float, TIED>(pos, lam);
     const Query<double, TIED> q64 = make_query<double, TIED>(pos, lam);
-    const long ix = lrint(((double)pos.x - pd.x0) / pd.hx);
-    const long iy = lrint(((double)pos.y - pd.y0) / pd.hy);
-    const long i0 = ix - NEAR_W < 0 ? 0 : ix - NEAR_W;
-    const long i1 = ix + NEAR_W > pd.nx - 1 ? pd.nx - 1 : ix + NEAR_W;
-    const long j0 = iy - NEAR_W < 0 ? 0 : iy - NEAR_W;
-    const long j1 = iy + NEAR_W > pd.ny - 1 ? pd.ny - 1 : iy + NEAR_W;
+    const int W = pd.near_w > 0 ? pd.near_w : NEAR_W;
+    const long ix = near_index((double)pos.x, pd.x0, pd.hx, pd.nx, pd);
+    const long iy = near_index((double)pos.y, pd.y0, pd.hy, pd.ny, pd);
+    const long i0 = ix - W < 0 ? 0 : ix - W;
+    const long i1 = ix + W > pd.nx - 1 ? pd.nx - 1 : ix + W;
+    const long j0 = iy - W < 0 ? 0 : iy - W;
+    const long j1 = iy + W > pd.ny - 1 ? pd.ny - 1 : iy + W;
     const long wi = i1 - i0 + 1, wj = j1 - j0 + 1;
     double c[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) c[s] = 0.0;
-    if (wi > 0 && wj > 0 && wi <= WW && wj <= WW) {
+    if (wi > 0 && wj > 0 && wi <= 2 * W + 1 && wj <= 2 * W + 1) {
       const int nwin = (int)(wi * wj);
       for (int e = lane; e < nwin; e += 32) {
         const int64_t k = (j0 + e / wi) * (int64_t)pd.nx + (i0 + e % wi);
-        const float b32[3] = {*tile_field(pd.tiles32, k, 2), *tile_field(pd.tiles32, k, 3),
-                              *tile_field(pd.tiles32, k, 4)};
+        const int nf = pd.nf32 > 0 ? pd.nf32 : NFIELD;
+        const float b32[3] = {*tile_field(pd.tiles32, k, 2, nf), *tile_field(pd.tiles32, k, 3, nf),
+                              *tile_field(pd.tiles32, k, 4, nf)};
         const double b64[3] = {*tile_field(pd.tiles64, k, 2), *tile_field(pd.tiles64, k, 3),
                                *tile_field(pd.tiles64, k, 4)};
         Terms32<VAR, TIED> t32;
         Terms64<VAR, TIED> t64;
-        pair_terms32<VAR, TIED>(q32, *tile_field(pd.tiles32, k, 0), *tile_field(pd.tiles32, k, 1),
-                                b32, t32);
+        if (nf == NFIELD_SPLIT)
+          pair_terms32_split<VAR, TIED>(q32, *tile_field(pd.tiles32, k, 0, nf),
+                                        *tile_field(pd.tiles32, k, 1, nf),
+                                        *tile_field(pd.tiles32, k, 5, nf),
+                                        *tile_field(pd.tiles32, k, 6, nf), b32, t32);
+        else
+          pair_terms32<VAR, TIED>(q32, *tile_field(pd.tiles32, k, 0), *tile_field(pd.tiles32, k, 1),
+                                  b32, t32);
         pair_terms64<VAR, TIED>(q64, *tile_field(pd.tiles64, k, 0), *tile_field(pd.tiles64, k, 1),
                                 b64, t64);
 #pragma unroll

@@ -148,6 +148,12 @@ struct dbie_ctx {
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
   DBuf tv32, tv64, probv;         // noise-variance tiles and their problem descriptor
+  DBuf b0raw;                     // the magnetogram as given (3 x npix float32), for restaging
+  DBuf vtmp;                      // per-quadrature-point adjoint before the gather to nodes
+  int quad_g = 0;                 // 0: pixel centres (Eq. 16); g: nine-node elements (Eq. 15)
+  QuadInfo qi{};
+  int64_t nquad = 0;              // quadrature points: npix, or (elements x g)^2
+  int32_t qnx = 0, qny = 0;       // quadrature-point grid
   SolveBufs sb;
   int cfg[NVAR][2] = {};   // tuned launch configuration per variant / tied
   int vjp_cfg = 0;
@@ -267,7 +273,9 @@ int var_of(bool grad, bool dlam) {
 }
 
 KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64) {
-  return fp64 ? g1_ref_f64(var, tied) : g1_ref_f32(var, tied, c->cfg[var][tied ? 1 : 0]);
+  if (fp64) return g1_ref_f64(var, tied);
+  if (c->quad_g != 0) return g1_ref_f32_split(var, tied);   // element Gauss points
+  return g1_ref_f32(var, tied, c->cfg[var][tied ? 1 : 0]);
 }
 
 // One pair-sum pass over n queries of this context (single problem): pack, plan, sweep,
@@ -317,7 +325,7 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   if (c->profiling) {
     CUDA_TRY(cudaEventRecord(e1, s));
     c->pending.push_back({e0, e1});
-    c->pending_pairs.push_back((double)n * (double)c->npix);
+    c->pending_pairs.push_back((double)n * (double)c->nquad);
   }
   if (near_on)
     launch_nearfield(var, tied, c->prob.as<ProbDesc>(), c->near_list.as<int32_t>(), &m->near_cnt,
@@ -442,7 +450,7 @@ void dbie_destroy(dbie_ctx* c) {
   cudaDeviceSynchronize();
   for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
-                  &c->tv64, &c->probv})
+                  &c->tv64, &c->probv, &c->b0raw, &c->vtmp})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -456,23 +464,49 @@ void dbie_destroy(dbie_ctx* c) {
   delete c;
 }
 
+// Problem descriptor of the context's current quadrature (problem-specific search fields 0).
+static ProbDesc desc_of(const dbie_ctx* c) {
+  ProbDesc pd{};
+  pd.tiles32 = c->t32.as<float>();
+  pd.tiles64 = c->t64.as<double>();
+  pd.ntiles = c->ntiles;
+  pd.nx = c->qnx;
+  pd.ny = c->qny;
+  pd.quad_g = c->quad_g;
+  pd.near_w = c->quad_g == 0 ? NEAR_W : std::max(1, (NEAR_W * c->quad_g + 1) / 2);
+  pd.nf32 = c->quad_g == 0 ? NFIELD : NFIELD_SPLIT;
+  for (int a = 0; a < MAX_GAUSS; ++a) pd.gx[a] = c->qi.gx[a];
+  pd.x0 = c->x0; pd.y0 = c->y0; pd.hx = c->hx; pd.hy = c->hy;
+  return pd;
+}
+
+// Quadrature-point tiles from the stored magnetogram: pixel centres with b = B0 dA / 2 pi, or the
+// Gauss points of the nine-node elements with the interpolated, weighted field.
+static dbie_status restage(dbie_ctx* c, cudaStream_t s) {
+  const float* B0 = c->b0raw.as<float>();
+  if (c->quad_g == 0)
+    launch_stage_boundary(B0, B0 + c->npix, B0 + 2 * c->npix, c->nx, c->ny, c->x0, c->y0, c->hx,
+                          c->hy, c->dA / TWO_PI, c->ntiles, c->t32.as<float>(),
+                          c->t64.as<double>(), s);
+  else
+    launch_stage_q9(B0, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy, c->qi, c->ntiles,
+                    c->t32.as<float>(), c->t64.as<double>(), s);
+  CUDA_TRY(cudaGetLastError());
+  return DBIE_OK;
+}
+
 static dbie_status stage_boundary(dbie_ctx* c, const float* Bx, const float* By, const float* Bz,
                                   int32_t mem_kind, cudaStream_t s) {
   const float* src[3] = {Bx, By, Bz};
   const int64_t npix = c->npix;
+  float* raw = c->b0raw.as<float>();
   if (mem_kind == DBIE_MEM_HOST) {
     for (int p = 0; p < 3; ++p) DBIE_TRY(host_finite(src[p], npix, "magnetogram"));
-    DBIE_TRY(ensure(c->st_in, 3 * align256(sizeof(float) * npix)));
-    Staging st{0, c->st_in.as<char>()};
-    float* d[3];
-    for (int p = 0; p < 3; ++p) {
-      d[p] = st.take<float>(npix);
-      CUDA_TRY(cudaMemcpyAsync(d[p], src[p], sizeof(float) * npix, cudaMemcpyHostToDevice, s));
-    }
-    launch_stage_boundary(d[0], d[1], d[2], c->nx, c->ny, c->x0, c->y0, c->hx, c->hy,
-                          c->dA / TWO_PI, c->ntiles, c->t32.as<float>(), c->t64.as<double>(), s);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(cudaStreamSynchronize(s));   // staging buffer may be reused by the next call
+    for (int p = 0; p < 3; ++p)
+      CUDA_TRY(cudaMemcpyAsync(raw + p * npix, src[p], sizeof(float) * npix,
+                               cudaMemcpyHostToDevice, s));
+    DBIE_TRY(restage(c, s));
+    CUDA_TRY(cudaStreamSynchronize(s));   // the caller may free its arrays after the call
   } else {
     Misc* m = c->misc.as<Misc>();
     CUDA_TRY(cudaMemsetAsync(&m->bad, 0, sizeof(int32_t), s));
@@ -481,9 +515,10 @@ static dbie_status stage_boundary(dbie_ctx* c, const float* Bx, const float* By,
     CUDA_TRY(cudaMemcpyAsync(&bad, &m->bad, sizeof bad, cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (bad) return fail(DBIE_EINVAL, "magnetogram has a non-finite value");
-    launch_stage_boundary(Bx, By, Bz, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy, c->dA / TWO_PI,
-                          c->ntiles, c->t32.as<float>(), c->t64.as<double>(), s);
-    CUDA_TRY(cudaGetLastError());
+    for (int p = 0; p < 3; ++p)
+      CUDA_TRY(cudaMemcpyAsync(raw + p * npix, src[p], sizeof(float) * npix,
+                               cudaMemcpyDeviceToDevice, s));
+    DBIE_TRY(restage(c, s));
   }
   return DBIE_OK;
 }
@@ -530,11 +565,15 @@ dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, doubl
   c->sm_count = device_sm_count(c->device);
   c->nx = nx; c->ny = ny; c->x0 = x0; c->y0 = y0; c->hx = hx; c->hy = hy; c->dA = pixel_area;
   c->npix = (int64_t)nx * ny;
+  c->nquad = c->npix;
+  c->qnx = nx;
+  c->qny = ny;
   c->ntiles = (int32_t)((c->npix + TILE - 1) / TILE);
   auto bail = [&](dbie_status st) { std::string m = g_err; dbie_destroy(c); g_err = m; return st; };
   dbie_status st;
   if ((st = ensure(c->t32, sizeof(float) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
   if ((st = ensure(c->t64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->b0raw, sizeof(float) * 3 * (size_t)c->npix)) != DBIE_OK) return bail(st);
   if ((st = ensure(c->prob, sizeof(ProbDesc))) != DBIE_OK) return bail(st);
   if ((st = ensure(c->err, sizeof(unsigned))) != DBIE_OK) return bail(st);
   if ((st = ensure(c->misc, sizeof(Misc))) != DBIE_OK) return bail(st);
@@ -543,14 +582,7 @@ dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, doubl
       cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaHostAlloc((void**)&c->pinned, 64, cudaHostAllocDefault) != cudaSuccess)
     return bail(fail(DBIE_ECUDA, "context set-up failed"));
-  ProbDesc pd{};
-  pd.tiles32 = c->t32.as<float>();
-  pd.tiles64 = c->t64.as<double>();
-  pd.ntiles = c->ntiles;
-  pd.nx = nx; pd.ny = ny;
-  pd.x0 = x0; pd.y0 = y0; pd.hx = hx; pd.hy = hy;
-  pd.step = 0.0; pd.g_scale = 0.0; pd.near_z = 0.0;
-  pd.q_off = 0; pd.pt_off = 0; pd.npts = 0;
+  const ProbDesc pd = desc_of(c);
   if (cudaMemcpyAsync(c->prob.p, &pd, sizeof pd, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return bail(fail(DBIE_ECUDA, "copy of the problem descriptor failed"));
   if ((st = stage_boundary(c, Bx, By, Bz, mem_kind, s)) != DBIE_OK) return bail(st);
@@ -566,6 +598,77 @@ dbie_status dbie_set_boundary(dbie_ctx* c, const float* Bx, const float* By, con
   if (!Bx || !By || !Bz) return fail(DBIE_EINVAL, "Bx, By, Bz must not be NULL");
   CUDA_TRY(cudaSetDevice(c->device));
   return stage_boundary(c, Bx, By, Bz, mem_kind, static_cast<cudaStream_t>(stream));
+}
+
+// Gauss-Legendre rule with m points on [-1, 1]: roots of P_m by Newton's method (P_m and its
+// derivative from the three-term recurrence), weights 2 / ((1 - x^2) P_m'(x)^2), ascending.
+static void gauss_rule(int m, double* x, double* w) {
+  for (int i = 0; i < (m + 1) / 2; ++i) {
+    double t = std::cos(3.14159265358979323846 * (i + 0.75) / (m + 0.5));
+    double d = 1.0;
+    for (int it = 0; it < 64; ++it) {
+      double p_prev = 1.0, p = t;
+      for (int k = 2; k <= m; ++k) {
+        const double pk = ((2 * k - 1) * t * p - (k - 1) * p_prev) / k;
+        p_prev = p;
+        p = pk;
+      }
+      d = m * (t * p - p_prev) / (t * t - 1.0);
+      const double step = p / d;
+      t -= step;
+      if (std::fabs(step) <= 1e-16 * std::fabs(t) + 1e-300) {
+        // one more evaluation at the converged root for the weight
+        p_prev = 1.0; p = t;
+        for (int k = 2; k <= m; ++k) {
+          const double pk = ((2 * k - 1) * t * p - (k - 1) * p_prev) / k;
+          p_prev = p;
+          p = pk;
+        }
+        d = m * (t * p - p_prev) / (t * t - 1.0);
+        break;
+      }
+    }
+    const double wt = 2.0 / ((1.0 - t * t) * d * d);
+    x[m - 1 - i] = t;     // t > 0 first: fill from the top
+    w[m - 1 - i] = wt;
+    x[i] = -t;
+    w[i] = wt;
+  }
+  if (m % 2 == 1) x[m / 2] = 0.0;
+}
+
+dbie_status dbie_set_quadrature(dbie_ctx* c, int32_t order, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  if (order < 0 || order > MAX_GAUSS)
+    return fail(DBIE_EINVAL, "order must be 0 (pixel centres) or 1.." + std::to_string(MAX_GAUSS));
+  if (order > 0 && (c->nx < 3 || c->ny < 3 || c->nx % 2 == 0 || c->ny % 2 == 0))
+    return fail(DBIE_EINVAL, "nine-node elements need odd nx, ny >= 3");
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaStreamSynchronize(s));   // no pass of the old quadrature may still read the tiles
+  c->quad_g = order;
+  c->qi = QuadInfo{};
+  c->qi.g = order;
+  if (order > 0) {
+    gauss_rule(order, c->qi.gx, c->qi.gw);
+    c->qnx = (c->nx - 1) / 2 * order;
+    c->qny = (c->ny - 1) / 2 * order;
+  } else {
+    c->qnx = c->nx;
+    c->qny = c->ny;
+  }
+  c->nquad = (int64_t)c->qnx * c->qny;
+  if (c->nquad > (int64_t)1 << 30) return fail(DBIE_EINVAL, "too many quadrature points");
+  c->ntiles = (int32_t)((c->nquad + TILE - 1) / TILE);
+  DBIE_TRY(ensure(c->t32, sizeof(float) * (order > 0 ? NFIELD_SPLIT : NFIELD) * TILE *
+                              (size_t)c->ntiles));
+  DBIE_TRY(ensure(c->t64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles));
+  c->sb.release();   // cached solve graphs hold the old tile pointers
+  const ProbDesc pd = desc_of(c);
+  CUDA_TRY(cudaMemcpyAsync(c->prob.p, &pd, sizeof pd, cudaMemcpyHostToDevice, s));
+  DBIE_TRY(restage(c, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return DBIE_OK;
 }
 
 dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lambda,
@@ -665,6 +768,21 @@ dbie_status dbie_objective(dbie_ctx* c, int64_t n, const float* xyz, const float
   return DBIE_OK;
 }
 
+// Per-quadrature-point adjoint sums (item chunks of 3 sums) -> dL/dB0 per node: scaled by
+// dA / 2 pi at pixel centres, or gathered through the nine-node shape functions.
+static dbie_status finalize_adjoint(dbie_ctx* c, const PlanHdr* plan, double* gB0, int accumulate,
+                                    cudaStream_t s) {
+  if (c->quad_g == 0) {
+    launch_finalize_vjp(c->npix, plan, c->out.as<double>(), c->dA / TWO_PI, gB0, accumulate, s);
+  } else {
+    DBIE_TRY(ensure(c->vtmp, sizeof(double) * 3 * (size_t)c->nquad));
+    launch_finalize_vjp(c->nquad, plan, c->out.as<double>(), 1.0, c->vtmp.as<double>(), 0, s);
+    launch_q9_gather(c->vtmp.as<double>(), c->nx, c->ny, c->hx, c->hy, c->qi, gB0, accumulate, s);
+  }
+  CUDA_TRY(cudaGetLastError());
+  return DBIE_OK;
+}
+
 dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lambda,
                      const double* gB, const dbie_options* opt, int32_t mem_kind, double* gB0,
                      double* glam, int32_t accumulate, void* stream) {
@@ -714,9 +832,11 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
     DBIE_TRY(ensure(c->ptiles, (size_t)nptiles * VJP_NFIELD * TILE * (fp64 ? 8 : 4)));
     launch_pack_vjp(n, d_xyz, d_lam, d_gB, 0, nptiles, c->ptiles.as<float>(),
                     c->ptiles.as<double>(), fp64 ? 1 : 0, s);
-    const KernelRef k = vjp_ref(fp64, false, c->vjp_cfg);
+    const KernelRef k = (!fp64 && c->quad_g != 0) ? vjp_ref_split(false)
+                                                   : vjp_ref(fp64, false, c->vjp_cfg);
     const int grid = persistent_grid(k, c->device);
-    const int64_t nblk = (npix + k.qper - 1) / k.qper;
+    const int64_t nq = c->nquad;   // quadrature points (pixels, or element Gauss points)
+    const int64_t nblk = (nq + k.qper - 1) / k.qper;
     const int64_t target = 2LL * grid;
     int64_t nsplit = 1;
     if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, nptiles);
@@ -724,12 +844,12 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
     DBIE_TRY(ensure(c->out, sizeof(double) * nitems * 3 * k.qper));
     Misc* m = c->misc.as<Misc>();
     launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit,
-                       k.qper, (int)npix, s);
+                       k.qper, (int)nq, s);
     VjpArgs a{};
     a.ptiles32 = c->ptiles.as<float>();
     a.ptiles64 = c->ptiles.as<double>();
     a.nptiles = nptiles;
-    a.npix = (int32_t)npix;
+    a.npix = (int32_t)nq;
     a.btiles32 = c->t32.as<float>();
     a.btiles64 = c->t64.as<double>();
     a.plan = &m->plan;
@@ -746,11 +866,9 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
     if (c->profiling) {
       CUDA_TRY(cudaEventRecord(e1, s));
       c->pending.push_back({e0, e1});
-      c->pending_pairs.push_back((double)n * (double)npix);
+      c->pending_pairs.push_back((double)n * (double)nq);
     }
-    launch_finalize_vjp(npix, &m->plan, c->out.as<double>(), c->dA / TWO_PI, d_gB0,
-                        accumulate ? 1 : 0, s);
-    CUDA_TRY(cudaGetLastError());
+    DBIE_TRY(finalize_adjoint(c, &m->plan, d_gB0, accumulate ? 1 : 0, s));
     if (d_glam) {
       // dL/dlambda_p = gB_p * z lambda_p Sl_p, from a value + dB/dlambda pass.
       DBIE_TRY(pass_single(c, VAR_VL, fp64, o, n, d_xyz, nullptr, d_lam, s));
@@ -896,9 +1014,10 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
                             o.g_scale, o.w_g, c->ptiles.as<float>(), c->ptiles.as<double>(),
                             fp64 ? 1 : 0, d_v, d_fl, s);
     CUDA_TRY(cudaGetLastError());
-    const KernelRef k = vjp7_ref(fp64, tied);
+    const KernelRef k = (!fp64 && c->quad_g != 0) ? vjp7_ref_split(tied) : vjp7_ref(fp64, tied);
     const int grid = persistent_grid(k, c->device);
-    const int64_t nblk = (npix + k.qper - 1) / k.qper;
+    const int64_t nq = c->nquad;   // quadrature points (pixels, or element Gauss points)
+    const int64_t nblk = (nq + k.qper - 1) / k.qper;
     const int64_t target = 2LL * grid;
     int64_t nsplit = 1;
     if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, nptiles);
@@ -907,12 +1026,12 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
     // orders the reuse of c->out and of the plan block)
     DBIE_TRY(ensure(c->out, sizeof(double) * nitems * 3 * k.qper));
     launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit,
-                       k.qper, (int)npix, s);
+                       k.qper, (int)nq, s);
     VjpArgs a{};
     a.ptiles32 = c->ptiles.as<float>();
     a.ptiles64 = c->ptiles.as<double>();
     a.nptiles = nptiles;
-    a.npix = (int32_t)npix;
+    a.npix = (int32_t)nq;
     a.btiles32 = c->t32.as<float>();
     a.btiles64 = c->t64.as<double>();
     a.plan = &m->plan;
@@ -929,11 +1048,9 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
     if (c->profiling) {
       CUDA_TRY(cudaEventRecord(e1, s));
       c->pending.push_back({e0, e1});
-      c->pending_pairs.push_back((double)n * (double)npix);
+      c->pending_pairs.push_back((double)n * (double)nq);
     }
-    launch_finalize_vjp(npix, &m->plan, c->out.as<double>(), c->dA / TWO_PI, d_gB0,
-                        accumulate ? 1 : 0, s);
-    CUDA_TRY(cudaGetLastError());
+    DBIE_TRY(finalize_adjoint(c, &m->plan, d_gB0, accumulate ? 1 : 0, s));
   }
   if (mem_kind == DBIE_MEM_HOST) {
     CUDA_TRY(cudaMemcpyAsync(gB0, d_gB0, sizeof(double) * 3 * npix, cudaMemcpyDeviceToHost, s));
@@ -955,6 +1072,8 @@ dbie_status dbie_noise_var(dbie_ctx* c, int64_t n, const float* xyz, const doubl
   if (n > 0 && (!xyz || !lambda || !var))
     return fail(DBIE_EINVAL, "xyz, lambda and var must not be NULL");
   if (!std::isfinite(sigma0)) return fail(DBIE_EINVAL, "sigma0 must be finite");
+  if (c->quad_g != 0)
+    return fail(DBIE_EINVAL, "the noise variance needs the pixel-centre rule (dbie_set_quadrature 0)");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
   if (n == 0) return DBIE_OK;
@@ -1017,6 +1136,11 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   const bool fp64 = o.precision == DBIE_PREC_FP64;
   const bool tied = o.lambda_mode == DBIE_LAMBDA_TIED;
   const int dim = tied ? 1 : 3;
+  // one pair-sum kernel serves every problem: the FP32 tile layout must agree
+  for (int p = 1; p < nprob; ++p)
+    if ((ctxs[p]->quad_g != 0) != (c->quad_g != 0))
+      return fail(DBIE_EINVAL, "a batched solve needs all contexts on pixel centres or all on "
+                               "nine-node elements");
   // Per-problem offsets.
   std::vector<int64_t> pt_off(nprob + 1, 0);
   for (int p = 0; p < nprob; ++p) pt_off[p + 1] = pt_off[p] + n[p];
@@ -1065,19 +1189,14 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   std::vector<int> order(nprob), slot_of(nprob);
   for (int p = 0; p < nprob; ++p) order[p] = p;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b2) {
-    return (double)n[a] * ctxs[a]->npix > (double)n[b2] * ctxs[b2]->npix;
+    return (double)n[a] * ctxs[a]->nquad > (double)n[b2] * ctxs[b2]->nquad;
   });
   for (int q = 0; q < nprob; ++q) slot_of[order[q]] = q;
   std::vector<ProbDesc> pds(nprob);
   for (int p = 0; p < nprob; ++p) {
     dbie_ctx* cp = ctxs[p];
     ProbDesc& pd = pds[slot_of[p]];
-    pd = ProbDesc{};
-    pd.tiles32 = cp->t32.as<float>();
-    pd.tiles64 = cp->t64.as<double>();
-    pd.ntiles = cp->ntiles;
-    pd.nx = cp->nx; pd.ny = cp->ny;
-    pd.x0 = cp->x0; pd.y0 = cp->y0; pd.hx = cp->hx; pd.hy = cp->hy;
+    pd = desc_of(cp);
     const dbie_options op = resolved(cp, opt);   // size- and spacing-dependent defaults
     pd.step = op.simplex_step;
     pd.g_scale = op.g_scale;
@@ -1415,11 +1534,12 @@ dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
   const int pairs[9][2] = {{VAR_OBJ, 0},  {VAR_OBJ, 1},  {VAR_V, 0},    {VAR_VL, 0},
                            {VAR_OBJL, 0}, {VAR_OBJN, 0}, {VAR_OBJN, 1}, {VAR_HESS, 0},
                            {VAR_NV, 0}};
-  status = stage_variance(c, nullptr, nullptr, nullptr, 1.0, s);
+  if (c->quad_g == 0) status = stage_variance(c, nullptr, nullptr, nullptr, 1.0, s);
   for (const auto& vt : pairs) {
     if (status != DBIE_OK) break;
     const int var = vt[0], tied = vt[1];
-    const std::string key = tune_key(c->device, "g1", var, tied, c->npix);
+    if (var == VAR_NV && c->quad_g != 0) continue;   // noise variance: pixel-centre rule only
+    const std::string key = tune_key(c->device, "g1", var, tied, c->nquad);
     const int cached = tune_lookup(key);
     if (cached >= 0) {
       c->cfg[var][tied] = cached;
@@ -1439,7 +1559,7 @@ dbie_status dbie_autotune(dbie_ctx* c, void* stream) {
     if (status == DBIE_OK) tune_store(key, best);
   }
   {
-    const std::string key = tune_key(c->device, "vjp", 0, 0, c->npix);
+    const std::string key = tune_key(c->device, "vjp", 0, 0, c->nquad);
     const int cached = tune_lookup(key);
     if (cached >= 0) {
       c->vjp_cfg = cached;

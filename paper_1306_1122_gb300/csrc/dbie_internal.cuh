@@ -14,6 +14,10 @@ namespace dbie {
 
 constexpr int TILE = 256;            // pixels (or points, for the adjoint) per tile
 constexpr int NFIELD = 5;            // x, y, bx, by, bz
+// FP32 tiles of element Gauss points (Eq. 15) carry their positions as float pairs (hi + lo):
+// x, y, bx, by, bz, x_lo, y_lo.  The pair sums form x_i - x_k as (x_i - x_hi) - x_lo, so the
+// FP32 rounding of an irrational Gauss abscissa does not enter the kernel.
+constexpr int NFIELD_SPLIT = 7;
 constexpr int VJP_NFIELD = 9;        // x, y, z^2, lx, ly, lz, wx, wy, wz
 constexpr int VJP7_NW = 7;           // weights per component of the general adjoint (see VjpArgs)
 constexpr int VJP7_NFIELD = 6 + 3 * VJP7_NW;   // x, y, z^2, lx, ly, lz, 21 weights
@@ -70,13 +74,18 @@ struct __align__(32) Lam4 {
 __host__ __device__ inline Lam4 make_lam4(double x, double y, double z) { return Lam4{x, y, z, 0.0}; }
 
 // ------------------------------------------------------------------ problem and plan ----
+constexpr int MAX_GAUSS = 8;          // Gauss points per element side (Eq. 15 elements)
+
 struct ProbDesc {
-  const float* tiles32;     // tile-blocked float boundary
+  const float* tiles32;     // tile-blocked float boundary (quadrature points)
   const double* tiles64;    // tile-blocked double boundary
   int32_t ntiles;
-  int32_t nx, ny;
-  int32_t pad0;
-  double x0, y0, hx, hy;
+  int32_t nx, ny;           // quadrature-point grid: pixels, or (elements x quad_g) per side
+  int32_t quad_g;           // 0: pixel centres (Eq. 16); g: nine-node elements, g x g Gauss (Eq. 15)
+  int32_t near_w;           // near-field window half width in quadrature-point indices
+  int32_t nf32;             // fields per FP32 tile: NFIELD, or NFIELD_SPLIT (Gauss points)
+  double gx[MAX_GAUSS];     // Gauss abscissae on [-1, 1] (quad_g > 0)
+  double x0, y0, hx, hy;     // node (pixel-centre) origin and spacing
   double step;              // initial simplex edge of this problem's lambda search
   double g_scale;           // Delta V / Delta sigma of Eq. 9 for this problem
   double near_z;            // FP64 near field for z <= near_z (0: off)
@@ -270,10 +279,10 @@ struct Geom32 {
 };
 
 template <bool TIED>
-__device__ __forceinline__ Geom32 pair_geom32(const Query<float, TIED>& q, float px, float py) {
+__device__ __forceinline__ Geom32 pair_geom32_d(const Query<float, TIED>& q, float dx, float dy) {
   Geom32 g;
-  g.dx = __fsub_rn(q.x, px);
-  g.dy = __fsub_rn(q.y, py);
+  g.dx = dx;
+  g.dy = dy;
   const float r2 = __fmaf_rn(g.dx, g.dx, __fmaf_rn(g.dy, g.dy, q.z2));
   g.ri = rsqrt_mufu(r2);
   g.r = __fmul_rn(r2, g.ri);
@@ -281,6 +290,17 @@ __device__ __forceinline__ Geom32 pair_geom32(const Query<float, TIED>& q, float
   g.ri3 = __fmul_rn(ri2, g.ri);
   g.ri2x3 = __fmul_rn(3.f, ri2);
   return g;
+}
+template <bool TIED>
+__device__ __forceinline__ Geom32 pair_geom32(const Query<float, TIED>& q, float px, float py) {
+  return pair_geom32_d<TIED>(q, __fsub_rn(q.x, px), __fsub_rn(q.y, py));
+}
+// Same, for a pixel position given as a float pair (hi + lo).
+template <bool TIED>
+__device__ __forceinline__ Geom32 pair_geom32_split(const Query<float, TIED>& q, float px, float py,
+                                                    float pxl, float pyl) {
+  return pair_geom32_d<TIED>(q, __fsub_rn(__fsub_rn(q.x, px), pxl),
+                             __fsub_rn(__fsub_rn(q.y, py), pyl));
 }
 
 // Angular part: sin, cos of lambda r (SFU) and the factors of the sums.
@@ -332,6 +352,12 @@ __device__ __forceinline__ void pair_terms32(const Query<float, TIED>& q, float 
                                              const float b[3], Terms32<VAR, TIED>& t) {
   pair_angular32<VAR, TIED>(q, pair_geom32<TIED>(q, px, py), b, t);
 }
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_terms32_split(const Query<float, TIED>& q, float px, float py,
+                                                   float pxl, float pyl, const float b[3],
+                                                   Terms32<VAR, TIED>& t) {
+  pair_angular32<VAR, TIED>(q, pair_geom32_split<TIED>(q, px, py, pxl, pyl), b, t);
+}
 
 // FP64 terms (used by the FP64 form and by the near-field correction).
 template <int VAR, bool TIED>
@@ -371,10 +397,11 @@ __device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, doubl
   }
 }
 
-// Address of field f (0..4) of pixel k in a tile-blocked boundary.
+// Address of field f of pixel (quadrature point) k in a tile-blocked boundary of nf fields.
 template <typename Real>
-__device__ __forceinline__ const Real* tile_field(const Real* tiles, int64_t k, int f) {
-  return tiles + (k / TILE) * (int64_t)(NFIELD * TILE) + f * TILE + (k % TILE);
+__device__ __forceinline__ const Real* tile_field(const Real* tiles, int64_t k, int f,
+                                                  int nf = NFIELD) {
+  return tiles + (k / TILE) * (int64_t)(nf * TILE) + f * TILE + (k % TILE);
 }
 
 }  // namespace dbie

@@ -33,8 +33,22 @@ KernelRef g1_ref_f32(int var, bool tied, int cfg);   // pairsum_f32_*.cu
 KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
 KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
 KernelRef vjp7_ref(bool fp64, bool tied);            // vjp.cu (seven-weight adjoint)
+// FP32 form over element Gauss points with float-pair positions (pairsum_f32_split.cu)
+KernelRef g1_ref_f32_split(int var, bool tied);
+KernelRef vjp_ref_split(bool tied);
+KernelRef vjp7_ref_split(bool tied);
+
+// Gauss rule of the nine-node elements (Eq. 15): g points per side, abscissae and weights.
+struct QuadInfo {
+  int g;
+  double gx[MAX_GAUSS], gw[MAX_GAUSS];
+};
 
 // aux.cu
+void launch_stage_q9(const float* B0, int nx, int ny, double x0, double y0, double hx, double hy,
+                     const QuadInfo& qi, int ntiles, float* t32, double* t64, cudaStream_t s);
+void launch_q9_gather(const double* T, int nx, int ny, double hx, double hy, const QuadInfo& qi,
+                      double* gB0, int accumulate, cudaStream_t s);
 void launch_stage_boundary(const float* Bx, const float* By, const float* Bz, int nx, int ny,
                            double x0, double y0, double hx, double hy, double scale,
                            int ntiles, float* t32, double* t64, cudaStream_t s);

@@ -138,6 +138,7 @@ extern "C" dbie_status dbie_eval_noalloc(int32_t nx, int32_t ny, double x0, doub
   pd.ntiles = ntiles;
   pd.nx = nx;
   pd.ny = ny;
+  pd.near_w = NEAR_W;
   pd.x0 = x0; pd.y0 = y0; pd.hx = hx; pd.hy = hy;
   // Everything that must start at zero (counters, error word) is cleared here.
   if (cudaMemsetAsync(ctl, 0, sizeof(Ctl), s) != cudaSuccess ||

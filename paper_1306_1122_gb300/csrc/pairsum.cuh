@@ -188,13 +188,15 @@ __device__ __forceinline__ int find_problem(const int32_t* item_off, int nprob, 
 }
 
 // ---------------------------------------------------------------------------- g1 ----
-template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __device__ __forceinline__ void g1_body(const G1Args& a) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
   constexpr int Q = NT * P;
   constexpr int NWARP = NT / 32;
   constexpr bool F32 = sizeof(Real) == 4;
+  static_assert(!SPLIT || F32, "split positions are an FP32-form feature");
+  constexpr int NF = SPLIT ? NFIELD_SPLIT : NFIELD;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[NSTAGE];
@@ -204,7 +206,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 
   const int tid = threadIdx.x;
   TileRing<Real, NSTAGE, NWARP> ring{reinterpret_cast<Real*>(smem_raw), full_bar, empty_bar,
-                                     &s_abort, a.err, (uint32_t)(NFIELD * TILE), 0u, 0u};
+                                     &s_abort, a.err, (uint32_t)(NF * TILE), 0u, 0u};
   if (tid == 0) {
     ring.init_barriers();
     s_abort = 0;
@@ -269,6 +271,13 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
             const float4 BX = *reinterpret_cast<const float4*>(sx + 2 * TILE + k);
             const float4 BY = *reinterpret_cast<const float4*>(sx + 3 * TILE + k);
             const float4 BZ = *reinterpret_cast<const float4*>(sx + 4 * TILE + k);
+            float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL;
+            if constexpr (SPLIT) {
+              XL = *reinterpret_cast<const float4*>(sx + 5 * TILE + k);
+              YL = *reinterpret_cast<const float4*>(sx + 6 * TILE + k);
+            }
+            const float pxl[4] = {XL.x, XL.y, XL.z, XL.w};
+            const float pyl[4] = {YL.x, YL.y, YL.z, YL.w};
             const float px[4] = {X.x, X.y, X.z, X.w};
             const float py[4] = {Y.x, Y.y, Y.z, Y.w};
             const float bx[4] = {BX.x, BX.y, BX.z, BX.w};
@@ -280,7 +289,9 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
             for (int e = 0; e < 4; ++e)
 #pragma unroll
-              for (int u = 0; u < P; ++u) gm[e][u] = pair_geom32<TIED>(q[u], px[e], py[e]);
+              for (int u = 0; u < P; ++u)
+                gm[e][u] = SPLIT ? pair_geom32_split<TIED>(q[u], px[e], py[e], pxl[e], pyl[e])
+                                 : pair_geom32<TIED>(q[u], px[e], py[e]);
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float b[3] = {bx[e], by[e], bz[e]};
@@ -298,7 +309,10 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
               for (int u = 0; u < P; ++u) {
                 Terms32<VAR, TIED> tm;
-                pair_terms32<VAR, TIED>(q[u], px[e], py[e], b, tm);
+                if constexpr (SPLIT)
+                  pair_terms32_split<VAR, TIED>(q[u], px[e], py[e], pxl[e], pyl[e], b, tm);
+                else
+                  pair_terms32<VAR, TIED>(q[u], px[e], py[e], b, tm);
                 accumulate32<VAR, TIED, NS>(acc[u], tm, b);
               }
             }
@@ -342,12 +356,13 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 // --------------------------------------------------------------------------- vjp ----
 
 
-template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
   constexpr int Q = NT * P;
   constexpr int NWARP = NT / 32;
   constexpr bool F32 = sizeof(Real) == 4;
   constexpr int NL = TIED ? 1 : 3;
+  constexpr int NF = SPLIT ? NFIELD_SPLIT : NFIELD;   // fields of the boundary (pixel) tiles
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[NSTAGE];
@@ -380,7 +395,7 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
     const int t0 = (int)(((int64_t)sp * a.nptiles) / plan.nsplit);
     const int t1 = (int)(((int64_t)(sp + 1) * a.nptiles) / plan.nsplit);
 
-    Real px[P], py[P];
+    Real px[P], py[P], pxl[P], pyl[P];
     bool valid[P];
     int kpix[P];
 #pragma unroll
@@ -388,8 +403,10 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
       kpix[u] = blk * Q + tid + u * NT;
       valid[u] = kpix[u] < a.npix;
       const int k = valid[u] ? kpix[u] : 0;
-      px[u] = *tile_field(btiles, k, 0);
-      py[u] = *tile_field(btiles, k, 1);
+      px[u] = *tile_field(btiles, k, 0, NF);
+      py[u] = *tile_field(btiles, k, 1, NF);
+      pxl[u] = SPLIT ? *tile_field(btiles, k, 5, NF) : Real(0);
+      pyl[u] = SPLIT ? *tile_field(btiles, k, 6, NF) : Real(0);
     }
     Real acc[P][3];
     float hi[F32 ? P : 1][3];
@@ -419,7 +436,11 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
             const float w[3] = {W[k], W[TILE + k], W[2 * TILE + k]};
 #pragma unroll
             for (int u = 0; u < P; ++u) {
-              const float dx = __fsub_rn(px[u], xi), dy = __fsub_rn(py[u], yi);
+              float dx = __fsub_rn(px[u], xi), dy = __fsub_rn(py[u], yi);
+              if constexpr (SPLIT) {
+                dx = __fadd_rn(dx, pxl[u]);
+                dy = __fadd_rn(dy, pyl[u]);
+              }
               const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, z2));
               const float ri = rsqrt_mufu(r2);
               const float r = __fmul_rn(r2, ri);
@@ -489,12 +510,13 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
 // phi = u / r^3, psi = (lambda^2 cos(lambda r) - 3 u / r^2) / r^3, dx = x_i - x_k, dy = y_i - y_k,
 // with the seven weights W_m of point i and component p in its record (VJP7_NFIELD fields:
 // x, y, z^2, lambda_x, lambda_y, lambda_z, then W[p * 7 + m]).
-template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
   constexpr int Q = NT * P;
   constexpr int NWARP = NT / 32;
   constexpr bool F32 = sizeof(Real) == 4;
   constexpr int NL = TIED ? 1 : 3;
+  constexpr int NF = SPLIT ? NFIELD_SPLIT : NFIELD;
 
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[NSTAGE];
@@ -527,15 +549,17 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
     const int t0 = (int)(((int64_t)sp * a.nptiles) / plan.nsplit);
     const int t1 = (int)(((int64_t)(sp + 1) * a.nptiles) / plan.nsplit);
 
-    Real px[P], py[P];
+    Real px[P], py[P], pxl[P], pyl[P];
     bool valid[P];
 #pragma unroll
     for (int u = 0; u < P; ++u) {
       const int kp = blk * Q + tid + u * NT;
       valid[u] = kp < a.npix;
       const int k = valid[u] ? kp : 0;
-      px[u] = *tile_field(btiles, k, 0);
-      py[u] = *tile_field(btiles, k, 1);
+      px[u] = *tile_field(btiles, k, 0, NF);
+      py[u] = *tile_field(btiles, k, 1, NF);
+      pxl[u] = SPLIT ? *tile_field(btiles, k, 5, NF) : Real(0);
+      pyl[u] = SPLIT ? *tile_field(btiles, k, 6, NF) : Real(0);
     }
     Real acc[P][3];
     float hi[F32 ? P : 1][3];
@@ -567,7 +591,11 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
             }
 #pragma unroll
             for (int u = 0; u < P; ++u) {
-              const float dx = __fsub_rn(xi, px[u]), dy = __fsub_rn(yi, py[u]);
+              float dx = __fsub_rn(xi, px[u]), dy = __fsub_rn(yi, py[u]);
+              if constexpr (SPLIT) {
+                dx = __fsub_rn(dx, pxl[u]);
+                dy = __fsub_rn(dy, pyl[u]);
+              }
               const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, z2));
               const float ri = rsqrt_mufu(r2);
               const float r = __fmul_rn(r2, ri);
@@ -654,25 +682,25 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
 
 // Kernel entry points.  MINB > 1 caps registers so that MINB CTAs fit on an SM; MINB = 1 leaves
 // the register allocation to the compiler (a plain __launch_bounds__(NT)).
-template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
-  g1_body<Real, VAR, TIED, P, NT, NSTAGE>(a);
+  g1_body<Real, VAR, TIED, P, NT, NSTAGE, SPLIT>(a);
 }
 template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(NT, MINB) g1_kernel_mb(const G1Args a) {
   g1_body<Real, VAR, TIED, P, NT, NSTAGE>(a);
 }
-template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {
-  vjp_body<Real, TIED, P, NT, NSTAGE>(a);
+  vjp_body<Real, TIED, P, NT, NSTAGE, SPLIT>(a);
 }
 template <typename Real, bool TIED, int P, int NT, int NSTAGE, int MINB>
 __global__ void __launch_bounds__(NT, MINB) vjp_kernel_mb(const VjpArgs a) {
   vjp_body<Real, TIED, P, NT, NSTAGE>(a);
 }
-template <typename Real, bool TIED, int P, int NT, int NSTAGE>
+template <typename Real, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __global__ void __launch_bounds__(NT) vjp7_kernel(const VjpArgs a) {
-  vjp7_body<Real, TIED, P, NT, NSTAGE>(a);
+  vjp7_body<Real, TIED, P, NT, NSTAGE, SPLIT>(a);
 }
 
 }  // namespace dbie

@@ -170,6 +170,11 @@ class DBIEField:
                    _ptr(gl), int(acc), _stream())
         return gB0, gl
 
+    def set_quadrature(self, order: int):
+        """0: midpoint rule at pixel centres (Eq. 16); g in 1..8: nine-node elements with g x g
+        Gauss points (Eq. 15; nx, ny odd)."""
+        N.dbie_set_quadrature(self._h, int(order), _stream())
+
     def hessian(self, xyz, lam, options: Options | None = None):
         """Phi (n,), dPhi/dlambda (n, 3) and the lambda-Hessian (n, 3, 3) at fixed lambda (tied
         mode: the derivatives along the shared lambda in entry 0)."""
