@@ -132,8 +132,9 @@ def box_scale(nx: int) -> float:
     return nx / 2.0
 
 
-def to_box(nx: int, ny: int, xpx, ypx, zpx):
-    """Pixel coordinates (pixel (i, j) centred at (i, j), z in pixels) to box coordinates."""
-    s = box_scale(nx)
+def to_box(nx: int, ny: int, xpx, ypx, zpx, scale: float | None = None):
+    """Pixel coordinates (pixel (i, j) centred at (i, j), z in pixels) to box coordinates, with
+    the magnetogram centred on the box origin and `scale` pixels per unit (default nx / 2)."""
+    s = box_scale(nx) if scale is None else scale
     return ((np.asarray(xpx) - (nx - 1) / 2.0) / s, (np.asarray(ypx) - (ny - 1) / 2.0) / s,
             np.asarray(zpx) / s)

@@ -7,6 +7,10 @@
               (2i, 2j, k + 1), i < 256, j < 128, k < 64 (2,097,152 points).
   batch64     64 magnetograms of side U{32..256} (seed 4), 1-4 patches each, 1k-200k points each.
   ar1024      1024 x 512, 6 patches (seed 5), traced field-line samples plus a 128^3 grid.
+  table1      Low & Lou (n=3, m=1, l=0.3, Phi=4 pi/5) on 192 x 192 pixels, 32 pixels per unit,
+              so that the central 64 x 64 x 64 test region is the unit box [-1, 1]^2 x [0, 2]
+              (the paper's Table 1 case after Schrijver et al. 2006); points: the test region's
+              pixel grid at z = 1..63 (258,048; the z = 0 layer is the boundary data itself).
 
 Coordinates are in pixels: pixel (i, j) is centred at (i, j), pixel area 1.
 This module holds none of the DBIE arithmetic.
@@ -31,10 +35,12 @@ class Workload:
     meta: dict = field(default_factory=dict)
 
 
-def lowlou_magnetogram(nx: int, ll: LowLou | None = None) -> Magnetogram:
+def lowlou_magnetogram(nx: int, ll: LowLou | None = None, scale: float | None = None) -> Magnetogram:
+    """nx x nx pixels centred on the source; `scale` pixels per box unit (default nx / 2: the box
+    [-1, 1]^2 spans the magnetogram)."""
     ll = ll or LowLou()
     j, i = np.mgrid[0:nx, 0:nx].astype(np.float64)
-    bx, by, bz = to_box(nx, nx, i, j, np.zeros_like(i))
+    bx, by, bz = to_box(nx, nx, i, j, np.zeros_like(i), scale)
     B = ll.field(bx, by, bz)
     f32 = lambda a: np.ascontiguousarray(a, dtype=np.float32)
     return Magnetogram(nx, nx, f32(B[..., 0]), f32(B[..., 1]), f32(B[..., 2]))
@@ -92,6 +98,26 @@ def batch64(seed: int = 4, nprob: int = 64, max_points: int = 200_000):
                         rng.uniform(1, 64, ne)], axis=1).astype(np.float32)
         out.append(Workload(f"batch64[{p}]", mag, pts, meta=dict(side=n, patches=npatch)))
     return out
+
+
+def table1(nx: int = 192, scale: float = 32.0, nz: int = 63) -> Workload:
+    """The paper's Table 1 case (Low & Lou n=3, m=1, l=0.3, Phi=4 pi/5).  nx = 193 gives the same
+    field on the odd node grid that nine-node elements need (nodes at the same spacing, the
+    source at the centre node); points keep their physical positions."""
+    ll = LowLou(3, 1, 0.3, 4 * np.pi / 5)
+    mag = lowlou_magnetogram(nx, ll, scale)
+    # the central 64 x 64 pixels of the 192 grid, at the same box positions for any nx
+    c192 = (192 - 1) / 2.0
+    xs = np.arange(64, 128) - c192 + (nx - 1) / 2.0
+    pts = grid_points(xs, xs, range(1, nz + 1))
+    bx, by, bz = to_box(nx, nx, pts[:, 0], pts[:, 1], pts[:, 2], scale)
+    truth = ll.field(bx, by, bz)
+    # the z = 0 layer of the test region: its boundary data and the analytic field there
+    bottom = grid_points(xs, xs, [0.0])
+    b0x, b0y, b0z = to_box(nx, nx, bottom[:, 0], bottom[:, 1], bottom[:, 2], scale)
+    return Workload("table1", mag, pts, truth, None,
+                    dict(field="lowlou n=3 m=1 l=0.3 Phi=4pi/5", scale=scale,
+                         bottom=bottom, bottom_truth=ll.field(b0x, b0y, b0z)))
 
 
 def ar1024(nsamples: int = 4_194_304, grid: bool = True, seed: int = 5) -> Workload:

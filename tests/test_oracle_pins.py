@@ -231,11 +231,13 @@ def test_objective_special_cases(oracle_lib):
     assert np.allclose(phi, f + 2.0 * g)
 
 
-def test_lowlou_field_satisfies_force_free_conditions(oracle_lib):
+@pytest.mark.parametrize("n,Phi", [(1, np.pi / 4), (3, 4 * np.pi / 5)])
+def test_lowlou_field_satisfies_force_free_conditions(oracle_lib, n, Phi):
     """The generator's Low & Lou field gives f ~ 0, g ~ 0 through the oracle's Eq. 8/9 when its
-    gradient is taken by central differences (checks the test field and the objective together)."""
+    gradient is taken by central differences (checks the test field and the objective together);
+    n = 1 is the workloads' case, n = 3, Phi = 4 pi / 5 the case of the paper's Table 1."""
     from synth import LowLou
-    ll = LowLou()
+    ll = LowLou(n, 1, 0.3, Phi)
     P = np.array([[0.1, -0.2, 0.3], [-0.4, 0.5, 0.2], [0.3, 0.3, 0.6]])
     h = 1e-5
     G = np.zeros((len(P), 3, 3))
