@@ -26,6 +26,7 @@ UNITS = {
     "second_order.cu": ["-fmad=false"],
     "pairsum_f32_val.cu": [],
     "pairsum_f32_obj.cu": [],
+    "pairsum_f32_objl.cu": [],
     "pairsum_f32_newton.cu": [],
     "pairsum_f32_hess.cu": [],
     "pairsum_f32_nv.cu": [],

@@ -272,10 +272,12 @@ int var_of(bool grad, bool dlam) {
   return grad ? (dlam ? VAR_OBJL : VAR_OBJ) : (dlam ? VAR_VL : VAR_V);
 }
 
-KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64) {
+// rows < 0: from this context's quadrature-point grid (aligned groups of 4 on one row).
+KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64, int rows = -1) {
   if (fp64) return g1_ref_f64(var, tied);
-  if (c->quad_g != 0) return g1_ref_f32_split(var, tied);   // element Gauss points
-  return g1_ref_f32(var, tied, c->cfg[var][tied ? 1 : 0]);
+  const bool r = rows < 0 ? (c->qnx % 4 == 0) : rows != 0;
+  if (c->quad_g != 0) return g1_ref_f32_split(var, tied, r);   // element Gauss points
+  return g1_ref_f32(var, tied, c->cfg[var][tied ? 1 : 0], r);
 }
 
 // One pair-sum pass over n queries of this context (single problem): pack, plan, sweep,
@@ -1157,7 +1159,9 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   const bool qn = o.method == DBIE_METHOD_QUASI_NEWTON;
   const int var = qn ? VAR_OBJN : VAR_OBJ;            // quasi-Newton needs the gradient sums
   const int nsum = 3 * nsum_per_comp(var);
-  const KernelRef k = g1_ref(c, var, tied, fp64);
+  bool rows_all = true;   // one kernel for all problems: rows only if every grid allows it
+  for (int p = 0; p < nprob; ++p) rows_all &= ctxs[p]->qnx % 4 == 0;
+  const KernelRef k = g1_ref(c, var, tied, fp64, rows_all ? 1 : 0);
   const int grid = persistent_grid(k, c->device);
   const int target = 2 * grid;
   const int64_t items_cap = std::max<int64_t>((Qcap + k.qper - 1) / k.qper + nprob, 2LL * target) + 1;

@@ -253,6 +253,86 @@ __device__ __forceinline__ Query<Real, TIED> make_query(float4 pos, Lam4 lam) {
   return q;
 }
 
+// ---------------------------------------------------------------- FP32 lanes ----
+// The FP32 pair terms are written once for a "lane" type V: float (one pixel), or f32x2 (two
+// pixels packed in a 64-bit register pair, PTX add/sub/mul/fma.rn.f32x2).  Every packed operation
+// rounds each lane exactly like its scalar counterpart, so a packed term equals the scalar one bit
+// for bit; the SFU operations (rsqrt, sin, cos) act lane by lane.  The packed form issues one
+// instruction for two pixels' FP32 arithmetic.
+struct f32x2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f32x2 pack2(float a, float b) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v));
+}
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ f32x2 vadd(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 vsub(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 vmul(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f32x2 vfma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ float vsin(float x) { return sin_mufu(x); }
+__device__ __forceinline__ float vcos(float x) { return cos_mufu(x); }
+__device__ __forceinline__ float vrsqrt(float x) { return rsqrt_mufu(x); }
+__device__ __forceinline__ f32x2 vsin(f32x2 x) {
+  float a, b;
+  unpack2(x, a, b);
+  return pack2(sin_mufu(a), sin_mufu(b));
+}
+__device__ __forceinline__ f32x2 vcos(f32x2 x) {
+  float a, b;
+  unpack2(x, a, b);
+  return pack2(cos_mufu(a), cos_mufu(b));
+}
+__device__ __forceinline__ f32x2 vrsqrt(f32x2 x) {
+  float a, b;
+  unpack2(x, a, b);
+  return pack2(rsqrt_mufu(a), rsqrt_mufu(b));
+}
+template <typename V>
+__device__ __forceinline__ V vconst(float a) {
+  if constexpr (sizeof(V) == 4) return a;
+  else return pack2(a, a);
+}
+
+// A query with every member in both lanes.
+template <bool TIED>
+__device__ __forceinline__ Query<f32x2, TIED> splat_query(const Query<float, TIED>& q) {
+  Query<f32x2, TIED> r;
+  r.x = pack2(q.x, q.x);
+  r.y = pack2(q.y, q.y);
+  r.z2 = pack2(q.z2, q.z2);
+#pragma unroll
+  for (int p = 0; p < (TIED ? 1 : 3); ++p) {
+    r.l[p] = pack2(q.l[p], q.l[p]);
+    r.l2[p] = pack2(q.l2[p], q.l2[p]);
+  }
+  return r;
+}
+
 // Per-pair factors of the FP32 form.  The running sums take them as
 //   S0 += u * rb (fused), S1 += t1, Sx += t1 * dx (fused), Sy += t1 * dy (fused),
 //   Sl += cr * b (fused),  with rb = b / r^3, t1 = psi b = (lambda^2 c - 3 u / r^2) rb, cr = c / r,
@@ -260,36 +340,54 @@ __device__ __forceinline__ Query<Real, TIED> make_query(float4 pos, Lam4 lam) {
 // is computed with an explicit rounding so that the near-field kernel, which replaces these
 // contributions by FP64 ones, reproduces them bit for bit (a product of two FP32 values is exact
 // in FP64).
+template <typename V, int VAR, bool TIED>
+struct TermsV {
+  V dx, dy;
+  V u[TIED ? 1 : 3];
+  V rb[3];
+  V t1[has_grad(VAR) ? 3 : 1];
+  V cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
+  V t0[has_newton(VAR) || is_nv(VAR) ? 3 : 1];  // phi b = u rb (rounded): Tx, Ty; phi s (NV)
+  V sn[has_hess(VAR) ? (TIED ? 1 : 3) : 1];      // sin(lambda r), the factor of Q
+  V tl[has_hess(VAR) ? 3 : 1];                   // cos(lambda r) b / r (rounded): Ux, Uy
+  V ph[is_nv(VAR) ? (TIED ? 1 : 3) : 1];         // phi = u / r^3 (rounded)
+};
 template <int VAR, bool TIED>
-struct Terms32 {
-  float dx, dy;
-  float u[TIED ? 1 : 3];
-  float rb[3];
-  float t1[has_grad(VAR) ? 3 : 1];
-  float cr[has_dlam(VAR) ? (TIED ? 1 : 3) : 1];
-  float t0[has_newton(VAR) || is_nv(VAR) ? 3 : 1];  // phi b = u rb (rounded): Tx, Ty; phi s (NV)
-  float sn[has_hess(VAR) ? (TIED ? 1 : 3) : 1];      // sin(lambda r), the factor of Q
-  float tl[has_hess(VAR) ? 3 : 1];                   // cos(lambda r) b / r (rounded): Ux, Uy
-  float ph[is_nv(VAR) ? (TIED ? 1 : 3) : 1];         // phi = u / r^3 (rounded)
-};
+using Terms32 = TermsV<float, VAR, TIED>;
 
-// Geometry of one pair: dx, dy, r, 1/r^2 (times 3) and 1/r^3 (SFU rsqrt).
-struct Geom32 {
-  float dx, dy, r, ri, ri2x3, ri3;
+// Geometry of one pair: dx, dy, r, -3/r^2 and 1/r^3 (SFU rsqrt).
+template <typename V>
+struct GeomV {
+  V dx, dy, r, ri, m3ri2, ri3;
 };
+using Geom32 = GeomV<float>;
 
-template <bool TIED>
-__device__ __forceinline__ Geom32 pair_geom32_d(const Query<float, TIED>& q, float dx, float dy) {
-  Geom32 g;
+// From dx, dy and dyz = dy^2 + z^2 (rounded as fma(dy, dy, z^2)): pixels of one boundary row
+// share dy and dyz, so a group of them computes these once (same bits as per pixel).
+template <typename V>
+__device__ __forceinline__ GeomV<V> pair_geomv_dz(V dx, V dy, V dyz) {
+  GeomV<V> g;
   g.dx = dx;
   g.dy = dy;
-  const float r2 = __fmaf_rn(g.dx, g.dx, __fmaf_rn(g.dy, g.dy, q.z2));
-  g.ri = rsqrt_mufu(r2);
-  g.r = __fmul_rn(r2, g.ri);
-  const float ri2 = __fmul_rn(g.ri, g.ri);
-  g.ri3 = __fmul_rn(ri2, g.ri);
-  g.ri2x3 = __fmul_rn(3.f, ri2);
+  const V r2 = vfma(g.dx, g.dx, dyz);
+  g.ri = vrsqrt(r2);
+  g.r = vmul(r2, g.ri);
+  const V ri2 = vmul(g.ri, g.ri);
+  g.ri3 = vmul(ri2, g.ri);
+  g.m3ri2 = vmul(vconst<V>(-3.f), ri2);
   return g;
+}
+template <typename V, bool TIED>
+__device__ __forceinline__ GeomV<V> pair_geomv_d(const Query<V, TIED>& q, V dx, V dy) {
+  return pair_geomv_dz<V>(dx, dy, vfma(dy, dy, q.z2));
+}
+template <bool TIED>
+__device__ __forceinline__ Geom32 pair_geom32_dz(float dx, float dy, float dyz) {
+  return pair_geomv_dz<float>(dx, dy, dyz);
+}
+template <bool TIED>
+__device__ __forceinline__ Geom32 pair_geom32_d(const Query<float, TIED>& q, float dx, float dy) {
+  return pair_geomv_d<float, TIED>(q, dx, dy);
 }
 template <bool TIED>
 __device__ __forceinline__ Geom32 pair_geom32(const Query<float, TIED>& q, float px, float py) {
@@ -304,47 +402,53 @@ __device__ __forceinline__ Geom32 pair_geom32_split(const Query<float, TIED>& q,
 }
 
 // Angular part: sin, cos of lambda r (SFU) and the factors of the sums.
-template <int VAR, bool TIED>
-__device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, const Geom32& g,
-                                               const float b[3], Terms32<VAR, TIED>& t) {
+template <typename V, int VAR, bool TIED>
+__device__ __forceinline__ void pair_angularv(const Query<V, TIED>& q, const GeomV<V>& g,
+                                              const V b[3], TermsV<V, VAR, TIED>& t) {
   t.dx = g.dx;
   t.dy = g.dy;
 #pragma unroll
-  for (int p = 0; p < 3; ++p) t.rb[p] = __fmul_rn(g.ri3, b[p]);
+  for (int p = 0; p < 3; ++p) t.rb[p] = vmul(g.ri3, b[p]);
 #pragma unroll
   for (int p = 0; p < (TIED ? 1 : 3); ++p) {
-    const float th = __fmul_rn(q.l[p], g.r);
-    const float s = sin_mufu(th), c = cos_mufu(th);
-    t.u[p] = __fmaf_rn(th, s, c);
-    if constexpr (is_nv(VAR)) t.ph[p] = __fmul_rn(t.u[p], g.ri3);
+    const V th = vmul(q.l[p], g.r);
+    const V s = vsin(th), c = vcos(th);
+    t.u[p] = vfma(th, s, c);
+    if constexpr (is_nv(VAR)) t.ph[p] = vmul(t.u[p], g.ri3);
     if constexpr (has_hess(VAR)) t.sn[p] = s;
     if constexpr (has_newton(VAR) || is_nv(VAR)) {
       if constexpr (TIED) {
 #pragma unroll
-        for (int pp = 0; pp < 3; ++pp) t.t0[pp] = __fmul_rn(t.u[0], t.rb[pp]);
+        for (int pp = 0; pp < 3; ++pp) t.t0[pp] = vmul(t.u[0], t.rb[pp]);
       } else {
-        t.t0[p] = __fmul_rn(t.u[p], t.rb[p]);
+        t.t0[p] = vmul(t.u[p], t.rb[p]);
       }
     }
     if constexpr (has_grad(VAR)) {
-      const float w = __fmaf_rn(-t.u[p], g.ri2x3, __fmul_rn(q.l2[p], c));
+      // w = lambda^2 c - 3 u / r^2, as fma(u, -3 / r^2, lambda^2 c)
+      const V w = vfma(t.u[p], g.m3ri2, vmul(q.l2[p], c));
       if constexpr (TIED) {
 #pragma unroll
-        for (int pp = 0; pp < 3; ++pp) t.t1[pp] = __fmul_rn(w, t.rb[pp]);
+        for (int pp = 0; pp < 3; ++pp) t.t1[pp] = vmul(w, t.rb[pp]);
       } else {
-        t.t1[p] = __fmul_rn(w, t.rb[p]);
+        t.t1[p] = vmul(w, t.rb[p]);
       }
     }
-    if constexpr (has_dlam(VAR)) t.cr[p] = __fmul_rn(c, g.ri);
+    if constexpr (has_dlam(VAR)) t.cr[p] = vmul(c, g.ri);
     if constexpr (has_hess(VAR)) {
       if constexpr (TIED) {
 #pragma unroll
-        for (int pp = 0; pp < 3; ++pp) t.tl[pp] = __fmul_rn(t.cr[0], b[pp]);
+        for (int pp = 0; pp < 3; ++pp) t.tl[pp] = vmul(t.cr[0], b[pp]);
       } else {
-        t.tl[p] = __fmul_rn(t.cr[p], b[p]);
+        t.tl[p] = vmul(t.cr[p], b[p]);
       }
     }
   }
+}
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_angular32(const Query<float, TIED>& q, const Geom32& g,
+                                               const float b[3], Terms32<VAR, TIED>& t) {
+  pair_angularv<float, VAR, TIED>(q, g, b, t);
 }
 
 template <int VAR, bool TIED>

@@ -29,12 +29,13 @@ struct KernelRef {
   size_t smem;        // dynamic shared memory bytes
 };
 
-KernelRef g1_ref_f32(int var, bool tied, int cfg);   // pairsum_f32_*.cu
+// rows: every aligned group of 4 quadrature points lies on one row (row length % 4 == 0)
+KernelRef g1_ref_f32(int var, bool tied, int cfg, bool rows);   // pairsum_f32_*.cu
 KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
 KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
 KernelRef vjp7_ref(bool fp64, bool tied);            // vjp.cu (seven-weight adjoint)
 // FP32 form over element Gauss points with float-pair positions (pairsum_f32_split.cu)
-KernelRef g1_ref_f32_split(int var, bool tied);
+KernelRef g1_ref_f32_split(int var, bool tied, bool rows);
 KernelRef vjp_ref_split(bool tied);
 KernelRef vjp7_ref_split(bool tied);
 

@@ -90,7 +90,7 @@ extern "C" dbie_status dbie_eval_noalloc(int32_t nx, int32_t ny, double x0, doub
 
   // Set-up, once per device, with that device current: the device address of the scratch array
   // (host code may not use the symbol itself) and the value kernel's resident grid.
-  const KernelRef k = g1_ref_f32(VAR_V, false, 0);
+  const KernelRef k = g1_ref_f32(VAR_V, false, 0, false);
   char* base = nullptr;
   int grid = 0;
   {

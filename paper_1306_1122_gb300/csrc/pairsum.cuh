@@ -30,6 +30,9 @@ namespace dbie {
 #ifndef DBIE_GROUP_UNROLL
 #define DBIE_GROUP_UNROLL 8
 #endif
+#ifndef DBIE_PACKED
+#define DBIE_PACKED 1     // FP32 pair sums on pixel pairs packed in f32x2 (0: one pixel per op)
+#endif
 constexpr int SUB = DBIE_FOLD_PIXELS;  // elements summed in plain FP32 before a compensated fold
 constexpr int GROUP_UNROLL = DBIE_GROUP_UNROLL;  // 4-pixel groups unrolled within a block
 
@@ -114,31 +117,35 @@ __device__ __forceinline__ void sweep_tiles(TileRing<Elem, NSTAGE, NWARP>& ring,
   }
 }
 
-template <int VAR, bool TIED, int NS>
-__device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED>& t,
-                                             const float b[3]) {
+template <typename V, int VAR, bool TIED, int NS>
+__device__ __forceinline__ void accumulatev(V* acc, const TermsV<V, VAR, TIED>& t, const V b[3]) {
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int lp = TIED ? 0 : p;
-    if constexpr (is_nv(VAR)) acc[p * NS + 0] = __fmaf_rn(t.ph[lp], t.t0[p], acc[p * NS + 0]);
-    else acc[p * NS + 0] = __fmaf_rn(t.u[lp], t.rb[p], acc[p * NS + 0]);
+    if constexpr (is_nv(VAR)) acc[p * NS + 0] = vfma(t.ph[lp], t.t0[p], acc[p * NS + 0]);
+    else acc[p * NS + 0] = vfma(t.u[lp], t.rb[p], acc[p * NS + 0]);
     if constexpr (has_grad(VAR)) {
-      acc[p * NS + 1] = __fadd_rn(acc[p * NS + 1], t.t1[p]);
-      acc[p * NS + 2] = __fmaf_rn(t.t1[p], t.dx, acc[p * NS + 2]);
-      acc[p * NS + 3] = __fmaf_rn(t.t1[p], t.dy, acc[p * NS + 3]);
+      acc[p * NS + 1] = vadd(acc[p * NS + 1], t.t1[p]);
+      acc[p * NS + 2] = vfma(t.t1[p], t.dx, acc[p * NS + 2]);
+      acc[p * NS + 3] = vfma(t.t1[p], t.dy, acc[p * NS + 3]);
     }
     if constexpr (has_dlam(VAR))
-      acc[p * NS + idx_sl(VAR)] = __fmaf_rn(t.cr[lp], b[p], acc[p * NS + idx_sl(VAR)]);
+      acc[p * NS + idx_sl(VAR)] = vfma(t.cr[lp], b[p], acc[p * NS + idx_sl(VAR)]);
     if constexpr (has_newton(VAR)) {
-      acc[p * NS + IDX_TX] = __fmaf_rn(t.t0[p], t.dx, acc[p * NS + IDX_TX]);
-      acc[p * NS + IDX_TY] = __fmaf_rn(t.t0[p], t.dy, acc[p * NS + IDX_TY]);
+      acc[p * NS + IDX_TX] = vfma(t.t0[p], t.dx, acc[p * NS + IDX_TX]);
+      acc[p * NS + IDX_TY] = vfma(t.t0[p], t.dy, acc[p * NS + IDX_TY]);
     }
     if constexpr (has_hess(VAR)) {
-      acc[p * NS + IDX_Q] = __fmaf_rn(t.sn[lp], b[p], acc[p * NS + IDX_Q]);
-      acc[p * NS + IDX_UX] = __fmaf_rn(t.tl[p], t.dx, acc[p * NS + IDX_UX]);
-      acc[p * NS + IDX_UY] = __fmaf_rn(t.tl[p], t.dy, acc[p * NS + IDX_UY]);
+      acc[p * NS + IDX_Q] = vfma(t.sn[lp], b[p], acc[p * NS + IDX_Q]);
+      acc[p * NS + IDX_UX] = vfma(t.tl[p], t.dx, acc[p * NS + IDX_UX]);
+      acc[p * NS + IDX_UY] = vfma(t.tl[p], t.dy, acc[p * NS + IDX_UY]);
     }
   }
+}
+template <int VAR, bool TIED, int NS>
+__device__ __forceinline__ void accumulate32(float* acc, const Terms32<VAR, TIED>& t,
+                                             const float b[3]) {
+  accumulatev<float, VAR, TIED, NS>(acc, t, b);
 }
 
 template <int VAR, bool TIED, int NS>
@@ -168,10 +175,11 @@ __device__ __forceinline__ void accumulate64(double* acc, const Terms64<VAR, TIE
 // Fold a plain FP32 block sum `a` into the running sum `hi` with an error-free two-sum; the
 // rounding error of the fold becomes the starting value of the next block's sum (so it is not
 // lost), and hi + a is the compensated total at any time.
-__device__ __forceinline__ void fold2(float& hi, float& a) {
-  const float s = __fadd_rn(hi, a);
-  const float bp = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(a, bp));
+template <typename V>
+__device__ __forceinline__ void fold2(V& hi, V& a) {
+  const V s = vadd(hi, a);
+  const V bp = vsub(s, hi);
+  const V e = vadd(vsub(hi, vsub(s, bp)), vsub(a, bp));
   hi = s;
   a = e;
 }
@@ -188,7 +196,10 @@ __device__ __forceinline__ int find_problem(const int32_t* item_off, int nprob, 
 }
 
 // ---------------------------------------------------------------------------- g1 ----
-template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
+// ROWS: every aligned group of 4 tile pixels lies on one boundary row (the host checks that the
+// quadrature-point grid's row length is a multiple of 4), so dy and dy^2 + z^2 are per group.
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false,
+          bool ROWS = false>
 __device__ __forceinline__ void g1_body(const G1Args& a) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
@@ -252,16 +263,81 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 
     Real acc[P][NSUM];
     float hi[F32 ? P : 1][F32 ? NSUM : 1];
+    constexpr bool PK = F32 && DBIE_PACKED;
+    // packed form: lane 0 sums the even pixels of each group of 4, lane 1 the odd ones
+    f32x2 acc2[PK ? P : 1][PK ? NSUM : 1], hi2[PK ? P : 1][PK ? NSUM : 1];
 #pragma unroll
     for (int u = 0; u < P; ++u)
 #pragma unroll
       for (int s = 0; s < NSUM; ++s) {
         acc[u][s] = Real(0);
         if constexpr (F32) hi[u][s] = 0.f;
+        if constexpr (PK) acc2[u][s] = hi2[u][s] = pack2(0.f, 0.f);
       }
 
     sweep_tiles(ring, tiles, t0, t1, tid, [&](const Real* sx) {
-      if constexpr (F32) {
+      if constexpr (PK) {
+        Query<f32x2, TIED> q2[P];
+#pragma unroll
+        for (int u = 0; u < P; ++u) q2[u] = splat_query<TIED>(q[u]);
+#pragma unroll 1
+        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+#pragma unroll GROUP_UNROLL
+          for (int k = k0; k < k0 + SUB; k += 4) {
+            const float4 X = *reinterpret_cast<const float4*>(sx + k);
+            const float4 Y = *reinterpret_cast<const float4*>(sx + TILE + k);
+            const float4 BX = *reinterpret_cast<const float4*>(sx + 2 * TILE + k);
+            const float4 BY = *reinterpret_cast<const float4*>(sx + 3 * TILE + k);
+            const float4 BZ = *reinterpret_cast<const float4*>(sx + 4 * TILE + k);
+            float4 XL = make_float4(0.f, 0.f, 0.f, 0.f), YL = XL;
+            if constexpr (SPLIT) {
+              XL = *reinterpret_cast<const float4*>(sx + 5 * TILE + k);
+              YL = *reinterpret_cast<const float4*>(sx + 6 * TILE + k);
+            }
+            // pixel pairs (0, 1) and (2, 3) of the group
+            const f32x2 px2[2] = {pack2(X.x, X.y), pack2(X.z, X.w)};
+            const f32x2 py2[2] = {pack2(Y.x, Y.y), pack2(Y.z, Y.w)};
+            const f32x2 pxl2[2] = {pack2(XL.x, XL.y), pack2(XL.z, XL.w)};
+            const f32x2 pyl2[2] = {pack2(YL.x, YL.y), pack2(YL.z, YL.w)};
+            const f32x2 b2[2][3] = {{pack2(BX.x, BX.y), pack2(BY.x, BY.y), pack2(BZ.x, BZ.y)},
+                                    {pack2(BX.z, BX.w), pack2(BY.z, BY.w), pack2(BZ.z, BZ.w)}};
+            f32x2 dy2[P], dyz2[P];
+            if constexpr (ROWS) {
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                const float dy = SPLIT ? __fsub_rn(__fsub_rn(q[u].y, Y.x), YL.x)
+                                       : __fsub_rn(q[u].y, Y.x);
+                const float dyz = __fmaf_rn(dy, dy, q[u].z2);
+                dy2[u] = pack2(dy, dy);
+                dyz2[u] = pack2(dyz, dyz);
+              }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                f32x2 dx = vsub(q2[u].x, px2[h]);
+                if constexpr (SPLIT) dx = vsub(dx, pxl2[h]);
+                GeomV<f32x2> g;
+                if constexpr (ROWS) {
+                  g = pair_geomv_dz<f32x2>(dx, dy2[u], dyz2[u]);
+                } else {
+                  f32x2 dy = vsub(q2[u].y, py2[h]);
+                  if constexpr (SPLIT) dy = vsub(dy, pyl2[h]);
+                  g = pair_geomv_d<f32x2, TIED>(q2[u], dx, dy);
+                }
+                TermsV<f32x2, VAR, TIED> tm;
+                pair_angularv<f32x2, VAR, TIED>(q2[u], g, b2[h], tm);
+                accumulatev<f32x2, VAR, TIED, NS>(acc2[u], tm, b2[h]);
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < P; ++u)
+#pragma unroll
+            for (int s = 0; s < NSUM; ++s) fold2(hi2[u][s], acc2[u][s]);
+        }
+      } else if constexpr (F32) {
 #pragma unroll 1
         for (int k0 = 0; k0 < TILE; k0 += SUB) {
 #pragma unroll GROUP_UNROLL
@@ -303,16 +379,29 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
               }
             }
 #else
+            float dyg[P], dyzg[P];
+            if constexpr (ROWS) {
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                dyg[u] = SPLIT ? __fsub_rn(__fsub_rn(q[u].y, py[0]), pyl[0]) : __fsub_rn(q[u].y, py[0]);
+                dyzg[u] = __fmaf_rn(dyg[u], dyg[u], q[u].z2);
+              }
+            }
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const float b[3] = {bx[e], by[e], bz[e]};
 #pragma unroll
               for (int u = 0; u < P; ++u) {
                 Terms32<VAR, TIED> tm;
-                if constexpr (SPLIT)
+                if constexpr (ROWS) {
+                  const float dx = SPLIT ? __fsub_rn(__fsub_rn(q[u].x, px[e]), pxl[e])
+                                         : __fsub_rn(q[u].x, px[e]);
+                  pair_angular32<VAR, TIED>(q[u], pair_geom32_dz<TIED>(dx, dyg[u], dyzg[u]), b, tm);
+                } else if constexpr (SPLIT) {
                   pair_terms32_split<VAR, TIED>(q[u], px[e], py[e], pxl[e], pyl[e], b, tm);
-                else
+                } else {
                   pair_terms32<VAR, TIED>(q[u], px[e], py[e], b, tm);
+                }
                 accumulate32<VAR, TIED, NS>(acc[u], tm, b);
               }
             }
@@ -344,8 +433,16 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
       for (int s = 0; s < NSUM; ++s) {
         double v;
-        if constexpr (F32) v = (double)hi[u][s] + (double)acc[u][s];
-        else v = (double)acc[u][s];
+        if constexpr (PK) {
+          float h0, h1, a0, a1;
+          unpack2(hi2[u][s], h0, h1);
+          unpack2(acc2[u][s], a0, a1);
+          v = ((double)h0 + (double)h1) + ((double)a0 + (double)a1);
+        } else if constexpr (F32) {
+          v = (double)hi[u][s] + (double)acc[u][s];
+        } else {
+          v = (double)acc[u][s];
+        }
         a.out[((int64_t)it * NSUM + s) * Q + (tid + u * NT)] = v;
       }
     }
@@ -682,13 +779,15 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
 
 // Kernel entry points.  MINB > 1 caps registers so that MINB CTAs fit on an SM; MINB = 1 leaves
 // the register allocation to the compiler (a plain __launch_bounds__(NT)).
-template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false,
+          bool ROWS = false>
 __global__ void __launch_bounds__(NT) g1_kernel(const G1Args a) {
-  g1_body<Real, VAR, TIED, P, NT, NSTAGE, SPLIT>(a);
+  g1_body<Real, VAR, TIED, P, NT, NSTAGE, SPLIT, ROWS>(a);
 }
-template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, int MINB>
+template <typename Real, int VAR, bool TIED, int P, int NT, int NSTAGE, int MINB,
+          bool ROWS = false>
 __global__ void __launch_bounds__(NT, MINB) g1_kernel_mb(const G1Args a) {
-  g1_body<Real, VAR, TIED, P, NT, NSTAGE>(a);
+  g1_body<Real, VAR, TIED, P, NT, NSTAGE, false, ROWS>(a);
 }
 template <typename Real, bool TIED, int P, int NT, int NSTAGE, bool SPLIT = false>
 __global__ void __launch_bounds__(NT) vjp_kernel(const VjpArgs a) {

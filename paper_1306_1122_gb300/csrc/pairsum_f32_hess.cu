@@ -3,7 +3,7 @@
 #include "pairsum_inst.cuh"
 
 namespace dbie {
-KernelRef g1_ref_f32_hess(bool tied, int cfg) {
-  return tied ? g1_ref_cfg<float, VAR_HESS, true>(cfg) : g1_ref_cfg<float, VAR_HESS, false>(cfg);
+KernelRef g1_ref_f32_hess(bool tied, int cfg, bool rows) {
+  return tied ? g1_ref_cfg<float, VAR_HESS, true>(cfg, rows) : g1_ref_cfg<float, VAR_HESS, false>(cfg, rows);
 }
 }  // namespace dbie

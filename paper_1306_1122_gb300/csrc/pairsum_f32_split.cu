@@ -5,20 +5,24 @@
 
 namespace dbie {
 
-template <int VAR, bool TIED>
-KernelRef split_ref() {
-  return KernelRef{(const void*)&g1_kernel<float, VAR, TIED, 1, 128, NSTAGE, true>, 128, 128,
+template <int VAR, bool TIED, bool ROWS>
+KernelRef split_ref_r() {
+  return KernelRef{(const void*)&g1_kernel<float, VAR, TIED, 1, 128, NSTAGE, true, ROWS>, 128, 128,
                    (size_t)NSTAGE * NFIELD_SPLIT * TILE * sizeof(float)};
 }
+template <int VAR, bool TIED>
+KernelRef split_ref(bool rows) {
+  return rows ? split_ref_r<VAR, TIED, true>() : split_ref_r<VAR, TIED, false>();
+}
 
-KernelRef g1_ref_f32_split(int var, bool tied) {
+KernelRef g1_ref_f32_split(int var, bool tied, bool rows) {
   switch (var) {
-    case VAR_V: return tied ? split_ref<VAR_V, true>() : split_ref<VAR_V, false>();
-    case VAR_VL: return tied ? split_ref<VAR_VL, true>() : split_ref<VAR_VL, false>();
-    case VAR_OBJ: return tied ? split_ref<VAR_OBJ, true>() : split_ref<VAR_OBJ, false>();
-    case VAR_OBJL: return tied ? split_ref<VAR_OBJL, true>() : split_ref<VAR_OBJL, false>();
-    case VAR_OBJN: return tied ? split_ref<VAR_OBJN, true>() : split_ref<VAR_OBJN, false>();
-    default: return tied ? split_ref<VAR_HESS, true>() : split_ref<VAR_HESS, false>();
+    case VAR_V: return tied ? split_ref<VAR_V, true>(rows) : split_ref<VAR_V, false>(rows);
+    case VAR_VL: return tied ? split_ref<VAR_VL, true>(rows) : split_ref<VAR_VL, false>(rows);
+    case VAR_OBJ: return tied ? split_ref<VAR_OBJ, true>(rows) : split_ref<VAR_OBJ, false>(rows);
+    case VAR_OBJL: return tied ? split_ref<VAR_OBJL, true>(rows) : split_ref<VAR_OBJL, false>(rows);
+    case VAR_OBJN: return tied ? split_ref<VAR_OBJN, true>(rows) : split_ref<VAR_OBJN, false>(rows);
+    default: return tied ? split_ref<VAR_HESS, true>(rows) : split_ref<VAR_HESS, false>(rows);
   }
 }
 
@@ -29,9 +33,9 @@ KernelRef vjp_ref_split(bool tied) {
 }
 
 KernelRef vjp7_ref_split(bool tied) {
-  const void* fn = tied ? (const void*)&vjp7_kernel<float, true, 1, 128, NSTAGE, true>
-                        : (const void*)&vjp7_kernel<float, false, 1, 128, NSTAGE, true>;
-  return KernelRef{fn, 128, 128, (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(float)};
+  const void* fn = tied ? (const void*)&vjp7_kernel<float, true, 4, 256, NSTAGE, true>
+                        : (const void*)&vjp7_kernel<float, false, 4, 256, NSTAGE, true>;
+  return KernelRef{fn, 256, 1024, (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(float)};
 }
 
 }  // namespace dbie

@@ -27,10 +27,11 @@ KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
 }
 
 // The seven-weight adjoint (gradient through the lambda search) runs once per call, after a
-// Hessian pass; it uses one launch shape (128 threads, one pixel per thread).
+// Hessian pass; one launch shape: 256 threads, four pixels per thread, so that each 27-field
+// point record read from shared memory serves four pairs.
 template <typename Real, bool TIED>
 KernelRef vjp7_ref_t() {
-  return KernelRef{(const void*)&vjp7_kernel<Real, TIED, 1, 128, NSTAGE>, 128, 128,
+  return KernelRef{(const void*)&vjp7_kernel<Real, TIED, 4, 256, NSTAGE>, 256, 1024,
                    (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(Real)};
 }
 
