@@ -35,6 +35,11 @@ WORKLOAD = "ll128: Low&Lou n=1 m=1 l=0.3 Phi=pi/4, 128x128 boundary, 64x64x32 po
 SMS, MUFU_PER_SM_CLK, MAX_SM_MHZ = 152, 16, 2070.0
 MUFU_PER_PAIR = 7           # objective variant, one lambda per component: rsqrt + 3 x (sin, cos)
 FP32_PER_PAIR = 44
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one objective launch, the first
+# simplex round of this workload (131,072 queries x 16,384 pixels), from one ncu capture of the
+# current kernel: 6.665 MB read (queries and boundary tiles, each read once) + 5.623 MB written
+# (partial sums).
+OBJ_TRAFFIC_BYTES = 6.665216e6 + 5.623040e6
 THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                  0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                  0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
@@ -283,7 +288,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "pipe": "MUFU (rsqrt, sin, cos)",
                      "kernel": "g1_kernel<float, objective, per-component lambda>",
                      "achieved": achieved, "peak": peak, "unit": "T MUFU-op/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": OBJ_TRAFFIC_BYTES if WORKLOAD.startswith("ll128") else None,
+                     "traffic_launch": "first simplex round: 131072 queries x 16384 pixels",
                      "per_pair": {"mufu": MUFU_PER_PAIR, "fp32": FP32_PER_PAIR},
                      "kernel_ms_per_step": obj_ms / args.steps,
                      "kernel_launches_per_step": launches / args.steps,
