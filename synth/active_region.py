@@ -117,22 +117,24 @@ def trace_samples(m: Magnetogram, nsamples: int, seed: int, step: float = 0.5,
         p = np.stack([pick[:, 1] + rng.uniform(-0.5, 0.5, batch),
                       pick[:, 0] + rng.uniform(-0.5, 0.5, batch), np.full(batch, zmin)], axis=1)
         sgn = np.sign(m.Bz[pick[:, 0], pick[:, 1]]).astype(np.float64)[:, None]
-        alive = np.ones(batch, bool)
 
-        def v(q):
+        def v(q, s):
             b = monopole_field(m, q)
-            return sgn * b / np.maximum(np.linalg.norm(b, axis=1, keepdims=True), 1e-30)
+            return s * b / np.maximum(np.linalg.norm(b, axis=1, keepdims=True), 1e-30)
 
+        # only lines still inside the box are stepped (a line that left stays out)
         for it in range(max_steps):
-            k1 = v(p); k2 = v(p + 0.5 * step * k1); k3 = v(p + 0.5 * step * k2); k4 = v(p + step * k3)
+            k1 = v(p, sgn); k2 = v(p + 0.5 * step * k1, sgn)
+            k3 = v(p + 0.5 * step * k2, sgn); k4 = v(p + step * k3, sgn)
             p = p + step / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
-            alive &= ((p[:, 2] >= zmin) & (p[:, 2] <= zmax) & (p[:, 0] >= 0) & (p[:, 0] <= m.nx - 1)
+            inside = ((p[:, 2] >= zmin) & (p[:, 2] <= zmax) & (p[:, 0] >= 0) & (p[:, 0] <= m.nx - 1)
                       & (p[:, 1] >= 0) & (p[:, 1] <= m.ny - 1))
-            if not alive.any():
+            p, sgn = p[inside], sgn[inside]
+            if len(p) == 0:
                 break
             if it % stride == 0:
-                pool.append(p[alive].copy())
-                have += int(alive.sum())
+                pool.append(p.copy())
+                have += len(p)
     allp = np.concatenate(pool)
     idx = rng.choice(len(allp), nsamples, replace=False)
     return allp[np.sort(idx)].astype(np.float32)

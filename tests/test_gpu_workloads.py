@@ -3,7 +3,9 @@
   ar512   sheared quadrupolar active region 512 x 256: lambda search on the 32^3 sub-volume, then
           dB/dlambda and dL/dB0 for L = sum |B|^2 against central finite differences (FP64 form).
   ar1024  1024 x 512 active region with traced field-line samples and a grid: mixed against the
-          FP64 GPU form on 20k points and against the CPU oracle on a 2k subsample.
+          FP64 GPU form on 20k points and against the CPU oracle on a 2k subsample; and at full
+          size (6.3 M points) forward + adjoint with sampled checks and the adjoint identity.
+  ar512   the full 256 x 128 x 64 volume with the lambda search, sampled against the oracle.
 """
 import numpy as np
 import pytest
@@ -136,4 +138,66 @@ def test_ll128_metrics_match_oracle_solution(dbie):
     B0 = f.eval(torch.from_numpy(pts).cuda(), torch.zeros((len(pts), 3)).cuda())["B"]
     m0 = field_metrics(B0.cpu().numpy(), w.truth[idx])
     print("metrics searched", mg, "oracle", mo, "lambda=0", m0)
+    f.close()
+
+
+def test_ar1024_full_size_forward_backward(dbie):
+    """All 6,291,456 points of the 1024 x 512 workload (4,194,304 traced samples + the 128^3
+    grid), mixed precision, forward at a fixed seeded lambda and the adjoint: sampled outputs
+    against the FP64 GPU form (20k points) and the oracle (300 points); the adjoint identity
+    <gB, A B0> = <A^T gB, B0> over the whole set (a property at any size)."""
+    w = workloads.ar1024()
+    m = w.mag
+    n = len(w.points)
+    assert n == 4_194_304 + 128 ** 3
+    rng = np.random.default_rng(9)
+    lam = rng.uniform(0.0, 0.02, (n, 3)).astype(np.float32)
+    f = dbie.DBIEField.from_magnetogram(m)
+    f.autotune()
+    P, L = torch.from_numpy(w.points).cuda(), torch.from_numpy(lam).cuda()
+    B = f.eval(P, L)["B"]
+    gB = torch.from_numpy(rng.normal(size=(n, 3))).cuda()
+    gB0, _ = f.vjp(P, L.double(), gB, glam=False)
+    torch.cuda.synchronize()
+    B0 = torch.from_numpy(np.stack([m.Bx, m.By, m.Bz], -1).astype(np.float64)).cuda()
+    lhs = float((gB * B).sum())
+    rhs = float((gB0 * B0).sum())
+    scale = float((gB.abs() * B.abs()).sum())
+    assert abs(lhs - rhs) <= 1e-6 * scale, (lhs, rhs, scale)
+    sub = torch.from_numpy(np.sort(rng.choice(n, 20000, replace=False))).cuda()
+    ref = f.eval(P[sub], L[sub], options=dbie.Options(precision=1))["B"]
+    Bm = B[sub].cpu().numpy()
+    Br = ref.cpu().numpy()
+    rel = np.linalg.norm(Bm - Br, axis=1) / np.linalg.norm(Br, axis=1)
+    assert np.median(rel) < 1e-6 and np.percentile(rel, 99) < 1e-5, (np.median(rel), rel.max())
+    assert np.linalg.norm(Bm - Br) / np.linalg.norm(Br) < 1e-5
+    few = np.sort(rng.choice(n, 300, replace=False))
+    Bo, _, _ = oracle.field(oracle_boundary(m), w.points[few].astype(np.float64),
+                            lam[few].astype(np.float64))
+    assert check_B(B[torch.from_numpy(few).cuda()].cpu().numpy(), Bo,
+                   np.zeros_like(Bo))["frob"] < 1e-5
+    f.close()
+
+
+def test_ar512_full_volume_solve(dbie):
+    """The 256 x 128 x 64 volume (2,097,152 points) over the 512 x 256 boundary with the lambda
+    search (10 simplex iterations): B at the GPU's lambda against the oracle on 200 sampled
+    points, and every point ends with a finite lambda and status."""
+    w = workloads.ar512()
+    n = len(w.points)
+    assert n == 256 * 128 * 64
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    f.autotune()
+    r = f.solve(torch.from_numpy(w.points).cuda(), dbie.Options(max_iter=10))
+    torch.cuda.synchronize()
+    lam = r["lam"].cpu().numpy()
+    assert np.all(np.isfinite(lam)) and np.all(np.isfinite(r["B"].cpu().numpy()))
+    st = r["status"].cpu().numpy()
+    assert set(np.unique(st)) <= {0, 1}
+    rng = np.random.default_rng(10)
+    few = np.sort(rng.choice(n, 200, replace=False))
+    Bo, _, _ = oracle.field(oracle_boundary(w.mag), w.points[few].astype(np.float64), lam[few])
+    sB, _ = abs_scales(w.mag, w.points[few], lam[few])
+    rb = check_B(r["B"].cpu().numpy()[few], Bo, sB)
+    assert rb["bad"].size == 0, rb
     f.close()
