@@ -5,8 +5,10 @@ the same (replicated) magnetogram, with no exchange during the solve.  The one r
 the backward pass: dL/dB0 = A^T gB is a sum over all points, i.e. a sum over the ranks' partial
 adjoints (one all-reduce of (ny, nx, 3) FP64 at the end).
 
-The functions take the per-rank compute as a callable so that the same host logic drives the
-GPU library (DBIEField.vjp / .solve) and can be exercised with CPU process groups.
+The gradient through the lambda search (DBIEField.vjp_implicit) is also a sum over points, so it
+shards the same way.  The functions take the per-rank compute as a callable so that the same
+host logic drives the GPU library (DBIEField.vjp / .vjp_implicit / .solve) and can be exercised
+with CPU process groups.
 """
 from __future__ import annotations
 

@@ -1,6 +1,6 @@
 """Multi-rank logic on CPU (gloo, world size 2): point partition, the all-reduce of partial
-boundary adjoints, and the all-gather of per-point solve results, with the FP64 oracle standing
-in for each rank's GPU compute."""
+boundary adjoints (at fixed lambda and through the lambda search), and the all-gather of
+per-point solve results, with the FP64 oracle standing in for each rank's GPU compute."""
 import os
 import socket
 
@@ -42,6 +42,15 @@ def _worker(rank, world, port, q):
     full = sharded_vjp(vjp_fn, xyz, lam, gB)
     ref = oracle.vjp(bd, xyz.numpy(), lam.numpy(), gB.numpy(), nthreads=1)
 
+    # the gradient through the lambda search is a sum over points too: same all-reduce
+    def ivjp_fn(x, l, gb):
+        return torch.from_numpy(oracle.implicit_vjp(bd, x.numpy(), l.numpy(), gb.numpy(),
+                                                    1.0 / 6.0, nthreads=1)[0])
+
+    ifull = sharded_vjp(ivjp_fn, xyz, lam, gB)
+    iref = oracle.implicit_vjp(bd, xyz.numpy(), lam.numpy(), gB.numpy(), 1.0 / 6.0, nthreads=1)[0]
+    ierr = float(np.abs(ifull.numpy() - iref).max() / np.abs(iref).max())
+
     def solve_fn(x):
         r = oracle.solve(bd, x.numpy(), oracle.Options(max_iter=8), nthreads=1)
         return {"lam": torch.from_numpy(r["lam"]), "B": torch.from_numpy(r["B"]),
@@ -49,7 +58,7 @@ def _worker(rank, world, port, q):
 
     sol = sharded_solve(solve_fn, xyz)
     sref = oracle.solve(bd, xyz.numpy(), oracle.Options(max_iter=8), nthreads=1)
-    q.put((rank, float(np.abs(full.numpy() - ref).max() / np.abs(ref).max()),
+    q.put((rank, max(float(np.abs(full.numpy() - ref).max() / np.abs(ref).max()), ierr),
            bool(np.array_equal(sol["lam"].numpy(), sref["lam"])),
            bool(np.array_equal(sol["iters"].numpy(), sref["iters"])),
            partition(n, world)))
