@@ -22,19 +22,22 @@
 namespace dbie {
 
 #ifndef DBIE_FOLD_PIXELS
-#define DBIE_FOLD_PIXELS 32
+#define DBIE_FOLD_PIXELS 64   // packed: each f32x2 lane sums 32 of them between folds
 #endif
 #ifndef DBIE_STAGED
 #define DBIE_STAGED 0
 #endif
 #ifndef DBIE_GROUP_UNROLL
-#define DBIE_GROUP_UNROLL 8
+#define DBIE_GROUP_UNROLL 16
 #endif
 #ifndef DBIE_PACKED
 #define DBIE_PACKED 1     // FP32 pair sums on pixel pairs packed in f32x2 (0: one pixel per op)
 #endif
-constexpr int SUB = DBIE_FOLD_PIXELS;  // elements summed in plain FP32 before a compensated fold
+constexpr int SUB = DBIE_FOLD_PIXELS;  // pixels summed in plain FP32 before a compensated fold
+constexpr int SUB1 = 32;  // elements per fold where one accumulator takes every element (adjoints,
+                          // the unpacked FP32 form): the per-accumulator length of the packed form
 constexpr int GROUP_UNROLL = DBIE_GROUP_UNROLL;  // 4-pixel groups unrolled within a block
+static_assert(TILE % SUB == 0 && SUB % 4 == 0, "fold blocks must tile the 256-pixel tile");
 
 // Ring of NSTAGE shared-memory tile buffers filled by TMA bulk copies.  Thread 0 issues; all
 // warps consume.  `issued` / `consumed` count tiles over the CTA's lifetime, which fixes the
@@ -339,9 +342,9 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
         }
       } else if constexpr (F32) {
 #pragma unroll 1
-        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+        for (int k0 = 0; k0 < TILE; k0 += SUB1) {
 #pragma unroll GROUP_UNROLL
-          for (int k = k0; k < k0 + SUB; k += 4) {
+          for (int k = k0; k < k0 + SUB1; k += 4) {
             const float4 X = *reinterpret_cast<const float4*>(sx + k);
             const float4 Y = *reinterpret_cast<const float4*>(sx + TILE + k);
             const float4 BX = *reinterpret_cast<const float4*>(sx + 2 * TILE + k);
@@ -523,9 +526,9 @@ __device__ __forceinline__ void vjp_body(const VjpArgs& a) {
       const Real* W = sx + 6 * TILE;
       if constexpr (F32) {
 #pragma unroll 1
-        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+        for (int k0 = 0; k0 < TILE; k0 += SUB1) {
 #pragma unroll 4
-          for (int k = k0; k < k0 + SUB; ++k) {
+          for (int k = k0; k < k0 + SUB1; ++k) {
             const float xi = X[k], yi = Y[k], z2 = Z2[k];
             float lam[NL];
 #pragma unroll
@@ -676,9 +679,9 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
       const Real* W = sx + 6 * TILE;
       if constexpr (F32) {
 #pragma unroll 1
-        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+        for (int k0 = 0; k0 < TILE; k0 += SUB1) {
 #pragma unroll 2
-          for (int k = k0; k < k0 + SUB; ++k) {
+          for (int k = k0; k < k0 + SUB1; ++k) {
             const float xi = X[k], yi = Y[k], z2 = Z2[k];
             float lam[NL], lam2[NL];
 #pragma unroll
