@@ -309,6 +309,9 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   G1Args a{};
   a.probs = var == VAR_NV ? c->probv.as<ProbDesc>() : c->prob.as<ProbDesc>();
   a.nprob = 1;
+  // Fault injection for tests of the bounded waits: the CTA that takes work item 0 never issues
+  // its tile copies, its waits expire after their time limit and the call reports DBIE_ETIMEOUT.
+  if (const char* fi = std::getenv("DBIE_FAULT_INJECT")) a.fault = std::atoi(fi) == 1 ? 1 : 0;
   a.plan = &m->plan;
   a.item_off = m->item_off;
   a.q_cnt = m->q_cnt;

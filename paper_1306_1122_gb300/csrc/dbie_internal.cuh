@@ -106,7 +106,7 @@ struct PlanHdr {
 struct G1Args {
   const ProbDesc* probs;
   int32_t nprob;
-  int32_t pad0;
+  int32_t fault;            // fault injection (tests): 1 = the CTA of item 0 issues no tile copy
   const PlanHdr* plan;
   const int32_t* item_off;  // [nprob + 1] prefix of items per problem
   const int32_t* q_cnt;     // [nprob] queries per problem in this pass

@@ -51,6 +51,7 @@ struct TileRing {
   unsigned* err;
   uint32_t tile_elems;
   uint32_t issued, consumed;
+  bool skip_issue = false;   // fault injection: never issue, so the consumers' bounded waits expire
 
   __device__ void init_barriers() {  // thread 0, before the first __syncthreads
     for (int s = 0; s < NSTAGE; ++s) {
@@ -61,6 +62,7 @@ struct TileRing {
   }
   // Thread 0: copy tile `src` into the next stage (waits until that stage is released).
   __device__ bool issue(const Elem* src) {
+    if (skip_issue) return false;
     const uint32_t st = issued % NSTAGE;
     if (issued >= NSTAGE &&
         !mbar_wait_bounded(smem_addr(&empty[st]), ((issued / NSTAGE) - 1) & 1, err,
@@ -235,6 +237,8 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
     const int it = s_item;
     __syncthreads();  // every thread has read s_item before it can be overwritten
     if (it >= plan.nitems) break;
+    // fault injection: the CTA holding item 0 (its first item) never issues a tile copy
+    ring.skip_issue = a.fault == 1 && it == 0;
 
     const int pidx = find_problem(a.item_off, a.nprob, it);
     const ProbDesc& pd = a.probs[pidx];
