@@ -16,6 +16,10 @@
 
 using namespace dbie;
 
+#ifndef DBIE_SPLIT_TARGET_PCT
+#define DBIE_SPLIT_TARGET_PCT 200
+#endif
+
 namespace {
 
 thread_local std::string g_err;
@@ -1166,7 +1170,9 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   for (int p = 0; p < nprob; ++p) rows_all &= ctxs[p]->qnx % 4 == 0;
   const KernelRef k = g1_ref(c, var, tied, fp64, rows_all ? 1 : 0);
   const int grid = persistent_grid(k, c->device);
-  const int target = 2 * grid;
+  // Split a round's queries over tile ranges until the items cover this many CTAs (percent of
+  // the persistent grid): more items balance the queue, fewer items mean fewer partial sums.
+  const int target = (int)((int64_t)grid * DBIE_SPLIT_TARGET_PCT / 100);
   const int64_t items_cap = std::max<int64_t>((Qcap + k.qper - 1) / k.qper + nprob, 2LL * target) + 1;
 
   DBIE_TRY(ensure(b.probs, sizeof(ProbDesc) * nprob));
