@@ -37,9 +37,9 @@ MUFU_PER_PAIR = 7           # objective variant, one lambda per component: rsqrt
 FP32_PER_PAIR = 44
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one objective launch, the first
 # simplex round of this workload (131,072 queries x 16,384 pixels), from one ncu capture of the
-# current kernel: 6.681 MB read (queries and boundary tiles, each read once) + 4.455 MB written
+# current kernel: 6.679 MB read (queries and boundary tiles, each read once) + 4.378 MB written
 # (partial sums).
-OBJ_TRAFFIC_BYTES = 6.680576e6 + 4.455424e6
+OBJ_TRAFFIC_BYTES = 6.679296e6 + 4.377600e6
 THROTTLE_BITS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap",
                  0x8: "hw_slowdown", 0x10: "sync_boost", 0x20: "sw_thermal_slowdown",
                  0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown",
