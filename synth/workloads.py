@@ -64,6 +64,20 @@ def _ll_workload(name, nx, lo, hi, zmax, with_truth=True):
     return Workload(name, mag, pts, truth, alpha, dict(field="lowlou n=1 m=1 l=0.3 Phi=pi/4"))
 
 
+def ll129_nodes(with_truth: bool = True) -> Workload:
+    """The ll128 field on the 129 x 129 node grid at the same 64 px per box unit (nodes at the
+    box edges, as nine-node elements need), with the ll128 points at the same box positions."""
+    ll = LowLou(1, 1, 0.3, np.pi / 4)
+    mag = lowlou_magnetogram(129, ll, scale=64.0)
+    pts = grid_points(np.arange(32, 96) + 0.5, np.arange(32, 96) + 0.5, range(1, 33))
+    truth = None
+    if with_truth:
+        bx, by, bz = to_box(129, 129, pts[:, 0], pts[:, 1], pts[:, 2], 64.0)
+        truth = ll.field(bx, by, bz)
+    return Workload("ll129_nodes", mag, pts, truth, None,
+                    dict(field="lowlou n=1 m=1 l=0.3 Phi=pi/4", scale=64.0))
+
+
 def small_ll() -> Workload:
     return _ll_workload("small_ll", 32, 8, 23, 8)
 
