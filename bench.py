@@ -440,7 +440,8 @@ def quadrature_compare(w, dev):
         return c_vec, e_n
 
     out = {}
-    for name, wk, order in (("pixel_centres", w, 0), ("elements_g4", workloads.ll129_nodes(), 4)):
+    for name, wk, order in (("pixel_centres", workloads.ll128(with_truth=True), 0),
+                            ("elements_g4", workloads.ll129_nodes(), 4)):
         f = dbie.DBIEField.from_magnetogram(wk.mag, device=dev)
         if order:
             f.set_quadrature(order)
