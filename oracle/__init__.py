@@ -61,7 +61,7 @@ class _Options(ctypes.Structure):
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("deriv", ctypes.c_int32),
                 ("fd_delta", ctypes.c_double), ("method", ctypes.c_int32),
-                ("quad_order", ctypes.c_int32)]
+                ("quad_order", ctypes.c_int32), ("pxe_near_z", ctypes.c_double)]
 
 
 class _NMResult(ctypes.Structure):
@@ -93,7 +93,8 @@ def _load():
             lib.orc_bfgs.argtypes = [ctypes.c_int32, P, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_int32, FUN_GRAD, P, P]
             lib.orc_objective_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double,
-                                               ctypes.c_double, P, P, ctypes.c_int32]
+                                               ctypes.c_double, ctypes.c_double, P, P,
+                                               ctypes.c_int32]
             lib.orc_field_dl.argtypes = [P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P,
                                          P, P, P, P]
             lib.orc_gauss_legendre.argtypes = [ctypes.c_int32, P, P]
@@ -103,11 +104,18 @@ def _load():
                                              ctypes.c_int32]
             lib.orc_vjp_q9.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int32, P, ctypes.c_int32]
             lib.orc_hessian_many.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_int32,
-                                             ctypes.c_double, ctypes.c_double, P, P, P, P,
-                                             ctypes.c_int32]
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             P, P, P, P, ctypes.c_int32]
             lib.orc_implicit_vjp.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_int32,
-                                             ctypes.c_double, ctypes.c_double, P, P, P,
-                                             ctypes.c_int32]
+                                             ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                             P, P, P, ctypes.c_int32]
+            lib.orc_rect_exact.argtypes = [ctypes.c_double] * 5 + [P]
+            lib.orc_pxe_correction.argtypes = [P, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, P, P]
+            lib.orc_eval_many_pxe.argtypes = [P, ctypes.c_int64, P, P, ctypes.c_double, P, P, P,
+                                              ctypes.c_int32]
+            lib.orc_vjp_pxe.argtypes = [P, ctypes.c_int64, P, P, P, ctypes.c_double, P,
+                                        ctypes.c_int32]
             lib.orc_noise_var.argtypes = [P, ctypes.c_int64, P, P, P, P, P, ctypes.c_double, P,
                                           ctypes.c_int32]
             _lib = lib
@@ -169,7 +177,9 @@ class Options:
     deriv: int = 0
     fd_delta: float = 0.0       # 0 -> 1e-3 * hx (one thousandth of a pixel, Sect. 2.1)
     method: int = 0             # 0: Downhill Simplex (the paper), 1: quasi-Newton (BFGS)
-    quad_order: int = 0         # 0: midpoint rule (Eq. 16); g: nine-node elements, g x g Gauss (Eq. 15)
+    quad_order: int = 0         # 0: midpoint rule (Eq. 16); g: nine-node elements, g x g Gauss (Eq. 15);
+                                # -1: pixel-exact near field (field(..., pxe_near_z=...))
+    pxe_near_z: float = 0.0     # quad_order -1: correction for z <= this (0 -> 2 hx)
 
     def resolved(self, grid: Grid) -> "Options":
         o = Options(**self.__dict__)
@@ -179,14 +189,19 @@ class Options:
             o.g_scale = grid.hx / 6.0
         if o.fd_delta == 0.0:
             o.fd_delta = 1e-3 * grid.hx
+        if o.pxe_near_z == 0.0:
+            o.pxe_near_z = 2.0 * grid.hx
         return o
 
     def c(self, grid: Grid) -> _Options:
         o = self.resolved(grid)
-        if o.quad_order and o.method:
+        if o.quad_order > 0 and o.method:
             raise ValueError("the oracle's element rule (quad_order > 0) runs with the simplex only")
+        if o.quad_order < -1:
+            raise ValueError("quad_order must be -1, 0 or a Gauss order")
         return _Options(o.eps_f, o.eps_g, o.tol, o.max_iter, o.lambda_mode, o.simplex_step,
-                        o.w_g, o.g_scale, o.deriv, o.fd_delta, o.method, o.quad_order)
+                        o.w_g, o.g_scale, o.deriv, o.fd_delta, o.method, o.quad_order,
+                        o.pxe_near_z if o.quad_order == -1 else 0.0)
 
 
 def _threads(nthreads):
@@ -194,16 +209,20 @@ def _threads(nthreads):
 
 
 def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthreads=None,
-          quad_order: int = 0):
+          quad_order: int = 0, pxe_near_z: float | None = None):
     """B (n,3), G (n,3,3) with G[i,p,j] = dB_p/dx_j, and dB/dlambda (n,3) at given lambda (n,3).
     quad_order 0: midpoint rule (Eq. 16); g >= 1: nine-node elements with g x g Gauss points
-    (Eq. 15; nx, ny odd)."""
+    (Eq. 15; nx, ny odd); -1: pixel-exact near field for z <= pxe_near_z (default 2 hx)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     n = xyz.shape[0]
     B = np.zeros((n, 3)); G = np.zeros((n, 3, 3)); dl = np.zeros((n, 3))
-    if quad_order:
+    if quad_order == -1:
+        nz = 2.0 * bd.grid.hx if pxe_near_z is None else float(pxe_near_z)
+        lib.orc_eval_many_pxe(bd.ref, n, _ptr(xyz), _ptr(lam), nz, _ptr(B), _ptr(G), _ptr(dl),
+                              _threads(nthreads))
+    elif quad_order:
         _check_q9(bd)
         lib.orc_eval_many_q9(bd.ref, n, _ptr(xyz), _ptr(lam), quad_order, _ptr(B), _ptr(G),
                              _ptr(dl), _threads(nthreads))
@@ -216,6 +235,24 @@ def field(bd: Boundary, xyz, lam, deriv: int = 0, fd_delta: float = 1e-3, nthrea
 def _check_q9(bd: Boundary):
     if bd.grid.nx < 3 or bd.grid.ny < 3 or bd.grid.nx % 2 == 0 or bd.grid.ny % 2 == 0:
         raise ValueError("nine-node elements need odd nx, ny >= 3")
+
+
+def rect_exact(xa, xb, ya, yb, z):
+    """Exact integral of z / (2 pi r^3) over [xa, xb] x [ya, yb] (corner minus point coordinates)
+    and its derivatives with respect to the point's x, y, z."""
+    lib = _load()
+    out = np.zeros(4)
+    lib.orc_rect_exact(float(xa), float(xb), float(ya), float(yb), float(z), _ptr(out))
+    return out
+
+
+def pxe_correction(bd: Boundary, point):
+    """The pixel-exact correction of B (3,) and of G (3, 3) at one point, whatever its z."""
+    lib = _load()
+    dB = np.zeros(3); dG = np.zeros(9)
+    lib.orc_pxe_correction(bd.ref, float(point[0]), float(point[1]), float(point[2]), _ptr(dB),
+                           _ptr(dG))
+    return dB, dG.reshape(3, 3)
 
 
 def gauss_legendre(m: int):
@@ -250,15 +287,17 @@ def field_dl(bd: Boundary, xyz, lam):
     return B, G.reshape(n, 3, 3), dl, dG.reshape(n, 3, 3)
 
 
-def objective_grad(bd: Boundary, xyz, lam, g_scale: float, w_g: float = 1.0, nthreads=None):
-    """f, g, Phi (n,) and dPhi/dlambda (n,3) at given lambda (n,3)."""
+def objective_grad(bd: Boundary, xyz, lam, g_scale: float, w_g: float = 1.0, nthreads=None,
+                   pxe_near_z: float = 0.0):
+    """f, g, Phi (n,) and dPhi/dlambda (n,3) at given lambda (n,3) (pxe_near_z > 0: with the
+    pixel-exact correction at points with z <= pxe_near_z)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     n = xyz.shape[0]
     fgp = np.zeros((n, 3)); dphi = np.zeros((n, 3))
-    lib.orc_objective_many(bd.ref, n, _ptr(xyz), _ptr(lam), g_scale, w_g, _ptr(fgp), _ptr(dphi),
-                           _threads(nthreads))
+    lib.orc_objective_many(bd.ref, n, _ptr(xyz), _ptr(lam), g_scale, w_g, float(pxe_near_z),
+                           _ptr(fgp), _ptr(dphi), _threads(nthreads))
     return fgp[:, 0], fgp[:, 1], fgp[:, 2], dphi
 
 
@@ -320,16 +359,21 @@ def solve(bd: Boundary, xyz, opt: Options | None = None, lam0=None, nthreads=Non
                 codes=code_str)
 
 
-def vjp(bd: Boundary, xyz, lam, gB, nthreads=None, quad_order: int = 0):
+def vjp(bd: Boundary, xyz, lam, gB, nthreads=None, quad_order: int = 0,
+        pxe_near_z: float | None = None):
     """dL/dB0 (ny, nx, 3) for dL/dB = gB (n, 3) at fixed lambda: the transpose of Eq. 16 (of the
-    element weights of Eq. 15 when quad_order > 0)."""
+    element weights of Eq. 15 when quad_order > 0; with the pixel-exact correction when -1)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     gB = _f64(gB).reshape(-1, 3)
     g = bd.grid
     out = np.zeros((g.ny * g.nx, 3))
-    if quad_order:
+    if quad_order == -1:
+        nz = 2.0 * g.hx if pxe_near_z is None else float(pxe_near_z)
+        lib.orc_vjp_pxe(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), nz, _ptr(out),
+                        _threads(nthreads))
+    elif quad_order:
         _check_q9(bd)
         lib.orc_vjp_q9(bd.ref, xyz.shape[0], _ptr(xyz), _ptr(lam), _ptr(gB), quad_order, _ptr(out),
                        _threads(nthreads))
@@ -340,24 +384,26 @@ def vjp(bd: Boundary, xyz, lam, gB, nthreads=None, quad_order: int = 0):
 
 
 def hessian(bd: Boundary, xyz, lam, g_scale: float, w_g: float = 1.0, lambda_mode: int = 0,
-            nthreads=None):
+            nthreads=None, pxe_near_z: float = 0.0):
     """Phi (n,), dPhi/dlambda (n,3), the lambda-Hessian (n,3,3) and dB_p/dlambda_p (n,3), all by
-    hyper-dual arithmetic through the quadrature.  Tied mode: entry 0 (and H[:,0,0]) only."""
+    hyper-dual arithmetic through the quadrature.  Tied mode: entry 0 (and H[:,0,0]) only.
+    pxe_near_z > 0: with the pixel-exact correction at points with z <= pxe_near_z."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
     n = xyz.shape[0]
     phi = np.zeros(n); grad = np.zeros((n, 3)); H = np.zeros((n, 9)); dl = np.zeros((n, 3))
-    lib.orc_hessian_many(bd.ref, n, _ptr(xyz), _ptr(lam), lambda_mode, g_scale, w_g, _ptr(phi),
-                         _ptr(grad), _ptr(H), _ptr(dl), _threads(nthreads))
+    lib.orc_hessian_many(bd.ref, n, _ptr(xyz), _ptr(lam), lambda_mode, g_scale, w_g,
+                         float(pxe_near_z), _ptr(phi), _ptr(grad), _ptr(H), _ptr(dl),
+                         _threads(nthreads))
     return phi, grad, H.reshape(n, 3, 3), dl
 
 
 def implicit_vjp(bd: Boundary, xyz, lam, gB, g_scale: float, w_g: float = 1.0,
-                 lambda_mode: int = 0, nthreads=None):
+                 lambda_mode: int = 0, nthreads=None, pxe_near_z: float = 0.0):
     """dL/dB0 (ny, nx, 3) through the lambda search (lambda* a stationary point of Phi), the
     adjoint vectors v = H^-1 dL/dlambda (n, 3) and flags (n,) = 1 where H is not positive
-    definite."""
+    definite.  pxe_near_z > 0: with the pixel-exact correction (as hessian)."""
     lib = _load()
     xyz = _f64(xyz).reshape(-1, 3)
     lam = _f64(lam).reshape(-1, 3)
@@ -366,7 +412,7 @@ def implicit_vjp(bd: Boundary, xyz, lam, gB, g_scale: float, w_g: float = 1.0,
     g = bd.grid
     out = np.zeros((g.ny * g.nx, 3)); v = np.zeros((n, 3)); flags = np.zeros(n, np.int32)
     lib.orc_implicit_vjp(bd.ref, n, _ptr(xyz), _ptr(lam), _ptr(gB), lambda_mode, g_scale, w_g,
-                         _ptr(out), _ptr(v), _ptr(flags), _threads(nthreads))
+                         float(pxe_near_z), _ptr(out), _ptr(v), _ptr(flags), _threads(nthreads))
     return out.reshape(g.ny, g.nx, 3), v, flags
 
 

@@ -388,12 +388,21 @@ void orc_nelder_mead(int32_t n, const double x0[3], double step, double tol, int
   orc_nelder_mead_sim(n, sim, tol, max_iter, fun, ctx, res, codes, codes_cap);
 }
 
+static void pxe_terms(const orc_boundary* bd, double xi, double yi, double zi, double pxe_near_z,
+                      double dB[3], double dG[9]);
+
 /* The per-point objective of Sect. 2.1: Phi(lambda) = f + w_g g at point r_i. */
 typedef struct {
   const orc_boundary* bd;
   const orc_options* opt;
   double x, y, z;
+  double cB[3], cG[9];    /* pixel-exact correction of B and grad B (quad_order -1), else 0 */
 } dbie_point_ctx;
+
+static void add_correction(const dbie_point_ctx* pc, double B[3], double G[9]) {
+  for (int p = 0; p < 3; ++p) B[p] += pc->cB[p];
+  for (int q = 0; q < 9; ++q) G[q] += pc->cG[q];
+}
 
 static void expand_lambda(const orc_options* opt, const double* x, double lam[3]) {
   if (opt->lambda_mode == 1) { lam[0] = lam[1] = lam[2] = x[0]; }
@@ -406,6 +415,7 @@ static void eval_point(const dbie_point_ctx* pc, const double lam[3], double B[3
   if (pc->opt->quad_order > 0) orc_field_q9(pc->bd, pc->x, pc->y, pc->z, lam, pc->opt->quad_order, B, G, NULL);
   else if (pc->opt->deriv == 1) orc_field_fd(pc->bd, pc->x, pc->y, pc->z, lam, pc->opt->fd_delta, B, G);
   else orc_field(pc->bd, pc->x, pc->y, pc->z, lam, B, G, NULL);
+  if (pc->opt->quad_order == -1) add_correction(pc, B, G);
   orc_objective(B, G, pc->opt->g_scale, pc->opt->w_g, f, g, phi, NULL, NULL);
 }
 
@@ -424,6 +434,7 @@ static double dbie_phi_grad(void* ctx, const double* x, double* grad, int32_t* f
   double lam[3], B[3], G[9], dBdl[3], dGdl[9], f, g, phi, dphi[3];
   expand_lambda(pc->opt, x, lam);
   orc_field_dl(pc->bd, pc->x, pc->y, pc->z, lam, B, G, dBdl, dGdl);
+  if (pc->opt->quad_order == -1) add_correction(pc, B, G);
   orc_objective_grad(B, G, dBdl, dGdl, pc->opt->g_scale, pc->opt->w_g, &f, &g, &phi, dphi);
   if (pc->opt->lambda_mode == 1) grad[0] = dphi[0] + dphi[1] + dphi[2];
   else { grad[0] = dphi[0]; grad[1] = dphi[1]; grad[2] = dphi[2]; }
@@ -432,14 +443,17 @@ static double dbie_phi_grad(void* ctx, const double* x, double* grad, int32_t* f
 }
 
 void orc_objective_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
-                        double g_scale, double w_g, double* fgphi, double* dphi,
-                        int32_t nthreads) {
+                        double g_scale, double w_g, double pxe_near_z, double* fgphi,
+                        double* dphi, int32_t nthreads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   for (int64_t i = 0; i < n; ++i) {
-    double B[3], G[9], dBdl[3], dGdl[9], f, g, phi;
+    double B[3], G[9], dBdl[3], dGdl[9], f, g, phi, cB[3], cG[9];
     orc_field_dl(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, B, G, dBdl, dGdl);
+    pxe_terms(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], pxe_near_z, cB, cG);
+    for (int p = 0; p < 3; ++p) B[p] += cB[p];
+    for (int q = 0; q < 9; ++q) G[q] += cG[q];
     orc_objective_grad(B, G, dBdl, dGdl, g_scale, w_g, &f, &g, &phi, dphi + 3 * i);
     fgphi[3 * i] = f;
     fgphi[3 * i + 1] = g;
@@ -475,7 +489,15 @@ void orc_solve_many(const orc_boundary* bd, int64_t n, const double* xyz, const 
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   for (int64_t i = 0; i < n; ++i) {
-    dbie_point_ctx pc = {bd, opt, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+    dbie_point_ctx pc;
+    memset(&pc, 0, sizeof pc);
+    pc.bd = bd;
+    pc.opt = opt;
+    pc.x = xyz[3 * i];
+    pc.y = xyz[3 * i + 1];
+    pc.z = xyz[3 * i + 2];
+    if (opt->quad_order == -1 && pc.z <= opt->pxe_near_z)
+      orc_pxe_correction(bd, pc.x, pc.y, pc.z, pc.cB, pc.cG);
     double x0[3] = {0, 0, 0};
     if (lam0) for (int d = 0; d < dim; ++d) x0[d] = lam0[3 * i + d];
     orc_nm_result r;
@@ -633,15 +655,35 @@ static hd objective_hd(const hd B[3], const hd G[9], double g_scale, double w_g)
   return hd_add(f, hd_scl(g, w_g));
 }
 
+static void pxe_pixel_weights(const orc_boundary* bd, double xi, double yi, double zi, int i, int j,
+                              double c[4]);
+
+/* The pixel-exact correction (orc_pxe_correction) of B and grad B at a point with
+ * z <= pxe_near_z (pxe_near_z <= 0: none); it does not depend on lambda. */
+static void pxe_terms(const orc_boundary* bd, double xi, double yi, double zi, double pxe_near_z,
+                      double dB[3], double dG[9]) {
+  memset(dB, 0, 3 * sizeof(double));
+  memset(dG, 0, 9 * sizeof(double));
+  if (pxe_near_z > 0.0 && zi <= pxe_near_z) orc_pxe_correction(bd, xi, yi, zi, dB, dG);
+}
+static void field_hd_pxe(const orc_boundary* bd, double xi, double yi, double zi, const hd lam[3],
+                         const double dB[3], const double dG[9], hd B[3], hd G[9]) {
+  field_hd(bd, xi, yi, zi, lam, B, G);
+  for (int p = 0; p < 3; ++p) B[p].v += dB[p];
+  for (int q = 0; q < 9; ++q) G[q].v += dG[q];
+}
+
 void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
-                 int32_t lambda_mode, double g_scale, double w_g, double* phi, double grad[3],
-                 double H[9], double dBdl[3]) {
+                 int32_t lambda_mode, double g_scale, double w_g, double pxe_near_z, double* phi,
+                 double grad[3], double H[9], double dBdl[3]) {
   hd lh[3], B[3], G[9];
+  double cB[3], cG[9];
+  pxe_terms(bd, xi, yi, zi, pxe_near_z, cB, cG);
   for (int q = 0; q < 9; ++q) H[q] = 0.0;
   for (int q = 0; q < 3; ++q) grad[q] = dBdl[q] = 0.0;
   if (lambda_mode == 1) {
     for (int p = 0; p < 3; ++p) { lh[p].v = lam[p]; lh[p].a = 1.0; lh[p].b = 1.0; lh[p].c = 0.0; }
-    field_hd(bd, xi, yi, zi, lh, B, G);
+    field_hd_pxe(bd, xi, yi, zi, lh, cB, cG, B, G);
     const hd ph = objective_hd(B, G, g_scale, w_g);
     *phi = ph.v;
     grad[0] = ph.a;
@@ -657,7 +699,7 @@ void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const 
         lh[p].b = p == k ? 1.0 : 0.0;
         lh[p].c = 0.0;
       }
-      field_hd(bd, xi, yi, zi, lh, B, G);
+      field_hd_pxe(bd, xi, yi, zi, lh, cB, cG, B, G);
       const hd ph = objective_hd(B, G, g_scale, w_g);
       H[3 * j + k] = H[3 * k + j] = ph.c;
       if (j == k) {
@@ -669,14 +711,14 @@ void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const 
 }
 
 void orc_hessian_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
-                      int32_t lambda_mode, double g_scale, double w_g, double* phi, double* grad,
-                      double* H, double* dBdl, int32_t nthreads) {
+                      int32_t lambda_mode, double g_scale, double w_g, double pxe_near_z,
+                      double* phi, double* grad, double* H, double* dBdl, int32_t nthreads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
 #endif
   for (int64_t i = 0; i < n; ++i)
     orc_hessian(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, lambda_mode, g_scale,
-                w_g, phi + i, grad + 3 * i, H + 9 * i, dBdl + 3 * i);
+                w_g, pxe_near_z, phi + i, grad + 3 * i, H + 9 * i, dBdl + 3 * i);
 }
 
 /* Solve H v = r for a symmetric m x m matrix (m <= 3) by Cholesky; returns 0 when H is not
@@ -709,7 +751,8 @@ static int chol_solve(int m, const double* H, const double* r, double* v) {
 
 void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                       const double* gB, int32_t lambda_mode, double g_scale, double w_g,
-                      double* gB0, double* v_out, int32_t* flags, int32_t nthreads) {
+                      double pxe_near_z, double* gB0, double* v_out, int32_t* flags,
+                      int32_t nthreads) {
   const int m = lambda_mode == 1 ? 1 : 3;
   const double w = bd->dA / TWO_PI;
   double* vp = (double*)calloc((size_t)(n > 0 ? n : 1) * 3, sizeof(double));
@@ -722,14 +765,17 @@ void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, cons
   for (int64_t i = 0; i < n; ++i) {
     const double xi = xyz[3 * i], yi = xyz[3 * i + 1], zi = xyz[3 * i + 2];
     double phi, grad[3], H[9], dBdl[3], gl[3] = {0, 0, 0}, v[3] = {0, 0, 0};
-    orc_hessian(bd, xi, yi, zi, lam + 3 * i, lambda_mode, g_scale, w_g, &phi, grad, H, dBdl);
+    orc_hessian(bd, xi, yi, zi, lam + 3 * i, lambda_mode, g_scale, w_g, pxe_near_z, &phi, grad, H,
+                dBdl);
     if (lambda_mode == 1) gl[0] = gB[3 * i] * dBdl[0] + gB[3 * i + 1] * dBdl[1] + gB[3 * i + 2] * dBdl[2];
     else for (int p = 0; p < 3; ++p) gl[p] = gB[3 * i + p] * dBdl[p];
     if (!chol_solve(m, H, gl, v)) { fl[i] = 1; v[0] = v[1] = v[2] = 0.0; }
     for (int p = 0; p < 3; ++p) vp[3 * i + p] = lambda_mode == 1 ? v[0] : v[p];
     hd lh[3], B[3], G[9];
+    double cB[3], cG[9];
+    pxe_terms(bd, xi, yi, zi, pxe_near_z, cB, cG);
     for (int p = 0; p < 3; ++p) { lh[p] = hd_k(lam[3 * i + p]); lh[p].a = vp[3 * i + p]; }
-    field_hd(bd, xi, yi, zi, lh, B, G);
+    field_hd_pxe(bd, xi, yi, zi, lh, cB, cG, B, G);
     for (int p = 0; p < 3; ++p) q[12 * i + p] = B[p];
     for (int e = 0; e < 9; ++e) q[12 * i + 3 + e] = G[e];
     if (v_out) for (int p = 0; p < 3; ++p) v_out[3 * i + p] = vp[3 * i + p];
@@ -751,6 +797,11 @@ void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, cons
         l.a = vp[3 * i + p];
         hd w4[4];
         weights_hd(xyz[3 * i] - xk, xyz[3 * i + 1] - yk, xyz[3 * i + 2], l, w, w4);
+        if (pxe_near_z > 0.0 && xyz[3 * i + 2] <= pxe_near_z) {
+          double c[4];
+          pxe_pixel_weights(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], i_, j_, c);
+          for (int e = 0; e < 4; ++e) w4[e].v += c[e];
+        }
         double t = gB[3 * i + p] * w4[0].v;
         if (!fl[i]) {
           hd B[3], G[9];
@@ -939,4 +990,117 @@ void orc_vjp_q9(const orc_boundary* bd, int64_t n, const double* xyz, const doub
       gB0[3 * k + p] = nsum_get(&s);
     }
   free(A);
+}
+
+/* ------------------------------------- pixel-exact near field (piecewise-constant B0) ---- */
+/* Exact integral of K0 = z / (2 pi r^3) (the lambda = 0 kernel) over the rectangle
+ * [xa, xb] x [ya, yb], given in corner-minus-point coordinates, and its derivatives with respect
+ * to the point (x_i, y_i, z_i).  With F(a, b) = arctan(a b / (z R)), R = sqrt(a^2 + b^2 + z^2),
+ * the integral is the solid angle over 2 pi,
+ *   (1 / 2 pi) [F(xb, yb) - F(xa, yb) - F(xb, ya) + F(xa, ya)],
+ * and dF/da = b z / (R (a^2 + z^2)), dF/db = a z / (R (b^2 + z^2)),
+ * dF/dz = -a b (R^2 + z^2) / (R (a^2 + z^2) (b^2 + z^2)); a corner coordinate a = x_c - x_i
+ * moves as -x_i. */
+void orc_rect_exact(double xa, double xb, double ya, double yb, double z, double out[4]) {
+  const double cx[2] = {xa, xb}, cy[2] = {ya, yb};
+  double v = 0, gx = 0, gy = 0, gz = 0;
+  for (int u = 0; u < 2; ++u)
+    for (int w = 0; w < 2; ++w) {
+      const double s = (u == w) ? 1.0 : -1.0;
+      const double a = cx[u], b = cy[w];
+      const double R = sqrt(a * a + b * b + z * z);
+      v += s * atan(a * b / (z * R));
+      gx -= s * (b * z / (R * (a * a + z * z)));
+      gy -= s * (a * z / (R * (b * b + z * z)));
+      gz -= s * (a * b * (R * R + z * z) / (R * (a * a + z * z) * (b * b + z * z)));
+    }
+  out[0] = v / TWO_PI;
+  out[1] = gx / TWO_PI;
+  out[2] = gy / TWO_PI;
+  out[3] = gz / TWO_PI;
+}
+
+/* Weights of pixel (i, j) in the pixel-exact correction at a point: the exact integral of K0
+ * over the pixel minus the midpoint rule's dA K0 at its centre, for B (c[0]) and for the
+ * derivatives with respect to the point's x, y, z (c[1..3]); dK0/dx_i = -3 z dx / (2 pi r^5),
+ * dK0/dz = (1 / r^3 - 3 z^2 / r^5) / (2 pi). */
+static void pxe_pixel_weights(const orc_boundary* bd, double xi, double yi, double zi, int i, int j,
+                              double c[4]) {
+  const double hx = bd->hx, hy = bd->hy, dA = bd->dA;
+  const double xk = bd->x0 + i * hx, yk = bd->y0 + j * hy;
+  const double dx = xi - xk, dy = yi - yk;
+  const double r2 = dx * dx + dy * dy + zi * zi, r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2;
+  double e[4];
+  orc_rect_exact(xk - 0.5 * hx - xi, xk + 0.5 * hx - xi, yk - 0.5 * hy - yi, yk + 0.5 * hy - yi,
+                 zi, e);
+  c[0] = e[0] - dA * zi / (TWO_PI * r3);
+  c[1] = e[1] - dA * (-3.0 * zi * dx / (TWO_PI * r5));
+  c[2] = e[2] - dA * (-3.0 * zi * dy / (TWO_PI * r5));
+  c[3] = e[3] - dA * ((1.0 / r3 - 3.0 * zi * zi / r5) / TWO_PI);
+}
+
+void orc_pxe_correction(const orc_boundary* bd, double xi, double yi, double zi, double dB[3],
+                        double dG[9]) {
+  nsum sB[3], sG[9];
+  memset(sB, 0, sizeof sB);
+  memset(sG, 0, sizeof sG);
+  for (int j = 0; j < bd->ny; ++j)
+    for (int i = 0; i < bd->nx; ++i) {
+      double c[4];
+      pxe_pixel_weights(bd, xi, yi, zi, i, j, c);
+      for (int p = 0; p < 3; ++p) {
+        const double b0 = (double)comp_ptr(bd, p)[(int64_t)j * bd->nx + i];
+        nsum_add(&sB[p], c[0] * b0);
+        for (int q = 0; q < 3; ++q) nsum_add(&sG[3 * p + q], c[1 + q] * b0);
+      }
+    }
+  for (int p = 0; p < 3; ++p) {
+    dB[p] = nsum_get(&sB[p]);
+    for (int q = 0; q < 3; ++q) dG[3 * p + q] = nsum_get(&sG[3 * p + q]);
+  }
+}
+
+void orc_field_pxe(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                   double near_z, double B[3], double G[9], double dBdl[3]) {
+  double Gl[9];
+  orc_field(bd, xi, yi, zi, lam, B, Gl, dBdl);
+  if (zi <= near_z) {
+    double dB[3], dG[9];
+    orc_pxe_correction(bd, xi, yi, zi, dB, dG);
+    for (int p = 0; p < 3; ++p) B[p] += dB[p];
+    for (int q = 0; q < 9; ++q) Gl[q] += dG[q];
+  }
+  if (G) memcpy(G, Gl, sizeof Gl);
+}
+
+void orc_eval_many_pxe(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                       double near_z, double* B, double* G, double* dBdl, int32_t nthreads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t i = 0; i < n; ++i)
+    orc_field_pxe(bd, xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lam + 3 * i, near_z, B + 3 * i,
+                  G ? G + 9 * i : NULL, dBdl ? dBdl + 3 * i : NULL);
+}
+
+void orc_vjp_pxe(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                 const double* gB, double near_z, double* gB0, int32_t nthreads) {
+  /* the midpoint adjoint plus, for every point with z <= near_z, its pixel weights c[0] times gB */
+  orc_vjp(bd, n, xyz, lam, gB, gB0, nthreads);
+  const int64_t nb = (int64_t)bd->nx * bd->ny;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads > 0 ? nthreads : 1)
+#endif
+  for (int64_t k = 0; k < nb; ++k) {
+    const int i = (int)(k % bd->nx), j = (int)(k / bd->nx);
+    nsum s[3];
+    memset(s, 0, sizeof s);
+    for (int64_t q = 0; q < n; ++q) {
+      if (!(xyz[3 * q + 2] <= near_z)) continue;
+      double c[4];
+      pxe_pixel_weights(bd, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2], i, j, c);
+      for (int p = 0; p < 3; ++p) nsum_add(&s[p], gB[3 * q + p] * c[0]);
+    }
+    for (int p = 0; p < 3; ++p) gB0[3 * k + p] += nsum_get(&s[p]);
+  }
 }

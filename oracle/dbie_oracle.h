@@ -40,7 +40,9 @@ typedef struct {
                             so lambda = 0 itself is a stationary point */
   int32_t quad_order;    /* 0: midpoint rule at pixel centres (Eq. 16); g >= 1: nine-node
                             elements with g x g Gauss points each (Eq. 15, orc_field_q9);
+                            -1: pixel-exact near field for z <= pxe_near_z (orc_field_pxe);
                             the simplex only */
+  double pxe_near_z;
 } orc_options;
 
 /* Field and its derivatives at one point for a given lambda triple:
@@ -117,17 +119,38 @@ void orc_eval_many_q9(const orc_boundary* bd, int64_t n, const double* xyz, cons
 void orc_vjp_q9(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                 const double* gB, int32_t order, double* gB0, int32_t nthreads);
 
+/* Pixel-exact near field (the exact near-field integration of the lambda = 0 kernel):
+ * for a point with z <= near_z the boundary is read as constant on each pixel rectangle
+ * (hx x hy around the pixel centre), and the lambda = 0 part of the kernel, K0 = z / (2 pi r^3),
+ * is integrated exactly over every pixel (the closed-form solid angle, orc_rect_exact), while the
+ * lambda-dependent remainder z [lambda r sin(lambda r) + cos(lambda r) - 1] / (2 pi r^3) stays on
+ * the midpoint rule of Eq. 16.  So B = B_midpoint(lambda) + sum_k B0_k (int_pixel K0 - dA K0(c_k)),
+ * a correction that does not depend on lambda.  Points above near_z take the midpoint rule.
+ * orc_rect_exact: the integral of K0 over [xa, xb] x [ya, yb] (corner minus point coordinates)
+ * and its derivatives with respect to the point (out[1..3]: x_i, y_i, z_i).
+ * orc_pxe_correction: the correction of B (3) and of dB_p/dx_j (9) at one point, whatever z. */
+void orc_rect_exact(double xa, double xb, double ya, double yb, double z, double out[4]);
+void orc_pxe_correction(const orc_boundary* bd, double xi, double yi, double zi, double dB[3],
+                        double dG[9]);
+void orc_field_pxe(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
+                   double near_z, double B[3], double G[9], double dBdl[3]);
+void orc_eval_many_pxe(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                       double near_z, double* B, double* G, double* dBdl, int32_t nthreads);
+void orc_vjp_pxe(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
+                 const double* gB, double near_z, double* gB0, int32_t nthreads);
+
 /* Second order, by hyper-dual numbers through the whole quadrature (no difference step; not in
  * the paper).  At one point and lambda: Phi, its gradient grad[q] = dPhi/dlambda_q, the Hessian
  * H[3q+r] = d^2 Phi / dlambda_q dlambda_r and dBdl[p] = dB_p/dlambda_p.  lambda_mode = 1 (one
  * shared lambda): grad[0], H[0] and dBdl[p] = dB_p/dlambda are the derivatives along the shared
- * lambda, the other entries 0. */
+ * lambda, the other entries 0.  pxe_near_z > 0: B and grad B carry the pixel-exact correction
+ * (orc_pxe_correction) at points with z <= pxe_near_z; <= 0: the midpoint rule. */
 void orc_hessian(const orc_boundary* bd, double xi, double yi, double zi, const double lam[3],
-                 int32_t lambda_mode, double g_scale, double w_g, double* phi, double grad[3],
-                 double H[9], double dBdl[3]);
+                 int32_t lambda_mode, double g_scale, double w_g, double pxe_near_z, double* phi,
+                 double grad[3], double H[9], double dBdl[3]);
 void orc_hessian_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
-                      int32_t lambda_mode, double g_scale, double w_g, double* phi, double* grad,
-                      double* H, double* dBdl, int32_t nthreads);
+                      int32_t lambda_mode, double g_scale, double w_g, double pxe_near_z,
+                      double* phi, double* grad, double* H, double* dBdl, int32_t nthreads);
 
 /* Gradient of L(B) with respect to the magnetogram THROUGH the lambda search: lambda* is taken as
  * a stationary point of Phi (grad_lambda Phi = 0), so d(lambda*) / dB0 = -H^-1 d(grad_lambda Phi) / dB0
@@ -135,10 +158,12 @@ void orc_hessian_many(const orc_boundary* bd, int64_t n, const double* xyz, cons
  *   gB0[k][p] = sum_i gB_pi a_ik(lambda_pi) - d/dB0_pk sum_i v_i . grad_lambda Phi_i,
  *   v_i = H_i^-1 dL/dlambda_i,  dL/dlambda_p = gB_p dB_p/dlambda_p (summed over p when tied).
  * v_out (n, 3, nullable) gets v per component; flags (n, nullable) is 1 where H is not positive
- * definite (that point keeps only the fixed-lambda term). */
+ * definite (that point keeps only the fixed-lambda term).  pxe_near_z as for orc_hessian: the
+ * weights a_ik then include the pixel-exact correction at the points with z <= pxe_near_z. */
 void orc_implicit_vjp(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                       const double* gB, int32_t lambda_mode, double g_scale, double w_g,
-                      double* gB0, double* v_out, int32_t* flags, int32_t nthreads);
+                      double pxe_near_z, double* gB0, double* v_out, int32_t* flags,
+                      int32_t nthreads);
 
 /* Noise propagation at fixed lambda: with independent zero-mean noise of standard deviation
  * s_p[k] on pixel k of component p (sx, sy, sz are (ny, nx); a NULL array means sigma0), B is
@@ -149,7 +174,8 @@ void orc_noise_var(const orc_boundary* bd, int64_t n, const double* xyz, const d
 
 /* Batched entry points over n points (OpenMP over points when nthreads > 1). */
 void orc_objective_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
-                        double g_scale, double w_g, double* fgphi, double* dphi, int32_t nthreads);
+                        double g_scale, double w_g, double pxe_near_z, double* fgphi,
+                        double* dphi, int32_t nthreads);
 void orc_eval_many(const orc_boundary* bd, int64_t n, const double* xyz, const double* lam,
                    int32_t deriv, double fd_delta, double* B, double* G, double* dBdl,
                    int32_t nthreads);
