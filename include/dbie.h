@@ -81,7 +81,9 @@ typedef struct {
                           and the search starts at lambda_init + simplex_step (1, 1, 1) (Phi is even
                           in every lambda_p, so lambda_init = 0 itself is a stationary point). */
   double near_z;       /* mixed precision: points with z <= near_z get their near-field pixels
-                          (a 7 x 7 window) summed in FP64; < 0 selects 2 * hx, 0 disables */
+                          (a 7 x 7 window) summed in FP64; with DBIE_QUAD_PIXEL_EXACT also the
+                          height up to which the exact near-field integration applies (both
+                          precisions); < 0 selects 2 * hx, 0 disables */
 } dbie_options;
 
 /* Per-point outputs of dbie_solve; every pointer may be NULL except B and lambda. */
@@ -136,8 +138,19 @@ dbie_status dbie_set_boundary(dbie_ctx* ctx, const float* Bx, const float* By, c
  *     used).  The pair sums then run over the ((nx-1)/2 g) x ((ny-1)/2 g) Gauss points, each
  *     carrying the interpolated field times its weights; adjoints are gathered back to the
  *     nodes.  dbie_noise_var needs order 0.
+ *   order = DBIE_QUAD_PIXEL_EXACT (-1): the midpoint rule plus the exact near-field integration
+ *     of the lambda = 0 kernel (the closed-form solid angle of each pixel rectangle, Eq. 6 at
+ *     lambda = 0).  At points with z <= opt->near_z the magnetogram is read as constant on each
+ *     hx x hy pixel, z / (2 pi r^3) is integrated exactly over every pixel, and the
+ *     lambda-dependent remainder z [lambda r sin(lambda r) + cos(lambda r) - 1] / (2 pi r^3)
+ *     stays on the midpoint rule; this removes the midpoint rule's lattice error at small z.
+ *     The correction of B and grad B does not depend on lambda (a solve computes it once per
+ *     point), and it enters every call that returns B, grad B, Phi or an adjoint; dB/dlambda and
+ *     the other lambda-derivatives are the midpoint rule's.  opt->near_z = 0 turns it off for a
+ *     call.  dbie_noise_var is not available in this mode.
  * Restages the stored magnetogram; synchronises `stream`.  DBIE_EINVAL for an order outside
- * 0..8 or even / too small nx, ny with order > 0. */
+ * -1..8 or even / too small nx, ny with order > 0. */
+#define DBIE_QUAD_PIXEL_EXACT (-1)
 dbie_status dbie_set_quadrature(dbie_ctx* ctx, int32_t order, void* stream);
 
 /* Evaluate Eq. 16 at n points for given lambda (n, 3) float32, and optionally

@@ -34,6 +34,7 @@ UNITS = {
     "pairsum_f64.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],
+    "pxe.cu": [],
 }
 
 

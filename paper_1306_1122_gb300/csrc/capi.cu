@@ -78,14 +78,14 @@ struct Misc {
 };
 
 struct SolveBufs {
-  DBuf probs, ppos, lam0, sd, si, q_cnt_pass, item_off, ctrl, out, res, codes;
+  DBuf probs, ppos, lam0, sd, si, q_cnt_pass, item_off, ctrl, out, res, codes, corr;
   DBuf qpos[2], qlam[2], q_cnt[2], act[2], near[2];
   cudaGraphExec_t exec = nullptr;
   std::vector<unsigned char> key;   // launch arguments the cached graph was captured with
   std::vector<cudaEvent_t> ev;      // profiling events inside the graph (2 per round)
   void release() {
     for (DBuf* b : {&probs, &ppos, &lam0, &sd, &si, &q_cnt_pass, &item_off, &ctrl, &out, &res,
-                    &codes})
+                    &codes, &corr})
       b->release();
     for (int s = 0; s < 2; ++s)
       for (DBuf* b : {&qpos[s], &qlam[s], &q_cnt[s], &act[s], &near[s]}) b->release();
@@ -155,6 +155,8 @@ struct dbie_ctx {
   DBuf b0raw;                     // the magnetogram as given (3 x npix float32), for restaging
   DBuf vtmp;                      // per-quadrature-point adjoint before the gather to nodes
   int quad_g = 0;                 // 0: pixel centres (Eq. 16); g: nine-node elements (Eq. 15)
+  bool pxe = false;               // pixel-exact near field on the pixel-centre rule
+  DBuf pxe_corr, pxe_pos, pxe_list, pxe_w;   // its per-call scratch
   QuadInfo qi{};
   int64_t nquad = 0;              // quadrature points: npix, or (elements x g)^2
   int32_t qnx = 0, qny = 0;       // quadrature-point grid
@@ -459,7 +461,8 @@ void dbie_destroy(dbie_ctx* c) {
   cudaDeviceSynchronize();
   for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
-                  &c->tv64, &c->probv, &c->b0raw, &c->vtmp})
+                  &c->tv64, &c->probv, &c->b0raw, &c->vtmp, &c->pxe_corr, &c->pxe_pos,
+                  &c->pxe_list, &c->pxe_w})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -486,6 +489,7 @@ static ProbDesc desc_of(const dbie_ctx* c) {
   pd.nf32 = c->quad_g == 0 ? NFIELD : NFIELD_SPLIT;
   for (int a = 0; a < MAX_GAUSS; ++a) pd.gx[a] = c->qi.gx[a];
   pd.x0 = c->x0; pd.y0 = c->y0; pd.hx = c->hx; pd.hy = c->hy;
+  pd.area = c->dA;
   return pd;
 }
 
@@ -500,6 +504,32 @@ static dbie_status restage(dbie_ctx* c, cudaStream_t s) {
   else
     launch_stage_q9(B0, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy, c->qi, c->ntiles,
                     c->t32.as<float>(), c->t64.as<double>(), s);
+  CUDA_TRY(cudaGetLastError());
+  return DBIE_OK;
+}
+
+// Pixel-exact near field of one call: on for this context and options (near_z > 0 bounds it).
+static bool pxe_on(const dbie_ctx* c, const dbie_options& o) { return c->pxe && o.near_z > 0; }
+
+// Correction of B and grad B (12 per point, c->pxe_corr) at n points packed as float4 (problem 0).
+static dbie_status pxe_correct(dbie_ctx* c, int64_t n, const float4* pos, bool fp64,
+                               const dbie_options& o, cudaStream_t s) {
+  DBIE_TRY(ensure(c->pxe_corr, sizeof(double) * 12 * n));
+  launch_pxe_corr(fp64, c->prob.as<ProbDesc>(), n, pos, o.near_z, c->pxe_corr.as<double>(),
+                  16 * c->sm_count, s);
+  CUDA_TRY(cudaGetLastError());
+  return DBIE_OK;
+}
+
+// gB0 += the transpose of the correction at n points with weights w (full: 12 per point,
+// else 3 = gB).
+static dbie_status pxe_adjoint(dbie_ctx* c, int64_t n, const float4* pos, const double* w,
+                               bool full, bool fp64, const dbie_options& o, double* gB0,
+                               cudaStream_t s) {
+  DBIE_TRY(ensure(c->pxe_list, sizeof(int32_t) * (n + 1)));
+  int32_t* list = c->pxe_list.as<int32_t>();
+  launch_pxe_adjoint(fp64, full, c->prob.as<ProbDesc>(), n, c->npix, pos, o.near_z, w, list,
+                     list + n, gB0, s);
   CUDA_TRY(cudaGetLastError());
   return DBIE_OK;
 }
@@ -648,14 +678,18 @@ static void gauss_rule(int m, double* x, double* w) {
 
 dbie_status dbie_set_quadrature(dbie_ctx* c, int32_t order, void* stream) {
   if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
-  if (order < 0 || order > MAX_GAUSS)
-    return fail(DBIE_EINVAL, "order must be 0 (pixel centres) or 1.." + std::to_string(MAX_GAUSS));
+  if (order < DBIE_QUAD_PIXEL_EXACT || order > MAX_GAUSS)
+    return fail(DBIE_EINVAL, "order must be -1 (pixel-exact near field), 0 (pixel centres) or "
+                             "1.." + std::to_string(MAX_GAUSS));
+  const bool pxe = order == DBIE_QUAD_PIXEL_EXACT;
+  if (pxe) order = 0;
   if (order > 0 && (c->nx < 3 || c->ny < 3 || c->nx % 2 == 0 || c->ny % 2 == 0))
     return fail(DBIE_EINVAL, "nine-node elements need odd nx, ny >= 3");
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   CUDA_TRY(cudaStreamSynchronize(s));   // no pass of the old quadrature may still read the tiles
   c->quad_g = order;
+  c->pxe = pxe;
   c->qi = QuadInfo{};
   c->qi.g = order;
   if (order > 0) {
@@ -717,9 +751,12 @@ dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lam
     dF = fgphi ? so.take<double>(3 * n) : nullptr;
   }
   DBIE_TRY(pass_single(c, var, fp64, o, n, d_xyz, d_lam, nullptr, s));
+  const bool pxe = pxe_on(c, o);
+  if (pxe) DBIE_TRY(pxe_correct(c, n, c->qpos.as<float4>(), fp64, o, s));
   Misc* m = c->misc.as<Misc>();
   launch_finalize_eval(var, n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
-                       c->qlam.as<Lam4>(), o.g_scale, o.w_g, dB, dG, dL, nullptr, dF, s);
+                       c->qlam.as<Lam4>(), o.g_scale, o.w_g, dB, dG, dL, nullptr, dF,
+                       pxe ? c->pxe_corr.as<double>() : nullptr, s);
   CUDA_TRY(cudaGetLastError());
   if (mem_kind == DBIE_MEM_HOST) {
     CUDA_TRY(cudaMemcpyAsync(B, dB, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
@@ -765,9 +802,12 @@ dbie_status dbie_objective(dbie_ctx* c, int64_t n, const float* xyz, const float
     dD = dphi ? so.take<double>(3 * n) : nullptr;
   }
   DBIE_TRY(pass_single(c, VAR_OBJN, fp64, o, n, d_xyz, d_lam, nullptr, s));
+  const bool pxe = pxe_on(c, o);
+  if (pxe) DBIE_TRY(pxe_correct(c, n, c->qpos.as<float4>(), fp64, o, s));
   Misc* m = c->misc.as<Misc>();
   launch_finalize_objective(n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
-                            c->qlam.as<Lam4>(), o.g_scale, o.w_g, dF, dD, nullptr, s);
+                            c->qlam.as<Lam4>(), o.g_scale, o.w_g, dF, dD, nullptr,
+                            pxe ? c->pxe_corr.as<double>() : nullptr, s);
   CUDA_TRY(cudaGetLastError());
   if (mem_kind == DBIE_MEM_HOST) {
     if (fgphi) CUDA_TRY(cudaMemcpyAsync(fgphi, dF, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
@@ -878,12 +918,17 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
       c->pending_pairs.push_back((double)n * (double)nq);
     }
     DBIE_TRY(finalize_adjoint(c, &m->plan, d_gB0, accumulate ? 1 : 0, s));
+    if (pxe_on(c, o)) {
+      DBIE_TRY(ensure(c->pxe_pos, sizeof(float4) * n));
+      launch_pack_points(n, d_xyz, 0, c->pxe_pos.as<float4>(), s);
+      DBIE_TRY(pxe_adjoint(c, n, c->pxe_pos.as<float4>(), d_gB, false, fp64, o, d_gB0, s));
+    }
     if (d_glam) {
       // dL/dlambda_p = gB_p * z lambda_p Sl_p, from a value + dB/dlambda pass.
       DBIE_TRY(pass_single(c, VAR_VL, fp64, o, n, d_xyz, nullptr, d_lam, s));
       launch_finalize_eval(VAR_VL, n, &m->plan, m->item_off, c->out.as<double>(),
                            c->qpos.as<float4>(), c->qlam.as<Lam4>(), o.g_scale, o.w_g, nullptr,
-                           nullptr, d_glam, d_gB, nullptr, s);
+                           nullptr, d_glam, d_gB, nullptr, nullptr, s);
       CUDA_TRY(cudaGetLastError());
     }
   }
@@ -965,9 +1010,12 @@ dbie_status dbie_hessian(dbie_ctx* c, int64_t n, const float* xyz, const double*
     dH = hess ? so.take<double>(9 * n) : nullptr;
   }
   DBIE_TRY(pass_single(c, VAR_HESS, fp64, o, n, d.xyz, nullptr, d.lam, s, tied));
+  const bool pxe = pxe_on(c, o);
+  if (pxe) DBIE_TRY(pxe_correct(c, n, c->qpos.as<float4>(), fp64, o, s));
   Misc* m = c->misc.as<Misc>();
   launch_finalize_hessian(n, &m->plan, m->item_off, c->out.as<double>(), c->qpos.as<float4>(),
-                          c->qlam.as<Lam4>(), tied ? 1 : 3, o.g_scale, o.w_g, dP, dG, dH, s);
+                          c->qlam.as<Lam4>(), tied ? 1 : 3, o.g_scale, o.w_g, dP, dG, dH,
+                          pxe ? c->pxe_corr.as<double>() : nullptr, s);
   CUDA_TRY(cudaGetLastError());
   if (mem_kind == DBIE_MEM_HOST) {
     if (phi) CUDA_TRY(cudaMemcpyAsync(phi, dP, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -1015,13 +1063,19 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
     // 1. Hessian pass at lambda (ten sums per component) -> 2. per-point H, v and the adjoint
     // weights, written as point records -> 3. seven-weight adjoint sweep over the pixels.
     DBIE_TRY(pass_single(c, VAR_HESS, fp64, o, n, d.xyz, nullptr, d.lam, s, tied));
+    const bool pxe = pxe_on(c, o);
+    if (pxe) {
+      DBIE_TRY(pxe_correct(c, n, c->qpos.as<float4>(), fp64, o, s));
+      DBIE_TRY(ensure(c->pxe_w, sizeof(double) * 12 * n));
+    }
     Misc* m = c->misc.as<Misc>();
     const int nptiles = (int)((n + TILE - 1) / TILE);
     DBIE_TRY(ensure(c->ptiles, (size_t)nptiles * VJP7_NFIELD * TILE * (fp64 ? 8 : 4)));
     launch_implicit_weights(n, nptiles, &m->plan, m->item_off, c->out.as<double>(),
                             c->qpos.as<float4>(), c->qlam.as<Lam4>(), d.gB, tied ? 1 : 3,
                             o.g_scale, o.w_g, c->ptiles.as<float>(), c->ptiles.as<double>(),
-                            fp64 ? 1 : 0, d_v, d_fl, s);
+                            fp64 ? 1 : 0, d_v, d_fl, pxe ? c->pxe_corr.as<double>() : nullptr,
+                            pxe ? c->pxe_w.as<double>() : nullptr, s);
     CUDA_TRY(cudaGetLastError());
     const KernelRef k = (!fp64 && c->quad_g != 0) ? vjp7_ref_split(tied) : vjp7_ref(fp64, tied);
     const int grid = persistent_grid(k, c->device);
@@ -1060,6 +1114,9 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
       c->pending_pairs.push_back((double)n * (double)nq);
     }
     DBIE_TRY(finalize_adjoint(c, &m->plan, d_gB0, accumulate ? 1 : 0, s));
+    if (pxe)
+      DBIE_TRY(pxe_adjoint(c, n, c->qpos.as<float4>(), c->pxe_w.as<double>(), true, fp64, o,
+                           d_gB0, s));
   }
   if (mem_kind == DBIE_MEM_HOST) {
     CUDA_TRY(cudaMemcpyAsync(gB0, d_gB0, sizeof(double) * 3 * npix, cudaMemcpyDeviceToHost, s));
@@ -1081,7 +1138,7 @@ dbie_status dbie_noise_var(dbie_ctx* c, int64_t n, const float* xyz, const doubl
   if (n > 0 && (!xyz || !lambda || !var))
     return fail(DBIE_EINVAL, "xyz, lambda and var must not be NULL");
   if (!std::isfinite(sigma0)) return fail(DBIE_EINVAL, "sigma0 must be finite");
-  if (c->quad_g != 0)
+  if (c->quad_g != 0 || c->pxe)
     return fail(DBIE_EINVAL, "the noise variance needs the pixel-centre rule (dbie_set_quadrature 0)");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
@@ -1214,6 +1271,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     pd.step = op.simplex_step;
     pd.g_scale = op.g_scale;
     pd.near_z = (!fp64 && op.near_z > 0) ? op.near_z : 0.0;
+    pd.pxe_z = pxe_on(cp, op) ? op.near_z : 0.0;
     pd.q_off = (int64_t)(dim + 1) * pt_off[p];
     pd.pt_off = pt_off[p];
     pd.npts = n[p];
@@ -1254,6 +1312,15 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   }
   for (int sd = 0; sd < 2; ++sd) CUDA_TRY(cudaMemsetAsync(b.q_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
   if (codes_stride) CUDA_TRY(cudaMemsetAsync(b.codes.p, 0, (size_t)codes_stride * N, s));
+  // Pixel-exact near field: the lambda-independent corrections of every point, once per solve.
+  bool pxe_any = false;
+  for (int q = 0; q < nprob; ++q) pxe_any |= pds[q].pxe_z > 0;
+  if (pxe_any) {
+    DBIE_TRY(ensure(b.corr, sizeof(double) * 12 * N));
+    launch_pxe_corr(fp64, b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), -1.0,
+                    b.corr.as<double>(), 16 * c->sm_count, s);
+    CUDA_TRY(cudaGetLastError());
+  }
 
   // Kernel arguments.
   char* rb = b.res.as<char>();
@@ -1295,6 +1362,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     a.codes = codes_stride ? b.codes.as<char>() : nullptr;
     a.codes_stride = codes_stride;
     a.err = c->err.as<unsigned>();
+    a.corr = pxe_any ? b.corr.as<double>() : nullptr;
   }
   // Initial simplex and its queries go to side 0.
   SolveArgs a0 = sa[1];  // "next" of the side-1 round is side 0

@@ -89,6 +89,8 @@ struct ProbDesc {
   double step;              // initial simplex edge of this problem's lambda search
   double g_scale;           // Delta V / Delta sigma of Eq. 9 for this problem
   double near_z;            // FP64 near field for z <= near_z (0: off)
+  double pxe_z;             // pixel-exact near field for z <= pxe_z (0: off)
+  double area;              // pixel area of the midpoint weights (dA; usually hx hy)
   int64_t q_off;            // first query slot of this problem
   int64_t pt_off;           // first global point index
   int64_t npts;

@@ -67,28 +67,40 @@ void launch_pack_vjp(int64_t n, const float* xyz, const double* lam, const doubl
 void launch_finalize_vjp(int64_t npix, const PlanHdr* plan, const double* out, double scale,
                          double* gB0, int accumulate, cudaStream_t s);
 
+// pxe.cu (pixel-exact near field)
+void launch_pxe_corr(bool fp64, const ProbDesc* probs, int64_t n, const float4* pos, double zmax,
+                     double* corr, int grid, cudaStream_t s);
+void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int64_t npix,
+                        const float4* pos, double zmax, const double* w, int32_t* list,
+                        int32_t* cnt, double* gB0, cudaStream_t s);
+
 void launch_count_bad(const float* a, int64_t n, int mode, int32_t* cnt, cudaStream_t s);
 void launch_pack_points(int64_t n, const float* xyz, int pidx, float4* ppos, cudaStream_t s);
 
 // solve.cu
+// corr (nullable): per query the pixel-exact correction of B (3) and grad B (9), added after the
+// sums are assembled.
 void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t* item_off,
                           const double* out, const float4* qpos, const Lam4* qlam, double g_scale,
                           double w_g, double* B, double* gradB, double* dBdl,
-                          const double* gB_for_glam, double* fgphi, cudaStream_t s);
+                          const double* gB_for_glam, double* fgphi, const double* corr,
+                          cudaStream_t s);
 void launch_finalize_objective(int64_t n, const PlanHdr* plan, const int32_t* item_off,
                                const double* out, const float4* qpos, const Lam4* qlam,
                                double g_scale, double w_g, double* fgphi, double* dphi, double* B,
-                               cudaStream_t s);
+                               const double* corr, cudaStream_t s);
 // second_order.cu
 void launch_finalize_hessian(int64_t n, const PlanHdr* plan, const int32_t* item_off,
                              const double* out, const float4* qpos, const Lam4* qlam, int dim,
                              double g_scale, double w_g, double* phi, double* grad, double* hess,
-                             cudaStream_t s);
+                             const double* corr, cudaStream_t s);
+// corr as above; pxe_w (nullable, with corr): per point the 12 weights of the transposed
+// correction, gB_p - dW/dB_p and -dW/d(dB_p/dx_j) with W = v . grad_lambda Phi (at 4 p + m).
 void launch_implicit_weights(int64_t n, int nptiles, const PlanHdr* plan, const int32_t* item_off,
                              const double* out, const float4* qpos, const Lam4* qlam,
                              const double* gB, int dim, double g_scale, double w_g, float* p32,
                              double* p64, int fp64, double* v_out, int32_t* flags,
-                             cudaStream_t s);
+                             const double* corr, double* pxe_w, cudaStream_t s);
 void launch_finalize_nv(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,
                         const float4* qpos, double* var, cudaStream_t s);
 void launch_stage_variance(const float* sx, const float* sy, const float* sz, double sigma0,

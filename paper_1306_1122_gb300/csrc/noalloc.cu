@@ -167,7 +167,7 @@ extern "C" dbie_status dbie_eval_noalloc(int32_t nx, int32_t ny, double x0, doub
   launch_nearfield(VAR_V, false, prob, near, &ctl->near_cnt, qpos, qlam, &ctl->plan,
                    ctl->item_off, out, 2 * sms, s);
   launch_finalize_eval(VAR_V, n, &ctl->plan, ctl->item_off, out, qpos, qlam, hx / 6.0, 1.0, B,
-                       nullptr, nullptr, nullptr, nullptr, s);
+                       nullptr, nullptr, nullptr, nullptr, nullptr, s);
   e = cudaGetLastError();
   if (e != cudaSuccess) return err(DBIE_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   // Synchronous: report a bounded-wait timeout of this call's kernels.

@@ -170,7 +170,7 @@ __global__ void finalize_hessian_kernel(int64_t n, const PlanHdr* __restrict__ p
                                         const float4* __restrict__ qpos,
                                         const Lam4* __restrict__ qlam, int dim, double g_scale,
                                         double w_g, double* phi_out, double* grad_out,
-                                        double* hess_out) {
+                                        double* hess_out, const double* __restrict__ corr) {
   constexpr int NSUM = 3 * nsum_per_comp(VAR_HESS);
   const PlanHdr h = *plan;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -182,6 +182,8 @@ __global__ void finalize_hessian_kernel(int64_t n, const PlanHdr* __restrict__ p
     const double lam[3] = {l.x, dim == 1 ? l.x : l.y, dim == 1 ? l.x : l.z};
     double q[12], d1[12], d2[12], phi = 0.0, grad[3], H[9];
     q_derivs(S, (double)qpos[i].z, lam, q, d1, d2);
+    if (corr)   // pixel-exact near field: B and grad B move, their lambda-derivatives do not
+      for (int m = 0; m < 12; ++m) q[m] += corr[12 * i + m];
     hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
     if (phi_out) phi_out[i] = phi;
     if (grad_out)
@@ -200,7 +202,8 @@ __global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* _
                                         const Lam4* __restrict__ qlam,
                                         const double* __restrict__ gB, int dim, double g_scale,
                                         double w_g, float* p32, double* p64, int fp64,
-                                        double* v_out, int32_t* flags) {
+                                        double* v_out, int32_t* flags,
+                                        const double* __restrict__ corr, double* pxe_w) {
   constexpr int NSUM = 3 * nsum_per_comp(VAR_HESS);
   const PlanHdr h = *plan;
   const int64_t total = (int64_t)nptiles * TILE;
@@ -223,6 +226,8 @@ __global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* _
       for (int s = 0; s < NSUM; ++s) S[s] = gsum(out, h, item_off, i, NSUM, s);
       double q[12], d1[12], d2[12], phi = 0.0, grad[3], H[9];
       q_derivs(S, z, lam, q, d1, d2);
+      if (corr)
+        for (int m = 0; m < 12; ++m) q[m] += corr[12 * i + m];
       hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
       const double g[3] = {gB[3 * i], gB[3 * i + 1], gB[3 * i + 2]};
       double gl[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
@@ -268,6 +273,14 @@ __global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* _
         w[4] = -(vl * (z * FB + Fz));                         // cos(lambda r) / r
         w[5] = vl * z * Fx;                                   // phi dx
         w[6] = vl * z * Fy;                                   // phi dy
+        if (pxe_w) {
+          // the correction moves B_p and grad B_p only (linear in B0, lambda-independent)
+          double* o = pxe_w + 12 * i + 4 * p;
+          o[0] = g[p] - wB;
+          o[1] = -wx;
+          o[2] = -wy;
+          o[3] = -wz;
+        }
       }
     }
     const int64_t base = (i / TILE) * (int64_t)(VJP7_NFIELD * TILE) + (i % TILE);
@@ -338,22 +351,23 @@ int grid_for(int64_t n, int cap) {
 void launch_finalize_hessian(int64_t n, const PlanHdr* plan, const int32_t* item_off,
                              const double* out, const float4* qpos, const Lam4* qlam, int dim,
                              double g_scale, double w_g, double* phi, double* grad, double* hess,
-                             cudaStream_t s) {
+                             const double* corr, cudaStream_t s) {
   if (n <= 0) return;
   finalize_hessian_kernel<<<grid_for(n, 4096), 256, 0, s>>>(n, plan, item_off, out, qpos, qlam,
-                                                            dim, g_scale, w_g, phi, grad, hess);
+                                                            dim, g_scale, w_g, phi, grad, hess,
+                                                            corr);
 }
 
 void launch_implicit_weights(int64_t n, int nptiles, const PlanHdr* plan, const int32_t* item_off,
                              const double* out, const float4* qpos, const Lam4* qlam,
                              const double* gB, int dim, double g_scale, double w_g, float* p32,
                              double* p64, int fp64, double* v_out, int32_t* flags,
-                             cudaStream_t s) {
+                             const double* corr, double* pxe_w, cudaStream_t s) {
   const int64_t total = (int64_t)nptiles * TILE;
   if (total <= 0) return;
   implicit_weights_kernel<<<grid_for(total, 4096), 128, 0, s>>>(
       n, nptiles, plan, item_off, out, qpos, qlam, gB, dim, g_scale, w_g, p32, p64, fp64, v_out,
-      flags);
+      flags, corr, pxe_w);
 }
 
 void launch_finalize_nv(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,

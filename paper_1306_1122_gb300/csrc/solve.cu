@@ -47,9 +47,18 @@ __device__ __forceinline__ double gather_sum(const double* out, const PlanHdr& h
   return v;
 }
 
-// B, gradient and objective from the 12 objective sums of one query.
+// Pixel-exact near field: add the point's lambda-independent correction of B and grad B
+// (corr: dB_p at p, d(dB_p/dx_j) at 3 + 3 p + j).
+__device__ __forceinline__ void add_corr(const double* corr, double B[3], double G[9]) {
+  if (!corr) return;
+  for (int p = 0; p < 3; ++p) B[p] += corr[p];
+  for (int j = 0; j < 9; ++j) G[j] += corr[3 + j];
+}
+
+// B, gradient and objective from the 12 objective sums of one query (corr: see add_corr).
 __device__ __forceinline__ void assemble_obj(const double S[12], double z, double g_scale,
-                                             double w_g, Eval& e, double G[9]) {
+                                             double w_g, Eval& e, double G[9],
+                                             const double* corr) {
   for (int p = 0; p < 3; ++p) {
     const double S0 = S[p * 4 + 0], S1 = S[p * 4 + 1], Sx = S[p * 4 + 2], Sy = S[p * 4 + 3];
     e.B[p] = z * S0;
@@ -57,6 +66,7 @@ __device__ __forceinline__ void assemble_obj(const double S[12], double z, doubl
     G[3 * p + 1] = z * Sy;
     G[3 * p + 2] = S0 + z * z * S1;
   }
+  add_corr(corr, e.B, G);
   objective(e.B, G, g_scale, w_g, e.f, e.g, e.phi);
 }
 
@@ -68,7 +78,7 @@ __global__ void finalize_eval_kernel(int64_t n, const PlanHdr* __restrict__ plan
                                      const float4* __restrict__ qpos,
                                      const Lam4* __restrict__ qlam, double g_scale, double w_g,
                                      double* B, double* gradB, double* dBdl, const double* gB,
-                                     double* fgphi) {
+                                     double* fgphi, const double* corr) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
   const PlanHdr h = *plan;
@@ -78,17 +88,19 @@ __global__ void finalize_eval_kernel(int64_t n, const PlanHdr* __restrict__ plan
     const double z = (double)pos.z;
     double S[NSUM];
     for (int s = 0; s < NSUM; ++s) S[s] = gather_sum(out, h, item_off, 0, i, NSUM, s);
-    double Bv[3], G[9];
-    for (int p = 0; p < 3; ++p) {
-      Bv[p] = z * S[p * NS];
-      if (B) B[3 * i + p] = Bv[p];
-    }
+    double Bv[3], G[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int p = 0; p < 3; ++p) Bv[p] = z * S[p * NS];
     if constexpr (has_grad(VAR)) {
       for (int p = 0; p < 3; ++p) {
         G[3 * p + 0] = z * S[p * NS + 2];
         G[3 * p + 1] = z * S[p * NS + 3];
         G[3 * p + 2] = S[p * NS] + z * z * S[p * NS + 1];
       }
+    }
+    add_corr(corr ? corr + 12 * i : nullptr, Bv, G);
+    if (B)
+      for (int p = 0; p < 3; ++p) B[3 * i + p] = Bv[p];
+    if constexpr (has_grad(VAR)) {
       if (gradB)
         for (int j = 0; j < 9; ++j) gradB[9 * i + j] = G[j];
       if (fgphi) {
@@ -117,12 +129,12 @@ __global__ void finalize_eval_kernel(int64_t n, const PlanHdr* __restrict__ plan
 void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t* item_off,
                           const double* out, const float4* qpos, const Lam4* qlam, double g_scale,
                           double w_g, double* B, double* gradB, double* dBdl, const double* gB,
-                          double* fgphi, cudaStream_t s) {
+                          double* fgphi, const double* corr, cudaStream_t s) {
   if (n <= 0) return;
   const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
 #define FIN(V)                                                                              \
   finalize_eval_kernel<V><<<grid, 256, 0, s>>>(n, plan, item_off, out, qpos, qlam, g_scale, \
-                                               w_g, B, gradB, dBdl, gB, fgphi)
+                                               w_g, B, gradB, dBdl, gB, fgphi, corr)
   switch (var) {
     case VAR_V: FIN(VAR_V); break;
     case VAR_VL: FIN(VAR_VL); break;
@@ -161,14 +173,20 @@ __device__ __forceinline__ void store_vert(const SolveArgs& a, int64_t g, int v,
   SD(a, D_VPHI + v, g) = x.phi;
 }
 
+// The pixel-exact correction of point g, or null (none, or the point is above its height).
+__device__ __forceinline__ const double* corr_of(const SolveArgs& a, const ProbDesc& pd,
+                                                 int64_t g, double z) {
+  return (a.corr && pd.pxe_z > 0.0 && z <= pd.pxe_z) ? a.corr + 12 * g : nullptr;
+}
+
 // Objective of the k-th pending query of point g.
 __device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, int pidx,
-                                          int64_t slot, double z, Eval& e) {
+                                          int64_t slot, double z, Eval& e, int64_t g) {
   const ProbDesc& pd = a.probs[pidx];
   const int64_t j = slot - pd.q_off;
   double S[12], G[9];
   for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 12, s);
-  assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G);
+  assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
 }
 
 // Queue k trial points (lambda rows) of point g for the next round.
@@ -285,7 +303,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     if (stage == ST_INIT) {
       for (int k = 0; k <= n; ++k) {
         Eval e;
-        read_eval(a, h, pidx, slot + k, z, e);
+        read_eval(a, h, pidx, slot + k, z, e, g);
         for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
         v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
       }
@@ -293,7 +311,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       to_check = true;
     } else if (stage == ST_REFLECT) {
       Eval e;
-      read_eval(a, h, pidx, slot, z, e);
+      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       double lr[3];
       for (int d = 0; d < 3; ++d) lr[d] = SD(a, D_TL + d, g);
@@ -320,7 +338,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       }
     } else if (stage == ST_EXPAND) {
       Eval e;
-      read_eval(a, h, pidx, slot, z, e);
+      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       const double phr = SD(a, D_RPHI, g);
       double l[3];
@@ -339,7 +357,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       to_check = true;
     } else if (stage == ST_OCONTRACT || stage == ST_ICONTRACT) {
       Eval e;
-      read_eval(a, h, pidx, slot, z, e);
+      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       const bool ok = (stage == ST_OCONTRACT) ? (e.phi <= SD(a, D_RPHI, g)) : (e.phi < v[n].phi);
       if (ok) {
@@ -354,7 +372,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     } else if (stage == ST_SHRINK) {
       for (int k = 1; k <= n; ++k) {
         Eval e;
-        read_eval(a, h, pidx, slot + (k - 1), z, e);
+        read_eval(a, h, pidx, slot + (k - 1), z, e, g);
         for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
         v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
       }
@@ -468,7 +486,7 @@ namespace dbie {
 // d(dB_q/dy) = -z lambda Ty, d(dB_q/dz) = lambda Sl - z^2 lambda S0; the rest is the chain rule
 // through J = curl B, div B and the norms (kinks of f and g contribute 0).
 __device__ void objective_grad(const double* S, double z, const double lam[3], double g_scale,
-                               double w_g, Eval& e, double dphi[3]) {
+                               double w_g, Eval& e, double dphi[3], const double* corr) {
   double G[9], dBdl[3], dGdl[9];
   for (int p = 0; p < 3; ++p) {
     const double* s = S + 7 * p;
@@ -481,6 +499,7 @@ __device__ void objective_grad(const double* S, double z, const double lam[3], d
     dGdl[3 * p + 1] = -(z * lam[p] * s[6]);
     dGdl[3 * p + 2] = lam[p] * s[4] - z * z * lam[p] * s[0];
   }
+  add_corr(corr, e.B, G);
   objective(e.B, G, g_scale, w_g, e.f, e.g, e.phi);
   const double* B = e.B;
   const double J[3] = {G[3 * 2 + 1] - G[3 * 1 + 2], G[3 * 0 + 2] - G[3 * 2 + 0],
@@ -522,7 +541,8 @@ __global__ void finalize_objective_kernel(int64_t n, const PlanHdr* __restrict__
                                           const double* __restrict__ out,
                                           const float4* __restrict__ qpos,
                                           const Lam4* __restrict__ qlam, double g_scale,
-                                          double w_g, double* fgphi, double* dphi, double* B) {
+                                          double w_g, double* fgphi, double* dphi, double* B,
+                                          const double* corr) {
   const PlanHdr h = *plan;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -532,7 +552,7 @@ __global__ void finalize_objective_kernel(int64_t n, const PlanHdr* __restrict__
     const double lam[3] = {l.x, l.y, l.z};
     Eval e;
     double dp[3];
-    objective_grad(S, (double)qpos[i].z, lam, g_scale, w_g, e, dp);
+    objective_grad(S, (double)qpos[i].z, lam, g_scale, w_g, e, dp, corr ? corr + 12 * i : nullptr);
     if (fgphi) {
       fgphi[3 * i] = e.f;
       fgphi[3 * i + 1] = e.g;
@@ -548,11 +568,11 @@ __global__ void finalize_objective_kernel(int64_t n, const PlanHdr* __restrict__
 void launch_finalize_objective(int64_t n, const PlanHdr* plan, const int32_t* item_off,
                                const double* out, const float4* qpos, const Lam4* qlam,
                                double g_scale, double w_g, double* fgphi, double* dphi, double* B,
-                               cudaStream_t s) {
+                               const double* corr, cudaStream_t s) {
   if (n <= 0) return;
   const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   finalize_objective_kernel<<<grid, 256, 0, s>>>(n, plan, item_off, out, qpos, qlam, g_scale,
-                                                 w_g, fgphi, dphi, B);
+                                                 w_g, fgphi, dphi, B, corr);
 }
 
 // ----------------------------------------------------------------------- quasi-Newton ----
@@ -621,7 +641,7 @@ __global__ void bfgs_step_kernel(const SolveArgs a) {
     for (int s = 0; s < 21; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 21, s);
     Eval e;
     double dp[3], gt[3] = {0, 0, 0};
-    objective_grad(S, z, lamt, pd.g_scale, a.o.w_g, e, dp);
+    objective_grad(S, z, lamt, pd.g_scale, a.o.w_g, e, dp, corr_of(a, pd, g, z));
     if (n == 1) gt[0] = dp[0] + dp[1] + dp[2];
     else { gt[0] = dp[0]; gt[1] = dp[1]; gt[2] = dp[2]; }
     const bool flagt = e.f <= a.o.eps_f && e.g <= a.o.eps_g;

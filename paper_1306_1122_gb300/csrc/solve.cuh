@@ -71,6 +71,7 @@ struct SolveArgs {
   int32_t codes_stride;
   int32_t pad1;
   unsigned* err;
+  const double* corr;        // [N * 12] pixel-exact corrections (dB, d grad B), or null
 };
 
 struct PlanArgs {

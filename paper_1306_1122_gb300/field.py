@@ -19,6 +19,8 @@ import torch
 
 from . import _native as N
 
+QUAD_PIXEL_EXACT = -1   # DBIE_QUAD_PIXEL_EXACT: exact near-field integration of the lambda = 0 kernel
+
 
 @dataclass
 class Options:
@@ -172,7 +174,9 @@ class DBIEField:
 
     def set_quadrature(self, order: int):
         """0: midpoint rule at pixel centres (Eq. 16); g in 1..8: nine-node elements with g x g
-        Gauss points (Eq. 15; nx, ny odd)."""
+        Gauss points (Eq. 15; nx, ny odd); QUAD_PIXEL_EXACT (-1): the midpoint rule plus the
+        exact integration of the lambda = 0 kernel over every pixel at points with
+        z <= Options.near_z (the lambda-dependent remainder stays on the midpoint rule)."""
         N.dbie_set_quadrature(self._h, int(order), _stream())
 
     def hessian(self, xyz, lam, options: Options | None = None):

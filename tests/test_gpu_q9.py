@@ -169,7 +169,7 @@ def test_q9_argument_errors(dbie):
     f.close()
     mag = random_mag(21, 21, 231)
     f = dbie.DBIEField.from_magnetogram(mag)
-    for bad in (-1, 9):
+    for bad in (-2, 9):
         with pytest.raises(N.DBIEError):
             f.set_quadrature(bad)
     f.set_quadrature(3)
