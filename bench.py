@@ -308,7 +308,7 @@ def run_ours(args):
         line["fp64_form"] = fp64_compare(w, args.fp64_points, dev)
         line["quasi_newton"] = method_compare(w, dev)
         line["backward_through_search"] = backward_compare(w, dev)
-        line["quadrature_elements"] = quadrature_compare(w, dev)
+        line["quadrature_rules"] = quadrature_compare(w, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if world > 1:
@@ -424,11 +424,13 @@ def backward_compare(w, dev):
 
 
 def quadrature_compare(w, dev):
-    """The paper's pixel-centre rule (Eq. 16, 128 x 128 pixels) against Eq. 15's nine-node
-    elements with 4 x 4 Gauss points (the same field on the 129 x 129 node grid at the same scale),
-    each with the full simplex search on the same 131,072 physical points: solve time, pair
-    evaluations per second and agreement with the analytic field (vector correlation C_vec and
-    1 - normalised vector error)."""
+    """The paper's pixel-centre rule (Eq. 16, 128 x 128 pixels) against the same rule with the
+    exact near-field integration of the lambda = 0 kernel (points with z <= 2 px) and against
+    Eq. 15's nine-node elements with 4 x 4 Gauss points (the same field on the 129 x 129 node grid
+    at the same scale), each with the full simplex search on the same 131,072 physical points:
+    solve time, pair evaluations per second and agreement with the analytic field (vector
+    correlation C_vec and 1 - normalised vector error), over all points and over the two layers
+    nearest the boundary (z <= 2 px, where the rules differ)."""
     import torch
 
     import paper_1306_1122_gb300 as dbie
@@ -440,7 +442,10 @@ def quadrature_compare(w, dev):
         return c_vec, e_n
 
     out = {}
-    for name, wk, order in (("pixel_centres", workloads.ll128(with_truth=True), 0),
+    lam_ref = None       # the pixel-centre search's lambda, to compare the rules at equal lambda
+    ll128 = workloads.ll128(with_truth=True)
+    for name, wk, order in (("pixel_centres", ll128, 0),
+                            ("pixel_exact_near_field", ll128, dbie.QUAD_PIXEL_EXACT),
                             ("elements_g4", workloads.ll129_nodes(), 4)):
         f = dbie.DBIEField.from_magnetogram(wk.mag, device=dev)
         if order:
@@ -453,11 +458,19 @@ def quadrature_compare(w, dev):
         r = f.solve(pts)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        nq = wk.mag.npix if order == 0 else ((wk.mag.nx - 1) // 2 * order) ** 2
-        c_vec, e_n = agreement(r["B"].cpu().numpy(), wk.truth)
+        nq = wk.mag.npix if order <= 0 else ((wk.mag.nx - 1) // 2 * order) ** 2
+        B = r["B"].cpu().numpy()
+        c_vec, e_n = agreement(B, wk.truth)
+        near = wk.points[:, 2] <= 2.0 * wk.mag.hx
+        c_near, e_near = agreement(B[near], wk.truth[near])
+        if lam_ref is None:
+            lam_ref = r["lam"].to(torch.float32)
+        Bq = f.eval(pts, lam_ref)["B"].cpu().numpy()
+        _, e_same = agreement(Bq[near], wk.truth[near])
         out[name] = {"solve_s": dt, "quadrature_points": int(nq),
                      "pair_evals_per_s": float(r["nfev"].sum()) * nq / dt,
-                     "C_vec": c_vec, "E_n": e_n}
+                     "C_vec": c_vec, "E_n": e_n, "C_vec_z_le_2": c_near, "E_n_z_le_2": e_near,
+                     "E_n_z_le_2_at_pixel_centre_lambda": e_same}
         f.close()
     return out
 
