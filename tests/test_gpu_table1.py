@@ -64,6 +64,11 @@ def test_table1_reproduction(dbie):
         r = f.solve(pts, opt)
         torch.cuda.synchronize()
         out[name] = _metrics(w, r["B"].cpu().numpy())
+    # the same search with the exact near-field integration for z <= 2 px
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    r = f.solve(pts, dbie.Options())
+    torch.cuda.synchronize()
+    out["simplex, exact near field"] = _metrics(w, r["B"].cpu().numpy())
     f.close()
     # the same field on the 193-node grid, nine-node elements with 4 x 4 Gauss points
     w9 = workloads.table1(193)
@@ -85,6 +90,6 @@ def test_table1_reproduction(dbie):
     assert abs(z0["C_vec"] - nb["C_vec"]) < 0.01 and abs(z0["C_cs"] - nb["C_cs"]) < 0.01
     assert abs(z0["eps"] - nb["eps"]) < 0.03 and abs(z0["E_n"] - nb["E_n"]) < 0.1
     assert z0["E_m"] < -5 and nb["E_m"] < -5          # both dominated by the upper layers
-    for name in ("simplex (paper)", "simplex, Eq. 15 elements"):
+    for name in ("simplex (paper)", "simplex, Eq. 15 elements", "simplex, exact near field"):
         m = out[name]
         assert m["C_vec"] > 0.9 and 0.8 < m["eps"] < 1.4, (name, m)
