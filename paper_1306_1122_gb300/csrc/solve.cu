@@ -189,11 +189,41 @@ __device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, 
   assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
 }
 
+// atomicAdd(ctr, v) for the lanes of a warp that reach it together (whatever branch they are
+// in): lanes with the same counter add their total with one atomic and take consecutive ranges
+// in lane order.  Every simplex or quasi-Newton point emits its trial queries through these
+// counters each round, so one atomic per lane would serialise N updates of one address.
+__device__ __forceinline__ int atomic_add_warp(int* ctr, int v) {
+  const unsigned active = __activemask();
+  const unsigned peers = __match_any_sync(active, reinterpret_cast<unsigned long long>(ctr));
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  const unsigned below = peers & ((1u << lane) - 1u);
+  int same = 0;
+  __match_all_sync(peers, v, &same);
+  int prefix = 0, total = 0;
+  if (same) {
+    prefix = v * __popc(below);
+    total = v * __popc(peers);
+  } else {
+    for (unsigned m = peers; m; m &= m - 1u) {
+      const int l = __ffs(m) - 1;
+      const int vl = __shfl_sync(peers, v, l);
+      if (l < lane) prefix += vl;
+      total += vl;
+    }
+  }
+  int base = 0;
+  if (lane == leader) base = atomicAdd(ctr, total);
+  base = __shfl_sync(peers, base, leader);
+  return base + prefix;
+}
+
 // Queue k trial points (lambda rows) of point g for the next round.
 __device__ void emit(const SolveArgs& a, int64_t g, const float4& pos, int pidx, int k,
                      const double (*lam)[3]) {
   const ProbDesc& pd = a.probs[pidx];
-  const int base = atomicAdd(a.nxt.q_cnt + pidx, k);
+  const int base = atomic_add_warp(a.nxt.q_cnt + pidx, k);
   const int64_t slot0 = pd.q_off + base;
   for (int j = 0; j < k; ++j) {
     a.nxt.qpos[slot0 + j] = pos;
@@ -201,11 +231,11 @@ __device__ void emit(const SolveArgs& a, int64_t g, const float4& pos, int pidx,
     else a.nxt.qlam[slot0 + j] = make_lam4(lam[j][0], lam[j][1], lam[j][2]);
   }
   if (a.o.near_on && (double)pos.z <= pd.near_z) {
-    const int nb = atomicAdd(a.nxt.near_cnt, k);
+    const int nb = atomic_add_warp(a.nxt.near_cnt, k);
     for (int j = 0; j < k; ++j) a.nxt.near[nb + j] = (int32_t)(slot0 + j);
   }
   SI(a, I_QSLOT, g) = (int32_t)slot0;
-  a.nxt.act[atomicAdd(a.nxt.act_cnt, 1)] = (int32_t)g;
+  a.nxt.act[atomic_add_warp(a.nxt.act_cnt, 1)] = (int32_t)g;
 }
 
 __global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ lam_init) {

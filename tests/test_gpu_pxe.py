@@ -311,3 +311,37 @@ def test_pxe_height_switch_batched_and_errors(dbie):
         f.set_quadrature(-2)
     f.close()
     g.close()
+
+
+def test_pxe_full_size_ll128_sampled(dbie):
+    """The bench's workload at full size with the exact near field: all 131,072 points of the
+    128^2 Low & Lou case through the full simplex search on the GPU (mixed), then on a seeded
+    sample of 384 points (half of them at z <= 2 px) B at the GPU's lambda against the oracle's
+    exact rule, and the fixed-lambda adjoint of the sample against the oracle's."""
+    from synth import workloads
+    w = workloads.ll128()
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    pts = torch.from_numpy(w.points).cuda()
+    r = f.solve(pts)
+    torch.cuda.synchronize()
+    B, lam = r["B"].cpu().numpy(), r["lam"].cpu().numpy()
+    assert np.isfinite(B).all() and (r["status"].cpu().numpy() >= 0).all()
+    rng = np.random.default_rng(470)
+    near = np.nonzero(w.points[:, 2] <= 2.0)[0]
+    far = np.nonzero(w.points[:, 2] > 2.0)[0]
+    idx = np.sort(np.concatenate([rng.choice(near, 192, replace=False),
+                                  rng.choice(far, 192, replace=False)]))
+    bd = oracle_boundary(w.mag)
+    x64 = w.points[idx].astype(np.float64)
+    Bo, _, _ = oracle.field(bd, x64, lam[idx], quad_order=-1)
+    sB, _ = pxe_scales(w.mag, w.points[idx], lam[idx], 2.0)
+    rb = check_B(B[idx], Bo, sB)
+    assert rb["bad"].size == 0, rb
+    gB = rng.normal(size=(len(idx), 3))
+    gB0, _ = f.vjp(torch.from_numpy(w.points[idx]), torch.from_numpy(lam[idx]),
+                   torch.from_numpy(gB), glam=False)
+    torch.cuda.synchronize()
+    ref = oracle.vjp(bd, x64, lam[idx], gB, quad_order=-1)
+    assert np.linalg.norm(gB0.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    f.close()
