@@ -173,53 +173,69 @@ def test_pxe_vjp_matches_oracle(dbie, precision):
     f.close()
 
 
-def _newton(bd, pts, lam, gs, nz):
+def _newton(bd, pts, lam, gs, nz, mode=0):
     lam = lam.copy()
     for _ in range(30):
-        _, gr, H, _ = oracle.hessian(bd, pts, lam, gs, pxe_near_z=nz)
-        ok = np.linalg.eigvalsh(H)[:, 0] > 0
-        Hs = np.where(ok[:, None, None], H, np.eye(3))
-        st = np.where(ok[:, None], np.linalg.solve(Hs, gr[:, :, None])[:, :, 0], 0.0)
-        lam -= st
+        _, gr, H, _ = oracle.hessian(bd, pts, lam, gs, pxe_near_z=nz, lambda_mode=mode)
+        if mode == 1:
+            ok = H[:, 0, 0] > 0
+            st = np.where(ok, gr[:, 0] / np.where(ok, H[:, 0, 0], 1.0), 0.0)
+            lam -= st[:, None]
+        else:
+            ok = np.linalg.eigvalsh(H)[:, 0] > 0
+            Hs = np.where(ok[:, None, None], H, np.eye(3))
+            st = np.where(ok[:, None], np.linalg.solve(Hs, gr[:, :, None])[:, :, 0], 0.0)
+            lam -= st
         if np.abs(st).max() < 1e-15:
             break
     return lam
 
 
 @pytest.mark.parametrize("precision", [1, 0])
-def test_pxe_implicit_vjp_matches_oracle(dbie, precision):
-    """At well-conditioned minima of the corrected objective (oracle quasi-Newton, then Newton)."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_pxe_implicit_vjp_matches_oracle(dbie, precision, mode):
+    """At well-conditioned minima of the corrected objective (oracle quasi-Newton, then Newton),
+    per-component and tied lambda."""
     from synth.workloads import small_ll
     w = small_ll()
     bd = oracle_boundary(w.mag)
     gs = w.mag.hx / 6.0
     nz = 2.0 * w.mag.hx
-    rng = np.random.default_rng(430)
+    rng = np.random.default_rng(430 + mode)
     near = w.points[w.points[:, 2] <= nz]
     pts = near[np.sort(rng.choice(len(near), min(192, len(near)), replace=False))].astype(np.float64)
-    r = oracle.solve(bd, pts, oracle.Options(method=1, max_iter=80, tol=1e-13, quad_order=-1))
-    lam = _newton(bd, pts, r["lam"], gs, nz)
-    _, gr, H, _ = oracle.hessian(bd, pts, lam, gs, pxe_near_z=nz)
-    ev = np.linalg.eigvalsh(H)
+    r = oracle.solve(bd, pts, oracle.Options(method=1, max_iter=80, tol=1e-13, quad_order=-1,
+                                               lambda_mode=mode))
+    lam = _newton(bd, pts, r["lam"], gs, nz, mode)
+    _, gr, H, _ = oracle.hessian(bd, pts, lam, gs, pxe_near_z=nz, lambda_mode=mode)
+    ev = np.linalg.eigvalsh(H[:, :1, :1] if mode == 1 else H)
     good = (np.abs(gr).max(1) < 1e-10) & (ev[:, 0] > 0) & (ev[:, -1] < 1e3 * ev[:, 0])
     assert good.sum() >= 32, good.sum()
     pts, lam = pts[good].astype(np.float32), lam[good]
     gB = rng.normal(size=(len(pts), 3))
-    ref, v_ref, fl_ref = oracle.implicit_vjp(bd, pts.astype(np.float64), lam, gB, gs, pxe_near_z=nz)
+    ref, v_ref, fl_ref = oracle.implicit_vjp(bd, pts.astype(np.float64), lam, gB, gs,
+                                             lambda_mode=mode, pxe_near_z=nz)
     assert not fl_ref.any()
     f = dbie.DBIEField.from_magnetogram(w.mag)
     f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    opt = dbie.Options(precision=precision, lambda_mode=mode)
     gB0, v, fl = f.vjp_implicit(torch.from_numpy(pts), torch.from_numpy(lam), torch.from_numpy(gB),
-                                options=dbie.Options(precision=precision))
+                                options=opt)
+    h = f.hessian(torch.from_numpy(pts), torch.from_numpy(lam), opt)
     torch.cuda.synchronize()
     gB0, v = gB0.cpu().numpy(), v.cpu().numpy()
     assert not fl.cpu().numpy().any()
     err = np.linalg.norm(gB0 - ref) / np.linalg.norm(ref)
+    _, _, Ho, _ = oracle.hessian(bd, pts.astype(np.float64), lam, gs, pxe_near_z=nz,
+                                 lambda_mode=mode)
+    herr = np.linalg.norm(h["hess"].cpu().numpy() - Ho) / np.linalg.norm(Ho)
     if precision == 1:
         assert err <= 1e-9, err
         assert np.abs(v - v_ref).max() <= 1e-8 * np.abs(v_ref).max()
+        assert herr <= 1e-9, herr
     else:
         assert err <= 1e-4, err
+        assert herr <= 1e-3, herr
     f.close()
 
 
