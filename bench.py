@@ -389,7 +389,8 @@ def method_compare(w, dev):
 def backward_compare(w, dev):
     """Cost of the gradient through the lambda search (Hessian pass + seven-weight adjoint) next to
     the fixed-lambda adjoint, and of the noise variance, on all points of the workload at the
-    simplex's lambda (mixed precision, tuned launch shapes, CUDA events, 3 repeats, minimum)."""
+    simplex's lambda (mixed precision, tuned launch shapes, CUDA events, 3 repeats, minimum);
+    both adjoints also with the exact near field."""
     import torch
 
     import paper_1306_1122_gb300 as dbie
@@ -416,11 +417,17 @@ def backward_compare(w, dev):
     t_impl = timed(lambda: f.vjp_implicit(pts, r["lam"], gB))
     t_nv = timed(lambda: f.noise_var(pts, r["lam"], sigma0=10.0))
     _, _, fl = f.vjp_implicit(pts, r["lam"], gB)
+    # the same two adjoints with the exact near field (its transpose for the points at z <= 2 px)
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    t_fixed_x = timed(lambda: f.vjp(pts, r["lam"], gB, glam=False))
+    t_impl_x = timed(lambda: f.vjp_implicit(pts, r["lam"], gB))
     f.close()
     return {"points": n, "pixels": npix, "fixed_lambda_adjoint_ms": t_fixed,
             "implicit_adjoint_ms": t_impl, "noise_variance_ms": t_nv,
             "implicit_pair_evals_per_s": 2.0 * n * npix / (t_impl / 1e3),
-            "points_without_positive_definite_hessian": int(fl.sum().item())}
+            "points_without_positive_definite_hessian": int(fl.sum().item()),
+            "exact_near_field": {"fixed_lambda_adjoint_ms": t_fixed_x,
+                                 "implicit_adjoint_ms": t_impl_x}}
 
 
 def quadrature_compare(w, dev):

@@ -70,9 +70,11 @@ void launch_finalize_vjp(int64_t npix, const PlanHdr* plan, const double* out, d
 // pxe.cu (pixel-exact near field)
 void launch_pxe_corr(bool fp64, const ProbDesc* probs, int64_t n, const float4* pos, double zmax,
                      double* corr, int grid, cudaStream_t s);
+// chunks of near points per pixel (the partial buffer holds nchunk * npix * 3 doubles)
+int pxe_adjoint_chunks(int64_t n, int64_t npix, int sm_count);
 void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int64_t npix,
                         const float4* pos, double zmax, const double* w, int32_t* list,
-                        int32_t* cnt, double* gB0, cudaStream_t s);
+                        int32_t* cnt, int nchunk, double* part, double* gB0, cudaStream_t s);
 
 void launch_count_bad(const float* a, int64_t n, int mode, int32_t* cnt, cudaStream_t s);
 void launch_pack_points(int64_t n, const float* xyz, int pidx, float4* ppos, cudaStream_t s);

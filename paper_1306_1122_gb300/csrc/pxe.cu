@@ -23,8 +23,8 @@
 //
 // Kernels: pxe_corr (one CTA per near point; the window in FP64, one pixel per thread, then the
 // other pixels strided over the CTA; FP64 block reduction), pxe_compact (stable list of the near
-// points) and pxe_adj (the transpose, one thread per pixel, near points through shared memory,
-// added into dL/dB0).
+// points), pxe_adj (the transpose, one thread per pixel and chunk of near points, the points
+// through shared memory) and pxe_adj_reduce (the chunks in order, added into dL/dB0).
 #include "kernels.h"
 
 namespace dbie {
@@ -236,16 +236,18 @@ __global__ void __launch_bounds__(PXE_SCAN) pxe_compact_kernel(int64_t n,
   if (t == PXE_SCAN - 1) *cnt = s[t];
 }
 
-// Transpose of one problem's correction: gB0[3 k + p] += dA / 2 pi sum_i sum_m w_ipm c^m_ik over
-// the listed points (c^m: the per-pixel correction and its derivatives, as pxe_corr uses them).
-// Weights: FULL, 12 per point at 4 p + m; otherwise 3 per point (gB_p, m = 0 only).
+// Transpose of one problem's correction: sum_i sum_m w_ipm c^m_ik over the listed points
+// (c^m: the per-pixel correction and its derivatives, as pxe_corr uses them), for chunk
+// blockIdx.y of the list, into part[(chunk * npix + k) * 3 + p]; pxe_adj_reduce_kernel adds the
+// chunks in order (times dA / 2 pi) to gB0.  Weights: FULL, 12 per point at 4 p + m; otherwise
+// 3 per point (gB_p, m = 0 only).
 template <bool FP64, bool FULL>
 __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restrict__ prob,
                                                          const int32_t* __restrict__ list,
                                                          const int32_t* __restrict__ cnt,
                                                          const float4* __restrict__ pos,
                                                          const double* __restrict__ w,
-                                                         double* __restrict__ gB0) {
+                                                         double* __restrict__ part) {
   constexpr int NW = FULL ? 12 : 3;
   __shared__ float sx[PXE_NT], sy[PXE_NT], sz[PXE_NT];
   __shared__ int32_t sw0[PXE_NT];   // window origin of each point (packed i0, j0), mixed form
@@ -261,8 +263,10 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
   const float hx = (float)pd.hx, hy = (float)pd.hy, ga = (float)(pd.hx * pd.hy / pd.area);
   const double inv_dA = 1.0 / pd.area;
   double hi[3] = {0.0, 0.0, 0.0};
-  const int m = *cnt;
-  for (int j0 = 0; j0 < m; j0 += PXE_NT) {
+  const int m_all = *cnt;
+  const int jb = (int)(((int64_t)m_all * blockIdx.y) / gridDim.y);
+  const int m = (int)(((int64_t)m_all * (blockIdx.y + 1)) / gridDim.y);
+  for (int j0 = jb; j0 < m; j0 += PXE_NT) {
     __syncthreads();
     const int j = j0 + threadIdx.x;
     if (j < m) {
@@ -320,24 +324,47 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
     for (int p = 0; p < 3; ++p) hi[p] += (double)acc[p];
   }
   if (!live) return;
-  const double sc = pd.area / TWO_PI;
+  double* o = part + ((int64_t)blockIdx.y * npix + k) * 3;
 #pragma unroll
-  for (int p = 0; p < 3; ++p) gB0[3 * k + p] += sc * hi[p];
+  for (int p = 0; p < 3; ++p) o[p] = hi[p];
+}
+
+__global__ void pxe_adj_reduce_kernel(const ProbDesc* __restrict__ prob, int nchunk,
+                                      const double* __restrict__ part, double* __restrict__ gB0) {
+  const int64_t npix = (int64_t)prob->nx * prob->ny;
+  const double sc = prob->area / TWO_PI;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < 3 * npix;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int y = 0; y < nchunk; ++y) v += part[y * 3 * npix + e];
+    gB0[e] += sc * v;
+  }
+}
+
+int pxe_adjoint_chunks(int64_t n, int64_t npix, int sm_count) {
+  const int64_t gx = (npix + PXE_NT - 1) / PXE_NT;
+  int64_t c = (4LL * sm_count + gx - 1) / gx;          // about four CTAs per SM
+  const int64_t cmax = (n + PXE_NT - 1) / PXE_NT;       // at least one shared-memory batch each
+  c = c < cmax ? c : cmax;
+  return (int)(c < 1 ? 1 : (c > 65535 ? 65535 : c));
 }
 
 void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int64_t npix,
                         const float4* pos, double zmax, const double* w, int32_t* list,
-                        int32_t* cnt, double* gB0, cudaStream_t s) {
+                        int32_t* cnt, int nchunk, double* part, double* gB0, cudaStream_t s) {
   if (n <= 0) return;
   pxe_compact_kernel<<<1, PXE_SCAN, 0, s>>>(n, pos, zmax, list, cnt);
-  const int grid = (int)((npix + PXE_NT - 1) / PXE_NT);
-#define ADJ(D, F) pxe_adj_kernel<D, F><<<grid, PXE_NT, 0, s>>>(prob, list, cnt, pos, w, gB0)
+  const dim3 grid((unsigned)((npix + PXE_NT - 1) / PXE_NT), (unsigned)nchunk);
+#define ADJ(D, F) pxe_adj_kernel<D, F><<<grid, PXE_NT, 0, s>>>(prob, list, cnt, pos, w, part)
   if (fp64) {
     if (full) ADJ(true, true); else ADJ(true, false);
   } else {
     if (full) ADJ(false, true); else ADJ(false, false);
   }
 #undef ADJ
+  const int64_t e = 3 * npix;
+  const int g2 = (int)((e + 255) / 256 < 8192 ? (e + 255) / 256 : 8192);
+  pxe_adj_reduce_kernel<<<g2, 256, 0, s>>>(prob, nchunk, part, gB0);
 }
 
 }  // namespace dbie
