@@ -156,7 +156,7 @@ struct dbie_ctx {
   DBuf vtmp;                      // per-quadrature-point adjoint before the gather to nodes
   int quad_g = 0;                 // 0: pixel centres (Eq. 16); g: nine-node elements (Eq. 15)
   bool pxe = false;               // pixel-exact near field on the pixel-centre rule
-  DBuf pxe_corr, pxe_pos, pxe_list, pxe_w, pxe_part;   // its per-call scratch
+  DBuf pxe_corr, pxe_pos, pxe_list, pxe_w, pxe_part, pxe_bins;   // its per-call scratch
   QuadInfo qi{};
   int64_t nquad = 0;              // quadrature points: npix, or (elements x g)^2
   int32_t qnx = 0, qny = 0;       // quadrature-point grid
@@ -462,7 +462,7 @@ void dbie_destroy(dbie_ctx* c) {
   for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
                   &c->tv64, &c->probv, &c->b0raw, &c->vtmp, &c->pxe_corr, &c->pxe_pos,
-                  &c->pxe_list, &c->pxe_w, &c->pxe_part})
+                  &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -528,10 +528,11 @@ static dbie_status pxe_adjoint(dbie_ctx* c, int64_t n, const float4* pos, const 
                                cudaStream_t s) {
   DBIE_TRY(ensure(c->pxe_list, sizeof(int32_t) * (n + 1)));
   const int nchunk = pxe_adjoint_chunks(n, c->npix, c->sm_count);
-  DBIE_TRY(ensure(c->pxe_part, sizeof(double) * 3 * (size_t)c->npix * nchunk));
+  DBIE_TRY(ensure(c->pxe_part, sizeof(double) * 3 * (size_t)c->npix * (nchunk + 1)));
+  DBIE_TRY(ensure(c->pxe_bins, sizeof(int32_t) * (3 * (size_t)pxe_bins(c->nx, c->ny) + 1 + n)));
   int32_t* list = c->pxe_list.as<int32_t>();
-  launch_pxe_adjoint(fp64, full, c->prob.as<ProbDesc>(), n, c->npix, pos, o.near_z, w, list,
-                     list + n, nchunk, c->pxe_part.as<double>(), gB0, s);
+  launch_pxe_adjoint(fp64, full, c->prob.as<ProbDesc>(), n, c->nx, c->ny, pos, o.near_z, w, list,
+                     list + n, c->pxe_bins.as<int32_t>(), nchunk, c->pxe_part.as<double>(), gB0, s);
   CUDA_TRY(cudaGetLastError());
   return DBIE_OK;
 }

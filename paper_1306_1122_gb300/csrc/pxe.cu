@@ -21,10 +21,13 @@
 // in FP32 (its error there is below 1e-7 of the absolute-value sum, beyond W = 3); the FP64 form
 // integrates every pixel exactly in FP64.
 //
-// Kernels: pxe_corr (one CTA per near point; the window in FP64, one pixel per thread, then the
-// other pixels strided over the CTA; FP64 block reduction), pxe_compact (stable list of the near
-// points), pxe_adj (the transpose, one thread per pixel and chunk of near points, the points
-// through shared memory) and pxe_adj_reduce (the chunks in order, added into dL/dB0).
+// Kernels: pxe_window (FP64 window sums, one warp per point), pxe_gauss (the other pixels' FP32
+// Gauss sums, one CTA per near point, added) or, in the FP64 form, pxe_exact; pxe_compact (stable list of the near
+// points), pxe_adj (the transpose's Gauss-rule pairs, one thread per pixel and chunk of near
+// points, the points through shared memory), pxe_bin_* and pxe_adj_window (its window pairs,
+// pixel-major over binned near points) and pxe_adj_reduce (the parts in order, into dL/dB0).
+#include <type_traits>
+
 #include "kernels.h"
 
 namespace dbie {
@@ -35,26 +38,35 @@ constexpr int PXE_NT = 128;
 // and its derivatives with respect to the point (x_i, y_i, z); dx = x_i - x_k, dy = y_i - y_k.
 // The pixel is the hx x hy rectangle; dA is the midpoint rule's pixel area (usually hx hy).
 
-// Exactly, in FP64 (the solid angle).
+// Exactly, in FP64 (the solid angle).  The four corner terms s_c arctan(a_c b_c / (z R_c)) are
+// summed as one argument: arctan(ab / (zR)) is the argument of zR + i ab, so their signed sum is
+// the argument of the product of the factors zR + i s_c a_c b_c (one atan2 instead of four
+// arctangents and their divisions).  The sum is 2 pi times the pixel's weight, in (0, 2 pi), so a
+// negative atan2 is taken modulo 2 pi.  The derivatives share 1 / (R (a^2 + z^2) (b^2 + z^2)).
 __device__ __forceinline__ void pixel_exact(double dx, double dy, double z, double hx, double hy,
                                             double inv_dA, double w[4]) {
   const double ca[2] = {-dx - 0.5 * hx, -dx + 0.5 * hx}, cb[2] = {-dy - 0.5 * hy, -dy + 0.5 * hy};
   const double zz = z * z;
-  double v = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
+  double pr = 1.0, pim = 0.0, gx = 0.0, gy = 0.0, gz = 0.0;
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
-#pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const double s = (u == t) ? 1.0 : -1.0;
-      const double a = ca[u], b = cb[t];
-      const double a2 = a * a + zz, b2 = b * b + zz, R2 = a2 + b * b, R = sqrt(R2);
-      v += s * atan(a * b / (z * R));
-      gx -= s * (b * z / (R * a2));
-      gy -= s * (a * z / (R * b2));
-      gz -= s * (a * b * (R2 + zz) / (R * a2 * b2));
-    }
-  const double r2 = dx * dx + dy * dy + zz, r = sqrt(r2), ri3 = 1.0 / (r2 * r);
-  const double u5 = -3.0 * z * ri3 / r2;
+  for (int c = 0; c < 4; ++c) {
+    const int u = c >> 1, t = c & 1;
+    const double s = (u == t) ? 1.0 : -1.0;
+    const double a = ca[u], b = cb[t];
+    const double a2 = a * a + zz, b2 = b * b + zz, R2 = a2 + b * b, R = sqrt(R2);
+    const double fr = z * R, fi = s * (a * b);
+    const double nr = pr * fr - pim * fi;
+    pim = pr * fi + pim * fr;
+    pr = nr;
+    const double inv = 1.0 / (R * a2 * b2);
+    gx -= s * (b * z * b2 * inv);
+    gy -= s * (a * z * a2 * inv);
+    gz -= s * (a * b * (R2 + zz) * inv);
+  }
+  double v = atan2(pim, pr);
+  if (v < 0.0) v += TWO_PI;
+  const double r2 = dx * dx + dy * dy + zz, ri = 1.0 / sqrt(r2), ri2 = ri * ri, ri3 = ri2 * ri;
+  const double u5 = -3.0 * z * ri3 * ri2;
   w[0] = v * inv_dA - z * ri3;
   w[1] = gx * inv_dA - u5 * dx;
   w[2] = gy * inv_dA - u5 * dy;
@@ -124,11 +136,121 @@ __device__ __forceinline__ Win window_of(const ProbDesc& pd, double x, double y)
 }
 
 // corr[12 i ..]: dB_p (3), then d(dB_p/dx_j) at 3 + 3 p + j; zero for points above the height.
-template <bool FP64>
-__global__ void __launch_bounds__(PXE_NT) pxe_corr_kernel(const ProbDesc* __restrict__ probs,
-                                                          int64_t n,
-                                                          const float4* __restrict__ pos,
-                                                          double zmax, double* __restrict__ corr) {
+// Mixed form, in two kernels with their own register budgets: pxe_window_kernel sums the window
+// pixels exactly in FP64 (one warp per point) and writes corr; pxe_gauss_kernel then adds the FP32
+// Gauss-rule sum over the other pixels (one CTA per near point).  FP64 form: pxe_exact_kernel,
+// every pixel exactly.
+
+__device__ __forceinline__ void add_exact12(const ProbDesc& pd, int64_t k, double xd, double yd,
+                                            double zd, double inv_dA, double acc[12]) {
+  const int64_t base = tile_base(k);
+  double w[4];
+  pixel_exact(xd - pd.tiles64[base], yd - pd.tiles64[base + TILE], zd, pd.hx, pd.hy, inv_dA, w);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const double b = pd.tiles64[base + (2 + p) * TILE];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) acc[4 * p + m] += b * w[m];
+  }
+}
+
+__device__ __forceinline__ void store12(double* out, int m, double v) {
+  const int p = m >> 2, e = m & 3;
+  out[e == 0 ? p : 3 + 3 * p + (e - 1)] = v;
+}
+
+__global__ void pxe_window_kernel(const ProbDesc* __restrict__ probs, int64_t n,
+                                  const float4* __restrict__ pos, double zmax,
+                                  double* __restrict__ corr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nwarps) {
+    const float4 p4 = pos[i];
+    const ProbDesc& pd = probs[__float_as_int(p4.w)];
+    double acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) acc[m] = 0.0;
+    if (pxe_near(pd, p4.z, zmax)) {
+      const double xd = p4.x, yd = p4.y, zd = p4.z, inv_dA = 1.0 / pd.area;
+      const Win win = window_of(pd, xd, yd);
+      const long wi = win.i1 - win.i0 + 1, wj = win.j1 - win.j0 + 1;
+      if (wi > 0 && wj > 0)
+        for (long e = lane; e < wi * wj; e += 32)
+          add_exact12(pd, (win.j0 + e / wi) * (int64_t)pd.nx + (win.i0 + e % wi), xd, yd, zd,
+                      inv_dA, acc);
+    }
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      double v = acc[m];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) store12(corr + 12 * i, m, v);
+    }
+  }
+}
+
+// Block sum of v[12] (every thread of the block calls it); thread t < 12 gets entry t.
+__device__ __forceinline__ double block_sum12(double (*red)[12], const double v[12], int lane,
+                                              int warp) {
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    double x = v[m];
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    if (lane == 0) red[warp][m] = x;
+  }
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 12)
+    for (int w = 0; w < PXE_NT / 32; ++w) t += red[w][threadIdx.x];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(PXE_NT, 8) pxe_gauss_kernel(const ProbDesc* __restrict__ probs,
+                                                               int64_t n,
+                                                               const float4* __restrict__ pos,
+                                                               double zmax,
+                                                               double* __restrict__ corr) {
+  __shared__ double red[PXE_NT / 32][12];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const float4 p4 = pos[i];
+    const ProbDesc& pd = probs[__float_as_int(p4.w)];
+    if (!pxe_near(pd, p4.z, zmax)) continue;   // the same branch for the whole block
+    const Win win = window_of(pd, (double)p4.x, (double)p4.y);
+    const int64_t npix = (int64_t)pd.nx * pd.ny;
+    const float xf = p4.x, yf = p4.y, z = p4.z, zz = z * z;
+    const float hx = (float)pd.hx, hy = (float)pd.hy, ga = (float)(pd.hx * pd.hy / pd.area);
+    float acc[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) acc[m] = 0.0f;
+    for (int64_t k = threadIdx.x; k < npix; k += PXE_NT) {
+      if (win.has((long)(k % pd.nx), (long)(k / pd.nx))) continue;
+      const int64_t base = tile_base(k);
+      float w[4];
+      pixel_gauss(xf - pd.tiles32[base], yf - pd.tiles32[base + TILE], z, zz, hx, hy, ga, w);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const float b = pd.tiles32[base + (2 + p) * TILE];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[4 * p + m] += b * w[m];
+      }
+    }
+    double accd[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) accd[m] = (double)acc[m];
+    const double v = block_sum12(red, accd, lane, warp);
+    if (threadIdx.x < 12) {
+      const int p = threadIdx.x >> 2, e = threadIdx.x & 3;
+      corr[12 * i + (e == 0 ? p : 3 + 3 * p + (e - 1))] += v;   // after the window's sum
+    }
+  }
+}
+
+__global__ void __launch_bounds__(PXE_NT) pxe_exact_kernel(const ProbDesc* __restrict__ probs,
+                                                           int64_t n,
+                                                           const float4* __restrict__ pos,
+                                                           double zmax,
+                                                           double* __restrict__ corr) {
   __shared__ double red[PXE_NT / 32][12];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
@@ -141,62 +263,12 @@ __global__ void __launch_bounds__(PXE_NT) pxe_corr_kernel(const ProbDesc* __rest
     }
     const double xd = p4.x, yd = p4.y, zd = p4.z, inv_dA = 1.0 / pd.area;
     const int64_t npix = (int64_t)pd.nx * pd.ny;
-    double accd[12];
+    double acc[12];
 #pragma unroll
-    for (int m = 0; m < 12; ++m) accd[m] = 0.0;
-    auto add_exact = [&](int64_t k) {
-      const int64_t base = tile_base(k);
-      double w[4];
-      pixel_exact(xd - pd.tiles64[base], yd - pd.tiles64[base + TILE], zd, pd.hx, pd.hy, inv_dA, w);
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const double b = pd.tiles64[base + (2 + p) * TILE];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) accd[4 * p + m] += b * w[m];
-      }
-    };
-    if constexpr (FP64) {
-      for (int64_t k = threadIdx.x; k < npix; k += PXE_NT) add_exact(k);
-    } else {
-      const Win win = window_of(pd, xd, yd);
-      const long wi = win.i1 - win.i0 + 1, wj = win.j1 - win.j0 + 1;
-      if (wi > 0 && wj > 0)
-        for (long e = threadIdx.x; e < wi * wj; e += PXE_NT)
-          add_exact((win.j0 + e / wi) * (int64_t)pd.nx + (win.i0 + e % wi));
-      const float xf = p4.x, yf = p4.y, z = p4.z, zz = z * z;
-      const float hx = (float)pd.hx, hy = (float)pd.hy, ga = (float)(pd.hx * pd.hy / pd.area);
-      float acc[12];
-#pragma unroll
-      for (int m = 0; m < 12; ++m) acc[m] = 0.0f;
-      for (int64_t k = threadIdx.x; k < npix; k += PXE_NT) {
-        if (win.has((long)(k % pd.nx), (long)(k / pd.nx))) continue;
-        const int64_t base = tile_base(k);
-        float w[4];
-        pixel_gauss(xf - pd.tiles32[base], yf - pd.tiles32[base + TILE], z, zz, hx, hy, ga, w);
-#pragma unroll
-        for (int p = 0; p < 3; ++p) {
-          const float b = pd.tiles32[base + (2 + p) * TILE];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) acc[4 * p + m] += b * w[m];
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < 12; ++m) accd[m] += (double)acc[m];
-    }
-#pragma unroll
-    for (int m = 0; m < 12; ++m) {
-      double v = accd[m];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) red[warp][m] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 12) {
-      double v = 0.0;
-      for (int w = 0; w < PXE_NT / 32; ++w) v += red[w][threadIdx.x];
-      const int p = threadIdx.x >> 2, m = threadIdx.x & 3;
-      out[m == 0 ? p : 3 + 3 * p + (m - 1)] = v;
-    }
-    __syncthreads();
+    for (int m = 0; m < 12; ++m) acc[m] = 0.0;
+    for (int64_t k = threadIdx.x; k < npix; k += PXE_NT) add_exact12(pd, k, xd, yd, zd, inv_dA, acc);
+    const double v = block_sum12(red, acc, lane, warp);
+    if (threadIdx.x < 12) store12(out, threadIdx.x, v);
   }
 }
 
@@ -204,8 +276,13 @@ void launch_pxe_corr(bool fp64, const ProbDesc* probs, int64_t n, const float4* 
                      double* corr, int grid, cudaStream_t s) {
   if (n <= 0) return;
   const int g = (int)(n < grid ? n : grid);
-  if (fp64) pxe_corr_kernel<true><<<g, PXE_NT, 0, s>>>(probs, n, pos, zmax, corr);
-  else pxe_corr_kernel<false><<<g, PXE_NT, 0, s>>>(probs, n, pos, zmax, corr);
+  if (fp64) {
+    pxe_exact_kernel<<<g, PXE_NT, 0, s>>>(probs, n, pos, zmax, corr);
+  } else {
+    const int64_t gw = (n * 32 + 255) / 256;
+    pxe_window_kernel<<<(int)(gw < grid ? gw : grid), 256, 0, s>>>(probs, n, pos, zmax, corr);
+    pxe_gauss_kernel<<<g, PXE_NT, 0, s>>>(probs, n, pos, zmax, corr);
+  }
 }
 
 // Stable list of the points with z <= zmax (one block: each thread counts a contiguous range,
@@ -249,9 +326,12 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
                                                          const double* __restrict__ w,
                                                          double* __restrict__ part) {
   constexpr int NW = FULL ? 12 : 3;
+  // weights in the working precision (the mixed form converts once per point, not per pair:
+  // FP64-to-FP32 conversions run on GB300's narrow FP64 pipe)
+  using WT = typename std::conditional<FP64, double, float>::type;
   __shared__ float sx[PXE_NT], sy[PXE_NT], sz[PXE_NT];
   __shared__ int32_t sw0[PXE_NT];   // window origin of each point (packed i0, j0), mixed form
-  __shared__ double sw[NW][PXE_NT];
+  __shared__ WT sw[NW][PXE_NT];
   const ProbDesc& pd = *prob;
   const int64_t npix = (int64_t)pd.nx * pd.ny;
   const int64_t k = blockIdx.x * (int64_t)PXE_NT + threadIdx.x;
@@ -281,30 +361,31 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
       const long cy = iy < -32768 ? -32768 : (iy > 32767 ? 32767 : iy);
       sw0[threadIdx.x] = (int32_t)(((cy + 32768) << 16) | (cx + 32768));
 #pragma unroll
-      for (int e = 0; e < NW; ++e) sw[e][threadIdx.x] = w[NW * q + e];
+      for (int e = 0; e < NW; ++e) sw[e][threadIdx.x] = (WT)w[NW * q + e];
     }
     __syncthreads();
     if (!live) continue;
     const int len = m - j0 < PXE_NT ? m - j0 : PXE_NT;
     float acc[3] = {0.0f, 0.0f, 0.0f};
     for (int jj = 0; jj < len; ++jj) {
-      bool exact = FP64;
       if constexpr (!FP64) {
+        // window pairs are summed exactly by pxe_adj_window_kernel
         const int32_t pk = sw0[jj];
         const long ix = (long)(pk & 0xffff) - 32768, iy = (long)((pk >> 16) & 0xffff) - 32768;
-        exact = ki >= ix - NEAR_W && ki <= ix + NEAR_W && kj >= iy - NEAR_W && kj <= iy + NEAR_W;
+        if (ki >= ix - NEAR_W && ki <= ix + NEAR_W && kj >= iy - NEAR_W && kj <= iy + NEAR_W)
+          continue;
       }
-      if (exact) {
+      if constexpr (FP64) {
         double c[4];
         pixel_exact((double)sx[jj] - xk, (double)sy[jj] - yk, (double)sz[jj], pd.hx, pd.hy,
                     inv_dA, c);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           if constexpr (FULL)
-            hi[p] += sw[4 * p][jj] * c[0] + sw[4 * p + 1][jj] * c[1] + sw[4 * p + 2][jj] * c[2] +
-                     sw[4 * p + 3][jj] * c[3];
+            hi[p] += (double)sw[4 * p][jj] * c[0] + (double)sw[4 * p + 1][jj] * c[1] +
+                     (double)sw[4 * p + 2][jj] * c[2] + (double)sw[4 * p + 3][jj] * c[3];
           else
-            hi[p] += sw[p][jj] * c[0];
+            hi[p] += (double)sw[p][jj] * c[0];
         }
       } else {
         const float z = sz[jj];
@@ -313,10 +394,10 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           if constexpr (FULL)
-            acc[p] += (float)sw[4 * p][jj] * c[0] + (float)sw[4 * p + 1][jj] * c[1] +
-                      (float)sw[4 * p + 2][jj] * c[2] + (float)sw[4 * p + 3][jj] * c[3];
+            acc[p] += sw[4 * p][jj] * c[0] + sw[4 * p + 1][jj] * c[1] + sw[4 * p + 2][jj] * c[2] +
+                      sw[4 * p + 3][jj] * c[3];
           else
-            acc[p] += (float)sw[p][jj] * c[0];
+            acc[p] += sw[p][jj] * c[0];
         }
       }
     }
@@ -327,6 +408,126 @@ __global__ void __launch_bounds__(PXE_NT) pxe_adj_kernel(const ProbDesc* __restr
   double* o = part + ((int64_t)blockIdx.y * npix + k) * 3;
 #pragma unroll
   for (int p = 0; p < 3; ++p) o[p] = hi[p];
+}
+
+// ---- the window pairs of the transpose (mixed form), pixel-major without divergence ----------
+// Near points are binned by their nearest pixel (ix, iy) on the lattice extended by W on every
+// side; pixel (i, j) then takes the points of the (2W+1)^2 bins around it, in bin order and, within
+// a bin, in near-list order (a stable counting sort), so the sums do not depend on the schedule.
+__device__ __forceinline__ int64_t bin_of(const ProbDesc& pd, float4 p4) {
+  const long bx = pd.nx + 2 * NEAR_W, by = pd.ny + 2 * NEAR_W;
+  const long ix = lrint(((double)p4.x - pd.x0) / pd.hx) + NEAR_W;
+  const long iy = lrint(((double)p4.y - pd.y0) / pd.hy) + NEAR_W;
+  return (ix >= 0 && ix < bx && iy >= 0 && iy < by) ? (int64_t)iy * bx + ix : -1;
+}
+
+__global__ void pxe_bin_count_kernel(const ProbDesc* __restrict__ prob,
+                                     const int32_t* __restrict__ list,
+                                     const int32_t* __restrict__ cnt,
+                                     const float4* __restrict__ pos, int32_t* __restrict__ bcount) {
+  const int m = *cnt;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = bin_of(*prob, pos[list[j]]);
+    if (b >= 0) atomicAdd(bcount + b, 1);
+  }
+}
+
+// Exclusive prefix of bcount[0 .. nb) into boff[0 .. nb] (one block).
+__global__ void __launch_bounds__(PXE_SCAN) pxe_bin_scan_kernel(int64_t nb,
+                                                                const int32_t* __restrict__ bcount,
+                                                                int32_t* __restrict__ boff) {
+  __shared__ int32_t s[PXE_SCAN];
+  const int t = threadIdx.x;
+  const int64_t per = (nb + PXE_SCAN - 1) / PXE_SCAN;
+  const int64_t lo = t * per, hi = lo + per < nb ? lo + per : nb;
+  int32_t c = 0;
+  for (int64_t i = lo; i < hi; ++i) c += bcount[i];
+  s[t] = c;
+  __syncthreads();
+  for (int off = 1; off < PXE_SCAN; off <<= 1) {
+    const int32_t v = t >= off ? s[t - off] : 0;
+    __syncthreads();
+    s[t] += v;
+    __syncthreads();
+  }
+  int32_t o = s[t] - c;
+  for (int64_t i = lo; i < hi; ++i) {
+    boff[i] = o;
+    o += bcount[i];
+  }
+  if (t == PXE_SCAN - 1) boff[nb] = s[t];
+}
+
+__global__ void pxe_bin_fill_kernel(const ProbDesc* __restrict__ prob,
+                                    const int32_t* __restrict__ list,
+                                    const int32_t* __restrict__ cnt,
+                                    const float4* __restrict__ pos,
+                                    const int32_t* __restrict__ boff, int32_t* __restrict__ bfill,
+                                    int32_t* __restrict__ entries) {
+  const int m = *cnt;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = bin_of(*prob, pos[list[j]]);
+    if (b >= 0) entries[boff[b] + atomicAdd(bfill + b, 1)] = (int32_t)j;
+  }
+}
+
+// Near-list order within each bin (insertion sort; bins hold a few points).
+__global__ void pxe_bin_sort_kernel(int64_t nb, const int32_t* __restrict__ boff,
+                                    int32_t* __restrict__ entries) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t lo = boff[b], hi = boff[b + 1];
+    for (int32_t i = lo + 1; i < hi; ++i) {
+      const int32_t v = entries[i];
+      int32_t j = i - 1;
+      while (j >= lo && entries[j] > v) {
+        entries[j + 1] = entries[j];
+        --j;
+      }
+      entries[j + 1] = v;
+    }
+  }
+}
+
+template <bool FULL>
+__global__ void __launch_bounds__(PXE_NT) pxe_adj_window_kernel(
+    const ProbDesc* __restrict__ prob, const int32_t* __restrict__ list,
+    const int32_t* __restrict__ boff, const int32_t* __restrict__ entries,
+    const float4* __restrict__ pos, const double* __restrict__ w, double* __restrict__ part) {
+  constexpr int NW = FULL ? 12 : 3;
+  const ProbDesc& pd = *prob;
+  const int64_t npix = (int64_t)pd.nx * pd.ny;
+  const int64_t k = blockIdx.x * (int64_t)PXE_NT + threadIdx.x;
+  if (k >= npix) return;
+  const long ki = (long)(k % pd.nx), kj = (long)(k / pd.nx);
+  const int64_t base = tile_base(k);
+  const double xk = pd.tiles64[base], yk = pd.tiles64[base + TILE];
+  const double inv_dA = 1.0 / pd.area;
+  const long bx = pd.nx + 2 * NEAR_W;
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (long dj = -NEAR_W; dj <= NEAR_W; ++dj)
+    for (long di = -NEAR_W; di <= NEAR_W; ++di) {
+      const int64_t b = (kj + dj + NEAR_W) * bx + (ki + di + NEAR_W);
+      for (int32_t e = boff[b]; e < boff[b + 1]; ++e) {
+        const int64_t q = list[entries[e]];
+        const float4 p4 = pos[q];
+        double c[4];
+        pixel_exact((double)p4.x - xk, (double)p4.y - yk, (double)p4.z, pd.hx, pd.hy, inv_dA, c);
+        const double* wq = w + NW * q;
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          if constexpr (FULL)
+            acc[p] += wq[4 * p] * c[0] + wq[4 * p + 1] * c[1] + wq[4 * p + 2] * c[2] +
+                      wq[4 * p + 3] * c[3];
+          else
+            acc[p] += wq[p] * c[0];
+        }
+      }
+    }
+#pragma unroll
+  for (int p = 0; p < 3; ++p) part[3 * k + p] = acc[p];
 }
 
 __global__ void pxe_adj_reduce_kernel(const ProbDesc* __restrict__ prob, int nchunk,
@@ -349,11 +550,38 @@ int pxe_adjoint_chunks(int64_t n, int64_t npix, int sm_count) {
   return (int)(c < 1 ? 1 : (c > 65535 ? 65535 : c));
 }
 
-void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int64_t npix,
+int64_t pxe_bins(int nx, int ny) { return (int64_t)(nx + 2 * NEAR_W) * (ny + 2 * NEAR_W); }
+
+void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int nx, int ny,
                         const float4* pos, double zmax, const double* w, int32_t* list,
-                        int32_t* cnt, int nchunk, double* part, double* gB0, cudaStream_t s) {
+                        int32_t* cnt, int32_t* bins, int nchunk, double* part, double* gB0,
+                        cudaStream_t s) {
   if (n <= 0) return;
+  const int64_t npix = (int64_t)nx * ny;
   pxe_compact_kernel<<<1, PXE_SCAN, 0, s>>>(n, pos, zmax, list, cnt);
+  const int nparts = nchunk + (fp64 ? 0 : 1);
+  if (!fp64) {
+    // bins: count [nb], offsets [nb + 1], fill [nb], entries [n]
+    const int64_t nb = pxe_bins(nx, ny);
+    int32_t* bcount = bins;
+    int32_t* boff = bins + nb;
+    int32_t* bfill = boff + nb + 1;
+    int32_t* entries = bfill + nb;
+    cudaMemsetAsync(bcount, 0, sizeof(int32_t) * nb, s);
+    cudaMemsetAsync(bfill, 0, sizeof(int32_t) * nb, s);
+    const int gn = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    pxe_bin_count_kernel<<<gn, 256, 0, s>>>(prob, list, cnt, pos, bcount);
+    pxe_bin_scan_kernel<<<1, PXE_SCAN, 0, s>>>(nb, bcount, boff);
+    pxe_bin_fill_kernel<<<gn, 256, 0, s>>>(prob, list, cnt, pos, boff, bfill, entries);
+    const int gb = (int)((nb + 255) / 256 < 4096 ? (nb + 255) / 256 : 4096);
+    pxe_bin_sort_kernel<<<gb, 256, 0, s>>>(nb, boff, entries);
+    const int gp = (int)((npix + PXE_NT - 1) / PXE_NT);
+    double* wpart = part + (int64_t)nchunk * 3 * npix;
+    if (full)
+      pxe_adj_window_kernel<true><<<gp, PXE_NT, 0, s>>>(prob, list, boff, entries, pos, w, wpart);
+    else
+      pxe_adj_window_kernel<false><<<gp, PXE_NT, 0, s>>>(prob, list, boff, entries, pos, w, wpart);
+  }
   const dim3 grid((unsigned)((npix + PXE_NT - 1) / PXE_NT), (unsigned)nchunk);
 #define ADJ(D, F) pxe_adj_kernel<D, F><<<grid, PXE_NT, 0, s>>>(prob, list, cnt, pos, w, part)
   if (fp64) {
@@ -364,7 +592,7 @@ void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, i
 #undef ADJ
   const int64_t e = 3 * npix;
   const int g2 = (int)((e + 255) / 256 < 8192 ? (e + 255) / 256 : 8192);
-  pxe_adj_reduce_kernel<<<g2, 256, 0, s>>>(prob, nchunk, part, gB0);
+  pxe_adj_reduce_kernel<<<g2, 256, 0, s>>>(prob, nparts, part, gB0);
 }
 
 }  // namespace dbie
