@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--workload", default="ll128", choices=["ll128", "batch64"])
     ap.add_argument("--max-points", type=int, default=200_000,
                     help="batch64: upper end of the per-problem point count")
+    ap.add_argument("--case", default=None, choices=["exact_near_field"],
+                    help="a single-kernel-family case for profiling instead of the step")
     return ap.parse_args()
 
 
@@ -592,9 +594,43 @@ def run_batched(args):
         f.close()
 
 
+def run_case_exact_near_field():
+    """Profiling case of the exact near field on the ll128 workload: field evaluation and the
+    fixed-lambda adjoint of all 131,072 points at lambda_p = 0.02 with the correction (twice, to
+    warm up) and once more of each on the pixel-centre rule; prints the CUDA-event times."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ll128()
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    pts = torch.from_numpy(w.points).cuda()
+    lam = torch.full((len(w.points), 3), 0.02, device="cuda")
+    gB = torch.ones((len(w.points), 3), dtype=torch.float64, device="cuda")
+    out = {}
+    for name, order in (("exact_near_field", dbie.QUAD_PIXEL_EXACT), ("pixel_centres", 0)):
+        f.set_quadrature(order)
+        for _ in range(2):
+            f.eval(pts, lam)
+            f.vjp(pts, lam.double(), gB, glam=False)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        f.eval(pts, lam)
+        ev[1].record()
+        f.vjp(pts, lam.double(), gB, glam=False)
+        ev[2].record()
+        torch.cuda.synchronize()
+        out[name] = {"eval_ms": ev[0].elapsed_time(ev[1]), "vjp_ms": ev[1].elapsed_time(ev[2])}
+    f.close()
+    print(json.dumps({"case": "exact_near_field", "workload": "ll128 (131072 points, 128^2 pixels)",
+                      **out}))
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.case == "exact_near_field":
+        run_case_exact_near_field()
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":
         run_batched(args)
