@@ -361,3 +361,35 @@ def test_pxe_full_size_ll128_sampled(dbie):
     ref = oracle.vjp(bd, x64, lam[idx], gB, quad_order=-1)
     assert np.linalg.norm(gB0.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
     f.close()
+
+
+def test_pxe_host_memory_path_equals_device_path(dbie):
+    """The C ABI with host buffers (mem_kind = host) in the exact-near-field mode gives the same
+    bits as the device path: field evaluation (B, grad B) and the fixed-lambda adjoint."""
+    import ctypes
+
+    import paper_1306_1122_gb300._native as N
+    mag = random_mag(30, 26, 480)
+    xyz, lam = random_points(mag, 300, 481, zlo=0.3, zhi=3.5)
+    gB = np.random.default_rng(482).normal(size=(300, 3))
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True)
+    gd, _ = f.vjp(torch.from_numpy(xyz), torch.from_numpy(lam.astype(np.float64)),
+                  torch.from_numpy(gB), glam=False)
+    torch.cuda.synchronize()
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)   # noqa: E731
+    h = N.dbie_create(mag.nx, mag.ny, mag.x0, mag.y0, mag.hx, mag.hy, mag.dA,
+                      *(P(c) for c in (mag.Bx, mag.By, mag.Bz)), N.DBIE_MEM_HOST, None)
+    N.dbie_set_quadrature(h, -1, None)
+    B = np.zeros((300, 3))
+    G = np.zeros((300, 9))
+    N.dbie_eval(h, 300, P(xyz), P(lam), None, N.DBIE_MEM_HOST, P(B), P(G), None, None, None)
+    lam64 = np.ascontiguousarray(lam.astype(np.float64))
+    g0 = np.zeros((mag.ny * mag.nx, 3))
+    N.dbie_vjp(h, 300, P(xyz), P(lam64), P(gB), None, N.DBIE_MEM_HOST, P(g0), None, 0, None)
+    N.dbie_destroy(h)
+    f.close()
+    assert np.array_equal(B, r["B"].cpu().numpy())
+    assert np.array_equal(G.reshape(-1, 3, 3), r["gradB"].cpu().numpy())
+    assert np.array_equal(g0.reshape(mag.ny, mag.nx, 3), gd.cpu().numpy())
