@@ -531,9 +531,9 @@ static dbie_status pxe_adjoint(dbie_ctx* c, int64_t n, const float4* pos, const 
   DBIE_TRY(ensure(c->pxe_part, sizeof(double) * 3 * (size_t)c->npix * (nchunk + 1)));
   DBIE_TRY(ensure(c->pxe_bins, sizeof(int32_t) * (3 * (size_t)pxe_bins(c->nx, c->ny) + 1 + n)));
   int32_t* list = c->pxe_list.as<int32_t>();
-  launch_pxe_adjoint(fp64, full, c->prob.as<ProbDesc>(), n, c->nx, c->ny, pos, o.near_z, w, list,
-                     list + n, c->pxe_bins.as<int32_t>(), nchunk, c->pxe_part.as<double>(), gB0, s);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_pxe_adjoint(fp64, full, c->prob.as<ProbDesc>(), n, c->nx, c->ny, pos, o.near_z,
+                              w, list, list + n, c->pxe_bins.as<int32_t>(), nchunk,
+                              c->pxe_part.as<double>(), gB0, s));
   return DBIE_OK;
 }
 

@@ -74,10 +74,10 @@ void launch_pxe_corr(bool fp64, const ProbDesc* probs, int64_t n, const float4* 
 // extra part: the window pairs of the mixed form), the bin buffer 3 * pxe_bins + 1 + n int32
 int pxe_adjoint_chunks(int64_t n, int64_t npix, int sm_count);
 int64_t pxe_bins(int nx, int ny);
-void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int nx, int ny,
-                        const float4* pos, double zmax, const double* w, int32_t* list,
-                        int32_t* cnt, int32_t* bins, int nchunk, double* part, double* gB0,
-                        cudaStream_t s);
+cudaError_t launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int nx,
+                               int ny, const float4* pos, double zmax, const double* w,
+                               int32_t* list, int32_t* cnt, int32_t* bins, int nchunk,
+                               double* part, double* gB0, cudaStream_t s);
 
 void launch_count_bad(const float* a, int64_t n, int mode, int32_t* cnt, cudaStream_t s);
 void launch_pack_points(int64_t n, const float* xyz, int pidx, float4* ppos, cudaStream_t s);

@@ -552,11 +552,11 @@ int pxe_adjoint_chunks(int64_t n, int64_t npix, int sm_count) {
 
 int64_t pxe_bins(int nx, int ny) { return (int64_t)(nx + 2 * NEAR_W) * (ny + 2 * NEAR_W); }
 
-void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int nx, int ny,
-                        const float4* pos, double zmax, const double* w, int32_t* list,
-                        int32_t* cnt, int32_t* bins, int nchunk, double* part, double* gB0,
-                        cudaStream_t s) {
-  if (n <= 0) return;
+cudaError_t launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, int nx,
+                               int ny, const float4* pos, double zmax, const double* w,
+                               int32_t* list, int32_t* cnt, int32_t* bins, int nchunk,
+                               double* part, double* gB0, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
   const int64_t npix = (int64_t)nx * ny;
   pxe_compact_kernel<<<1, PXE_SCAN, 0, s>>>(n, pos, zmax, list, cnt);
   const int nparts = nchunk + (fp64 ? 0 : 1);
@@ -567,8 +567,9 @@ void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, i
     int32_t* boff = bins + nb;
     int32_t* bfill = boff + nb + 1;
     int32_t* entries = bfill + nb;
-    cudaMemsetAsync(bcount, 0, sizeof(int32_t) * nb, s);
-    cudaMemsetAsync(bfill, 0, sizeof(int32_t) * nb, s);
+    cudaError_t e = cudaMemsetAsync(bcount, 0, sizeof(int32_t) * nb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(bfill, 0, sizeof(int32_t) * nb, s);
+    if (e != cudaSuccess) return e;
     const int gn = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     pxe_bin_count_kernel<<<gn, 256, 0, s>>>(prob, list, cnt, pos, bcount);
     pxe_bin_scan_kernel<<<1, PXE_SCAN, 0, s>>>(nb, bcount, boff);
@@ -593,6 +594,7 @@ void launch_pxe_adjoint(bool fp64, bool full, const ProbDesc* prob, int64_t n, i
   const int64_t e = 3 * npix;
   const int g2 = (int)((e + 255) / 256 < 8192 ? (e + 255) / 256 : 8192);
   pxe_adj_reduce_kernel<<<g2, 256, 0, s>>>(prob, nparts, part, gB0);
+  return cudaGetLastError();
 }
 
 }  // namespace dbie
