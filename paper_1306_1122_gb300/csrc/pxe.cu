@@ -223,8 +223,18 @@ __global__ void __launch_bounds__(PXE_NT, 8) pxe_gauss_kernel(const ProbDesc* __
     float acc[12];
 #pragma unroll
     for (int m = 0; m < 12; ++m) acc[m] = 0.0f;
+    // column and row of pixel k, advanced with k (no integer division in the loop)
+    int ci = (int)(threadIdx.x % pd.nx), cj = (int)(threadIdx.x / pd.nx);
+    const int step_i = PXE_NT % pd.nx, step_j = PXE_NT / pd.nx;
     for (int64_t k = threadIdx.x; k < npix; k += PXE_NT) {
-      if (win.has((long)(k % pd.nx), (long)(k / pd.nx))) continue;
+      const bool in_win = win.has(ci, cj);
+      ci += step_i;
+      cj += step_j;
+      if (ci >= pd.nx) {
+        ci -= pd.nx;
+        ++cj;
+      }
+      if (in_win) continue;
       const int64_t base = tile_base(k);
       float w[4];
       pixel_gauss(xf - pd.tiles32[base], yf - pd.tiles32[base + TILE], z, zz, hx, hy, ga, w);
