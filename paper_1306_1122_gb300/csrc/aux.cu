@@ -187,7 +187,7 @@ void launch_plan_single(PlanHdr* plan, int32_t* item_off, int32_t* q_cnt, int32_
 // Near-field correction (mixed precision, points with z <= near_z): over the (2W+1)^2 pixels
 // around the point, replace the FP32 pair terms that the pair-sum kernel added by FP64 ones.
 // The FP32 terms are recomputed with the same explicitly rounded code (pair_terms32), so the
-// correction sum_k (t64 - t32) removes exactly what was added.  One warp per query; the
+// correction sum_k (t64 - t32) removes exactly what was added.  Eight lanes per query; the
 // correction is added in place to the query's split-0 partial sums (run after the pair sums).
 // Index (along one axis) of the quadrature point nearest to coordinate x: the pixel for the
 // midpoint rule; for nine-node elements of width 2h with g Gauss points, element e and the
@@ -218,11 +218,18 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
                                  const int32_t* __restrict__ item_off, double* __restrict__ out) {
   constexpr int NS = nsum_per_comp(VAR);
   constexpr int NSUM = 3 * NS;
-  const int lane = threadIdx.x & 31;
+  // Eight lanes per query, four queries per warp: a 7 x 7 window takes 7 passes of 8 lanes
+  // (49 of 56 lane slots busy) instead of 2 of 32 (49 of 64).  The loop runs warp-uniformly so
+  // the shuffles see every lane.
+  constexpr int GL = 8;
+  const int lane = threadIdx.x & 31, sub = lane & (GL - 1), grp = lane / GL;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int cnt = *near_cnt;
-  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < cnt; w += nwarps) {
-    const int64_t slot = near_list[w];
+  for (int64_t wb = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * (32 / GL); wb < cnt;
+       wb += nwarps * (32 / GL)) {
+    const int64_t w = wb + grp;
+    const bool valid = w < cnt;
+    const int64_t slot = near_list[valid ? w : wb];
     const float4 pos = qpos[slot];
     const Lam4 lam = qlam[slot];
     const int pidx = __float_as_int(pos.w);
@@ -240,9 +247,9 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
     double c[NSUM];
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) c[s] = 0.0;
-    if (wi > 0 && wj > 0 && wi <= 2 * W + 1 && wj <= 2 * W + 1) {
+    if (valid && wi > 0 && wj > 0 && wi <= 2 * W + 1 && wj <= 2 * W + 1) {
       const int nwin = (int)(wi * wj);
-      for (int e = lane; e < nwin; e += 32) {
+      for (int e = sub; e < nwin; e += GL) {
         const int64_t k = (j0 + e / wi) * (int64_t)pd.nx + (i0 + e % wi);
         const int nf = pd.nf32 > 0 ? pd.nf32 : NFIELD;
         const float b32[3] = {*tile_field(pd.tiles32, k, 2, nf), *tile_field(pd.tiles32, k, 3, nf),
@@ -290,8 +297,8 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
 #pragma unroll
     for (int s = 0; s < NSUM; ++s) {
       double v = c[s];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if (lane == 0) out[out_index(h, item_off, pidx, slot - pd.q_off, 0, s, NSUM)] += v;
+      for (int off = GL / 2; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (sub == 0 && valid) out[out_index(h, item_off, pidx, slot - pd.q_off, 0, s, NSUM)] += v;
     }
   }
 }

@@ -393,3 +393,42 @@ def test_pxe_host_memory_path_equals_device_path(dbie):
     assert np.array_equal(B, r["B"].cpu().numpy())
     assert np.array_equal(G.reshape(-1, 3, 3), r["gradB"].cpu().numpy())
     assert np.array_equal(g0.reshape(mag.ny, mag.nx, 3), gd.cpu().numpy())
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 7), (5, 3), (3, 300), (257, 2)])
+@pytest.mark.parametrize("precision", [1, 0])
+def test_pxe_ragged_grids_and_far_points(dbie, nx, ny, precision):
+    """Degenerate and ragged magnetograms (a single column, fewer pixels than the 7 x 7 window,
+    one tile plus a pixel) and points far outside the lattice (windows clipped to nothing, or to
+    a strip): B, grad B and the adjoint against the oracle's exact rule."""
+    mag = random_mag(nx, ny, 490 + nx + ny, x0=-1.0, y0=2.0, smooth=False)
+    rng = np.random.default_rng(491 + nx)
+    n = 120
+    x = rng.uniform(mag.x0 - 6, mag.x0 + (nx - 1) + 6, n)
+    y = rng.uniform(mag.y0 - 6, mag.y0 + (ny - 1) + 6, n)
+    z = rng.uniform(0.3, 2.5, n)
+    xyz = np.stack([x, y, z], 1).astype(np.float32)
+    lam = rng.uniform(-0.3, 0.3, (n, 3)).astype(np.float32)
+    gB = rng.normal(size=(n, 3))
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    opt = dbie.Options(precision=precision)
+    r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True, options=opt)
+    gB0, _ = f.vjp(torch.from_numpy(xyz), torch.from_numpy(lam.astype(np.float64)),
+                   torch.from_numpy(gB), glam=False, options=opt)
+    torch.cuda.synchronize()
+    bd = oracle_boundary(mag)
+    x64, l64 = xyz.astype(np.float64), lam.astype(np.float64)
+    B, G, _ = oracle.field(bd, x64, l64, quad_order=-1)
+    ref = oracle.vjp(bd, x64, l64, gB, quad_order=-1)
+    sB, sG = pxe_scales(mag, xyz, l64, 2.0)
+    got_B, got_G = r["B"].cpu().numpy(), r["gradB"].cpu().numpy()
+    if precision == 1:
+        assert np.all(np.abs(got_B - B) <= TOL_FP64 * sB)
+        assert np.all(np.abs(got_G - G) <= TOL_FP64 * sG[:, :, None])
+        assert np.linalg.norm(gB0.cpu().numpy() - ref) <= 1e-10 * np.linalg.norm(ref)
+    else:
+        assert check_B(got_B, B, sB)["bad"].size == 0
+        assert check_grad(got_G, G, sG[:, :, None])["ok"]
+        assert np.linalg.norm(gB0.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    f.close()
