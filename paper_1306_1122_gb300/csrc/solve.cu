@@ -292,6 +292,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     Vert v[4];
     for (int k = 0; k <= n; ++k) load_vert(a, g, k, v[k]);
     bool to_check = false;  // an iteration (or the initialisation) completed: sort and test
+    bool dirty = false;     // the vertices changed and must be stored back
     char code = 0;
 
     auto centroid = [&](double c[3]) {
@@ -307,6 +308,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       for (int d = 0; d < 3; ++d) out[d] = (d < n) ? coef_c * c[d] + coef_w * v[n].l[d] : 0.0;
     };
     auto accept_last = [&](const double l[3], const Eval& e) {
+      dirty = true;
       for (int d = 0; d < 3; ++d) v[n].l[d] = l[d];
       for (int p = 0; p < 3; ++p) v[n].B[p] = e.B[p];
       v[n].f = e.f;
@@ -320,6 +322,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       emit(a, g, pos, pidx, 1, rows);
     };
     auto start_shrink = [&]() {
+      dirty = true;
       double rows[3][3];
       for (int k = 1; k <= n; ++k) {
         for (int d = 0; d < 3; ++d)
@@ -339,6 +342,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       }
       nfev += n + 1;
       to_check = true;
+      dirty = true;
     } else if (stage == ST_REFLECT) {
       Eval e;
       read_eval(a, h, pidx, slot, z, e, g);
@@ -409,6 +413,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       nfev += n;
       code = 'S';
       to_check = true;
+      dirty = true;
     }
 
     if (code && a.codes && iters >= 1 && iters <= a.codes_stride)
@@ -432,6 +437,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         a.res_nfev[g] = nfev;
         stage = ST_DONE;
         SI(a, I_STATUS, g) = fin;
+        dirty = false;   // a finished point's vertices are not read again
       } else {
         iters += 1;
         double xr[3];
@@ -439,7 +445,8 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         emit_one(xr, ST_REFLECT);
       }
     }
-    for (int k = 0; k <= n; ++k) store_vert(a, g, k, v[k]);
+    if (dirty)
+      for (int k = 0; k <= n; ++k) store_vert(a, g, k, v[k]);
     SI(a, I_STAGE, g) = stage;
     SI(a, I_ITERS, g) = iters;
     SI(a, I_NFEV, g) = nfev;
