@@ -432,3 +432,35 @@ def test_pxe_ragged_grids_and_far_points(dbie, nx, ny, precision):
         assert check_grad(got_G, G, sG[:, :, None])["ok"]
         assert np.linalg.norm(gB0.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
     f.close()
+
+
+def test_pxe_gradcheck_and_set_boundary(dbie):
+    """With the exact near field: torch.autograd.gradcheck through dbie_apply (FP64 form, B0 on
+    multiples of 1/16 and a step of 1/64, exact in float32; the forward includes the correction
+    and the backward its transpose), and dbie_set_boundary restages the rule: the same bits as a
+    new context on the new magnetogram."""
+    rng = np.random.default_rng(495)
+    ny, nx, n = 5, 6, 5
+    B0 = torch.from_numpy(np.round(rng.normal(0, 20, (ny, nx, 3)) * 16) / 16).cuda()
+    f = dbie.DBIEField(B0[..., 0].float(), B0[..., 1].float(), B0[..., 2].float())
+    f.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    xyz = torch.from_numpy(np.stack([rng.uniform(0, 5, n), rng.uniform(0, 4, n),
+                                     rng.uniform(0.4, 2.5, n)], 1).astype(np.float32)).cuda()
+    lam = torch.from_numpy(np.round(rng.uniform(-0.4, 0.4, (n, 3)) * 4096) / 4096).cuda()
+    opt = dbie.Options(precision=1)
+    B0.requires_grad_(True)
+    lam.requires_grad_(True)
+    fn = lambda b0, l: dbie.dbie_apply(f, b0, l, xyz, opt)   # noqa: E731
+    assert torch.autograd.gradcheck(fn, (B0, lam), eps=2.0 ** -10, atol=1e-5, rtol=1e-4)
+    # set_boundary in the exact-near-field mode
+    mag2 = random_mag(nx, ny, 496)
+    f.set_boundary(torch.from_numpy(mag2.Bx).cuda(), torch.from_numpy(mag2.By).cuda(),
+                   torch.from_numpy(mag2.Bz).cuda())
+    a = f.eval(xyz, lam.detach().float(), grad=True)
+    g = dbie.DBIEField.from_magnetogram(mag2)
+    g.set_quadrature(dbie.QUAD_PIXEL_EXACT)
+    b = g.eval(xyz, lam.detach().float(), grad=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a["B"], b["B"]) and torch.equal(a["gradB"], b["gradB"])
+    f.close()
+    g.close()
