@@ -21,11 +21,15 @@
 // in FP32 (its error there is below 1e-7 of the absolute-value sum, beyond W = 3); the FP64 form
 // integrates every pixel exactly in FP64.
 //
-// Kernels: pxe_window (FP64 window sums, one warp per point), pxe_gauss (the other pixels' FP32
-// Gauss sums, one CTA per near point, added) or, in the FP64 form, pxe_exact; pxe_compact (stable list of the near
-// points), pxe_adj (the transpose's Gauss-rule pairs, one thread per pixel and chunk of near
-// points, the points through shared memory), pxe_bin_* and pxe_adj_window (its window pairs,
-// pixel-major over binned near points) and pxe_adj_reduce (the parts in order, into dL/dB0).
+// The exact rectangle integral is evaluated as one atan2 of the product of the four corner
+// factors z R + i a b (pixel_exact).
+//
+// Kernels.  Correction: pxe_window (FP64 window sums, one warp per point) and pxe_gauss (the other
+// pixels' FP32 Gauss sums, one CTA per near point, added to it), or pxe_exact in the FP64 form.
+// Transpose: pxe_compact (stable list of the near points); pxe_adj (the Gauss-rule pairs, one
+// thread per pixel and chunk of near points, the points through shared memory); pxe_bin_* and
+// pxe_adj_window (the window pairs, pixel-major over the near points binned by nearest pixel);
+// pxe_adj_reduce (the parts summed in order into dL/dB0).
 #include <type_traits>
 
 #include "kernels.h"
