@@ -181,3 +181,123 @@ def test_q9_argument_errors(dbie):
         dbie.solve_batched([f, g], [torch.from_numpy(xyz), torch.from_numpy(xyz)])
     f.close()
     g.close()
+
+
+def _q9_field(dbie, seed, n=24, g=3):
+    mag = random_mag(21, 19, seed)
+    rng = np.random.default_rng(seed + 1)
+    pts = np.stack([rng.uniform(5, 15, n), rng.uniform(5, 13, n), rng.uniform(1.0, 4.0, n)],
+                   1).astype(np.float32)
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_quadrature(g)
+    return mag, pts, f
+
+
+def test_q9_objective_gradient_and_hessian_are_consistent(dbie):
+    """Element rule, FP64 form: dPhi/dlambda of dbie_objective is the central difference of its
+    Phi, dbie_hessian's gradient equals it, and the Hessian is the central difference of the
+    gradient (the lambda-derivative sums over Gauss points)."""
+    mag, pts, f = _q9_field(dbie, 500)
+    rng = np.random.default_rng(502)
+    lam = rng.uniform(0.02, 0.2, (len(pts), 3))
+    opt = dbie.Options(precision=1)
+    P = torch.from_numpy(pts)
+
+    def obj(l):
+        r = f.objective(P, torch.from_numpy(l.astype(np.float32)), opt)
+        return r["phi"].cpu().numpy(), r["dphi"].cpu().numpy()
+
+    lam32 = lam.astype(np.float32).astype(np.float64)     # objective takes float32 lambda
+    phi, dphi = obj(lam32)
+    h = f.hessian(P, torch.from_numpy(lam32), opt)
+    torch.cuda.synchronize()
+    gh, H = h["grad"].cpu().numpy(), h["hess"].cpu().numpy()
+    assert np.allclose(h["phi"].cpu().numpy(), phi, rtol=1e-10, atol=1e-13)
+    assert np.abs(gh - dphi).max() <= 1e-9 * np.abs(dphi).max()
+    d = 2.0 ** -10                                          # exact in float32 around lambda
+    fd = np.zeros_like(dphi)
+    for q in range(3):
+        e = np.zeros(3)
+        e[q] = d
+        fd[:, q] = (obj(lam32 + e)[0] - obj(lam32 - e)[0]) / (2 * d)
+    # O(d^2) truncation of the differences: ~1e-6 of the gradient's scale
+    assert np.abs(fd - dphi).max() <= 1e-4 * np.abs(dphi).max(), np.abs(fd - dphi).max()
+    for q in range(3):
+        e = np.zeros(3)
+        e[q] = 1e-5
+        gp = f.hessian(P, torch.from_numpy(lam32 + e), opt)["grad"].cpu().numpy()
+        gm = f.hessian(P, torch.from_numpy(lam32 - e), opt)["grad"].cpu().numpy()
+        assert np.abs((gp - gm) / 2e-5 - H[:, :, q]).max() <= 1e-4 * np.abs(H).max()
+    f.close()
+
+
+def test_q9_quasi_newton_and_implicit_adjoint(dbie):
+    """Element rule, FP64 form: the quasi-Newton search lowers Phi from its start and returns B
+    equal to the oracle's element rule at its lambda.  At Newton-polished minima (the GPU's own
+    gradient and Hessian) the implicit adjoint equals the fixed-lambda adjoint minus
+    v . d(grad_lambda Phi)/dB0, with v the call's H^-1 dL/dlambda and the derivative of the
+    gradient (lambda held in FP64) by central differences in B0 (steps of 2^-4, exact in float32)."""
+    mag, pts, f = _q9_field(dbie, 510, n=48)
+    opt = dbie.Options(precision=1, method=1, max_iter=60, tol=1e-14)
+    P = torch.from_numpy(pts)
+    r = f.solve(P, opt)
+    torch.cuda.synchronize()
+    lam = r["lam"].cpu().numpy()
+    start = np.full_like(lam, 1.0 / (max(mag.nx, mag.ny) * mag.hx))
+    phi_end = f.objective(P, torch.from_numpy(lam.astype(np.float32)), dbie.Options(precision=1))
+    phi_start = f.objective(P, torch.from_numpy(start.astype(np.float32)), dbie.Options(precision=1))
+    torch.cuda.synchronize()
+    assert np.all(phi_end["phi"].cpu().numpy() <= phi_start["phi"].cpu().numpy() + 1e-12)
+    B, _, _ = oracle.field(oracle_boundary(mag), pts.astype(np.float64), lam, quad_order=3)
+    sB, _ = q9_abs_scales(mag, pts, lam, 3)
+    assert np.all(np.abs(r["B"].cpu().numpy() - B) <= TOL_FP64 * sB)
+
+    o1 = dbie.Options(precision=1)
+    ln = lam.copy()
+    for _ in range(30):
+        h = f.hessian(P, torch.from_numpy(ln), o1)
+        gr, H = h["grad"].cpu().numpy(), h["hess"].cpu().numpy()
+        ok = np.linalg.eigvalsh(H)[:, 0] > 0
+        Hs = np.where(ok[:, None, None], H, np.eye(3))
+        st = np.where(ok[:, None], np.linalg.solve(Hs, gr[:, :, None])[:, :, 0], 0.0)
+        ln -= st
+        if np.abs(st).max() < 1e-15:
+            break
+    h = f.hessian(P, torch.from_numpy(ln), o1)
+    gr, H = h["grad"].cpu().numpy(), h["hess"].cpu().numpy()
+    ev = np.linalg.eigvalsh(H)
+    good = (np.abs(gr).max(1) < 1e-10) & (ev[:, 0] > 0) & (ev[:, -1] < 1e3 * ev[:, 0])
+    assert good.sum() >= 4, good.sum()
+    Pg, lg = P[torch.from_numpy(np.nonzero(good)[0])], ln[good]
+    rng = np.random.default_rng(512)
+    gB = rng.normal(size=(len(lg), 3))
+    gB0, v, fl = f.vjp_implicit(Pg, torch.from_numpy(lg), torch.from_numpy(gB), options=o1)
+    gfix, _ = f.vjp(Pg, torch.from_numpy(lg), torch.from_numpy(gB), glam=False, options=o1)
+    torch.cuda.synchronize()
+    assert not fl.cpu().numpy().any()
+    gB0, v, gfix = gB0.cpu().numpy(), v.cpu().numpy(), gfix.cpu().numpy()
+    assert np.abs(gB0 - gfix).max() > 1e-2 * np.abs(gfix).max()   # the implicit term matters
+    comps = [np.array(c, np.float32) for c in (mag.Bx, mag.By, mag.Bz)]
+    g2 = dbie.DBIEField.from_magnetogram(mag)
+    g2.set_quadrature(3)
+
+    def grad_at(cs):
+        g2.set_boundary(*(torch.from_numpy(c).cuda() for c in cs))
+        return g2.hessian(Pg, torch.from_numpy(lg), o1)["grad"].cpu().numpy()
+
+    dd = 2.0 ** -4
+    top = np.argsort(np.abs(gB0 - gfix).ravel())[-3:]          # where the implicit term is largest
+    picks = [np.unravel_index(t, gB0.shape) for t in top]
+    picks += [(rng.integers(0, mag.ny), rng.integers(0, mag.nx), rng.integers(0, 3)) for _ in range(3)]
+    for j, i, p in picks:
+        cp = [c.copy() for c in comps]
+        cm = [c.copy() for c in comps]
+        cp[p][j, i] += dd
+        cm[p][j, i] -= dd
+        assert cp[p][j, i] - comps[p][j, i] == dd and comps[p][j, i] - cm[p][j, i] == dd
+        dgrad = (grad_at(cp) - grad_at(cm)) / (2 * dd)
+        ref = gfix[j, i, p] - np.sum(v * dgrad)
+        scale = np.abs(gfix[j, i, p]) + np.sum(np.abs(v * dgrad))
+        assert abs(gB0[j, i, p] - ref) <= 1e-6 * scale + 1e-13, (gB0[j, i, p], ref)
+    g2.close()
+    f.close()
