@@ -185,6 +185,7 @@ __device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, 
   const ProbDesc& pd = a.probs[pidx];
   const int64_t j = slot - pd.q_off;
   double S[12], G[9];
+#pragma unroll
   for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 12, s);
   assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
 }
@@ -219,65 +220,85 @@ __device__ __forceinline__ int atomic_add_warp(int* ctr, int v) {
   return base + prefix;
 }
 
-// Queue k trial points (lambda rows) of point g for the next round.
-__device__ void emit(const SolveArgs& a, int64_t g, const float4& pos, int pidx, int k,
-                     const double (*lam)[3]) {
+// Queue K trial points (lambda rows) of point g for the next round (K fixed at compile time, so
+// the rows stay in registers).
+template <int K>
+__device__ __forceinline__ void emit(const SolveArgs& a, int64_t g, const float4& pos, int pidx,
+                                     const double (*lam)[3]) {
   const ProbDesc& pd = a.probs[pidx];
-  const int base = atomic_add_warp(a.nxt.q_cnt + pidx, k);
+  const int base = atomic_add_warp(a.nxt.q_cnt + pidx, K);
   const int64_t slot0 = pd.q_off + base;
-  for (int j = 0; j < k; ++j) {
+#pragma unroll
+  for (int j = 0; j < K; ++j) {
     a.nxt.qpos[slot0 + j] = pos;
     if (a.o.dim == 1) a.nxt.qlam[slot0 + j] = make_lam4(lam[j][0], lam[j][0], lam[j][0]);
     else a.nxt.qlam[slot0 + j] = make_lam4(lam[j][0], lam[j][1], lam[j][2]);
   }
   if (a.o.near_on && (double)pos.z <= pd.near_z) {
-    const int nb = atomic_add_warp(a.nxt.near_cnt, k);
-    for (int j = 0; j < k; ++j) a.nxt.near[nb + j] = (int32_t)(slot0 + j);
+    const int nb = atomic_add_warp(a.nxt.near_cnt, K);
+#pragma unroll
+    for (int j = 0; j < K; ++j) a.nxt.near[nb + j] = (int32_t)(slot0 + j);
   }
   SI(a, I_QSLOT, g) = (int32_t)slot0;
   a.nxt.act[atomic_add_warp(a.nxt.act_cnt, 1)] = (int32_t)g;
 }
 
+// N: the number of free lambdas (3, or 1 when the components share one).
+template <int N>
 __global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ lam_init) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.N;
        g += (int64_t)gridDim.x * blockDim.x) {
     const float4 pos = a.ppos[g];
     const int pidx = __float_as_int(pos.w);
-    const int n = a.o.dim;
-    double lam[4][3];
+    constexpr int n = N;
+    double lam[N + 1][3];
+#pragma unroll
     for (int v = 0; v <= n; ++v)
+#pragma unroll
       for (int d = 0; d < 3; ++d) {
         const double l0 = lam_init ? lam_init[3 * g + d] : 0.0;
         lam[v][d] = (d < n) ? l0 + ((v == d + 1) ? a.probs[pidx].step : 0.0) : 0.0;
       }
+#pragma unroll
     for (int v = 0; v <= n; ++v)
+#pragma unroll
       for (int d = 0; d < 3; ++d) SD(a, D_VL + v * 3 + d, g) = lam[v][d];
     SI(a, I_STAGE, g) = ST_INIT;
     SI(a, I_ITERS, g) = 0;
     SI(a, I_NFEV, g) = 0;
     SI(a, I_STATUS, g) = PT_RUNNING;
-    emit(a, g, pos, pidx, n + 1, lam);
+    emit<N + 1>(a, g, pos, pidx, lam);
   }
 }
 
 void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s) {
-  solve_init_kernel<<<grid, 256, 0, s>>>(a, lam_init);
+  if (a.o.dim == 1) solve_init_kernel<1><<<grid, 256, 0, s>>>(a, lam_init);
+  else solve_init_kernel<3><<<grid, 256, 0, s>>>(a, lam_init);
 }
 
-// Stable insertion sort of the n+1 vertices by Phi (ties keep their order).
-__device__ __forceinline__ void sort_verts(Vert* v, int n) {
-  for (int i = 1; i <= n; ++i)
-    for (int j = i; j > 0 && v[j].phi < v[j - 1].phi; --j) {
-      const Vert t = v[j];
-      v[j] = v[j - 1];
-      v[j - 1] = t;
-    }
+// Stable insertion sort of the N+1 vertices by Phi (ties keep their order), unrolled into
+// adjacent compare-exchanges so the vertices stay in registers.  Without the early exit of the
+// textbook loop the result is the same: after inserting each vertex no adjacent pair of the
+// sorted prefix is out of order (v[j].phi < v[j-1].phi false), so the comparisons below the
+// insertion point never swap.
+template <int N>
+__device__ __forceinline__ void sort_verts(Vert* v) {
+#pragma unroll
+  for (int i = 1; i <= N; ++i)
+#pragma unroll
+    for (int j = i; j > 0; --j)
+      if (v[j].phi < v[j - 1].phi) {
+        const Vert t = v[j];
+        v[j] = v[j - 1];
+        v[j - 1] = t;
+      }
 }
 
+template <int N>
 __global__ void nm_step_kernel(const SolveArgs a) {
   const double rho = 1.0, chi = 2.0, psi = 0.5, sigma = 0.5;
   const int nact = *a.cur.act_cnt;
-  const int n = a.o.dim;
+  constexpr int n = N;
   const PlanHdr h = *a.plan;
   for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
     const int64_t g = a.cur.act[ia];
@@ -289,15 +310,18 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     int iters = SI(a, I_ITERS, g);
     int nfev = SI(a, I_NFEV, g);
 
-    Vert v[4];
+    Vert v[N + 1];
+#pragma unroll
     for (int k = 0; k <= n; ++k) load_vert(a, g, k, v[k]);
     bool to_check = false;  // an iteration (or the initialisation) completed: sort and test
     bool dirty = false;     // the vertices changed and must be stored back
     char code = 0;
 
     auto centroid = [&](double c[3]) {
+#pragma unroll
       for (int d = 0; d < n; ++d) {
         double s = 0.0;
+#pragma unroll
         for (int k = 0; k < n; ++k) s += v[k].l[d];
         c[d] = s / n;
       }
@@ -319,33 +343,53 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       double rows[1][3] = {{l[0], l[1], l[2]}};
       for (int d = 0; d < 3; ++d) SD(a, D_TL + d, g) = l[d];
       stage = st;
-      emit(a, g, pos, pidx, 1, rows);
+      emit<1>(a, g, pos, pidx, rows);
     };
     auto start_shrink = [&]() {
       dirty = true;
-      double rows[3][3];
+      double rows[N][3];
+#pragma unroll
       for (int k = 1; k <= n; ++k) {
         for (int d = 0; d < 3; ++d)
           v[k].l[d] = (d < n) ? v[0].l[d] + sigma * (v[k].l[d] - v[0].l[d]) : 0.0;
         for (int d = 0; d < 3; ++d) rows[k - 1][d] = v[k].l[d];
       }
       stage = ST_SHRINK;
-      emit(a, g, pos, pidx, n, rows);
+      emit<N>(a, g, pos, pidx, rows);
     };
 
-    if (stage == ST_INIT) {
-      for (int k = 0; k <= n; ++k) {
-        Eval e;
+    // The pending queries' objectives, evaluated at one site for every stage: a warp whose
+    // lanes are in different stages runs the FP64 objective once per query index instead of
+    // once per stage, and the kernel holds one copy of its code.  The initial simplex (n + 1
+    // queries into vertices 0..n) and a shrink (n queries into vertices 1..n) fill vertices by
+    // shifting each result in at the top (no run-time vertex index, so they stay in
+    // registers); the other stages read one trial point into e.
+    Eval e;
+    {
+      const int nev = stage == ST_INIT ? n + 1 : (stage == ST_SHRINK ? n : 1);
+      const int first = stage == ST_SHRINK ? 1 : 0;
+      const bool fill = stage == ST_INIT || stage == ST_SHRINK;
+#pragma unroll 1
+      for (int k = 0; k < nev; ++k) {
         read_eval(a, h, pidx, slot + k, z, e, g);
-        for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
-        v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
+        if (fill) {
+#pragma unroll
+          for (int m = 0; m < n; ++m)
+            if (m >= first) {
+              for (int p = 0; p < 3; ++p) v[m].B[p] = v[m + 1].B[p];
+              v[m].f = v[m + 1].f; v[m].g = v[m + 1].g; v[m].phi = v[m + 1].phi;
+            }
+          for (int p = 0; p < 3; ++p) v[n].B[p] = e.B[p];
+          v[n].f = e.f; v[n].g = e.g; v[n].phi = e.phi;
+        }
       }
+    }
+
+    if (stage == ST_INIT) {
       nfev += n + 1;
       to_check = true;
       dirty = true;
     } else if (stage == ST_REFLECT) {
-      Eval e;
-      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       double lr[3];
       for (int d = 0; d < 3; ++d) lr[d] = SD(a, D_TL + d, g);
@@ -371,8 +415,6 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         emit_one(xc, ST_ICONTRACT);
       }
     } else if (stage == ST_EXPAND) {
-      Eval e;
-      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       const double phr = SD(a, D_RPHI, g);
       double l[3];
@@ -390,8 +432,6 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       }
       to_check = true;
     } else if (stage == ST_OCONTRACT || stage == ST_ICONTRACT) {
-      Eval e;
-      read_eval(a, h, pidx, slot, z, e, g);
       nfev += 1;
       const bool ok = (stage == ST_OCONTRACT) ? (e.phi <= SD(a, D_RPHI, g)) : (e.phi < v[n].phi);
       if (ok) {
@@ -404,12 +444,6 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         start_shrink();
       }
     } else if (stage == ST_SHRINK) {
-      for (int k = 1; k <= n; ++k) {
-        Eval e;
-        read_eval(a, h, pidx, slot + (k - 1), z, e, g);
-        for (int p = 0; p < 3; ++p) v[k].B[p] = e.B[p];
-        v[k].f = e.f; v[k].g = e.g; v[k].phi = e.phi;
-      }
       nfev += n;
       code = 'S';
       to_check = true;
@@ -420,7 +454,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       a.codes[g * a.codes_stride + (iters - 1)] = code;
 
     if (to_check) {
-      sort_verts(v, n);
+      sort_verts<N>(v);
       int fin = -1;
       if (v[0].f <= a.o.eps_f && v[0].g <= a.o.eps_g) fin = PT_CONVERGED;
       else if (v[n].phi - v[0].phi <= a.o.tol) fin = PT_CONVERGED;
@@ -446,6 +480,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       }
     }
     if (dirty)
+#pragma unroll
       for (int k = 0; k <= n; ++k) store_vert(a, g, k, v[k]);
     SI(a, I_STAGE, g) = stage;
     SI(a, I_ITERS, g) = iters;
@@ -454,7 +489,8 @@ __global__ void nm_step_kernel(const SolveArgs a) {
 }
 
 void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s) {
-  nm_step_kernel<<<grid, 128, 0, s>>>(a);
+  if (a.o.dim == 1) nm_step_kernel<1><<<grid, 128, 0, s>>>(a);
+  else nm_step_kernel<3><<<grid, 128, 0, s>>>(a);
 }
 
 // --------------------------------------------------------------- per-round plan ----
@@ -584,6 +620,7 @@ __global__ void finalize_objective_kernel(int64_t n, const PlanHdr* __restrict__
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     double S[21];
+#pragma unroll
     for (int s = 0; s < 21; ++s) S[s] = gather_sum(out, h, item_off, 0, i, 21, s);
     const Lam4 l = qlam[i];
     const double lam[3] = {l.x, l.y, l.z};
@@ -633,7 +670,7 @@ __global__ void bfgs_init_kernel(const SolveArgs a, const double* __restrict__ l
     SI(a, I_ITERS, g) = 0;
     SI(a, I_NFEV, g) = 0;
     SI(a, I_STATUS, g) = PT_RUNNING;
-    emit(a, g, pos, pidx, 1, x);
+    emit<1>(a, g, pos, pidx, x);
   }
 }
 
@@ -641,9 +678,12 @@ void launch_bfgs_init(const SolveArgs& a, const double* lam_init, int grid, cuda
   bfgs_init_kernel<<<grid, 256, 0, s>>>(a, lam_init);
 }
 
+// N: the number of free lambdas (3, or 1 when the components share one); fixed at compile time
+// so the per-point state stays in registers.
+template <int N>
 __global__ void bfgs_step_kernel(const SolveArgs a) {
   const int nact = *a.cur.act_cnt;
-  const int n = a.o.dim;
+  constexpr int n = N;
   const PlanHdr h = *a.plan;
   for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
     const int64_t g = a.cur.act[ia];
@@ -675,6 +715,7 @@ __global__ void bfgs_step_kernel(const SolveArgs a) {
     const double lamt[3] = {xt[0], n == 1 ? xt[0] : xt[1], n == 1 ? xt[0] : xt[2]};
     double S[21];
     const int64_t j = (int64_t)SI(a, I_QSLOT, g) - pd.q_off;
+#pragma unroll
     for (int s = 0; s < 21; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 21, s);
     Eval e;
     double dp[3], gt[3] = {0, 0, 0};
@@ -737,7 +778,7 @@ __global__ void bfgs_step_kernel(const SolveArgs a) {
         for (int i = 0; i < n; ++i) row[0][i] = x[i] + alpha * dv[i];
         SD(a, B_ALPHA, g) = alpha;
         SI(a, I_NFEV, g) = nfev;
-        emit(a, g, pos, pidx, 1, row);
+        emit<1>(a, g, pos, pidx, row);
         continue;
       }
     }
@@ -762,7 +803,7 @@ __global__ void bfgs_step_kernel(const SolveArgs a) {
         alpha = 1.0;
         double row[1][3] = {{0, 0, 0}};
         for (int i = 0; i < n; ++i) row[0][i] = x[i] + alpha * dv[i];
-        emit(a, g, pos, pidx, 1, row);
+        emit<1>(a, g, pos, pidx, row);
       }
     }
     if (fin >= 0) {
@@ -797,7 +838,8 @@ __global__ void bfgs_step_kernel(const SolveArgs a) {
 }
 
 void launch_bfgs_step(const SolveArgs& a, int grid, cudaStream_t s) {
-  bfgs_step_kernel<<<grid, 128, 0, s>>>(a);
+  if (a.o.dim == 1) bfgs_step_kernel<1><<<grid, 128, 0, s>>>(a);
+  else bfgs_step_kernel<3><<<grid, 128, 0, s>>>(a);
 }
 
 }  // namespace dbie
