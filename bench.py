@@ -357,7 +357,11 @@ def fp64_compare(w, npts, dev):
                                                 "p99": float(np.percentile(rel, 99)),
                                                 "max": float(rel.max())},
             "same_step_sequence_frac": float(same.mean()),
-            "lambda_rel_err_where_same": float(lam_rel[same].max()) if same.any() else None}
+            "lambda_rel_err_where_same": ({
+                "median": float(np.median(lam_rel[same])),
+                "p99": float(np.percentile(lam_rel[same], 99)),
+                "max": float(lam_rel[same].max()),
+                "frac_le_1e-4": float((lam_rel[same] <= 1e-4).mean())} if same.any() else None)}
 
 
 def method_compare(w, dev):
