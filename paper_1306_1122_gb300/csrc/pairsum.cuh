@@ -665,15 +665,29 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
       pxl[u] = SPLIT ? *tile_field(btiles, k, 5, NF) : Real(0);
       pyl[u] = SPLIT ? *tile_field(btiles, k, 6, NF) : Real(0);
     }
-    Real acc[P][3];
-    float hi[F32 ? P : 1][3];
+    // FP64 form: one accumulator per pixel and component.  FP32 form: two points per f32x2
+    // (adjacent in shared memory, so one 64-bit load fetches a field of both), the thread's
+    // pixels in both lanes; each lane accumulates every second point and the lanes are added at
+    // the end.
+    Real acc[F32 ? 1 : P][3];
+    f32x2 acc2[F32 ? P : 1][3], hi2[F32 ? P : 1][3];
+    f32x2 px2[F32 ? P : 1], py2[F32 ? P : 1], pxl2[F32 ? P : 1], pyl2[F32 ? P : 1];
+    if constexpr (F32) {
 #pragma unroll
-    for (int u = 0; u < P; ++u)
+      for (int u = 0; u < P; ++u) {
+        px2[u] = pack2(px[u], px[u]);
+        py2[u] = pack2(py[u], py[u]);
+        pxl2[u] = pack2(pxl[u], pxl[u]);
+        pyl2[u] = pack2(pyl[u], pyl[u]);
 #pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        acc[u][p] = Real(0);
-        if constexpr (F32) hi[u][p] = 0.f;
+        for (int p = 0; p < 3; ++p) acc2[u][p] = hi2[u][p] = vconst<f32x2>(0.f);
       }
+    } else {
+#pragma unroll
+      for (int u = 0; u < P; ++u)
+#pragma unroll
+        for (int p = 0; p < 3; ++p) acc[u][p] = Real(0);
+    }
 
     sweep_tiles(ring, ptiles, t0, t1, tid, [&](const Real* sx) {
       const Real* X = sx;
@@ -682,55 +696,57 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
       const Real* L = sx + 3 * TILE;
       const Real* W = sx + 6 * TILE;
       if constexpr (F32) {
+        auto ld2 = [](const Real* q) { return *reinterpret_cast<const f32x2*>(q); };
 #pragma unroll 1
         for (int k0 = 0; k0 < TILE; k0 += SUB1) {
-#pragma unroll 2
-          for (int k = k0; k < k0 + SUB1; ++k) {
-            const float xi = X[k], yi = Y[k], z2 = Z2[k];
-            float lam[NL], lam2[NL];
+#pragma unroll 1
+          for (int k = k0; k < k0 + SUB1; k += 2) {
+            const f32x2 xi = ld2(X + k), yi = ld2(Y + k), z2 = ld2(Z2 + k);
+            f32x2 lam[NL], lam2[NL];
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
-              lam[l] = L[l * TILE + k];
-              lam2[l] = __fmul_rn(lam[l], lam[l]);
+              lam[l] = ld2(L + l * TILE + k);
+              lam2[l] = vmul(lam[l], lam[l]);
             }
 #pragma unroll
             for (int u = 0; u < P; ++u) {
-              float dx = __fsub_rn(xi, px[u]), dy = __fsub_rn(yi, py[u]);
+              f32x2 dx = vsub(xi, px2[u]), dy = vsub(yi, py2[u]);
               if constexpr (SPLIT) {
-                dx = __fsub_rn(dx, pxl[u]);
-                dy = __fsub_rn(dy, pyl[u]);
+                dx = vsub(dx, pxl2[u]);
+                dy = vsub(dy, pyl2[u]);
               }
-              const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, z2));
-              const float ri = rsqrt_mufu(r2);
-              const float r = __fmul_rn(r2, ri);
-              const float ri2 = __fmul_rn(ri, ri);
-              const float ri3 = __fmul_rn(ri2, ri);
-              const float ri2x3 = __fmul_rn(3.f, ri2);
-              float ph[NL], ps[NL], cr[NL];
+              const f32x2 r2 = vfma(dx, dx, vfma(dy, dy, z2));
+              const f32x2 ri = vrsqrt(r2);
+              const f32x2 r = vmul(r2, ri);
+              const f32x2 ri2 = vmul(ri, ri);
+              const f32x2 ri3 = vmul(ri2, ri);
+              const f32x2 m3ri2 = vmul(vconst<f32x2>(-3.f), ri2);
+              f32x2 ph[NL], ps[NL], cr[NL];
 #pragma unroll
               for (int l = 0; l < NL; ++l) {
-                const float th = __fmul_rn(lam[l], r);
-                const float sn = sin_mufu(th), c = cos_mufu(th);
-                const float uu = __fmaf_rn(th, sn, c);
-                ph[l] = __fmul_rn(uu, ri3);
-                ps[l] = __fmul_rn(__fmaf_rn(-uu, ri2x3, __fmul_rn(lam2[l], c)), ri3);
-                cr[l] = __fmul_rn(c, ri);
+                const f32x2 th = vmul(lam[l], r);
+                const f32x2 sn = vsin(th), c = vcos(th);
+                const f32x2 uu = vfma(th, sn, c);
+                ph[l] = vmul(uu, ri3);
+                ps[l] = vmul(vfma(uu, m3ri2, vmul(lam2[l], c)), ri3);
+                cr[l] = vmul(c, ri);
               }
 #pragma unroll
               for (int p = 0; p < 3; ++p) {
                 const int l = TIED ? 0 : p;
-                const float* w = W + p * VJP7_NW * TILE + k;
-                const float aph = __fmaf_rn(w[6 * TILE], dy, __fmaf_rn(w[5 * TILE], dx, w[0]));
-                const float aps = __fmaf_rn(w[3 * TILE], dy, __fmaf_rn(w[2 * TILE], dx, w[TILE]));
-                acc[u][p] = __fmaf_rn(ph[l], aph,
-                                      __fmaf_rn(ps[l], aps, __fmaf_rn(w[4 * TILE], cr[l], acc[u][p])));
+                const Real* w = W + p * VJP7_NW * TILE + k;
+                const f32x2 aph = vfma(ld2(w + 6 * TILE), dy, vfma(ld2(w + 5 * TILE), dx, ld2(w)));
+                const f32x2 aps =
+                    vfma(ld2(w + 3 * TILE), dy, vfma(ld2(w + 2 * TILE), dx, ld2(w + TILE)));
+                acc2[u][p] = vfma(ph[l], aph,
+                                  vfma(ps[l], aps, vfma(ld2(w + 4 * TILE), cr[l], acc2[u][p])));
               }
             }
           }
 #pragma unroll
           for (int u = 0; u < P; ++u)
 #pragma unroll
-            for (int p = 0; p < 3; ++p) fold2(hi[u][p], acc[u][p]);
+            for (int p = 0; p < 3; ++p) fold2(hi2[u][p], acc2[u][p]);
         }
       } else {
 #pragma unroll 1
@@ -775,8 +791,14 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
         double v;
-        if constexpr (F32) v = (double)hi[u][p] + (double)acc[u][p];
-        else v = (double)acc[u][p];
+        if constexpr (F32) {
+          float h0, h1, a0, a1;
+          unpack2(hi2[u][p], h0, h1);
+          unpack2(acc2[u][p], a0, a1);
+          v = (((double)h0 + (double)a0) + (double)h1) + (double)a1;
+        } else {
+          v = (double)acc[u][p];
+        }
         a.out[((int64_t)it * 3 + p) * Q + (tid + u * NT)] = v;
       }
     }

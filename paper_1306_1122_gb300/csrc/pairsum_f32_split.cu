@@ -33,9 +33,9 @@ KernelRef vjp_ref_split(bool tied) {
 }
 
 KernelRef vjp7_ref_split(bool tied) {
-  const void* fn = tied ? (const void*)&vjp7_kernel<float, true, 4, 256, NSTAGE, true>
-                        : (const void*)&vjp7_kernel<float, false, 4, 256, NSTAGE, true>;
-  return KernelRef{fn, 256, 1024, (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(float)};
+  const void* fn = tied ? (const void*)&vjp7_kernel<float, true, 2, 256, NSTAGE, true>
+                        : (const void*)&vjp7_kernel<float, false, 2, 256, NSTAGE, true>;
+  return KernelRef{fn, 256, 512, (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(float)};
 }
 
 }  // namespace dbie

@@ -27,11 +27,13 @@ KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
 }
 
 // The seven-weight adjoint (gradient through the lambda search) runs once per call, after a
-// Hessian pass; one launch shape: 256 threads, four pixels per thread, so that each 27-field
-// point record read from shared memory serves four pairs.
+// Hessian pass; one launch shape: 256 threads.  FP32: two pixels per thread, each 64-bit read of
+// the 27-field point records (two points) serving four pairs, at 123 registers (two CTAs per
+// SM; four pixels would need 170).  FP64: four pixels per thread.
 template <typename Real, bool TIED>
 KernelRef vjp7_ref_t() {
-  return KernelRef{(const void*)&vjp7_kernel<Real, TIED, 4, 256, NSTAGE>, 256, 1024,
+  constexpr int P = sizeof(Real) == 4 ? 2 : 4;
+  return KernelRef{(const void*)&vjp7_kernel<Real, TIED, P, 256, NSTAGE>, 256, P * 256,
                    (size_t)NSTAGE * VJP7_NFIELD * TILE * sizeof(Real)};
 }
 
