@@ -17,7 +17,7 @@ import pytest
 from scipy.integrate import quad
 
 import oracle
-from test_oracle_pins import square_integral, uniform_square
+from test_oracle_pins import uniform_square
 
 
 def _cos_mode(k, A):
