@@ -65,10 +65,25 @@ def test_argument_errors_are_reported_on_host(native):
         lambda: lib.dbie_vjp(None, 1, p, p, p, None, 0, p, None, 0, None),
         lambda: lib.dbie_solve_batched(0, None, None, None, None, None, 0, None, None),
         lambda: lib.dbie_set_profiling(None, 1),
+        lambda: lib.dbie_set_boundary(None, p, p, p, 0, None),
+        lambda: lib.dbie_set_quadrature(None, 0, None),
+        lambda: lib.dbie_objective(None, 1, p, p, None, 0, p, None, None),
+        lambda: lib.dbie_hessian(None, 1, p, p, None, 0, p, None, None, None),
+        lambda: lib.dbie_vjp_implicit(None, 1, p, p, p, None, 0, p, None, None, 0, None),
+        lambda: lib.dbie_noise_var(None, 1, p, p, None, None, None, 1.0, None, 0, p, None),
+        lambda: lib.dbie_autotune(None, None),
+        lambda: lib.dbie_get_config(None, p),
+        lambda: lib.dbie_set_config(None, p),
+        lambda: lib.dbie_get_stats(None, None, 0),
     ]
     for call in bad_calls:
         assert call() == native.DBIE_EINVAL
         assert native.dbie_last_error() != ""
+    # the no-allocation entry point checks its sizes on the host too (its message goes to stderr)
+    assert lib.dbie_eval_noalloc(0, 4, 0.0, 0.0, 1.0, 1.0, 1.0, p, p, p, 1, p, p, p,
+                                 None) == native.DBIE_EINVAL
+    assert lib.dbie_eval_noalloc(256, 257, 0.0, 0.0, 1.0, 1.0, 1.0, p, p, p, 1, p, p, p,
+                                 None) == native.DBIE_EINVAL
     lib.dbie_destroy(None)  # no-op
 
 
