@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the batch64, ar512 and ar1024 blocks of the default line")
     ap.add_argument("--fp64-points", type=int, default=8192)
     ap.add_argument("--workload", default="ll128", choices=["ll128", "batch64"])
     ap.add_argument("--max-points", type=int, default=200_000,
@@ -311,6 +313,10 @@ def run_ours(args):
         line["quasi_newton"] = method_compare(w, dev)
         line["backward_through_search"] = backward_compare(w, dev)
         line["quadrature_rules"] = quadrature_compare(w, dev)
+        if not args.no_large:
+            line["batch64"] = batch64_block(dev)
+            line["ar512"] = ar512_block(dev)
+            line["ar1024"] = ar1024_block(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     if world > 1:
@@ -349,6 +355,7 @@ def fp64_compare(w, npts, dev):
     lam_rel = ((rm["lam"] - rd["lam"]).abs() /
                torch.clamp(rd["lam"].abs(), min=1.0 / (w.mag.nx * w.mag.hx))).max(dim=1).values
     lam_rel = lam_rel.cpu().numpy()
+    b_stats = b_error_stats(f, w.mag, w.points[idx], rm["lam"].cpu().numpy(), dev)
     f.close()
     return {"points": int(len(idx)), "mixed_s": tm, "fp64_s": td, "speedup": td / tm,
             "mixed_iters_mean": float(rm["iters"].float().mean()),
@@ -356,6 +363,7 @@ def fp64_compare(w, npts, dev):
             "B_rel_err_vs_fp64_at_own_lambda": {"median": float(np.median(rel)),
                                                 "p99": float(np.percentile(rel, 99)),
                                                 "max": float(rel.max())},
+            "B_vs_fp64_at_mixed_lambda": b_stats,
             "same_step_sequence_frac": float(same.mean()),
             "lambda_rel_err_where_same": ({
                 "median": float(np.median(lam_rel[same])),
@@ -486,6 +494,231 @@ def quadrature_compare(w, dev):
                      "E_n_z_le_2_at_pixel_centre_lambda": e_same}
         f.close()
     return out
+
+
+# ------------------------------------------------------------- larger workloads ----
+def abs_sum_scale(mag, pts, lam, dev, chunk=128):
+    """S_i = | (sum_k |a_ik(lambda_p)| |B0_p,k|)_p |: the absolute-value sum of each point's
+    quadrature (the scale below which B is dominated by cancellation); FP32 torch, measurement
+    only."""
+    import torch
+    jj, ii = np.mgrid[0:mag.ny, 0:mag.nx]
+    px = torch.from_numpy((mag.x0 + ii * mag.hx).ravel().astype(np.float32)).to(dev)
+    py = torch.from_numpy((mag.y0 + jj * mag.hy).ravel().astype(np.float32)).to(dev)
+    b = [torch.from_numpy(np.abs(c).ravel().astype(np.float32)).to(dev) * (mag.dA / (2 * np.pi))
+         for c in (mag.Bx, mag.By, mag.Bz)]
+    P = torch.as_tensor(pts, dtype=torch.float32).to(dev)
+    L = torch.as_tensor(lam, dtype=torch.float32).to(dev).abs()
+    out = torch.empty(len(P), 3, dtype=torch.float64, device=dev)
+    for a in range(0, len(P), chunk):
+        p = P[a:a + chunk]
+        r = torch.sqrt((p[:, 0:1] - px) ** 2 + (p[:, 1:2] - py) ** 2 + p[:, 2:3] ** 2)
+        for c in range(3):
+            th = L[a:a + chunk, c:c + 1] * r
+            u = (th * torch.sin(th) + torch.cos(th)).abs()
+            out[a:a + chunk, c] = (p[:, 2:3] * u / r ** 3 * b[c]).sum(1).double()
+    return out.norm(dim=1).cpu().numpy()
+
+
+def b_error_stats(field, mag, pts, lam, dev):
+    """Mixed B against the FP64 GPU form at the same lambda (float32) on a point sample: relative
+    error distribution, the fraction above 1e-5, and that fraction split at S_i = 10 |B_i|
+    (S_i the absolute-value sum: above it the sum is dominated by cancellation)."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    P = torch.as_tensor(pts).to(dev)
+    Lm = torch.as_tensor(lam).to(dev, torch.float32)
+    Bm = field.eval(P, Lm)["B"]
+    Bd = field.eval(P, Lm, options=dbie.Options(precision=1))["B"]
+    nB = Bd.norm(dim=1)
+    rel = ((Bm - Bd).norm(dim=1) / nB).cpu().numpy()
+    S = abs_sum_scale(mag, pts, lam, dev)
+    canc = S > 10 * nB.cpu().numpy()
+    big = rel > 1e-5
+    return {"points": int(len(rel)), "median": float(np.median(rel)),
+            "p99": float(np.percentile(rel, 99)), "max": float(rel.max()),
+            "frac_gt_1e-5": float(big.mean()),
+            "frac_cancellation_dominated": float(canc.mean()),
+            "frac_gt_1e-5_where_S_le_10B": float(big[~canc].mean()) if (~canc).any() else 0.0,
+            "max_where_S_le_10B": float(rel[~canc].max()) if (~canc).any() else 0.0,
+            "max_err_over_S": float(((Bm - Bd).norm(dim=1).cpu().numpy() / S).max())}
+
+
+def batch64_block(dev, sub_per_problem=128):
+    """Config 4 in the default line: 64 magnetograms (sides 32..256), 1k..200k points each, one
+    full mixed-precision simplex solve of all 6.35 M points through the batched persistent path
+    (timed once after a warm-up solve of a subsample), the objective kernel's MUFU roofline from
+    CUDA events inside the solve's graphs, the per-problem iteration histogram; then the batched
+    mixed and batched FP64 forms on the same stated subsample (sub_per_problem points of every
+    problem), and the mixed B error against the FP64 form on that subsample."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    probs = workloads.batch64()
+    fields = [dbie.DBIEField.from_magnetogram(w.mag, device=dev) for w in probs]
+    fields[0].autotune()
+    pts = [torch.from_numpy(w.points).to(dev) for w in probs]
+    rng = np.random.default_rng(64)
+    sub = [np.sort(rng.choice(len(w.points), min(sub_per_problem, len(w.points)), replace=False))
+           for w in probs]
+    sub_pts = [p[torch.from_numpy(i).to(dev)] for p, i in zip(pts, sub)]
+    dbie.solve_batched(fields, sub_pts)                 # warm: kernels, buffers
+    torch.cuda.synchronize()
+    fields[0].set_profiling(True)
+    fields[0].stats(reset=True)
+    t0 = time.perf_counter()
+    outs = dbie.solve_batched(fields, pts)
+    torch.cuda.synchronize()
+    t_full = time.perf_counter() - t0
+    st = fields[0].stats(reset=True)
+    fields[0].set_profiling(False)
+    nfev = [int(o["nfev"].sum()) for o in outs]
+    pairs = float(sum(nf * w.mag.npix for nf, w in zip(nfev, probs)))
+    iters = torch.cat([o["iters"] for o in outs]).cpu().numpy()
+    hist = np.bincount(np.minimum(iters, 50), minlength=51)
+    mufu = st["objective_pairs"] * 7 / (st["objective_ms"] / 1e3) / 1e12 if st["objective_ms"] else None
+    peak = SMS * MUFU_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12
+    sub_t = {}
+    for name, prec in (("mixed", 0), ("fp64", 1)):
+        opt = dbie.Options(precision=prec)
+        dbie.solve_batched(fields, [q[:8] for q in sub_pts], opt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = dbie.solve_batched(fields, sub_pts, opt)
+        torch.cuda.synchronize()
+        sub_t[name] = (time.perf_counter() - t0, r)
+    errs = [b_error_stats(f, w.mag, w.points[i], o["lam"].cpu().numpy()[i], dev)
+            for f, w, i, o in zip(fields[:8], probs[:8], sub, outs[:8])]
+    for f in fields:
+        f.close()
+    n_sub = int(sum(len(i) for i in sub))
+    return {"workload": "batch64: 64 magnetograms, sides U{32..256}, 1-4 patches, 1k..200k "
+                        "points each, z in [1, 64] (seed 4)",
+            "points": int(sum(len(w.points) for w in probs)),
+            "solve_s": t_full, "pair_evals": pairs, "pair_evals_per_s": pairs / t_full,
+            "roofline": {"bound": "alu", "kernel": "g1_kernel objective (batched)",
+                         "achieved": mufu, "peak": peak, "unit": "T MUFU-op/s",
+                         "frac": mufu / peak if mufu else None,
+                         "kernel_s": st["objective_ms"] / 1e3},
+            "iters_hist": hist.tolist(), "iters_mean": float(iters.mean()),
+            "subsample": {"points": n_sub, "per_problem": sub_per_problem,
+                          "mixed_s": sub_t["mixed"][0], "fp64_s": sub_t["fp64"][0],
+                          "speedup_mixed_over_fp64": sub_t["fp64"][0] / sub_t["mixed"][0]},
+            "B_vs_fp64_first8_problems": {
+                k: (max(e[k] for e in errs) if k.startswith("max") else
+                    float(np.mean([e[k] for e in errs]))) for k in errs[0]}}
+
+
+def ar512_block(dev, max_iter=10, sub=8192):
+    """Config 3: the 512 x 256 active region, 2,097,152 points (256 x 128 x 64 volume); a short
+    simplex search (max_iter stated) over the whole volume, then the backward pass over the 32^3
+    sub-volume at the searched lambda: dB/dlambda (fused pass) and dL/dB0, dL/dlambda for
+    L = sum |B|^2 (fixed-lambda adjoint), and the gradient through the search (implicit adjoint);
+    the mixed B error against the FP64 form on a point sample."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ar512()
+    f = dbie.DBIEField.from_magnetogram(w.mag, device=dev)
+    f.autotune()
+    pts = torch.from_numpy(w.points).to(dev)
+    opt = dbie.Options(max_iter=max_iter)
+    f.solve(pts[:4096], opt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = f.solve(pts, opt)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    pairs = float(r["nfev"].sum()) * w.mag.npix
+    sv = torch.from_numpy(workloads.ar512_backward_subvolume(w)).to(dev)
+    xs, lam = pts[sv], r["lam"][sv]
+    gB = 2.0 * r["B"][sv]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+    t_dl = timed(lambda: f.eval(xs, lam.float(), dlam=True))
+    t_vjp = timed(lambda: f.vjp(xs, lam, gB))
+    t_impl = timed(lambda: f.vjp_implicit(xs, lam, gB))
+    idx = np.sort(np.random.default_rng(512).choice(len(w.points), sub, replace=False))
+    err = b_error_stats(f, w.mag, w.points[idx], r["lam"].cpu().numpy()[idx], dev)
+    f.close()
+    nsv = len(sv)
+    return {"workload": "ar512: 512x256 active region (seed 1306), 256x128x64 points (2097152); "
+                        "backward over the 32^3 sub-volume",
+            "search": {"max_iter": max_iter, "solve_s": t_solve, "pair_evals": pairs,
+                       "pair_evals_per_s": pairs / t_solve,
+                       "iters_mean": float(r["iters"].float().mean())},
+            "backward_subvolume": {"points": nsv, "dBdlambda_ms": t_dl, "fixed_lambda_adjoint_ms": t_vjp,
+                                   "implicit_adjoint_ms": t_impl,
+                                   "adjoint_pair_evals_per_s": nsv * w.mag.npix / (t_vjp / 1e3)},
+            "B_vs_fp64": err}
+
+
+def ar1024_block(dev, sub=20000, oracle_points=48):
+    """Config 5: 1024 x 512 active region (seed 5), 6,291,456 points (4,194,304 field-line samples
+    + the 128^3 grid).  Forward (B and dB/dlambda, one fused pass) and the fixed-lambda adjoint
+    dL/dB0 for L = sum |B|^2, at a seeded per-point lambda ~ U[0, 0.05]^3 (stated: no search at
+    this size), with the value kernel's MUFU roofline from CUDA events; the mixed B error against
+    the FP64 GPU form on a 20k-point sample, and against the FP64 CPU oracle on a smaller one."""
+    import torch
+
+    import oracle
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ar1024()
+    m = w.mag
+    f = dbie.DBIEField.from_magnetogram(m, device=dev)
+    f.autotune()
+    n = len(w.points)
+    pts = torch.from_numpy(w.points).to(dev)
+    lam = torch.from_numpy(np.random.default_rng(1024).uniform(0, 0.05, (n, 3)).astype(np.float32)).to(dev)
+    f.eval(pts[:65536], lam[:65536], dlam=True)
+    torch.cuda.synchronize()
+    f.set_profiling(True)
+    f.stats(reset=True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    r = f.eval(pts, lam, dlam=True)
+    e[1].record()
+    f.vjp(pts, lam.double(), 2.0 * r["B"], glam=False)
+    e[2].record()
+    torch.cuda.synchronize()
+    st = f.stats(reset=True)
+    f.set_profiling(False)
+    t_fwd, t_bwd = e[0].elapsed_time(e[1]) / 1e3, e[1].elapsed_time(e[2]) / 1e3
+    pairs = float(n) * m.npix
+    mufu = st["pair_evals"] * 7 / (st["kernel_ms"] / 1e3) / 1e12 if st["kernel_ms"] else None
+    peak = SMS * MUFU_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(n, sub, replace=False))
+    lam_np = lam.cpu().numpy()
+    err = b_error_stats(f, m, w.points[idx], lam_np[idx], dev)
+    oi = idx[:oracle_points]
+    bd = oracle.Boundary(oracle.Grid(m.nx, m.ny, m.x0, m.y0, m.hx, m.hy, m.dA), m.Bx, m.By, m.Bz)
+    Bo, _, _ = oracle.field(bd, w.points[oi].astype(np.float64), lam_np[oi].astype(np.float64))
+    Bg = r["B"][torch.from_numpy(oi).to(dev)].cpu().numpy()
+    orel = np.linalg.norm(Bg - Bo, axis=1) / np.linalg.norm(Bo, axis=1)
+    f.close()
+    return {"workload": "ar1024: 1024x512 active region (seed 5), 4194304 field-line samples + "
+                        "128^3 grid (6291456 points), lambda ~ U[0, 0.05]^3 seeded",
+            "points": n, "pixels": int(m.npix), "pairs_per_pass": pairs,
+            "forward_s": t_fwd, "forward_pair_evals_per_s": pairs / t_fwd,
+            "adjoint_s": t_bwd, "adjoint_pair_evals_per_s": pairs / t_bwd,
+            "roofline_forward_kernel": {"bound": "alu", "achieved": mufu, "peak": peak,
+                                        "unit": "T MUFU-op/s", "frac": mufu / peak if mufu else None},
+            "B_vs_fp64": err,
+            "B_vs_oracle": {"points": int(len(oi)), "max_rel": float(orel.max()),
+                            "median_rel": float(np.median(orel))}}
 
 
 # --------------------------------------------------------------------- oracle (CPU) ----

@@ -240,7 +240,7 @@ dbie_status dbie_noise_var(dbie_ctx* ctx, int64_t n, const float* xyz, const dou
  * memory pool or arena, real-time loops that cannot take an allocation's implicit device
  * synchronisation, plugin hosts that forbid allocations by third-party libraries).
  *   Computes B (n, 3) float64 as dbie_eval does with opt = NULL (mixed precision, FP64 near field
- *   for z <= 2 hx; the pixel-centre rule of Eq. 16 only), for the magnetogram (nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz: device
+ *   for z <= 2 hx; pixel-centre quadrature only), for the magnetogram (nx, ny, x0, y0, hx, hy, pixel_area, Bx, By, Bz: device
  *   float32, row-major (ny, nx)) at the points xyz (n, 3) device float32 with lambda (n, 3)
  *   device float32.  No context is needed.  All pointers are device memory.
  *   Limits: nx * ny <= 65536 and n <= 65536; larger sizes return DBIE_EINVAL.

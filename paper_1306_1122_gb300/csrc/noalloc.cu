@@ -54,7 +54,17 @@ constexpr size_t kOffQpos = kOffT64 + align256(sizeof(double) * NFIELD * TILE * 
 constexpr size_t kOffQlam = kOffQpos + align256(sizeof(float4) * kMaxPoints);
 constexpr size_t kOffNear = kOffQlam + align256(sizeof(Lam4) * kMaxPoints);
 constexpr size_t kOffOut = kOffNear + align256(sizeof(int32_t) * kMaxPoints);
+// Largest queries-per-CTA over the launch configurations (the call uses configuration 0).
+constexpr int64_t max_qper() {
+  int64_t m = 0;
+  for (int c = 0; c < NCFG; ++c) m = std::max<int64_t>(m, (int64_t)cfg_of(c).p * cfg_of(c).nt);
+  return m;
+}
+// The output region must hold at least one split of the largest call (3 sums per query, the
+// query count rounded up to whole CTAs); with less, nsplit would be forced below 1.
 static_assert(kOffOut < kScratchBytes, "scratch layout does not fit");
+static_assert(kScratchBytes - kOffOut >= sizeof(double) * 3 * (kMaxPoints + max_qper()),
+              "scratch output region cannot hold one split of the largest call");
 
 thread_local std::string t_err;
 std::mutex g_mu;
@@ -124,6 +134,7 @@ extern "C" dbie_status dbie_eval_noalloc(int32_t nx, int32_t ny, double x0, doub
   const int ntiles = (int)((npix + TILE - 1) / TILE);
   const int64_t nblk = (n + k.qper - 1) / k.qper;
   const int64_t max_items = (int64_t)((kScratchBytes - kOffOut) / (sizeof(double) * 3 * k.qper));
+  if (nblk > max_items) return err(DBIE_EINTERNAL, "scratch output region too small for this call");
   int64_t nsplit = 1;
   const int64_t target = 2LL * grid;
   if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, ntiles);

@@ -133,3 +133,60 @@ def test_solve_edge_cases(dbie, small):
                         oracle.Options(max_iter=5), lam0=np.array([[0.05, -0.02, 0.01]]))
     assert np.allclose(r1["lam"].cpu().numpy(), ref1["lam"], rtol=1e-9, atol=1e-12)
     f.close()
+
+
+def _uneven_batch():
+    """Five magnetograms of uneven size (square and not, sides not multiples of 4) with uneven
+    seeded point counts and heights, as a stand-in for the batched workload at oracle-sized
+    scale."""
+    rng = np.random.default_rng(21)
+    mags, pts = [], []
+    for k, (nx, ny, m) in enumerate([(32, 32, 200), (48, 40, 150), (75, 75, 120), (96, 96, 90),
+                                     (57, 33, 80)]):
+        mag = workloads.active_region(nx, ny, 1 + k % 3, seed=300 + k, peak=(500, 2000),
+                                      sigma=(3, max(3.0, nx / 8)))
+        mags.append(mag)
+        pts.append(np.stack([rng.uniform(0, nx - 1, m), rng.uniform(0, ny - 1, m),
+                             rng.uniform(1, 24, m)], 1).astype(np.float32))
+    return mags, pts
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_batched_against_oracle(dbie, precision):
+    """dbie_solve_batched over five uneven problems against the FP64 oracle's per-problem solve.
+    FP64 form: the oracle's exact step sequence on >= 99 % of all points (>= 95 % per problem),
+    and there lambda, iterations and B agree tightly.  Mixed form: B at the GPU's own lambda*
+    meets the B gate against the oracle's field at that lambda, for every point of every
+    problem."""
+    mags, pts = _uneven_batch()
+    opt = dbie.Options(precision=precision, max_iter=50)
+    fields = [dbie.DBIEField.from_magnetogram(m) for m in mags]
+    outs = dbie.solve_batched(fields, [torch.from_numpy(p) for p in pts], opt, codes=50)
+    torch.cuda.synchronize()
+    same_all = []
+    for mag, p, o in zip(mags, pts, outs):
+        got = {k: v.cpu().numpy() for k, v in o.items()}
+        codes = [bytes(row).rstrip(b"\0").decode() for row in got["codes"]]
+        ref = oracle_solve(mag, p)
+        same = np.array([a == b for a, b in zip(codes, ref["codes"])])
+        same_all.append(same)
+        L = float(max(mag.nx, mag.ny))
+        if precision == 1:
+            assert same.mean() >= 0.95, (mag.nx, mag.ny, same.mean())
+            assert lam_close(got["lam"][same], ref["lam"][same], L).all()
+            assert np.array_equal(got["iters"][same], ref["iters"][same])
+            assert np.array_equal(got["nfev"][same], ref["nfev"][same])
+            rel = np.linalg.norm(got["B"] - ref["B"], axis=1) / np.linalg.norm(ref["B"], axis=1)
+            assert rel[same].max() < 1e-9
+        else:
+            B, _, _ = oracle.field(oracle_boundary(mag), p.astype(np.float64), got["lam"])
+            sB, _ = abs_scales(mag, p, got["lam"])
+            rb = check_B(got["B"], B, sB)
+            assert rb["bad"].size == 0, (mag.nx, mag.ny, rb)
+        assert np.all(got["lam"] >= 0) and np.all(got["status"] >= 0)
+    frac = float(np.concatenate(same_all).mean())
+    print(f"batched precision {precision}: oracle step sequences on {frac:.4f} of points")
+    if precision == 1:
+        assert frac >= 0.99, frac
+    for f in fields:
+        f.close()

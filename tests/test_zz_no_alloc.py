@@ -1,7 +1,9 @@
 """dbie_eval_noalloc: the evaluation entry point that allocates nothing (its scratch is one fixed
 array in the library's device image), for callers that may not allocate device memory while
-they run.  Checked through the C ABI against dbie_eval on two calls in a row (the array keeps
-the previous call's contents, so the second call checks that every counter is cleared).
+they run.  Checked through the C ABI against dbie_eval on calls in a row (the array keeps the
+previous call's contents, so every later call checks that the counters are cleared), and
+directly against the FP64 oracle; one call is at the stated limits (256 x 256 pixels, 65,536
+points), where the scratch layout is fullest.
 
 Collected last on purpose: a failure here leaves the rest of the suite already run."""
 import ctypes
@@ -9,10 +11,14 @@ import ctypes
 import numpy as np
 import pytest
 
-from gates import check_B, check_grad
+import oracle
+from gates import abs_scales, check_B, check_grad
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
+
+CASES = [(100, 90, 3000), (37, 61, 777), (256, 256, 65536)]   # (nx, ny, points)
+ORACLE_SAMPLE = 256   # points per case compared with the oracle
 
 
 def _case(seed, nx, ny, n):
@@ -24,13 +30,22 @@ def _case(seed, nx, ny, n):
     return comps, xyz, lam
 
 
-def test_noalloc_matches_dbie_eval_twice():
+class _Mag:
+    def __init__(self, nx, ny, comps):
+        self.nx, self.ny = nx, ny
+        self.x0 = self.y0 = 0.0
+        self.hx = self.hy = self.dA = 1.0
+        self.Bx, self.By, self.Bz = comps
+
+
+def test_noalloc_matches_dbie_eval_and_oracle_on_calls_in_a_row():
     import paper_1306_1122_gb300._native as N
+    oracle.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     P = lambda t: ctypes.c_void_p(t.data_ptr())
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    for seed, (nx, ny, n) in enumerate([(100, 90, 3000), (37, 61, 777)]):
+    for seed, (nx, ny, n) in enumerate(CASES):
         comps, xyz, lam = _case(seed, nx, ny, n)
         Bd = [torch.from_numpy(c).to(dev) for c in comps]
         X = torch.from_numpy(xyz).to(dev)
@@ -53,6 +68,16 @@ def test_noalloc_matches_dbie_eval_twice():
         r = check_B(got, ref, scale)
         assert r["bad"].size == 0, r
         assert check_grad(got, ref, np.abs(ref).max())["ok"]
+        # directly against the FP64 oracle (Eq. 16) on a seeded sample of the points
+        pick = np.sort(np.random.default_rng(100 + seed).choice(n, min(n, ORACLE_SAMPLE),
+                                                               replace=False))
+        mag = _Mag(nx, ny, comps)
+        bd = oracle.Boundary(oracle.Grid(nx, ny), *comps)
+        xs, ls = xyz[pick].astype(np.float64), lam[pick].astype(np.float64)
+        B_orc, _, _ = oracle.field(bd, xs, ls)
+        sB, _ = abs_scales(mag, xs, ls)
+        r = check_B(got[pick], B_orc, sB)
+        assert r["bad"].size == 0, (nx, ny, n, r)
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits():
