@@ -61,7 +61,7 @@ def parse_args():
     ap.add_argument("--workload", default="ll128", choices=["ll128", "batch64"])
     ap.add_argument("--max-points", type=int, default=200_000,
                     help="batch64: upper end of the per-problem point count")
-    ap.add_argument("--case", default=None, choices=["exact_near_field"],
+    ap.add_argument("--case", default=None, choices=["exact_near_field", "float_float"],
                     help="a single-kernel-family case for profiling instead of the step")
     return ap.parse_args()
 
@@ -180,7 +180,8 @@ def run_ours(args):
                    ptr(gB0), ptr(glam), 0, stream)
         st = N.dbie_get_stats(h, True)   # synchronises: pair-sum kernel event timings
         stats_out.append(dict(queries=st.queries, rounds=st.rounds, obj_ms=st.objective_ms,
-                              launches=st.launches, obj_pairs=st.objective_pairs))
+                              launches=st.launches, obj_pairs=st.objective_pairs, ties=st.ties,
+                              ff_pairs=st.refine_pairs, ff_ms=st.refine_ms))
         return r
 
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
@@ -238,7 +239,8 @@ def run_ours(args):
     step_ms = sum(times) / len(times)
     clocks = clk.summary()
 
-    # pair evaluations of one step: simplex queries x pixels + adjoint + dB/dlambda pass
+    # pair evaluations of one step: simplex queries x pixels + adjoint + dB/dlambda pass (the
+    # float-float re-evaluations of certified decisions are reported apart, not counted here)
     q = stats[-1]["queries"]
     pairs_step = q * npix + 2 * n * npix
     t_tot = sum(times) / 1e3
@@ -282,13 +284,20 @@ def run_ours(args):
         "data": "synthetic (seeded Low & Lou field, no observational data)",
         "config": {"workload": WORKLOAD, "points": n, "boundary": [m.ny, m.nx],
                    "precision": "mixed (FP32 pair terms, float-float sums, FP64 near field "
-                                "z<=2px, FP64 objective and simplex)",
+                                "z<=2px, FP64 objective and simplex; near-tied simplex "
+                                "decisions re-evaluated in the float-float form)",
                    "fwd_bwd": "solve (Nelder-Mead, tol 1e-6, max 50 it) + adjoint + dL/dlambda",
                    "pairs_per_step": pairs_step, "simplex_rounds": rounds,
                    "objective_evals": q, "l2": "flushed before each step (256 MB write)",
                    "parallelism": f"replicas x{world} (points are independent)",
                    "launch_configs": tuned},
         "solve_ms": step_ms,
+        "certified_decisions": {
+            "near_ties_per_step": stats[-1]["ties"],
+            "near_tie_frac_of_evals": stats[-1]["ties"] / max(1, q),
+            "float_float_pairs_per_step": stats[-1]["ff_pairs"],
+            "float_float_ms_per_step": sum(s["ff_ms"] for s in stats) / args.steps,
+            "band": 0.02},
         "roofline": {"bound": "alu", "pipe": "MUFU (rsqrt, sin, cos)",
                      "kernel": "g1_kernel<float, objective, per-component lambda>",
                      "achieved": achieved, "peak": peak, "unit": "T MUFU-op/s",
@@ -302,9 +311,10 @@ def run_ours(args):
                                     "2070 MHz max SM clock"},
         "e2e": {"value": e2e_value, "unit": "pair-evals/s",
                 "h2d_bytes_per_step": int(h2d[-1]), "d2h_bytes_per_step": int(d2h[-1])},
-        # per step: staging 1, solve 3 + 4 per round (plan, pair sums, near field, simplex),
-        # backward 9 (pack, plan, adjoint, finalize; pack, plan, pair sums, near field, finalize)
-        "gpu_launches": int(args.steps * (1 + 3 + 4 * rounds + 9)),
+        # per step: staging 5 (checks, FP32/FP64 and float-float tiles), solve 4 + 7 per round (plan, pair sums, near field, simplex step;
+        # float-float plan, pair sums, simplex step), backward 9 (pack, plan, adjoint, finalize;
+        # pack, plan, pair sums, near field, finalize)
+        "gpu_launches": int(args.steps * (5 + 4 + 7 * rounds + 9)),
         "clocks": clocks,
         "wall_s": wall,
     }
@@ -326,10 +336,11 @@ def run_ours(args):
 
 
 def fp64_compare(w, npts, dev):
-    """Time-to-solution of the mixed form against the plain FP64 GPU form on the same points
-    (a seeded subsample), both running the full lambda search, and the mixed result's accuracy
-    against the FP64 one: B at each side's own lambda and, where both took the same simplex
-    steps, lambda itself."""
+    """Time-to-solution of the mixed form, with certified decisions (the default) and without,
+    against the plain FP64 GPU form on the same points (a seeded subsample), all running the full
+    lambda search; the mixed results' accuracy against the FP64 one: B at the mixed lambda and,
+    where both took the same simplex steps, lambda itself; the near ties that certification sent
+    to float-float re-evaluation and their cost."""
     import torch
 
     import paper_1306_1122_gb300 as dbie
@@ -339,37 +350,44 @@ def fp64_compare(w, npts, dev):
     f = dbie.DBIEField.from_magnetogram(w.mag, device=dev)
     f.autotune()
     out = {}
-    for name, prec in (("mixed", 0), ("fp64", 1)):
-        opt = dbie.Options(precision=prec)
+    for name, prec, cert in (("mixed", 0, 0.02), ("mixed_uncertified", 0, 0.0), ("fp64", 1, 0.0)):
+        opt = dbie.Options(precision=prec, certify=cert)
         f.solve(pts[:256], opt)                  # warm: graph capture, buffers
         torch.cuda.synchronize()
+        f.set_profiling(True)
+        f.stats(reset=True)
         t0 = time.perf_counter()
         r = f.solve(pts, opt, codes=50)
         torch.cuda.synchronize()
-        out[name] = (time.perf_counter() - t0, r)
-    (tm, rm), (td, rd) = out["mixed"], out["fp64"]
-    # B of the mixed solve against the FP64 evaluation at the mixed lambda
-    Bd_at_m = f.eval(pts, rm["lam"].to(torch.float32), options=dbie.Options(precision=1))["B"]
-    rel = ((rm["B"] - Bd_at_m).norm(dim=1) / Bd_at_m.norm(dim=1)).cpu().numpy()
-    same = (rm["codes"] == rd["codes"]).all(dim=1).cpu().numpy()
-    lam_rel = ((rm["lam"] - rd["lam"]).abs() /
-               torch.clamp(rd["lam"].abs(), min=1.0 / (w.mag.nx * w.mag.hx))).max(dim=1).values
-    lam_rel = lam_rel.cpu().numpy()
-    b_stats = b_error_stats(f, w.mag, w.points[idx], rm["lam"].cpu().numpy(), dev)
-    f.close()
-    return {"points": int(len(idx)), "mixed_s": tm, "fp64_s": td, "speedup": td / tm,
-            "mixed_iters_mean": float(rm["iters"].float().mean()),
-            "fp64_iters_mean": float(rd["iters"].float().mean()),
-            "B_rel_err_vs_fp64_at_own_lambda": {"median": float(np.median(rel)),
-                                                "p99": float(np.percentile(rel, 99)),
-                                                "max": float(rel.max())},
-            "B_vs_fp64_at_mixed_lambda": b_stats,
+        out[name] = (time.perf_counter() - t0, r, f.stats(reset=True))
+        f.set_profiling(False)
+    td, rd, _ = out["fp64"]
+    res = {"points": int(len(idx)), "fp64_s": td,
+           "fp64_iters_mean": float(rd["iters"].float().mean())}
+    for name in ("mixed", "mixed_uncertified"):
+        tm, rm, st = out[name]
+        same = (rm["codes"] == rd["codes"]).all(dim=1).cpu().numpy()
+        lam_rel = ((rm["lam"] - rd["lam"]).abs() /
+                   torch.clamp(rd["lam"].abs(), min=1.0 / (w.mag.nx * w.mag.hx))).max(dim=1).values
+        lam_rel = lam_rel.cpu().numpy()
+        res[name] = {
+            "solve_s": tm, "speedup_vs_fp64": td / tm,
+            "iters_mean": float(rm["iters"].float().mean()),
             "same_step_sequence_frac": float(same.mean()),
             "lambda_rel_err_where_same": ({
                 "median": float(np.median(lam_rel[same])),
                 "p99": float(np.percentile(lam_rel[same], 99)),
                 "max": float(lam_rel[same].max()),
-                "frac_le_1e-4": float((lam_rel[same] <= 1e-4).mean())} if same.any() else None)}
+                "frac_le_1e-4": float((lam_rel[same] <= 1e-4).mean())} if same.any() else None),
+            "near_ties": int(st["ties"]), "objective_evals": int(st["queries"]),
+            "near_tie_frac_of_evals": st["ties"] / max(1, st["queries"]),
+            "float_float_pairs": st["refine_pairs"], "float_float_ms": st["refine_ms"],
+            "objective_ms": st["objective_ms"]}
+    tm, rm, _ = out["mixed"]
+    res["mixed"]["B_vs_fp64_at_mixed_lambda"] = b_error_stats(f, w.mag, w.points[idx],
+                                                              rm["lam"].cpu().numpy(), dev)
+    f.close()
+    return res
 
 
 def method_compare(w, dev):
@@ -863,10 +881,39 @@ def run_case_exact_near_field():
                       **out}))
 
 
+def run_case_float_float():
+    """Profiling case of the float-float pair sums (the certified decisions' re-evaluation
+    kernel): objective sums of 8,192 ll128 points at lambda_p = 0.02 in DBIE_PREC_FLOAT_FLOAT,
+    twice to warm up and once timed; prints the CUDA-event time and pair rate."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ll128(with_truth=False)
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    pts = torch.from_numpy(w.points[::16].copy()).cuda()
+    lam = torch.full((len(pts), 3), 0.02, device="cuda")
+    opt = dbie.Options(precision=dbie._native.DBIE_PREC_FLOAT_FLOAT)
+    for _ in range(2):
+        f.eval(pts, lam, grad=True, options=opt)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    f.eval(pts, lam, grad=True, options=opt)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    f.close()
+    print(json.dumps({"case": "float_float", "workload": "ll128 objective sums, 8192 points x "
+                      "16384 pixels, float-float form", "ms": ms,
+                      "pairs_per_s": len(pts) * w.mag.npix / (ms / 1e3)}))
+
+
 def main():
     args = parse_args()
     if args.case == "exact_near_field":
         run_case_exact_near_field()
+    elif args.case == "float_float":
+        run_case_float_float()
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":

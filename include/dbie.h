@@ -54,7 +54,7 @@ typedef enum {
 } dbie_status;
 
 enum { DBIE_MEM_HOST = 0, DBIE_MEM_DEVICE = 1 };
-enum { DBIE_PREC_MIXED = 0, DBIE_PREC_FP64 = 1 };
+enum { DBIE_PREC_MIXED = 0, DBIE_PREC_FP64 = 1, DBIE_PREC_FLOAT_FLOAT = 2 };
 enum { DBIE_LAMBDA_PER_COMPONENT = 0, DBIE_LAMBDA_TIED = 1 };
 /* Per-point result status of dbie_solve. */
 enum { DBIE_PT_CONVERGED = 0, DBIE_PT_MAXITER = 1 };
@@ -73,7 +73,11 @@ typedef struct {
   double w_g;          /* objective Phi = f + w_g * g (default 1) */
   double g_scale;      /* Delta V_i / Delta sigma_i of Eq. 9; <= 0 selects hx / 6 */
   int32_t precision;   /* DBIE_PREC_MIXED (FP32 pair terms, compensated sums, FP64 near field
-                          and FP64 reductions) or DBIE_PREC_FP64 (FP64 throughout) */
+                          and FP64 reductions), DBIE_PREC_FP64 (FP64 throughout), or
+                          DBIE_PREC_FLOAT_FLOAT (every pair term and sum as a pair of floats,
+                          about 48 significant bits, on the FP32 pipe: FP64-grade sums at a
+                          fraction of the FP64 pipe's cost; dbie_eval only, without dBdlam;
+                          other entry points return DBIE_EINVAL) */
   int32_t method;      /* DBIE_METHOD_SIMPLEX (the paper's Downhill Simplex, default) or
                           DBIE_METHOD_QUASI_NEWTON (BFGS with Armijo backtracking on the exact
                           gradient dPhi/dlambda; not in the paper).  For the quasi-Newton method
@@ -84,6 +88,15 @@ typedef struct {
                           (a 7 x 7 window) summed in FP64; with DBIE_QUAD_PIXEL_EXACT also the
                           height up to which the exact near-field integration applies (both
                           precisions); < 0 selects 2 * hx, 0 disables */
+  double certify;      /* mixed precision, Downhill Simplex: certified decisions.  Every simplex
+                          comparison whose two Phi values differ by no more than `certify` times
+                          the sum of their error bounds (a worst-case bound of the FP32-term sums,
+                          from the point's absolute-value sums) re-evaluates those values in the
+                          float-float form before the step is taken, so that the search takes the
+                          decisions of sums accurate to ~1e-13 (those of the FP64 form up to its
+                          own rounding).  0 disables; default 0.02 (the largest measured gap of a
+                          decision that the FP32-term sums flipped was 0.009 times that sum of
+                          bounds).  Not used by the FP64 form or the quasi-Newton search. */
 } dbie_options;
 
 /* Per-point outputs of dbie_solve; every pointer may be NULL except B and lambda. */
@@ -109,6 +122,9 @@ typedef struct {
   double objective_ms;     /* CUDA-event time of those launches */
   int64_t rounds;          /* simplex rounds run by dbie_solve calls */
   int64_t queries;         /* objective evaluations (points x trial lambdas) */
+  int64_t ties;            /* certified decisions: near ties sent to float-float re-evaluation */
+  double refine_pairs;     /* their point x pixel pairs (float-float form) */
+  double refine_ms;        /* CUDA-event time of the float-float passes (while profiling) */
 } dbie_stats;
 
 /* Fill `opt` with the defaults listed above. */
@@ -158,7 +174,9 @@ dbie_status dbie_set_quadrature(dbie_ctx* ctx, int32_t order, void* stream);
  *   dBdlam (n, 3): d B_p / d lambda_p,
  *   fgphi  (n, 3): f (Eq. 8), g (Eq. 9), Phi = f + w_g g (needs gradB's sums; opt gives g_scale, w_g).
  * B is required when n > 0, the others may be NULL.  opt may be NULL (defaults; precision and near_z are
- * read from it).  n = 0 is a no-op. */
+ * read from it).  n = 0 is a no-op.  With precision DBIE_PREC_FLOAT_FLOAT the sums agree with the
+ * FP64 ones to about 1e-13 of their absolute-value sums (|lambda r| < 3200); dBdlam is then
+ * not available (DBIE_EINVAL). */
 dbie_status dbie_eval(dbie_ctx* ctx, int64_t n, const float* xyz, const float* lambda,
                       const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
                       double* dBdlam, double* fgphi, void* stream);

@@ -15,7 +15,7 @@ LIB_PATH = os.environ.get("DBIE_LIBRARY") or os.path.join(_PKG, "libdbie.so")
 
 DBIE_OK, DBIE_EINVAL, DBIE_ENOMEM, DBIE_ECUDA, DBIE_ETIMEOUT, DBIE_EINTERNAL = range(6)
 DBIE_MEM_HOST, DBIE_MEM_DEVICE = 0, 1
-DBIE_PREC_MIXED, DBIE_PREC_FP64 = 0, 1
+DBIE_PREC_MIXED, DBIE_PREC_FP64, DBIE_PREC_FLOAT_FLOAT = 0, 1, 2
 DBIE_LAMBDA_PER_COMPONENT, DBIE_LAMBDA_TIED = 0, 1
 DBIE_PT_CONVERGED, DBIE_PT_MAXITER = 0, 1
 DBIE_METHOD_SIMPLEX, DBIE_METHOD_QUASI_NEWTON = 0, 1
@@ -28,7 +28,8 @@ class dbie_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int32), ("lambda_mode", ctypes.c_int32),
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("precision", ctypes.c_int32),
-                ("method", ctypes.c_int32), ("near_z", ctypes.c_double)]
+                ("method", ctypes.c_int32), ("near_z", ctypes.c_double),
+                ("certify", ctypes.c_double)]
 
 
 class dbie_solve_out(ctypes.Structure):
@@ -42,7 +43,8 @@ class dbie_stats(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_int64), ("kernel_ms", ctypes.c_double),
                 ("pair_evals", ctypes.c_double), ("objective_pairs", ctypes.c_double),
                 ("objective_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
-                ("queries", ctypes.c_int64)]
+                ("queries", ctypes.c_int64), ("ties", ctypes.c_int64),
+                ("refine_pairs", ctypes.c_double), ("refine_ms", ctypes.c_double)]
 
 
 class DBIEError(RuntimeError):

@@ -32,6 +32,7 @@ UNITS = {
     "pairsum_f32_nv.cu": [],
     "pairsum_f32_split.cu": [],
     "pairsum_f64.cu": [],
+    "pairsum_ff.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],
     "pxe.cu": [],

@@ -16,6 +16,9 @@
 
 using namespace dbie;
 
+#ifndef DBIE_FF_SPLIT_TARGET_PCT
+#define DBIE_FF_SPLIT_TARGET_PCT 200   // the same for the float-float re-evaluation pass
+#endif
 #ifndef DBIE_SPLIT_TARGET_PCT
 #define DBIE_SPLIT_TARGET_PCT 200
 #endif
@@ -80,15 +83,19 @@ struct Misc {
 struct SolveBufs {
   DBuf probs, ppos, lam0, sd, si, q_cnt_pass, item_off, ctrl, out, res, codes, corr;
   DBuf qpos[2], qlam[2], q_cnt[2], act[2], near[2];
+  DBuf msc, fout, fq_cnt_pass, fitem_off;            // certified decisions
+  DBuf fpos[2], flam[2], fq_cnt[2], ref[2];
   cudaGraphExec_t exec = nullptr;
   std::vector<unsigned char> key;   // launch arguments the cached graph was captured with
-  std::vector<cudaEvent_t> ev;      // profiling events inside the graph (2 per round)
+  std::vector<cudaEvent_t> ev;      // profiling events inside the graph (4 per round)
   void release() {
     for (DBuf* b : {&probs, &ppos, &lam0, &sd, &si, &q_cnt_pass, &item_off, &ctrl, &out, &res,
-                    &codes, &corr})
+                    &codes, &corr, &msc, &fout, &fq_cnt_pass, &fitem_off})
       b->release();
     for (int s = 0; s < 2; ++s)
-      for (DBuf* b : {&qpos[s], &qlam[s], &q_cnt[s], &act[s], &near[s]}) b->release();
+      for (DBuf* b : {&qpos[s], &qlam[s], &q_cnt[s], &act[s], &near[s], &fpos[s], &flam[s],
+                      &fq_cnt[s], &ref[s]})
+        b->release();
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
     for (cudaEvent_t e : ev) cudaEventDestroy(e);
@@ -107,6 +114,13 @@ struct SolveCtrl {
   int32_t pad;
   unsigned long long stat_queries;
   double stat_pairs;
+  // certified decisions: the float-float re-evaluation pass of each round
+  PlanHdr fplan;
+  int32_t fwork;
+  int32_t ref_cnt[2];
+  int32_t pad2;
+  unsigned long long stat_ties;
+  double stat_ff_pairs;
 };
 
 int device_sm_count(int dev) {
@@ -148,7 +162,7 @@ struct dbie_ctx {
   int64_t npix = 0;
   int32_t ntiles = 0;
   int sm_count = 1;
-  DBuf t32, t64, prob, err, misc;
+  DBuf t32, t64, tff, prob, err, misc;
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
   DBuf tv32, tv64, probv;         // noise-variance tiles and their problem descriptor
@@ -189,13 +203,25 @@ dbie_status check_opts(const dbie_options& o) {
   if (o.max_iter < 0) return fail(DBIE_EINVAL, "max_iter must be >= 0");
   if (o.lambda_mode != DBIE_LAMBDA_PER_COMPONENT && o.lambda_mode != DBIE_LAMBDA_TIED)
     return fail(DBIE_EINVAL, "lambda_mode must be DBIE_LAMBDA_PER_COMPONENT or DBIE_LAMBDA_TIED");
-  if (o.precision != DBIE_PREC_MIXED && o.precision != DBIE_PREC_FP64)
-    return fail(DBIE_EINVAL, "precision must be DBIE_PREC_MIXED or DBIE_PREC_FP64");
+  if (o.precision != DBIE_PREC_MIXED && o.precision != DBIE_PREC_FP64 &&
+      o.precision != DBIE_PREC_FLOAT_FLOAT)
+    return fail(DBIE_EINVAL, "precision must be DBIE_PREC_MIXED, DBIE_PREC_FP64 or "
+                             "DBIE_PREC_FLOAT_FLOAT");
   if (o.method != DBIE_METHOD_SIMPLEX && o.method != DBIE_METHOD_QUASI_NEWTON)
     return fail(DBIE_EINVAL, "method must be DBIE_METHOD_SIMPLEX or DBIE_METHOD_QUASI_NEWTON");
+  if (!(o.certify >= 0) || !std::isfinite(o.certify))
+    return fail(DBIE_EINVAL, "certify must be finite and >= 0");
   if (!std::isfinite(o.simplex_step) || !std::isfinite(o.w_g) || !std::isfinite(o.g_scale) ||
       !std::isfinite(o.near_z) || !std::isfinite(o.eps_f) || !std::isfinite(o.eps_g))
     return fail(DBIE_EINVAL, "options must be finite");
+  return DBIE_OK;
+}
+
+// The float-float form serves field evaluation (B, grad B, f, g) only.
+dbie_status no_float_float(const dbie_options& o, const char* fn) {
+  if (o.precision == DBIE_PREC_FLOAT_FLOAT)
+    return fail(DBIE_EINVAL, std::string(fn) + ": DBIE_PREC_FLOAT_FLOAT is available in dbie_eval "
+                                               "(without dBdlam) only");
   return DBIE_OK;
 }
 
@@ -290,17 +316,17 @@ KernelRef g1_ref(dbie_ctx* c, int var, bool tied, bool fp64, int rows = -1) {
 // near-field correction.  Results are in c->out as item chunks described by c->misc.
 dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, int64_t n,
                         const float* d_xyz, const float* d_lamf, const double* d_lamd,
-                        cudaStream_t s, bool tied = false) {
+                        cudaStream_t s, bool tied = false, bool ffp = false) {
   Misc* m = c->misc.as<Misc>();
   DBIE_TRY(ensure(c->qpos, sizeof(float4) * n));
   DBIE_TRY(ensure(c->qlam, sizeof(Lam4) * n));
   // (the noise variance sums positive terms: FP32 is accurate there without a near field)
-  const bool near_on = !fp64 && o.near_z > 0 && var != VAR_NV;
+  const bool near_on = !fp64 && !ffp && o.near_z > 0 && var != VAR_NV;
   if (near_on) DBIE_TRY(ensure(c->near_list, sizeof(int32_t) * n));
   CUDA_TRY(cudaMemsetAsync(&m->near_cnt, 0, sizeof(int32_t), s));
   launch_pack_eval(n, d_xyz, d_lamf, d_lamd, c->qpos.as<float4>(), c->qlam.as<Lam4>(),
                    c->near_list.as<int32_t>(), &m->near_cnt, near_on ? 1 : 0, o.near_z, s);
-  const KernelRef k = g1_ref(c, var, tied, fp64);
+  const KernelRef k = ffp ? g1_ref_ff(var, tied) : g1_ref(c, var, tied, fp64);
   const int grid = persistent_grid(k, c->device);
   const int64_t nblk = (n + k.qper - 1) / k.qper;
   const int64_t target = 2LL * grid;
@@ -444,6 +470,7 @@ void dbie_default_options(dbie_options* o) {
   o->eps_f = 1e-3;
   o->eps_g = 1e-4;
   o->tol = 1e-6;
+  o->certify = 0.02;
   o->max_iter = 50;
   o->lambda_mode = DBIE_LAMBDA_PER_COMPONENT;
   o->simplex_step = 0.0;
@@ -459,7 +486,7 @@ void dbie_destroy(dbie_ctx* c) {
   cudaGetDevice(&prev);
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
-  for (DBuf* b : {&c->t32, &c->t64, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
+  for (DBuf* b : {&c->t32, &c->t64, &c->tff, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
                   &c->tv64, &c->probv, &c->b0raw, &c->vtmp, &c->pxe_corr, &c->pxe_pos,
                   &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins})
@@ -481,6 +508,7 @@ static ProbDesc desc_of(const dbie_ctx* c) {
   ProbDesc pd{};
   pd.tiles32 = c->t32.as<float>();
   pd.tiles64 = c->t64.as<double>();
+  pd.tilesff = c->tff.as<float>();
   pd.ntiles = c->ntiles;
   pd.nx = c->qnx;
   pd.ny = c->qny;
@@ -504,6 +532,7 @@ static dbie_status restage(dbie_ctx* c, cudaStream_t s) {
   else
     launch_stage_q9(B0, c->nx, c->ny, c->x0, c->y0, c->hx, c->hy, c->qi, c->ntiles,
                     c->t32.as<float>(), c->t64.as<double>(), s);
+  launch_stage_ff(c->t64.as<double>(), c->ntiles, c->tff.as<float>(), s);
   CUDA_TRY(cudaGetLastError());
   return DBIE_OK;
 }
@@ -615,6 +644,7 @@ dbie_status dbie_create(dbie_ctx** out, int32_t nx, int32_t ny, double x0, doubl
   dbie_status st;
   if ((st = ensure(c->t32, sizeof(float) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
   if ((st = ensure(c->t64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
+  if ((st = ensure(c->tff, sizeof(float) * 2 * NFIELD * TILE * (size_t)c->ntiles)) != DBIE_OK) return bail(st);
   if ((st = ensure(c->b0raw, sizeof(float) * 3 * (size_t)c->npix)) != DBIE_OK) return bail(st);
   if ((st = ensure(c->prob, sizeof(ProbDesc))) != DBIE_OK) return bail(st);
   if ((st = ensure(c->err, sizeof(unsigned))) != DBIE_OK) return bail(st);
@@ -709,6 +739,7 @@ dbie_status dbie_set_quadrature(dbie_ctx* c, int32_t order, void* stream) {
   DBIE_TRY(ensure(c->t32, sizeof(float) * (order > 0 ? NFIELD_SPLIT : NFIELD) * TILE *
                               (size_t)c->ntiles));
   DBIE_TRY(ensure(c->t64, sizeof(double) * NFIELD * TILE * (size_t)c->ntiles));
+  DBIE_TRY(ensure(c->tff, sizeof(float) * 2 * NFIELD * TILE * (size_t)c->ntiles));
   c->sb.release();   // cached solve graphs hold the old tile pointers
   const ProbDesc pd = desc_of(c);
   CUDA_TRY(cudaMemcpyAsync(c->prob.p, &pd, sizeof pd, cudaMemcpyHostToDevice, s));
@@ -732,6 +763,8 @@ dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lam
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool fp64 = o.precision == DBIE_PREC_FP64;
+  const bool ffp = o.precision == DBIE_PREC_FLOAT_FLOAT;
+  if (ffp && dBdlam) DBIE_TRY(no_float_float(o, "dbie_eval with dBdlam"));
   const int var = var_of(gradB || fgphi, dBdlam != nullptr);
   const float* d_xyz = xyz;
   const float* d_lam = lambda;
@@ -753,7 +786,7 @@ dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lam
     dL = dBdlam ? so.take<double>(3 * n) : nullptr;
     dF = fgphi ? so.take<double>(3 * n) : nullptr;
   }
-  DBIE_TRY(pass_single(c, var, fp64, o, n, d_xyz, d_lam, nullptr, s));
+  DBIE_TRY(pass_single(c, var, fp64, o, n, d_xyz, d_lam, nullptr, s, false, ffp));
   const bool pxe = pxe_on(c, o);
   if (pxe) DBIE_TRY(pxe_correct(c, n, c->qpos.as<float4>(), fp64, o, s));
   Misc* m = c->misc.as<Misc>();
@@ -782,6 +815,7 @@ dbie_status dbie_objective(dbie_ctx* c, int64_t n, const float* xyz, const float
   if (n > 0 && (!xyz || !lambda)) return fail(DBIE_EINVAL, "xyz and lambda must not be NULL");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_objective"));
   if (n == 0) return DBIE_OK;
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -846,6 +880,7 @@ dbie_status dbie_vjp(dbie_ctx* c, int64_t n, const float* xyz, const double* lam
   if (n > 0 && (!xyz || !lambda || !gB)) return fail(DBIE_EINVAL, "xyz, lambda, gB must not be NULL");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_vjp"));
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool fp64 = o.precision == DBIE_PREC_FP64;
@@ -995,6 +1030,7 @@ dbie_status dbie_hessian(dbie_ctx* c, int64_t n, const float* xyz, const double*
   if (n > 0 && (!xyz || !lambda)) return fail(DBIE_EINVAL, "xyz and lambda must not be NULL");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_hessian"));
   if (n == 0) return DBIE_OK;
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1040,6 +1076,7 @@ dbie_status dbie_vjp_implicit(dbie_ctx* c, int64_t n, const float* xyz, const do
   if (n > 0 && (!xyz || !lambda || !gB)) return fail(DBIE_EINVAL, "xyz, lambda, gB must not be NULL");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_vjp_implicit"));
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const bool fp64 = o.precision == DBIE_PREC_FP64;
@@ -1145,6 +1182,7 @@ dbie_status dbie_noise_var(dbie_ctx* c, int64_t n, const float* xyz, const doubl
     return fail(DBIE_EINVAL, "the noise variance needs the pixel-centre rule (dbie_set_quadrature 0)");
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_noise_var"));
   if (n == 0) return DBIE_OK;
   CUDA_TRY(cudaSetDevice(c->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1202,6 +1240,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   CUDA_TRY(cudaSetDevice(c->device));
   const dbie_options o = resolved(c, opt);
   DBIE_TRY(check_opts(o));
+  DBIE_TRY(no_float_float(o, "dbie_solve"));
   const bool fp64 = o.precision == DBIE_PREC_FP64;
   const bool tied = o.lambda_mode == DBIE_LAMBDA_TIED;
   const int dim = tied ? 1 : 3;
@@ -1225,6 +1264,8 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
 
   const bool qn = o.method == DBIE_METHOD_QUASI_NEWTON;
   const int var = qn ? VAR_OBJN : VAR_OBJ;            // quasi-Newton needs the gradient sums
+  // certified decisions: mixed-precision simplex with a positive near-tie band
+  const bool cert = !fp64 && !qn && o.certify > 0;
   const int nsum = 3 * nsum_per_comp(var);
   bool rows_all = true;   // one kernel for all problems: rows only if every grid allows it
   for (int p = 0; p < nprob; ++p) rows_all &= ctxs[p]->qnx % 4 == 0;
@@ -1234,6 +1275,12 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   // the persistent grid): more items balance the queue, fewer items mean fewer partial sums.
   const int target = (int)((int64_t)grid * DBIE_SPLIT_TARGET_PCT / 100);
   const int64_t items_cap = std::max<int64_t>((Qcap + k.qper - 1) / k.qper + nprob, 2LL * target) + 1;
+  // float-float re-evaluation pass (at most 2 queries per point and round)
+  const KernelRef kf = g1_ref_ff(VAR_OBJ, tied);
+  const int grid_ff = cert ? persistent_grid(kf, c->device) : 0;
+  const int target_ff = std::max(1, (int)((int64_t)grid_ff * DBIE_FF_SPLIT_TARGET_PCT / 100));
+  const int64_t fitems_cap = std::max<int64_t>((2 * N + kf.qper - 1) / kf.qper + nprob,
+                                               2LL * target_ff) + 1;
 
   DBIE_TRY(ensure(b.probs, sizeof(ProbDesc) * nprob));
   DBIE_TRY(ensure(b.ppos, sizeof(float4) * N));
@@ -1251,6 +1298,18 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     DBIE_TRY(ensure(b.q_cnt[sd], sizeof(int32_t) * nprob));
     DBIE_TRY(ensure(b.act[sd], sizeof(int32_t) * N));
     if (!fp64) DBIE_TRY(ensure(b.near[sd], sizeof(int32_t) * Qcap));
+  }
+  if (cert) {
+    DBIE_TRY(ensure(b.msc, sizeof(double) * 15 * N));
+    DBIE_TRY(ensure(b.fout, sizeof(double) * fitems_cap * 12 * kf.qper));
+    DBIE_TRY(ensure(b.fq_cnt_pass, sizeof(int32_t) * nprob));
+    DBIE_TRY(ensure(b.fitem_off, sizeof(int32_t) * (nprob + 1)));
+    for (int sd = 0; sd < 2; ++sd) {
+      DBIE_TRY(ensure(b.fpos[sd], sizeof(float4) * 2 * N));
+      DBIE_TRY(ensure(b.flam[sd], sizeof(Lam4) * 2 * N));
+      DBIE_TRY(ensure(b.fq_cnt[sd], sizeof(int32_t) * nprob));
+      DBIE_TRY(ensure(b.ref[sd], sizeof(int32_t) * N));
+    }
   }
   bool any_init = false;
   for (int p = 0; p < nprob; ++p) any_init |= (lam_init && lam_init[p]);
@@ -1276,6 +1335,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     pd.near_z = (!fp64 && op.near_z > 0) ? op.near_z : 0.0;
     pd.pxe_z = pxe_on(cp, op) ? op.near_z : 0.0;
     pd.q_off = (int64_t)(dim + 1) * pt_off[p];
+    pd.qff_off = 2 * pt_off[p];
     pd.pt_off = pt_off[p];
     pd.npts = n[p];
   }
@@ -1314,6 +1374,14 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (c->pinned[0]) return fail(DBIE_EINVAL, "a point is not finite or has z <= 0");
   }
   for (int sd = 0; sd < 2; ++sd) CUDA_TRY(cudaMemsetAsync(b.q_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
+  if (cert) {
+    for (int sd = 0; sd < 2; ++sd)
+      CUDA_TRY(cudaMemsetAsync(b.fq_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
+    // the error bounds' lambda-independent absolute-value sums of every point
+    launch_msc(b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), b.msc.as<double>(),
+               (int)std::min<int64_t>((N + 127) / 128, 32LL * c->sm_count), s);
+    CUDA_TRY(cudaGetLastError());
+  }
   if (codes_stride) CUDA_TRY(cudaMemsetAsync(b.codes.p, 0, (size_t)codes_stride * N, s));
   // Pixel-exact near field: the lambda-independent corrections of every point, once per solve.
   bool pxe_any = false;
@@ -1347,14 +1415,17 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     const int nx_ = cur ^ 1;
     a.cur = RoundBuf{b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(), b.q_cnt[cur].as<int32_t>(),
                      b.act[cur].as<int32_t>(), &ctrl->act_cnt[cur], b.near[cur].as<int32_t>(),
-                     &ctrl->near_cnt[cur]};
+                     &ctrl->near_cnt[cur], b.fpos[cur].as<float4>(), b.flam[cur].as<Lam4>(),
+                     b.fq_cnt[cur].as<int32_t>(), b.ref[cur].as<int32_t>(), &ctrl->ref_cnt[cur]};
     a.nxt = RoundBuf{b.qpos[nx_].as<float4>(), b.qlam[nx_].as<Lam4>(), b.q_cnt[nx_].as<int32_t>(),
                      b.act[nx_].as<int32_t>(), &ctrl->act_cnt[nx_], b.near[nx_].as<int32_t>(),
-                     &ctrl->near_cnt[nx_]};
+                     &ctrl->near_cnt[nx_], b.fpos[nx_].as<float4>(), b.flam[nx_].as<Lam4>(),
+                     b.fq_cnt[nx_].as<int32_t>(), b.ref[nx_].as<int32_t>(), &ctrl->ref_cnt[nx_]};
     a.out = b.out.as<double>();
     a.plan = &ctrl->plan;
     a.item_off = b.item_off.as<int32_t>();
-    a.o = SolveOpts{o.eps_f, o.eps_g, o.tol, o.w_g, o.max_iter, dim, near_on ? 1 : 0, 0};
+    a.o = SolveOpts{o.eps_f, o.eps_g, o.tol, o.w_g, cert ? o.certify : 0.0, o.max_iter, dim,
+                    near_on ? 1 : 0, 0};
     a.res_B = res_B;
     a.res_lam = res_lam;
     a.res_f = res_f;
@@ -1366,6 +1437,13 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     a.codes_stride = codes_stride;
     a.err = c->err.as<unsigned>();
     a.corr = pxe_any ? b.corr.as<double>() : nullptr;
+    if (cert) {
+      a.msc = b.msc.as<double>();
+      a.fout = b.fout.as<double>();
+      a.fplan = &ctrl->fplan;
+      a.fitem_off = b.fitem_off.as<int32_t>();
+      a.stat_ties = &ctrl->stat_ties;
+    }
   }
   // Initial simplex and its queries go to side 0.
   SolveArgs a0 = sa[1];  // "next" of the side-1 round is side 0
@@ -1393,6 +1471,10 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       pa.q_cnt_nxt = b.q_cnt[cur ^ 1].as<int32_t>();
       pa.act_cnt_nxt = &ctrl->act_cnt[cur ^ 1];
       pa.near_cnt_nxt = &ctrl->near_cnt[cur ^ 1];
+      if (cert) {
+        pa.fq_cnt_nxt = b.fq_cnt[cur ^ 1].as<int32_t>();
+        pa.ref_cnt_nxt = &ctrl->ref_cnt[cur ^ 1];
+      }
       pa.round_ctr = &ctrl->round;
       pa.stat_queries = &ctrl->stat_queries;
       pa.stat_pairs = &ctrl->stat_pairs;
@@ -1410,23 +1492,56 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       ga.err = c->err.as<unsigned>();
       // External event records become event-record nodes of the graph (plain records inside a
       // capture only order work and are never timestamped).
-      if (c->profiling) CUDA_TRY(cudaEventRecordWithFlags(b.ev[2 * r], cs, cudaEventRecordExternal));
+      if (c->profiling) CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r], cs, cudaEventRecordExternal));
       DBIE_TRY(launch_kernel(k, grid, &ga, cs));
       if (c->profiling)
-        CUDA_TRY(cudaEventRecordWithFlags(b.ev[2 * r + 1], cs, cudaEventRecordExternal));
+        CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 1], cs, cudaEventRecordExternal));
       if (near_on)
         launch_nearfield(var, tied, b.probs.as<ProbDesc>(), b.near[cur].as<int32_t>(),
                          &ctrl->near_cnt[cur], b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(),
                          &ctrl->plan, b.item_off.as<int32_t>(), b.out.as<double>(),
                          2 * c->sm_count, cs);
       (qn ? launch_bfgs_step : launch_nm_step)(sa[cur], nm_grid, cs);
+      if (cert) {
+        // the near-tied values of this round in float-float, then the waiting steps again
+        PlanArgs pf{};
+        pf.probs = b.probs.as<ProbDesc>();
+        pf.nprob = nprob;
+        pf.qper = kf.qper;
+        pf.target_items = target_ff;
+        pf.nsplit_cap = 1 << 20;
+        pf.q_cnt_cur = b.fq_cnt[cur].as<int32_t>();
+        pf.q_cnt_pass = b.fq_cnt_pass.as<int32_t>();
+        pf.item_off = b.fitem_off.as<int32_t>();
+        pf.plan = &ctrl->fplan;
+        pf.work = &ctrl->fwork;
+        pf.stat_pairs = &ctrl->stat_ff_pairs;
+        launch_plan_round(pf, cs);
+        G1Args gf{};
+        gf.probs = b.probs.as<ProbDesc>();
+        gf.nprob = nprob;
+        gf.plan = &ctrl->fplan;
+        gf.item_off = b.fitem_off.as<int32_t>();
+        gf.q_cnt = b.fq_cnt_pass.as<int32_t>();
+        gf.work = &ctrl->fwork;
+        gf.qpos = b.fpos[cur].as<float4>();
+        gf.qlam = b.flam[cur].as<Lam4>();
+        gf.out = b.fout.as<double>();
+        gf.err = c->err.as<unsigned>();
+        if (c->profiling)
+          CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 2], cs, cudaEventRecordExternal));
+        DBIE_TRY(launch_kernel(kf, grid_ff, &gf, cs));
+        if (c->profiling)
+          CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 3], cs, cudaEventRecordExternal));
+        launch_nm_refine(sa[cur], nm_grid, cs);
+      }
     }
     CUDA_TRY(cudaGetLastError());
     return DBIE_OK;
   };
-  if (c->profiling && b.ev.size() != 2 * K) {
+  if (c->profiling && b.ev.size() != 4 * K) {
     for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
-    b.ev.assign(2 * K, nullptr);
+    b.ev.assign(4 * K, nullptr);
     for (auto& e : b.ev) CUDA_TRY(cudaEventCreate(&e));
   }
   // Capture (or reuse) the graph of K rounds; the key is every launch argument.
@@ -1435,7 +1550,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     unsigned char* kp = key.data();
     std::memcpy(kp, sa, sizeof sa);
     std::memcpy(kp + sizeof sa, &k, sizeof k);
-    const int extra[3] = {grid, nm_grid, (c->profiling ? 1 : 0) | (qn ? 2 : 0)};
+    const int extra[3] = {grid, nm_grid, (c->profiling ? 1 : 0) | (qn ? 2 : 0) | (cert ? 4 : 0)};
     std::memcpy(kp + sizeof sa + sizeof k, extra, sizeof extra);
   }
   if (!b.exec || b.key != key) {
@@ -1457,21 +1572,31 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   }
   // Rounds a point can take: the simplex spends at most 3 per iteration; the quasi-Newton search
   // at most 31 line-search trials (alpha = 1 ... 2^-30) per accepted step.
-  const int max_rounds = (qn ? 31 : 3) * o.max_iter + 8;
+  // A certified step waits at most once per value it compares (4 vertices, the trial and the
+  // reflected point), each re-evaluation removing one bound.
+  const int max_rounds = (qn ? 31 : (cert ? 21 : 3)) * o.max_iter + (cert ? 14 : 8);
   const int max_launches = max_rounds / K + 2;
   int launches = 0;
   for (;;) {
     CUDA_TRY(cudaGraphLaunch(b.exec, s));
     CUDA_TRY(cudaMemcpyAsync(c->pinned, &ctrl->act_cnt[0], sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    c->pinned[1] = 0;
+    if (cert)
+      CUDA_TRY(cudaMemcpyAsync(c->pinned + 1, &ctrl->ref_cnt[0], sizeof(int32_t),
+                               cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     ++launches;
     if (c->profiling) {
       for (int r = 0; r < K; ++r) {
         float ms = 0.f;
-        const cudaError_t te = cudaEventElapsedTime(&ms, b.ev[2 * r], b.ev[2 * r + 1]);
-        if (te == cudaSuccess) {
+        const cudaError_t te = cudaEventElapsedTime(&ms, b.ev[4 * r], b.ev[4 * r + 1]);
+        float ms_ff = 0.f;
+        const cudaError_t tf = cert ? cudaEventElapsedTime(&ms_ff, b.ev[4 * r + 2], b.ev[4 * r + 3])
+                                    : cudaSuccess;
+        if (te == cudaSuccess && tf == cudaSuccess) {
           c->stats.kernel_ms += ms;
           c->stats.objective_ms += ms;
+          c->stats.refine_ms += ms_ff;
           c->stats.launches += 1;
         } else {
           (void)cudaGetLastError();  // timing unavailable: not an error of the solve
@@ -1481,7 +1606,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       }
     }
     DBIE_TRY(check_device_error(c, s));
-    if (c->pinned[0] == 0) break;
+    if (c->pinned[0] == 0 && c->pinned[1] == 0) break;
     if (launches >= max_launches) return fail(DBIE_EINTERNAL, "lambda-search rounds did not terminate");
   }
   // Statistics and outputs.
@@ -1489,6 +1614,8 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   CUDA_TRY(cudaMemcpy(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost));
   c->stats.rounds += hc.round;
   c->stats.queries += (int64_t)hc.stat_queries;
+  c->stats.ties += (int64_t)hc.stat_ties;
+  c->stats.refine_pairs += hc.stat_ff_pairs;
   if (c->profiling) {
     c->stats.pair_evals += hc.stat_pairs;
     c->stats.objective_pairs += hc.stat_pairs;

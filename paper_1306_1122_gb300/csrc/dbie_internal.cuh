@@ -79,6 +79,7 @@ constexpr int MAX_GAUSS = 8;          // Gauss points per element side (Eq. 15 e
 struct ProbDesc {
   const float* tiles32;     // tile-blocked float boundary (quadrature points)
   const double* tiles64;    // tile-blocked double boundary
+  const float* tilesff;     // tile-blocked float-float boundary (hi, lo pairs of tiles64)
   int32_t ntiles;
   int32_t nx, ny;           // quadrature-point grid: pixels, or (elements x quad_g) per side
   int32_t quad_g;           // 0: pixel centres (Eq. 16); g: nine-node elements, g x g Gauss (Eq. 15)
@@ -92,6 +93,7 @@ struct ProbDesc {
   double pxe_z;             // pixel-exact near field for z <= pxe_z (0: off)
   double area;              // pixel area of the midpoint weights (dA; usually hx hy)
   int64_t q_off;            // first query slot of this problem
+  int64_t qff_off;          // first float-float re-evaluation slot (2 per point)
   int64_t pt_off;           // first global point index
   int64_t npts;
 };

@@ -32,6 +32,8 @@ struct KernelRef {
 // rows: every aligned group of 4 quadrature points lies on one row (row length % 4 == 0)
 KernelRef g1_ref_f32(int var, bool tied, int cfg, bool rows);   // pairsum_f32_*.cu
 KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
+KernelRef g1_ref_ff(int var, bool tied);             // pairsum_ff.cu (VAR_V, VAR_OBJ)
+void launch_stage_ff(const double* t64, int ntiles, float* tff, cudaStream_t s);
 KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
 KernelRef vjp7_ref(bool fp64, bool tied);            // vjp.cu (seven-weight adjoint)
 // FP32 form over element Gauss points with float-pair positions (pairsum_f32_split.cu)
@@ -117,5 +119,8 @@ void launch_bfgs_step(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cudaStream_t s);
 void launch_plan_round(const PlanArgs& a, cudaStream_t s);
 void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s);
+void launch_nm_refine(const SolveArgs& a, int grid, cudaStream_t s);
+void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, int grid,
+                cudaStream_t s);
 
 }  // namespace dbie

@@ -18,6 +18,7 @@ namespace dbie {
 struct Eval {
   double B[3];
   double f, g, phi;
+  double s;   // error bound of phi (certified decisions; 0 when not computed)
 };
 
 __device__ __forceinline__ void objective(const double B[3], const double G[9], double g_scale,
@@ -145,10 +146,15 @@ void launch_finalize_eval(int var, int64_t n, const PlanHdr* plan, const int32_t
 }
 
 // ------------------------------------------------------------------ simplex state ----
+// A vertex (or the reflected or trial point) of one point's simplex: lambda, the field and
+// objective there, the error bound s of its Phi (0 after a float-float re-evaluation) and its
+// identity in the state the step started from (0..n vertex, VID_R reflected, VID_E trial).
 struct Vert {
   double l[3];
   double B[3];
   double f, g, phi;
+  double s;
+  int id;
 };
 
 __device__ __forceinline__ double& SD(const SolveArgs& a, int f, int64_t g) {
@@ -164,6 +170,8 @@ __device__ __forceinline__ void load_vert(const SolveArgs& a, int64_t g, int v, 
   x.f = SD(a, D_VF + v, g);
   x.g = SD(a, D_VG + v, g);
   x.phi = SD(a, D_VPHI + v, g);
+  x.s = SD(a, D_VS + v, g);
+  x.id = v;
 }
 __device__ __forceinline__ void store_vert(const SolveArgs& a, int64_t g, int v, const Vert& x) {
   for (int d = 0; d < 3; ++d) SD(a, D_VL + v * 3 + d, g) = x.l[d];
@@ -171,6 +179,49 @@ __device__ __forceinline__ void store_vert(const SolveArgs& a, int64_t g, int v,
   SD(a, D_VF + v, g) = x.f;
   SD(a, D_VG + v, g) = x.g;
   SD(a, D_VPHI + v, g) = x.phi;
+  SD(a, D_VS + v, g) = x.s;
+}
+// The reflected point (lambda at D_RL, value at D_RB..D_RPHI, bound at D_RS).
+__device__ __forceinline__ void load_r(const SolveArgs& a, int64_t g, Vert& x) {
+  for (int d = 0; d < 3; ++d) x.l[d] = SD(a, D_RL + d, g);
+  for (int p = 0; p < 3; ++p) x.B[p] = SD(a, D_RB + p, g);
+  x.f = SD(a, D_RF, g);
+  x.g = SD(a, D_RG, g);
+  x.phi = SD(a, D_RPHI, g);
+  x.s = SD(a, D_RS, g);
+  x.id = VID_R;
+}
+__device__ __forceinline__ void store_r(const SolveArgs& a, int64_t g, const Vert& x) {
+  for (int d = 0; d < 3; ++d) SD(a, D_RL + d, g) = x.l[d];
+  for (int p = 0; p < 3; ++p) SD(a, D_RB + p, g) = x.B[p];
+  SD(a, D_RF, g) = x.f;
+  SD(a, D_RG, g) = x.g;
+  SD(a, D_RPHI, g) = x.phi;
+  SD(a, D_RS, g) = x.s;
+}
+// The evaluated single trial point (lambda at D_TL, value at D_EB..D_ES).
+__device__ __forceinline__ void load_e(const SolveArgs& a, int64_t g, Vert& x) {
+  for (int d = 0; d < 3; ++d) x.l[d] = SD(a, D_TL + d, g);
+  for (int p = 0; p < 3; ++p) x.B[p] = SD(a, D_EB + p, g);
+  x.f = SD(a, D_EF, g);
+  x.g = SD(a, D_EG, g);
+  x.phi = SD(a, D_EPHI, g);
+  x.s = SD(a, D_ES, g);
+  x.id = VID_E;
+}
+__device__ __forceinline__ void store_e(const SolveArgs& a, int64_t g, const Vert& x) {
+  for (int p = 0; p < 3; ++p) SD(a, D_EB + p, g) = x.B[p];
+  SD(a, D_EF, g) = x.f;
+  SD(a, D_EG, g) = x.g;
+  SD(a, D_EPHI, g) = x.phi;
+  SD(a, D_ES, g) = x.s;
+}
+__device__ __forceinline__ void set_value(Vert& x, const Eval& e) {
+  for (int p = 0; p < 3; ++p) x.B[p] = e.B[p];
+  x.f = e.f;
+  x.g = e.g;
+  x.phi = e.phi;
+  x.s = e.s;
 }
 
 // The pixel-exact correction of point g, or null (none, or the point is above its height).
@@ -179,15 +230,104 @@ __device__ __forceinline__ const double* corr_of(const SolveArgs& a, const ProbD
   return (a.corr && pd.pxe_z > 0.0 && z <= pd.pxe_z) ? a.corr + 12 * g : nullptr;
 }
 
-// Objective of the k-th pending query of point g.
+// ------------------------------------------------------------- certified decisions ----
+// Error bound of Phi computed from the mixed form's sums (FP32 pair terms).  Per pair term the
+// error of the FP32 evaluation is bounded by the measured accuracy of its operations on GB300:
+// SFU sine and cosine within 3.3e-7 absolute on [0, pi] and about 1.1e-7 |theta| beyond (the
+// unit's own scaling of the argument), reciprocal square root within 1.25e-7 relative, plus
+// FP32 rounding.  With theta = lambda r and u = theta sin(theta) + cos(theta) that gives, for a
+// pixel of component p,
+//   |d(u b / r^3)|   <= (A0 + A1 theta + A2 theta^2) |b| / r^3,
+//   |d(psi b)|       <= [lambda^2 (A0 + A2 theta) + 3 (A3 + A4 theta + A2 theta^2) / r^2] |b| / r^3
+// (psi r^3 = lambda^2 cos(theta) - 3 u / r^2; Sx and Sy carry |dx|, |dy| <= r more), and the sum
+// over pixels turns these into polynomials in |lambda_p| whose coefficients are the point's
+// lambda-independent sums M_j = sum_k |b_pk| / r^j, j = 1..5.  The bounds of B and grad B are
+// carried to J = curl B, div B, f (Eq. 8) and g (Eq. 9) to first order:
+//   |df| <= |dJ| / |J| + |dB| / |B|  (at most 1),   |dg| <= g_scale |d div B| / |B| + g |dB| / |B|.
+// It is a worst case: on the Low & Lou and active-region workloads the measured error of Phi
+// stays below 5 % of it.
+constexpr double BND_A0 = 9.5e-7, BND_A1 = 1.06e-6, BND_A2 = 1.1e-7, BND_A3 = 1.45e-6,
+                 BND_A4 = 1.56e-6;
+
+__device__ __forceinline__ double mixed_phi_bound(const double* M, const double lam[3], int dim,
+                                                   double z, const double B[3], const double G[9],
+                                                   double g, double g_scale, double w_g) {
+  double dB[3], dG[9];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const double L = fabs(dim == 1 ? lam[0] : lam[p]);
+    const double* m = M + 5 * p;
+    const double L2 = L * L, L3 = L2 * L;
+    const double s0 = BND_A0 * m[2] + BND_A1 * L * m[1] + BND_A2 * L2 * m[0];
+    const double sx = BND_A0 * L2 * m[1] + BND_A2 * L3 * m[0] +
+                      3.0 * (BND_A3 * m[3] + BND_A4 * L * m[2] + BND_A2 * L2 * m[1]);
+    const double s1 = BND_A0 * L2 * m[2] + BND_A2 * L3 * m[1] +
+                      3.0 * (BND_A3 * m[4] + BND_A4 * L * m[3] + BND_A2 * L2 * m[2]);
+    dB[p] = z * s0;
+    dG[3 * p + 0] = z * sx;
+    dG[3 * p + 1] = z * sx;
+    dG[3 * p + 2] = s0 + z * z * s1;
+  }
+  const double Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
+  const double nJ = sqrt(Jx * Jx + Jy * Jy + Jz * Jz);
+  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  const double dJx = dG[7] + dG[5], dJy = dG[2] + dG[6], dJz = dG[3] + dG[1];
+  const double ndJ = sqrt(dJx * dJx + dJy * dJy + dJz * dJz);
+  const double ndB = sqrt(dB[0] * dB[0] + dB[1] * dB[1] + dB[2] * dB[2]);
+  if (!(nB > 0.0)) return 2.0;
+  double sf = nJ > 0.0 ? ndJ / nJ + ndB / nB : 1.0;
+  if (sf > 1.0) sf = 1.0;
+  const double sg = g_scale * (dG[0] + dG[4] + dG[8]) / nB + g * ndB / nB;
+  return sf + w_g * sg;
+}
+
+// The first near tie of a step: a comparison whose two values differ by no more than `band`
+// times the sum of their bounds (a value re-evaluated in float-float has bound 0).
+struct TieLog {
+  double band;   // 0: decisions are not certified
+  int a, b;      // ids of the first near-tied values (-1: none)
+  __device__ __forceinline__ void note(int ia, double sa, int ib, double sb, double gap) {
+    if (band > 0.0 && a < 0 && sa + sb > 0.0 && fabs(gap) <= band * (sa + sb)) {
+      a = sa > 0.0 ? ia : -1;
+      b = sb > 0.0 ? ib : -1;
+      if (a < 0) { a = b; b = -1; }
+    }
+  }
+  __device__ __forceinline__ bool lt(const Vert& x, const Vert& y) {
+    note(x.id, x.s, y.id, y.s, x.phi - y.phi);
+    return x.phi < y.phi;
+  }
+  __device__ __forceinline__ bool le(const Vert& x, const Vert& y) {
+    note(x.id, x.s, y.id, y.s, x.phi - y.phi);
+    return x.phi <= y.phi;
+  }
+};
+
+// Objective of the k-th pending query of point g; its error bound when decisions are certified.
 __device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, int pidx,
-                                          int64_t slot, double z, Eval& e, int64_t g) {
+                                          int64_t slot, double z, Eval& e, int64_t g,
+                                          const double lam[3]) {
   const ProbDesc& pd = a.probs[pidx];
   const int64_t j = slot - pd.q_off;
   double S[12], G[9];
 #pragma unroll
   for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.out, h, a.item_off, pidx, j, 12, s);
   assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
+  e.s = (a.o.tie > 0.0 && a.msc)
+            ? mixed_phi_bound(a.msc + 15 * g, lam, a.o.dim, z, e.B, G, e.g, pd.g_scale, a.o.w_g)
+            : 0.0;
+}
+
+// Objective of a float-float re-evaluation slot of point g (bound 0).
+__device__ __forceinline__ void read_eval_ff(const SolveArgs& a, const PlanHdr& hf, int pidx,
+                                             int64_t slot, double z, Eval& e, int64_t g) {
+  const ProbDesc& pd = a.probs[pidx];
+  const int64_t j = slot - pd.qff_off;
+  double S[12], G[9];
+#pragma unroll
+  for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.fout, hf, a.fitem_off, pidx, j, 12, s);
+  assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
+  e.s = 0.0;
 }
 
 // atomicAdd(ctr, v) for the lanes of a warp that reach it together (whatever branch they are
@@ -243,6 +383,27 @@ __device__ __forceinline__ void emit(const SolveArgs& a, int64_t g, const float4
   a.nxt.act[atomic_add_warp(a.nxt.act_cnt, 1)] = (int32_t)g;
 }
 
+// Queue the float-float re-evaluation of k (1 or 2) values of point g on side `sd` and put the
+// point on that side's waiting list; the value ids go to I_RTGT, one per byte.
+__device__ __forceinline__ void emit_ff(const SolveArgs& a, const RoundBuf& sd, int64_t g,
+                                        const float4& pos, int pidx, int k,
+                                        const double (&l)[2][3], int id0, int id1) {
+  const ProbDesc& pd = a.probs[pidx];
+  const int base = atomic_add_warp(sd.fq_cnt + pidx, k);
+  const int64_t slot0 = pd.qff_off + base;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    if (j >= k) break;
+    sd.fpos[slot0 + j] = pos;
+    sd.flam[slot0 + j] = a.o.dim == 1 ? make_lam4(l[j][0], l[j][0], l[j][0])
+                                      : make_lam4(l[j][0], l[j][1], l[j][2]);
+  }
+  SI(a, I_RSLOT, g) = (int32_t)slot0;
+  SI(a, I_RTGT, g) = (id0 & 0xff) | ((k > 1 ? id1 : 0xff) << 8);
+  sd.ref[atomic_add_warp(sd.ref_cnt, 1)] = (int32_t)g;
+  if (a.stat_ties) atomicAdd(a.stat_ties, 1ull);
+}
+
 // N: the number of free lambdas (3, or 1 when the components share one).
 template <int N>
 __global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ lam_init) {
@@ -267,6 +428,7 @@ __global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ 
     SI(a, I_ITERS, g) = 0;
     SI(a, I_NFEV, g) = 0;
     SI(a, I_STATUS, g) = PT_RUNNING;
+    SI(a, I_FLAGS, g) = 0;
     emit<N + 1>(a, g, pos, pidx, lam);
   }
 }
@@ -280,217 +442,295 @@ void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cud
 // adjacent compare-exchanges so the vertices stay in registers.  Without the early exit of the
 // textbook loop the result is the same: after inserting each vertex no adjacent pair of the
 // sorted prefix is out of order (v[j].phi < v[j-1].phi false), so the comparisons below the
-// insertion point never swap.
+// insertion point never swap.  The insertion's own comparisons (those down to the insertion
+// point) go through the tie log; the ones below it decide nothing.
 template <int N>
-__device__ __forceinline__ void sort_verts(Vert* v) {
+__device__ __forceinline__ void sort_verts(Vert* v, TieLog& tl) {
 #pragma unroll
-  for (int i = 1; i <= N; ++i)
+  for (int i = 1; i <= N; ++i) {
+    bool moving = true;
 #pragma unroll
-    for (int j = i; j > 0; --j)
-      if (v[j].phi < v[j - 1].phi) {
+    for (int j = i; j > 0; --j) {
+      const bool sw = moving ? tl.lt(v[j], v[j - 1]) : v[j].phi < v[j - 1].phi;
+      if (sw) {
         const Vert t = v[j];
         v[j] = v[j - 1];
         v[j - 1] = t;
+      } else {
+        moving = false;
       }
+    }
+  }
 }
 
-template <int N>
+// One simplex step per waiting point.  REF = false: the points whose queries the mixed pass of
+// this round evaluated (their results are read and their bounds computed); REF = true: the
+// points whose near-tied values the float-float pass of this round re-evaluated (the values are
+// replaced, bound 0, and the step is decided again).  A step is taken only when none of its
+// comparisons is a near tie (TieLog); otherwise the step's inputs stay in the state and the
+// near-tied values are queued for float-float re-evaluation, so every decision is the one that
+// sums accurate to the float-float level would take.  With a.o.tie == 0 every step is taken as
+// evaluated.
+template <int N, bool REF>
 __global__ void nm_step_kernel(const SolveArgs a) {
   const double rho = 1.0, chi = 2.0, psi = 0.5, sigma = 0.5;
-  const int nact = *a.cur.act_cnt;
+  const int nact = REF ? *a.cur.ref_cnt : *a.cur.act_cnt;
+  const int32_t* list = REF ? a.cur.ref : a.cur.act;
   constexpr int n = N;
   const PlanHdr h = *a.plan;
+  PlanHdr hf{};
+  if (REF) hf = *a.fplan;
   for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
-    const int64_t g = a.cur.act[ia];
+    const int64_t g = list[ia];
     const float4 pos = a.ppos[g];
     const int pidx = __float_as_int(pos.w);
     const double z = (double)pos.z;
-    const int64_t slot = SI(a, I_QSLOT, g);
     int stage = SI(a, I_STAGE, g);
     int iters = SI(a, I_ITERS, g);
     int nfev = SI(a, I_NFEV, g);
+    int flags = SI(a, I_FLAGS, g);
+    const bool single = stage != ST_INIT && stage != ST_SHRINK;
 
     Vert v[N + 1];
 #pragma unroll
     for (int k = 0; k <= n; ++k) load_vert(a, g, k, v[k]);
-    bool to_check = false;  // an iteration (or the initialisation) completed: sort and test
-    bool dirty = false;     // the vertices changed and must be stored back
-    char code = 0;
+    Vert e, R;
+    e.id = VID_E;
+    R.id = VID_R;
+    bool vdirty = false, rdirty = false;
 
-    auto centroid = [&](double c[3]) {
-#pragma unroll
-      for (int d = 0; d < n; ++d) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < n; ++k) s += v[k].l[d];
-        c[d] = s / n;
-      }
-    };
-    auto trial = [&](double coef_c, double coef_w, double out[3]) {  // coef_c * c + coef_w * v[n]
-      double c[3];
-      centroid(c);
-      for (int d = 0; d < 3; ++d) out[d] = (d < n) ? coef_c * c[d] + coef_w * v[n].l[d] : 0.0;
-    };
-    auto accept_last = [&](const double l[3], const Eval& e) {
-      dirty = true;
-      for (int d = 0; d < 3; ++d) v[n].l[d] = l[d];
-      for (int p = 0; p < 3; ++p) v[n].B[p] = e.B[p];
-      v[n].f = e.f;
-      v[n].g = e.g;
-      v[n].phi = e.phi;
-    };
-    auto emit_one = [&](const double l[3], int st) {
-      double rows[1][3] = {{l[0], l[1], l[2]}};
-      for (int d = 0; d < 3; ++d) SD(a, D_TL + d, g) = l[d];
-      stage = st;
-      emit<1>(a, g, pos, pidx, rows);
-    };
-    auto start_shrink = [&]() {
-      dirty = true;
-      double rows[N][3];
-#pragma unroll
-      for (int k = 1; k <= n; ++k) {
-        for (int d = 0; d < 3; ++d)
-          v[k].l[d] = (d < n) ? v[0].l[d] + sigma * (v[k].l[d] - v[0].l[d]) : 0.0;
-        for (int d = 0; d < 3; ++d) rows[k - 1][d] = v[k].l[d];
-      }
-      stage = ST_SHRINK;
-      emit<N>(a, g, pos, pidx, rows);
-    };
-
-    // The pending queries' objectives, evaluated at one site for every stage: a warp whose
-    // lanes are in different stages runs the FP64 objective once per query index instead of
-    // once per stage, and the kernel holds one copy of its code.  The initial simplex (n + 1
-    // queries into vertices 0..n) and a shrink (n queries into vertices 1..n) fill vertices by
-    // shifting each result in at the top (no run-time vertex index, so they stay in
-    // registers); the other stages read one trial point into e.
-    Eval e;
-    {
+    if (!(flags & F_EVAL)) {
+      // The pending queries' objectives, evaluated at one site for every stage: a warp whose
+      // lanes are in different stages runs the FP64 objective once per query index instead of
+      // once per stage.  The initial simplex (n + 1 queries into vertices 0..n) and a shrink
+      // (n queries into vertices 1..n) fill vertices by shifting each result in at the top (no
+      // run-time vertex index, so they stay in registers); the other stages read one trial point.
+      const int64_t slot = SI(a, I_QSLOT, g);
       const int nev = stage == ST_INIT ? n + 1 : (stage == ST_SHRINK ? n : 1);
       const int first = stage == ST_SHRINK ? 1 : 0;
-      const bool fill = stage == ST_INIT || stage == ST_SHRINK;
+      for (int d = 0; d < 3; ++d) e.l[d] = single ? SD(a, D_TL + d, g) : 0.0;
 #pragma unroll 1
       for (int k = 0; k < nev; ++k) {
-        read_eval(a, h, pidx, slot + k, z, e, g);
-        if (fill) {
+        double lq[3];   // the query's lambda (read back from the state: a register-array
+                        // index that depends on k would move the vertices to local memory)
+        for (int d = 0; d < 3; ++d)
+          lq[d] = single ? e.l[d] : SD(a, D_VL + 3 * (first + k) + d, g);
+        Eval ev;
+        read_eval(a, h, pidx, slot + k, z, ev, g, lq);
+        if (!single) {
 #pragma unroll
           for (int m = 0; m < n; ++m)
             if (m >= first) {
               for (int p = 0; p < 3; ++p) v[m].B[p] = v[m + 1].B[p];
               v[m].f = v[m + 1].f; v[m].g = v[m + 1].g; v[m].phi = v[m + 1].phi;
+              v[m].s = v[m + 1].s;
             }
-          for (int p = 0; p < 3; ++p) v[n].B[p] = e.B[p];
-          v[n].f = e.f; v[n].g = e.g; v[n].phi = e.phi;
+          set_value(v[n], ev);
+        } else {
+          set_value(e, ev);
+        }
+      }
+      nfev += nev;
+      vdirty = !single;
+      flags |= F_EVAL;
+    } else if (single) {
+      load_e(a, g, e);
+    }
+    if (stage == ST_EXPAND || stage == ST_OCONTRACT) load_r(a, g, R);
+    if (REF) {
+      // apply the float-float values of this point's re-evaluated targets
+      const int tg = SI(a, I_RTGT, g);
+      const int64_t rs = SI(a, I_RSLOT, g);
+#pragma unroll 1
+      for (int t = 0; t < 2; ++t) {
+        const int id = (tg >> (8 * t)) & 0xff;
+        if (id == 0xff) continue;
+        Eval ev;
+        read_eval_ff(a, hf, pidx, rs + t, z, ev, g);
+        if (id == VID_E) {
+          set_value(e, ev);
+        } else if (id == VID_R) {
+          set_value(R, ev);
+          rdirty = true;
+        } else {
+#pragma unroll
+          for (int k = 0; k <= n; ++k)
+            if (k == id) set_value(v[k], ev);
+          vdirty = true;
         }
       }
     }
 
+    // ---- the step.  With certified decisions the vertices the step starts from are in memory
+    // first (the step may turn out to wait), and nothing else is written until the step is
+    // known to be certain.
+    TieLog tl{a.o.tie, -1, -1};
+    if (vdirty && a.o.tie > 0.0)
+#pragma unroll
+      for (int m = 0; m <= n; ++m) store_vert(a, g, m, v[m]);
+    Vert (&w)[N + 1] = v;
+    bool to_check = false, accepted = false, store_R = false, emit_shrink = false;
+    bool emit_trial = false;
+    int next_stage = stage;
+    double xt[3] = {0.0, 0.0, 0.0};
+    char code = 0;
+    int fin = -1;
+    auto trial = [&](double coef_c, double coef_w, double out[3]) {  // coef_c c + coef_w w[n]
+      double c[3];
+#pragma unroll
+      for (int d = 0; d < n; ++d) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < n; ++k) s += w[k].l[d];
+        c[d] = s / n;
+      }
+      for (int d = 0; d < 3; ++d) out[d] = (d < n) ? coef_c * c[d] + coef_w * w[n].l[d] : 0.0;
+    };
+
     if (stage == ST_INIT) {
-      nfev += n + 1;
       to_check = true;
-      dirty = true;
     } else if (stage == ST_REFLECT) {
-      nfev += 1;
-      double lr[3];
-      for (int d = 0; d < 3; ++d) lr[d] = SD(a, D_TL + d, g);
-      if (e.phi < v[0].phi) {
-        for (int d = 0; d < 3; ++d) SD(a, D_RL + d, g) = lr[d];
-        for (int p = 0; p < 3; ++p) SD(a, D_RB + p, g) = e.B[p];
-        SD(a, D_RF, g) = e.f; SD(a, D_RG, g) = e.g; SD(a, D_RPHI, g) = e.phi;
-        double xe[3];
-        trial(1.0 + rho * chi, -(rho * chi), xe);
-        emit_one(xe, ST_EXPAND);
-      } else if (e.phi < v[n - 1].phi) {
-        accept_last(lr, e);
+      if (tl.lt(e, w[0])) {
+        store_R = true;
+        trial(1.0 + rho * chi, -(rho * chi), xt);
+        next_stage = ST_EXPAND;
+        emit_trial = true;
+      } else if (tl.lt(e, w[n - 1])) {
+        w[n] = e;
+        accepted = true;
         code = 'R';
         to_check = true;
-      } else if (e.phi < v[n].phi) {
-        SD(a, D_RPHI, g) = e.phi;
-        double xc[3];
-        trial(1.0 + psi * rho, -(psi * rho), xc);
-        emit_one(xc, ST_OCONTRACT);
+      } else if (tl.lt(e, w[n])) {
+        store_R = true;
+        trial(1.0 + psi * rho, -(psi * rho), xt);
+        next_stage = ST_OCONTRACT;
+        emit_trial = true;
       } else {
-        double xc[3];
-        trial(1.0 - psi, psi, xc);
-        emit_one(xc, ST_ICONTRACT);
+        trial(1.0 - psi, psi, xt);
+        next_stage = ST_ICONTRACT;
+        emit_trial = true;
       }
     } else if (stage == ST_EXPAND) {
-      nfev += 1;
-      const double phr = SD(a, D_RPHI, g);
-      double l[3];
-      if (e.phi < phr) {
-        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_TL + d, g);
-        accept_last(l, e);
+      if (tl.lt(e, R)) {
+        w[n] = e;
         code = 'E';
       } else {
-        Eval r;
-        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_RL + d, g);
-        for (int p = 0; p < 3; ++p) r.B[p] = SD(a, D_RB + p, g);
-        r.f = SD(a, D_RF, g); r.g = SD(a, D_RG, g); r.phi = phr;
-        accept_last(l, r);
+        w[n] = R;
         code = 'R';
       }
+      accepted = true;
       to_check = true;
     } else if (stage == ST_OCONTRACT || stage == ST_ICONTRACT) {
-      nfev += 1;
-      const bool ok = (stage == ST_OCONTRACT) ? (e.phi <= SD(a, D_RPHI, g)) : (e.phi < v[n].phi);
+      const bool ok = (stage == ST_OCONTRACT) ? tl.le(e, R) : tl.lt(e, w[n]);
       if (ok) {
-        double l[3];
-        for (int d = 0; d < 3; ++d) l[d] = SD(a, D_TL + d, g);
-        accept_last(l, e);
+        w[n] = e;
+        accepted = true;
         code = (stage == ST_OCONTRACT) ? 'O' : 'I';
         to_check = true;
       } else {
-        start_shrink();
+#pragma unroll
+        for (int k = 1; k <= n; ++k)
+          for (int d = 0; d < 3; ++d)
+            w[k].l[d] = (d < n) ? w[0].l[d] + sigma * (w[k].l[d] - w[0].l[d]) : 0.0;
+        next_stage = ST_SHRINK;
+        emit_shrink = true;
       }
     } else if (stage == ST_SHRINK) {
-      nfev += n;
       code = 'S';
       to_check = true;
-      dirty = true;
     }
-
-    if (code && a.codes && iters >= 1 && iters <= a.codes_stride)
-      a.codes[g * a.codes_stride + (iters - 1)] = code;
-
     if (to_check) {
-      sort_verts<N>(v);
-      int fin = -1;
-      if (v[0].f <= a.o.eps_f && v[0].g <= a.o.eps_g) fin = PT_CONVERGED;
-      else if (v[n].phi - v[0].phi <= a.o.tol) fin = PT_CONVERGED;
-      else if (iters >= a.o.max_iter) fin = PT_MAXITER;
-      if (fin >= 0) {
-        for (int p = 0; p < 3; ++p) {
-          a.res_B[3 * g + p] = v[0].B[p];
-          a.res_lam[3 * g + p] = fabs(n == 1 ? v[0].l[0] : v[0].l[p]);
-        }
-        a.res_f[g] = v[0].f;
-        a.res_g[g] = v[0].g;
-        a.res_iters[g] = iters;
-        a.res_status[g] = fin;
-        a.res_nfev[g] = nfev;
-        stage = ST_DONE;
-        SI(a, I_STATUS, g) = fin;
-        dirty = false;   // a finished point's vertices are not read again
+      sort_verts<N>(w, tl);
+      // Eq. 12 at the best vertex, then the value spread, then the iteration count
+      tl.note(w[0].id, w[0].s, -1, 0.0, w[0].f - a.o.eps_f);
+      if (w[0].f <= a.o.eps_f) tl.note(w[0].id, w[0].s, -1, 0.0, w[0].g - a.o.eps_g);
+      if (w[0].f <= a.o.eps_f && w[0].g <= a.o.eps_g) {
+        fin = PT_CONVERGED;
       } else {
-        iters += 1;
-        double xr[3];
-        trial(1.0 + rho, -rho, xr);
-        emit_one(xr, ST_REFLECT);
+        tl.note(w[n].id, w[n].s, w[0].id, w[0].s, w[n].phi - w[0].phi - a.o.tol);
+        if (w[n].phi - w[0].phi <= a.o.tol) fin = PT_CONVERGED;
+        else if (iters >= a.o.max_iter) fin = PT_MAXITER;
+      }
+      if (fin < 0) {
+        trial(1.0 + rho, -rho, xt);
+        next_stage = ST_REFLECT;
+        emit_trial = true;
       }
     }
-    if (dirty)
+
+    if (tl.a >= 0) {
+      // near tie: keep the step's inputs and re-evaluate the near-tied values in float-float
+      // (tl.a >= 0 always; tl.b >= 0 when both values carry a bound).  A vertex target's lambda
+      // comes from the stored state the step started from.
+      double lt[2][3];
+      const int ida = tl.a, idb = tl.b;
 #pragma unroll
-      for (int k = 0; k <= n; ++k) store_vert(a, g, k, v[k]);
+      for (int d = 0; d < 3; ++d) {
+        lt[0][d] = ida == VID_E ? e.l[d] : (ida == VID_R ? R.l[d] : SD(a, D_VL + 3 * ida + d, g));
+        lt[1][d] = idb < 0 ? 0.0 : idb == VID_E ? e.l[d]
+                 : (idb == VID_R ? R.l[d] : SD(a, D_VL + 3 * idb + d, g));
+      }
+      emit_ff(a, REF ? a.nxt : a.cur, g, pos, pidx, idb >= 0 ? 2 : 1, lt, ida, idb);
+      if (single) store_e(a, g, e);
+      if (rdirty) store_r(a, g, R);
+      SI(a, I_FLAGS, g) = flags;
+      SI(a, I_NFEV, g) = nfev;
+      continue;
+    }
+
+    // ---- the step is certain: take it
+    if (rdirty && !store_R) store_r(a, g, R);
+    if (store_R) {
+      Vert r = e;
+      store_r(a, g, r);
+    }
+    if (code && a.codes && iters >= 1 && iters <= a.codes_stride)
+      a.codes[g * a.codes_stride + (iters - 1)] = code;
+    if (fin >= 0) {
+      for (int p = 0; p < 3; ++p) {
+        a.res_B[3 * g + p] = w[0].B[p];
+        a.res_lam[3 * g + p] = fabs(n == 1 ? w[0].l[0] : w[0].l[p]);
+      }
+      a.res_f[g] = w[0].f;
+      a.res_g[g] = w[0].g;
+      a.res_iters[g] = iters;
+      a.res_status[g] = fin;
+      a.res_nfev[g] = nfev;
+      stage = ST_DONE;
+      SI(a, I_STATUS, g) = fin;
+    } else {
+      if (to_check) iters += 1;
+      if (emit_trial) {
+        double rows[1][3] = {{xt[0], xt[1], xt[2]}};
+        for (int d = 0; d < 3; ++d) SD(a, D_TL + d, g) = xt[d];
+        emit<1>(a, g, pos, pidx, rows);
+      } else if (emit_shrink) {
+        double rows[N][3];
+#pragma unroll
+        for (int k = 1; k <= n; ++k)
+          for (int d = 0; d < 3; ++d) rows[k - 1][d] = w[k].l[d];
+        emit<N>(a, g, pos, pidx, rows);
+      }
+      stage = next_stage;
+      // a finished point's vertices are not read again; otherwise store what changed
+      if (vdirty || to_check || accepted || emit_shrink)
+#pragma unroll
+        for (int k = 0; k <= n; ++k) store_vert(a, g, k, w[k]);
+    }
     SI(a, I_STAGE, g) = stage;
     SI(a, I_ITERS, g) = iters;
     SI(a, I_NFEV, g) = nfev;
+    SI(a, I_FLAGS, g) = 0;
   }
 }
 
 void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s) {
-  if (a.o.dim == 1) nm_step_kernel<1><<<grid, 128, 0, s>>>(a);
-  else nm_step_kernel<3><<<grid, 128, 0, s>>>(a);
+  if (a.o.dim == 1) nm_step_kernel<1, false><<<grid, 128, 0, s>>>(a);
+  else nm_step_kernel<3, false><<<grid, 128, 0, s>>>(a);
+}
+void launch_nm_refine(const SolveArgs& a, int grid, cudaStream_t s) {
+  if (a.o.dim == 1) nm_step_kernel<1, true><<<grid, 128, 0, s>>>(a);
+  else nm_step_kernel<3, true><<<grid, 128, 0, s>>>(a);
 }
 
 // --------------------------------------------------------------- per-round plan ----
@@ -538,16 +778,67 @@ __global__ void plan_round_kernel(const PlanArgs a) {
     h.pad0 = 0;
     *a.plan = h;
     *a.work = 0;
-    *a.act_cnt_nxt = 0;
-    *a.near_cnt_nxt = 0;
-    *a.round_ctr += 1;
+    // the plan of a float-float re-evaluation pass leaves the next round's counters alone
+    if (a.act_cnt_nxt) *a.act_cnt_nxt = 0;
+    if (a.near_cnt_nxt) *a.near_cnt_nxt = 0;
+    if (a.ref_cnt_nxt) *a.ref_cnt_nxt = 0;
+    if (a.round_ctr) *a.round_ctr += 1;
     if (a.stat_queries) *a.stat_queries += queries;
     if (a.stat_pairs) *a.stat_pairs += pairs;
   }
-  for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) a.q_cnt_nxt[p] = 0;
+  for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) {
+    if (a.q_cnt_nxt) a.q_cnt_nxt[p] = 0;
+    if (a.fq_cnt_nxt) a.fq_cnt_nxt[p] = 0;
+  }
 }
 
 void launch_plan_round(const PlanArgs& a, cudaStream_t s) { plan_round_kernel<<<1, 256, 0, s>>>(a); }
+
+// The lambda-independent absolute-value sums of every point, the coefficients of the mixed
+// form's error bound: msc[15 g + 5 p + j - 1] = sum_k |b_pk| / r_gk^j, j = 1..5, over the
+// quadrature points of the point's problem.  FP32 terms summed per tile, tiles summed in FP64
+// (relative error below 1e-4: a scale, not a result).
+__global__ void msc_kernel(const ProbDesc* __restrict__ probs, int64_t N,
+                           const float4* __restrict__ ppos, double* __restrict__ msc) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pos = ppos[g];
+    const ProbDesc& pd = probs[__float_as_int(pos.w)];
+    const float z2 = __fmul_rn(pos.z, pos.z);
+    double tot[15];
+#pragma unroll
+    for (int i = 0; i < 15; ++i) tot[i] = 0.0;
+    for (int t = 0; t < pd.ntiles; ++t) {
+      const float* T = pd.tiles32 + (int64_t)t * pd.nf32 * TILE;
+      float acc[15];
+#pragma unroll
+      for (int i = 0; i < 15; ++i) acc[i] = 0.f;
+#pragma unroll 2
+      for (int e = 0; e < TILE; ++e) {
+        const float dx = pos.x - __ldg(T + e), dy = pos.y - __ldg(T + TILE + e);
+        const float ri = rsqrtf(dx * dx + dy * dy + z2);
+        const float b[3] = {fabsf(__ldg(T + 2 * TILE + e)), fabsf(__ldg(T + 3 * TILE + e)),
+                            fabsf(__ldg(T + 4 * TILE + e))};
+        float wj = ri;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+#pragma unroll
+          for (int p = 0; p < 3; ++p) acc[5 * p + j] += b[p] * wj;
+          wj *= ri;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 15; ++i) tot[i] += (double)acc[i];
+    }
+#pragma unroll
+    for (int i = 0; i < 15; ++i) msc[15 * g + i] = tot[i];
+  }
+}
+
+void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, int grid,
+                cudaStream_t s) {
+  if (N > 0) msc_kernel<<<grid, 128, 0, s>>>(probs, N, ppos, msc);
+}
 
 }  // namespace dbie
 

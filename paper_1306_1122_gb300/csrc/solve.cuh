@@ -17,7 +17,15 @@ enum DField {
   D_RG = 43,
   D_RPHI = 44,
   D_TL = 45,     // pending single trial point lambda (3)
-  D_NFIELDS = 48
+  // certified decisions: the error bound of each value (0 once re-evaluated in float-float)
+  D_VS = 48,     // vertex bounds: D_VS + v
+  D_RS = 52,     // reflected point's bound
+  D_EB = 53,     // evaluated single trial point: B (3), f, g, Phi, bound (kept while its step
+  D_EF = 56,     // waits for a float-float re-evaluation)
+  D_EG = 57,
+  D_EPHI = 58,
+  D_ES = 59,
+  D_NFIELDS = 60
 };
 // Quasi-Newton state (same arrays, other meaning): x, grad Phi, inverse Hessian H (3 x 3),
 // direction d, B, f, g, Phi at x, line-search step alpha, grad . d, |grad|.
@@ -25,13 +33,21 @@ enum BField {
   B_X = 0, B_GR = 3, B_H = 6, B_D = 15, B_B = 18, B_F = 21, B_G = 22, B_PHI = 23, B_ALPHA = 24,
   B_GD = 25, B_GN = 26
 };
-enum IField { I_STAGE = 0, I_ITERS = 1, I_NFEV = 2, I_STATUS = 3, I_QSLOT = 4, I_NFIELDS = 5 };
+// I_FLAGS bit F_EVAL: this step's evaluations are in the state (the step waits for a float-float
+// re-evaluation); I_RSLOT: first float-float query slot of the point's pending re-evaluation;
+// I_RTGT: its targets, one value id per byte (0..3 vertex, 4 reflected point, 5 trial point),
+// 0xff = none.
+enum IField { I_STAGE = 0, I_ITERS = 1, I_NFEV = 2, I_STATUS = 3, I_QSLOT = 4, I_FLAGS = 5,
+              I_RSLOT = 6, I_RTGT = 7, I_NFIELDS = 8 };
+constexpr int F_EVAL = 1;
+constexpr int VID_R = 4, VID_E = 5;
 enum PtStatus { PT_RUNNING = -1, PT_CONVERGED = 0, PT_MAXITER = 1 };
 enum Stage { ST_INIT = 0, ST_REFLECT = 1, ST_EXPAND = 2, ST_OCONTRACT = 3, ST_ICONTRACT = 4,
              ST_SHRINK = 5, ST_DONE = 6, ST_BF_INIT = 10, ST_BF_LS = 11 };
 
 struct SolveOpts {
   double eps_f, eps_g, tol, w_g;
+  double tie;                // certified decisions: near-tie band factor (0: off)
   int32_t max_iter, dim, near_on, pad0;
 };
 
@@ -44,6 +60,12 @@ struct RoundBuf {
   int32_t* act_cnt;    // [1]
   int32_t* near;       // near-field query slots
   int32_t* near_cnt;   // [1]
+  // certified decisions: float-float re-evaluation queries and the points that wait for them
+  float4* fpos;        // [2 N] slots (problem p from its qff_off)
+  Lam4* flam;
+  int32_t* fq_cnt;     // [nprob]
+  int32_t* ref;        // waiting points
+  int32_t* ref_cnt;    // [1]
 };
 
 struct SolveArgs {
@@ -72,6 +94,12 @@ struct SolveArgs {
   int32_t pad1;
   unsigned* err;
   const double* corr;        // [N * 12] pixel-exact corrections (dB, d grad B), or null
+  // certified decisions
+  const double* msc;         // [N * 15] sum_k |b_pk| / r^j, j = 1..5, per component (or null)
+  const double* fout;        // float-float pass partial sums of the current round
+  const PlanHdr* fplan;
+  const int32_t* fitem_off;
+  unsigned long long* stat_ties;   // near-tie decisions sent to re-evaluation (or null)
 };
 
 struct PlanArgs {
@@ -88,6 +116,8 @@ struct PlanArgs {
   int32_t* q_cnt_nxt;        // zeroed
   int32_t* act_cnt_nxt;
   int32_t* near_cnt_nxt;
+  int32_t* fq_cnt_nxt;       // zeroed (certified decisions; may be null)
+  int32_t* ref_cnt_nxt;
   int32_t* round_ctr;        // incremented per round
   unsigned long long* stat_queries;
   double* stat_pairs;

@@ -33,10 +33,11 @@ def test_every_declared_symbol_is_exported(native):
 
 
 def test_struct_layouts_match_header(native):
-    # dbie_options: 3 doubles, 2 int32, 3 doubles, 2 int32, 1 double = 72 bytes
-    assert ctypes.sizeof(native.dbie_options) == 72
+    # dbie_options: 3 doubles, 2 int32, 3 doubles, 2 int32, 2 doubles = 80 bytes
+    assert ctypes.sizeof(native.dbie_options) == 80
     assert ctypes.sizeof(native.dbie_solve_out) == 8 * 8 + 8
-    assert ctypes.sizeof(native.dbie_stats) == 56
+    # dbie_stats: int64, 4 doubles, 2 int64, int64, 2 doubles = 80 bytes
+    assert ctypes.sizeof(native.dbie_stats) == 80
 
 
 def test_default_options(native):
@@ -45,6 +46,7 @@ def test_default_options(native):
     assert o.lambda_mode == native.DBIE_LAMBDA_PER_COMPONENT
     assert o.precision == native.DBIE_PREC_MIXED
     assert o.near_z < 0 and o.simplex_step == 0.0 and o.g_scale == 0.0 and o.w_g == 1.0
+    assert o.certify == 0.02
     assert native.dbie_version().startswith("dbie-gb300")
 
 

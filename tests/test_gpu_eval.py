@@ -47,8 +47,9 @@ def random_points(mag, n, seed, zlo=0.5, zhi=20.0, lam=0.3):
 def run_eval(dbie, mag, xyz, lam, precision, near_z=-1.0):
     f = dbie.DBIEField.from_magnetogram(mag)
     opt = dbie.Options(precision=precision, near_z=near_z)
-    r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True, dlam=True, objective=True,
-               options=opt)
+    # (the float-float form, precision 2, evaluates B, its gradient and the objective only)
+    r = f.eval(torch.from_numpy(xyz), torch.from_numpy(lam), grad=True, dlam=precision != 2,
+               objective=True, options=opt)
     torch.cuda.synchronize()
     out = {k: v.cpu().numpy() for k, v in r.items()}
     f.close()
@@ -97,6 +98,41 @@ def test_eval_large_lambda_r(dbie):
     rb = check_B(got["B"], B, sB)
     assert rb["bad"].size == 0, rb
     assert check_grad(got["gradB"], G, sG[:, :, None])["ok"]
+
+
+def test_eval_lambda_r_at_search_limit(dbie):
+    """lambda r up to ~280 rad, above the largest lambda r the searches reach on the workloads
+    (about 175 rad on ll128: |lambda| <= 0.97 at distances to 185 px; about 275 rad on ar512:
+    |lambda| <= 0.48 at distances to 570 px).  In the mixed form the angle theta = lambda r is
+    itself an FP32 value (r from the SFU reciprocal square root, 1.25e-7 relative, times lambda),
+    so sin and cos carry a phase error of about 1.5e-7 |theta| on top of the SFU's own (which
+    scales its argument by 1/(2 pi) in FP32: 1.1e-7 |theta| measured beyond pi).  An argument
+    reduction before the SFU would not remove the first part, so the mixed form's floor relative
+    to the absolute-value sum is stated as 1e-6 max(1, theta_max / 100) for a point whose largest
+    angle is theta_max; the float-float form, which carries theta and its reduction in
+    float-float, stays within 1e-11 of the absolute-value sum here."""
+    mag = random_mag(96, 96, 13)
+    rng = np.random.default_rng(14)
+    n = 300
+    xyz = np.stack([rng.uniform(0, 95, n), rng.uniform(0, 95, n), rng.uniform(1.0, 30.0, n)],
+                   1).astype(np.float32)
+    lam = rng.uniform(1.5, 2.1, (n, 3)).astype(np.float32) * rng.choice([-1, 1], (n, 3))
+    lam = lam.astype(np.float32)
+    jj, ii = np.mgrid[0:96, 0:96]
+    rmax = np.sqrt(np.maximum(xyz[:, 0], 95 - xyz[:, 0]) ** 2 +
+                   np.maximum(xyz[:, 1], 95 - xyz[:, 1]) ** 2 + xyz[:, 2] ** 2)
+    assert (np.abs(lam).max(axis=1) * rmax).max() > 270
+    got = run_eval(dbie, mag, xyz, lam, 0)
+    B, G, _ = oracle.field(oracle_boundary(mag), xyz.astype(np.float64), lam.astype(np.float64))
+    sB, sG = abs_scales(mag, xyz, lam)
+    theta_max = np.abs(lam).max(axis=1) * rmax
+    grow = np.maximum(1.0, theta_max / 100.0)[:, None]
+    rb = check_B(got["B"], B, sB * grow)
+    print(f"lambda r to {theta_max.max():.0f}: mixed max |dB| / S = {rb['max_err_over_S']:.2e}")
+    assert rb["bad"].size == 0, rb
+    assert check_grad(got["gradB"], G, sG[:, :, None])["ok"]
+    ff = run_eval(dbie, mag, xyz, lam, dbie._native.DBIE_PREC_FLOAT_FLOAT)
+    assert (np.abs(ff["B"] - B) / sB).max() <= 1e-11
 
 
 def test_near_field_fp64_correction(dbie):
