@@ -129,31 +129,33 @@ __global__ void __launch_bounds__(FF_NT) g1_ff_kernel(const G1Args a) {
         const D Y = D{ff_load(sx, 1, 0, k), ff_load(sx, 1, 1, k)};
         const D dx = ff::sub(xq, X);
         const D dy = ff::sub(yq, Y);
-        const D r2 = ff::add(ff::add(ff::mul(dx, dx), ff::mul(dy, dy)), z2);
+        // (products that feed a further float-float operation stay unnormalised: mul_nr)
+        const D r2 = ff::add(ff::add(ff::mul_nr(dx, dx), ff::mul_nr(dy, dy)), z2);
         D r, ri;
         ff::sqrt_rsqrt(r2, r, ri);
-        const D ri2 = ff::mul(ri, ri);
-        const D ri3 = ff::mul(ri2, ri);
+        const D ri2 = ff::mul_nr(ri, ri);
+        const D ri3 = ff::mul_nr(ri2, ri);
         D u[NL], c[NL];
 #pragma unroll
         for (int l = 0; l < NL; ++l) {
-          const D th = ff::mul(lam[l], r);
+          const D th = ff::mul_nr(lam[l], r);
           D s;
           ff::sincos_ds(th, s_tab, s, c[l]);
-          u[l] = ff::add(ff::mul(th, s), c[l]);
+          u[l] = ff::add(ff::mul_nr(th, s), c[l]);
         }
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           const int lp = TIED ? 0 : p;
-          const D rb = ff::mul(ri3, D{ff_load(sx, 2 + p, 0, k), ff_load(sx, 2 + p, 1, k)});
-          acc[p * NS] = ff::add(acc[p * NS], ff::mul(u[lp], rb));
+          const D rb = ff::mul_nr(ri3, D{ff_load(sx, 2 + p, 0, k), ff_load(sx, 2 + p, 1, k)});
+          ff::acc_add(acc[p * NS], ff::mul_nr(u[lp], rb));
           if constexpr (has_grad(VAR)) {
             // psi b = (lambda^2 cos(lambda r) - 3 u / r^2) b / r^3
-            const D w = ff::sub(ff::mul(lam2[lp], c[lp]), ff::mul_f(ff::mul(u[lp], ri2), 3.0f));
-            const D t1 = ff::mul(w, rb);
-            acc[p * NS + 1] = ff::add(acc[p * NS + 1], t1);
-            acc[p * NS + 2] = ff::add(acc[p * NS + 2], ff::mul(t1, dx));
-            acc[p * NS + 3] = ff::add(acc[p * NS + 3], ff::mul(t1, dy));
+            const D w = ff::sub(ff::mul_nr(lam2[lp], c[lp]),
+                                ff::mul_f_nr(ff::mul_nr(u[lp], ri2), 3.0f));
+            const D t1 = ff::mul_nr(w, rb);
+            ff::acc_add(acc[p * NS + 1], t1);
+            ff::acc_add(acc[p * NS + 2], ff::mul_nr(t1, dx));
+            ff::acc_add(acc[p * NS + 3], ff::mul_nr(t1, dy));
           }
         }
       }
