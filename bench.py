@@ -34,6 +34,8 @@ METRIC = ("point×boundary pair evals/s and solve time at ≤1e-5 rel err vs FP6
 WORKLOAD = "ll128: Low&Lou n=1 m=1 l=0.3 Phi=pi/4, 128x128 boundary, 64x64x32 points (131072)"
 SMS, MUFU_PER_SM_CLK, MAX_SM_MHZ = 152, 16, 2070.0
 MUFU_PER_PAIR = 7           # objective variant, one lambda per component: rsqrt + 3 x (sin, cos)
+FP32_PER_SM_CLK = 124       # measured FP32 FMA-pipe rate per SM and clock (of 128 lanes)
+FF_FP32_PER_PAIR = 727      # float-float objective sums: FP32 operations per point-pixel pair
 FP32_PER_PAIR = 44
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one objective launch, the first
 # simplex round of this workload (131,072 queries x 16,384 pixels), from one ncu capture of the
@@ -292,6 +294,15 @@ def run_ours(args):
                    "parallelism": f"replicas x{world} (points are independent)",
                    "launch_configs": tuned},
         "solve_ms": step_ms,
+        "roofline_float_float": {
+            "bound": "alu", "pipe": "FP32 (FMA)", "kernel": "g1_ff_kernel (float-float "
+            "re-evaluation of near-tied simplex decisions)",
+            "achieved": (stats[-1]["ff_pairs"] * FF_FP32_PER_PAIR /
+                         (sum(s["ff_ms"] for s in stats) / args.steps / 1e3) / 1e12)
+            if any(s["ff_ms"] for s in stats) else None,
+            "peak": SMS * FP32_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12, "unit": "T FP32-op/s",
+            "per_pair": {"fp32": FF_FP32_PER_PAIR, "mufu": 1},
+            "peak_source": "152 SMs x 124 FP32 ops/clk/SM (measured per-clock rate) x 2070 MHz"},
         "certified_decisions": {
             "near_ties_per_step": stats[-1]["ties"],
             "near_tie_frac_of_evals": stats[-1]["ties"] / max(1, q),
@@ -318,6 +329,8 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": wall,
     }
+    rf = line["roofline_float_float"]
+    rf["frac"] = rf["achieved"] / rf["peak"] if rf["achieved"] else None
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_form"] = fp64_compare(w, args.fp64_points, dev)
         line["quasi_newton"] = method_compare(w, dev)

@@ -94,7 +94,9 @@ typedef struct {
                           from the point's absolute-value sums) re-evaluates those values in the
                           float-float form before the step is taken, so that the search takes the
                           decisions of sums accurate to ~1e-13 (those of the FP64 form up to its
-                          own rounding).  0 disables; default 0.02 (the largest measured gap of a
+                          own rounding); at the end, every point whose final B the bound does not
+                          certify to 1e-5 relative (the cancellation-dominated points) gets its B
+                          again in float-float at lambda*.  0 disables; default 0.02 (the largest measured gap of a
                           decision that the FP32-term sums flipped was 0.009 times that sum of
                           bounds).  Not used by the FP64 form or the quasi-Newton search. */
 } dbie_options;
@@ -125,6 +127,8 @@ typedef struct {
   int64_t ties;            /* certified decisions: near ties sent to float-float re-evaluation */
   double refine_pairs;     /* their point x pixel pairs (float-float form) */
   double refine_ms;        /* CUDA-event time of the float-float passes (while profiling) */
+  int64_t b_refined;       /* certified decisions: points whose final B the error bound did not
+                              certify to 1e-5 relative, re-evaluated in float-float at lambda* */
 } dbie_stats;
 
 /* Fill `opt` with the defaults listed above. */

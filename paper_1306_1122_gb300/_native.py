@@ -44,7 +44,8 @@ class dbie_stats(ctypes.Structure):
                 ("pair_evals", ctypes.c_double), ("objective_pairs", ctypes.c_double),
                 ("objective_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
                 ("queries", ctypes.c_int64), ("ties", ctypes.c_int64),
-                ("refine_pairs", ctypes.c_double), ("refine_ms", ctypes.c_double)]
+                ("refine_pairs", ctypes.c_double), ("refine_ms", ctypes.c_double),
+                ("b_refined", ctypes.c_int64)]
 
 
 class DBIEError(RuntimeError):

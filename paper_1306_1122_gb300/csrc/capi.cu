@@ -165,6 +165,8 @@ struct dbie_ctx {
   DBuf t32, t64, tff, prob, err, misc;
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
+  DBuf trace;                     // DBIE_TRACE_ITEMS builds: item timeline of the last pass
+  int64_t trace_items = 0;
   DBuf tv32, tv64, probv;         // noise-variance tiles and their problem descriptor
   DBuf b0raw;                     // the magnetogram as given (3 x npix float32), for restaging
   DBuf vtmp;                      // per-quadrature-point adjoint before the gather to nodes
@@ -329,7 +331,7 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   const KernelRef k = ffp ? g1_ref_ff(var, tied) : g1_ref(c, var, tied, fp64);
   const int grid = persistent_grid(k, c->device);
   const int64_t nblk = (n + k.qper - 1) / k.qper;
-  const int64_t target = 2LL * grid;
+  const int64_t target = std::max<int64_t>(1, (int64_t)grid * DBIE_SPLIT_TARGET_PCT / 100);
   int64_t nsplit = 1;
   if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, c->ntiles);
   const int64_t nitems = nblk * nsplit;
@@ -352,6 +354,12 @@ dbie_status pass_single(dbie_ctx* c, int var, bool fp64, const dbie_options& o, 
   a.qlam = c->qlam.as<Lam4>();
   a.out = c->out.as<double>();
   a.err = c->err.as<unsigned>();
+#if DBIE_TRACE_ITEMS
+  DBIE_TRY(ensure(c->trace, sizeof(unsigned long long) * 3 * nitems));
+  CUDA_TRY(cudaMemsetAsync(c->trace.p, 0, sizeof(unsigned long long) * 3 * nitems, s));
+  a.trace = c->trace.as<unsigned long long>();
+  c->trace_items = nitems;
+#endif
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->profiling) {
     e0 = take_event(c);
@@ -489,7 +497,7 @@ void dbie_destroy(dbie_ctx* c) {
   for (DBuf* b : {&c->t32, &c->t64, &c->tff, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
                   &c->tv64, &c->probv, &c->b0raw, &c->vtmp, &c->pxe_corr, &c->pxe_pos,
-                  &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins})
+                  &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins, &c->trace})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -1609,6 +1617,42 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (c->pinned[0] == 0 && c->pinned[1] == 0) break;
     if (launches >= max_launches) return fail(DBIE_EINTERNAL, "lambda-search rounds did not terminate");
   }
+  // Certified B: the final field of every point whose error bound does not certify 1e-5
+  // relative (the cancellation-dominated points) again, in float-float at lambda* (side 0 is the
+  // current side after an even number of rounds).
+  if (cert) {
+    const KernelRef kv = g1_ref_ff(VAR_V, tied);
+    CUDA_TRY(cudaMemsetAsync(b.fq_cnt[0].p, 0, sizeof(int32_t) * nprob, s));
+    CUDA_TRY(cudaMemsetAsync(&ctrl->ref_cnt[0], 0, sizeof(int32_t), s));
+    launch_certb_flag(sa[0], 1e-5, (int)std::min<int64_t>((N + 127) / 128, 8LL * c->sm_count), s);
+    PlanArgs pf{};
+    pf.probs = b.probs.as<ProbDesc>();
+    pf.nprob = nprob;
+    pf.qper = kv.qper;
+    pf.target_items = std::max(1, 2 * persistent_grid(kv, c->device));
+    pf.nsplit_cap = 1 << 20;
+    pf.q_cnt_cur = b.fq_cnt[0].as<int32_t>();
+    pf.q_cnt_pass = b.fq_cnt_pass.as<int32_t>();
+    pf.item_off = b.fitem_off.as<int32_t>();
+    pf.plan = &ctrl->fplan;
+    pf.work = &ctrl->fwork;
+    launch_plan_round(pf, s);
+    G1Args gf{};
+    gf.probs = b.probs.as<ProbDesc>();
+    gf.nprob = nprob;
+    gf.plan = &ctrl->fplan;
+    gf.item_off = b.fitem_off.as<int32_t>();
+    gf.q_cnt = b.fq_cnt_pass.as<int32_t>();
+    gf.work = &ctrl->fwork;
+    gf.qpos = b.fpos[0].as<float4>();
+    gf.qlam = b.flam[0].as<Lam4>();
+    gf.out = b.fout.as<double>();
+    gf.err = c->err.as<unsigned>();
+    DBIE_TRY(launch_kernel(kv, persistent_grid(kv, c->device), &gf, s));
+    launch_certb_apply(sa[0], nm_grid, s);
+    CUDA_TRY(cudaGetLastError());
+    DBIE_TRY(check_device_error(c, s));
+  }
   // Statistics and outputs.
   SolveCtrl hc;
   CUDA_TRY(cudaMemcpy(&hc, ctrl, sizeof hc, cudaMemcpyDeviceToHost));
@@ -1616,6 +1660,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   c->stats.queries += (int64_t)hc.stat_queries;
   c->stats.ties += (int64_t)hc.stat_ties;
   c->stats.refine_pairs += hc.stat_ff_pairs;
+  if (cert) c->stats.b_refined += hc.ref_cnt[0];
   if (c->profiling) {
     c->stats.pair_evals += hc.stat_pairs;
     c->stats.objective_pairs += hc.stat_pairs;
@@ -1676,6 +1721,20 @@ dbie_status dbie_solve_batched(int32_t nprob, dbie_ctx* const* ctxs, const int64
   return solve_impl(nprob, ctxs, n, xyz, opt, lambda_init, mem_kind, out,
                     static_cast<cudaStream_t>(stream));
 }
+
+#if DBIE_TRACE_ITEMS
+// Debugging aid of DBIE_TRACE_ITEMS builds (not part of the ABI): copies the item timeline of the
+// context's last single pair-sum pass (3 uint64 per item: start ns, end ns, SM | CTA << 16) to
+// host memory and returns the item count, or -1.
+int64_t dbie_debug_item_trace(dbie_ctx* c, unsigned long long* dst, int64_t max_items) {
+  if (!c || !dst || !c->trace.p) return -1;
+  const int64_t n = std::min<int64_t>(max_items, c->trace_items);
+  if (cudaMemcpy(dst, c->trace.p, sizeof(unsigned long long) * 3 * n, cudaMemcpyDeviceToHost) !=
+      cudaSuccess)
+    return -1;
+  return n;
+}
+#endif
 
 dbie_status dbie_set_profiling(dbie_ctx* c, int32_t enable) {
   if (!c) return fail(DBIE_EINVAL, "ctx is NULL");

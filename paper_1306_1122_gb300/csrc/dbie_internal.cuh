@@ -119,6 +119,7 @@ struct G1Args {
   const Lam4* qlam;         // [slot] lambda_x, lambda_y, lambda_z
   double* out;              // per work item a chunk of nsum * qper partial sums (see out_index)
   unsigned* err;
+  unsigned long long* trace; // DBIE_TRACE_ITEMS builds: per item start, end (ns) and SM (or null)
 };
 
 // Position of partial sum s of the query with local index j (within its problem) for split

@@ -122,5 +122,7 @@ void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_nm_refine(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, int grid,
                 cudaStream_t s);
+void launch_certb_flag(const SolveArgs& a, double rel, int grid, cudaStream_t s);
+void launch_certb_apply(const SolveArgs& a, int grid, cudaStream_t s);
 
 }  // namespace dbie

@@ -30,6 +30,9 @@ namespace dbie {
 #ifndef DBIE_GROUP_UNROLL
 #define DBIE_GROUP_UNROLL 16
 #endif
+#ifndef DBIE_TRACE_ITEMS
+#define DBIE_TRACE_ITEMS 0   // 1: g1 work items record their start, end and SM (G1Args::trace)
+#endif
 #ifndef DBIE_PACKED
 #define DBIE_PACKED 1     // FP32 pair sums on pixel pairs packed in f32x2 (0: one pixel per op)
 #endif
@@ -237,6 +240,9 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
     const int it = s_item;
     __syncthreads();  // every thread has read s_item before it can be overwritten
     if (it >= plan.nitems) break;
+#if DBIE_TRACE_ITEMS
+    const unsigned long long t_item0 = global_ns();
+#endif
     // fault injection: the CTA holding item 0 (its first item) never issues a tile copy
     ring.skip_issue = a.fault == 1 && it == 0;
 
@@ -453,6 +459,16 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
         a.out[((int64_t)it * NSUM + s) * Q + (tid + u * NT)] = v;
       }
     }
+#if DBIE_TRACE_ITEMS
+    // debugging aid (off by default): the item's start and end time and its SM
+    if (tid == 0 && a.trace) {
+      unsigned smid;
+      asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+      a.trace[3 * (int64_t)it] = t_item0;
+      a.trace[3 * (int64_t)it + 1] = global_ns();
+      a.trace[3 * (int64_t)it + 2] = smid | ((unsigned long long)blockIdx.x << 16);
+    }
+#endif
   }
   if (tid == 0) ring.drain();
 }

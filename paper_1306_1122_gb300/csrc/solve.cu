@@ -840,6 +840,69 @@ void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* ms
   if (N > 0) msc_kernel<<<grid, 128, 0, s>>>(probs, N, ppos, msc);
 }
 
+// ------------------------------------------------------------------ certified B ----
+// Worst-case error of the mixed form's B at lambda (the B part of mixed_phi_bound): per
+// component z (A0 M3 + A1 |lambda| M2 + A2 lambda^2 M1); returns the Euclidean norm.
+__device__ __forceinline__ double mixed_b_bound(const double* M, const double lam[3], int dim,
+                                                double z) {
+  double s = 0.0;
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const double L = fabs(dim == 1 ? lam[0] : lam[p]);
+    const double* m = M + 5 * p;
+    const double d = z * (BND_A0 * m[2] + BND_A1 * L * m[1] + BND_A2 * L * L * m[0]);
+    s += d * d;
+  }
+  return sqrt(s);
+}
+
+// After a certified search: every point whose final B the bound does not certify to `rel`
+// relative (the cancellation-dominated points) queues a float-float value query at lambda* on
+// side cur and joins cur's waiting list.
+__global__ void certb_flag_kernel(const SolveArgs a, double rel) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < a.N;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const double lam[3] = {a.res_lam[3 * g], a.res_lam[3 * g + 1], a.res_lam[3 * g + 2]};
+    const double* B = a.res_B + 3 * g;
+    const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+    if (!(mixed_b_bound(a.msc + 15 * g, lam, a.o.dim, (double)pos.z) > rel * nB)) continue;
+    const ProbDesc& pd = a.probs[pidx];
+    const int base = atomic_add_warp(a.cur.fq_cnt + pidx, 1);
+    const int64_t slot = pd.qff_off + base;
+    a.cur.fpos[slot] = pos;
+    a.cur.flam[slot] = make_lam4(lam[0], lam[1], lam[2]);
+    SI(a, I_RSLOT, g) = (int32_t)slot;
+    a.cur.ref[atomic_add_warp(a.cur.ref_cnt, 1)] = (int32_t)g;
+  }
+}
+
+// B of the queued points from the float-float value sums (3 per query).
+__global__ void certb_apply_kernel(const SolveArgs a) {
+  const int n = *a.cur.ref_cnt;
+  const PlanHdr hf = *a.fplan;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int64_t g = a.cur.ref[i];
+    const float4 pos = a.ppos[g];
+    const int pidx = __float_as_int(pos.w);
+    const ProbDesc& pd = a.probs[pidx];
+    const double z = (double)pos.z;
+    const int64_t j = (int64_t)SI(a, I_RSLOT, g) - pd.qff_off;
+    const double* corr = corr_of(a, pd, g, z);
+    for (int p = 0; p < 3; ++p)
+      a.res_B[3 * g + p] = z * gather_sum(a.fout, hf, a.fitem_off, pidx, j, 3, p) +
+                           (corr ? corr[p] : 0.0);
+  }
+}
+
+void launch_certb_flag(const SolveArgs& a, double rel, int grid, cudaStream_t s) {
+  certb_flag_kernel<<<grid, 128, 0, s>>>(a, rel);
+}
+void launch_certb_apply(const SolveArgs& a, int grid, cudaStream_t s) {
+  certb_apply_kernel<<<grid, 128, 0, s>>>(a);
+}
+
 }  // namespace dbie
 
 // ======================================================= objective gradient, quasi-Newton ----

@@ -36,8 +36,8 @@ def test_struct_layouts_match_header(native):
     # dbie_options: 3 doubles, 2 int32, 3 doubles, 2 int32, 2 doubles = 80 bytes
     assert ctypes.sizeof(native.dbie_options) == 80
     assert ctypes.sizeof(native.dbie_solve_out) == 8 * 8 + 8
-    # dbie_stats: int64, 4 doubles, 2 int64, int64, 2 doubles = 80 bytes
-    assert ctypes.sizeof(native.dbie_stats) == 80
+    # dbie_stats: int64, 4 doubles, 2 int64, int64, 2 doubles, int64 = 88 bytes
+    assert ctypes.sizeof(native.dbie_stats) == 88
 
 
 def test_default_options(native):
