@@ -63,7 +63,8 @@ def parse_args():
     ap.add_argument("--workload", default="ll128", choices=["ll128", "batch64"])
     ap.add_argument("--max-points", type=int, default=200_000,
                     help="batch64: upper end of the per-problem point count")
-    ap.add_argument("--case", default=None, choices=["exact_near_field", "float_float"],
+    ap.add_argument("--case", default=None,
+                    choices=["exact_near_field", "float_float", "implicit_adjoint"],
                     help="a single-kernel-family case for profiling instead of the step")
     return ap.parse_args()
 
@@ -921,12 +922,55 @@ def run_case_float_float():
                       "pairs_per_s": len(pts) * w.mag.npix / (ms / 1e3)}))
 
 
+def run_case_implicit_adjoint():
+    """Profiling case of the gradient through the lambda search on the ll128 workload: tuned
+    launch shapes, the simplex search of all 131,072 points, then dbie_vjp_implicit at its lambda
+    (once to warm up, three times timed with CUDA events, minimum) and once more inside the NVTX
+    range "implicit_adjoint" (for ncu --nvtx-include); prints the times and the chosen launch
+    configurations."""
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ll128(with_truth=False)
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    cfg = f.autotune()
+    pts = torch.from_numpy(w.points).cuda()
+    r = f.solve(pts)
+    gB = 2.0 * r["B"]
+
+    def timed(fn):
+        fn()
+        best = 1e30
+        for _ in range(3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            best = min(best, ev[0].elapsed_time(ev[1]))
+        return best
+
+    out = {"implicit_adjoint_ms": timed(lambda: f.vjp_implicit(pts, r["lam"], gB)),
+           "hessian_ms": timed(lambda: f.hessian(pts, r["lam"])),
+           "fixed_lambda_adjoint_ms": timed(lambda: f.vjp(pts, r["lam"], gB, glam=False))}
+    torch.cuda.nvtx.range_push("implicit_adjoint")
+    f.vjp_implicit(pts, r["lam"], gB)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    f.close()
+    print(json.dumps({"case": "implicit_adjoint", "workload": "ll128 (131072 points, 128^2 "
+                      "pixels), simplex lambda", "config": [int(x) for x in cfg], **out}))
+
+
 def main():
     args = parse_args()
     if args.case == "exact_near_field":
         run_case_exact_near_field()
     elif args.case == "float_float":
         run_case_float_float()
+    elif args.case == "implicit_adjoint":
+        run_case_implicit_adjoint()
     elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch64":

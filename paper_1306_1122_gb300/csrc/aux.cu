@@ -273,13 +273,16 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
           const int lp = TIED ? 0 : p;
           // FP32 contributions exactly as the pair-sum kernel added them (products of two
           // FP32 factors, exact in FP64), replaced by the FP64 terms.
-          c[p * NS] += t64.t0[p] - (double)t32.u[lp] * (double)t32.rb[p];
+          if constexpr (has_hess(VAR)) c[p * NS] += t64.t0[p] - (double)t32.t0[p];
+          else c[p * NS] += t64.t0[p] - (double)t32.u[lp] * (double)t32.rb[p];
           if constexpr (has_grad(VAR)) {
             c[p * NS + 1] += t64.t1[p] - (double)t32.t1[p];
             c[p * NS + 2] += t64.t1[p] * t64.dx - (double)t32.t1[p] * (double)t32.dx;
             c[p * NS + 3] += t64.t1[p] * t64.dy - (double)t32.t1[p] * (double)t32.dy;
           }
-          if constexpr (has_dlam(VAR))
+          if constexpr (has_hess(VAR))
+            c[p * NS + idx_sl(VAR)] += t64.tl[p] - (double)t32.tl[p];
+          else if constexpr (has_dlam(VAR))
             c[p * NS + idx_sl(VAR)] += t64.tl[p] - (double)t32.cr[lp] * (double)b32[p];
           if constexpr (has_newton(VAR)) {
             c[p * NS + IDX_TX] += t64.t0[p] * t64.dx - (double)t32.t0[p] * (double)t32.dx;

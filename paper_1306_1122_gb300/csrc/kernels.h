@@ -10,16 +10,19 @@ namespace dbie {
 
 // Launch configurations of the pair-sum kernels: points (or pixels) per thread, CTA size, and a
 // minimum number of resident CTAs per SM (a register cap; 1 = none).  The autotuner picks one.
+// The two capped shapes depend on the variant: the Hessian pass (30 compensated sums, ~250
+// registers uncapped) is capped at 3 or 4 CTAs of 128 threads (168 or 128 registers), the others
+// at 6 or 7 (80 or 72 registers).
 constexpr int NCFG = 6;
 constexpr int NSTAGE = 3;
 struct LaunchCfg { int p, nt, minb; };
-__host__ __device__ constexpr LaunchCfg cfg_of(int c) {
+__host__ __device__ constexpr LaunchCfg cfg_of(int c, int var = -1) {
   return c == 0 ? LaunchCfg{1, 128, 1}
        : c == 1 ? LaunchCfg{2, 128, 1}
        : c == 2 ? LaunchCfg{1, 256, 1}
-       : c == 3 ? LaunchCfg{1, 128, 6}
+       : c == 3 ? LaunchCfg{1, 128, var == VAR_HESS ? 3 : 6}
        : c == 4 ? LaunchCfg{1, 64, 1}
-                : LaunchCfg{1, 128, 7};
+                : LaunchCfg{1, 128, var == VAR_HESS ? 4 : 7};
 }
 
 struct KernelRef {

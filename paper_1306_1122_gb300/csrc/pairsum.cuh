@@ -130,14 +130,19 @@ __device__ __forceinline__ void accumulatev(V* acc, const TermsV<V, VAR, TIED>& 
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int lp = TIED ? 0 : p;
+    // (the Hessian pass adds the rounded products phi b and cos(lambda r) b / r, which its
+    // row-group form sums in pairs; the near-field correction subtracts the same values)
     if constexpr (is_nv(VAR)) acc[p * NS + 0] = vfma(t.ph[lp], t.t0[p], acc[p * NS + 0]);
+    else if constexpr (has_hess(VAR)) acc[p * NS + 0] = vadd(acc[p * NS + 0], t.t0[p]);
     else acc[p * NS + 0] = vfma(t.u[lp], t.rb[p], acc[p * NS + 0]);
     if constexpr (has_grad(VAR)) {
       acc[p * NS + 1] = vadd(acc[p * NS + 1], t.t1[p]);
       acc[p * NS + 2] = vfma(t.t1[p], t.dx, acc[p * NS + 2]);
       acc[p * NS + 3] = vfma(t.t1[p], t.dy, acc[p * NS + 3]);
     }
-    if constexpr (has_dlam(VAR))
+    if constexpr (has_hess(VAR))
+      acc[p * NS + idx_sl(VAR)] = vadd(acc[p * NS + idx_sl(VAR)], t.tl[p]);
+    else if constexpr (has_dlam(VAR))
       acc[p * NS + idx_sl(VAR)] = vfma(t.cr[lp], b[p], acc[p * NS + idx_sl(VAR)]);
     if constexpr (has_newton(VAR)) {
       acc[p * NS + IDX_TX] = vfma(t.t0[p], t.dx, acc[p * NS + IDX_TX]);
@@ -148,6 +153,34 @@ __device__ __forceinline__ void accumulatev(V* acc, const TermsV<V, VAR, TIED>& 
       acc[p * NS + IDX_UX] = vfma(t.tl[p], t.dx, acc[p * NS + IDX_UX]);
       acc[p * NS + IDX_UY] = vfma(t.tl[p], t.dy, acc[p * NS + IDX_UY]);
     }
+  }
+}
+// Hessian-pass sums of two pixel pairs of one boundary row (one 4-pixel group, packed): the
+// pixels share dy, so each dy-weighted sum (Sy, Ty, Uy) takes one product of the two terms' sum
+// instead of two products: Sy += (t1a + t1b) dy with S1 += t1a + t1b, and likewise Ty with
+// S0 = sum phi b and Uy with Sl = sum cos(lambda r) b / r.  17 instead of 20 operations per
+// component and group.
+template <typename V, bool TIED, int NS>
+__device__ __forceinline__ void accumulate_hess_row(V* acc, const TermsV<V, VAR_HESS, TIED>& ta,
+                                                    const TermsV<V, VAR_HESS, TIED>& tb,
+                                                    const V (&ba)[3], const V (&bb)[3], V dy) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int lp = TIED ? 0 : p;
+    V* a = acc + p * NS;
+    const V s0 = vadd(ta.t0[p], tb.t0[p]);
+    a[0] = vadd(a[0], s0);
+    a[IDX_TY] = vfma(s0, dy, a[IDX_TY]);
+    a[IDX_TX] = vfma(tb.t0[p], tb.dx, vfma(ta.t0[p], ta.dx, a[IDX_TX]));
+    const V s1 = vadd(ta.t1[p], tb.t1[p]);
+    a[1] = vadd(a[1], s1);
+    a[3] = vfma(s1, dy, a[3]);
+    a[2] = vfma(tb.t1[p], tb.dx, vfma(ta.t1[p], ta.dx, a[2]));
+    const V sl = vadd(ta.tl[p], tb.tl[p]);
+    a[idx_sl(VAR_HESS)] = vadd(a[idx_sl(VAR_HESS)], sl);
+    a[IDX_UY] = vfma(sl, dy, a[IDX_UY]);
+    a[IDX_UX] = vfma(tb.tl[p], tb.dx, vfma(ta.tl[p], ta.dx, a[IDX_UX]));
+    a[IDX_Q] = vfma(tb.sn[lp], bb[p], vfma(ta.sn[lp], ba[p], a[IDX_Q]));
   }
 }
 template <int VAR, bool TIED, int NS>
@@ -325,6 +358,20 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
                 dyz2[u] = pack2(dyz, dyz);
               }
             }
+            if constexpr (ROWS && has_hess(VAR)) {
+#pragma unroll
+              for (int u = 0; u < P; ++u) {
+                TermsV<f32x2, VAR, TIED> tm[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                  f32x2 dx = vsub(q2[u].x, px2[h]);
+                  if constexpr (SPLIT) dx = vsub(dx, pxl2[h]);
+                  pair_angularv<f32x2, VAR, TIED>(q2[u], pair_geomv_dz<f32x2>(dx, dy2[u], dyz2[u]),
+                                                  b2[h], tm[h]);
+                }
+                accumulate_hess_row<f32x2, TIED, NS>(acc2[u], tm[0], tm[1], b2[0], b2[1], dy2[u]);
+              }
+            } else {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
@@ -343,6 +390,7 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
                 pair_angularv<f32x2, VAR, TIED>(q2[u], g, b2[h], tm);
                 accumulatev<f32x2, VAR, TIED, NS>(acc2[u], tm, b2[h]);
               }
+            }
             }
           }
 #pragma unroll
@@ -731,31 +779,49 @@ __device__ __forceinline__ void vjp7_body(const VjpArgs& a) {
                 dx = vsub(dx, pxl2[u]);
                 dy = vsub(dy, pyl2[u]);
               }
+              // A = W0 + W5 dx + W6 dy and B = W1 + W2 dx + W3 dy of the point record
+              auto wA = [&](const Real* w) {
+                return vfma(ld2(w + 6 * TILE), dy, vfma(ld2(w + 5 * TILE), dx, ld2(w)));
+              };
+              auto wB = [&](const Real* w) {
+                return vfma(ld2(w + 3 * TILE), dy, vfma(ld2(w + 2 * TILE), dx, ld2(w + TILE)));
+              };
               const f32x2 r2 = vfma(dx, dx, vfma(dy, dy, z2));
               const f32x2 ri = vrsqrt(r2);
               const f32x2 r = vmul(r2, ri);
               const f32x2 ri2 = vmul(ri, ri);
               const f32x2 ri3 = vmul(ri2, ri);
               const f32x2 m3ri2 = vmul(vconst<f32x2>(-3.f), ri2);
-              f32x2 ph[NL], ps[NL], cr[NL];
-#pragma unroll
-              for (int l = 0; l < NL; ++l) {
-                const f32x2 th = vmul(lam[l], r);
+              if constexpr (TIED) {
+                // one lambda: phi, psi and cos(lambda r) / r are shared by the three components
+                const f32x2 th = vmul(lam[0], r);
                 const f32x2 sn = vsin(th), c = vcos(th);
                 const f32x2 uu = vfma(th, sn, c);
-                ph[l] = vmul(uu, ri3);
-                ps[l] = vmul(vfma(uu, m3ri2, vmul(lam2[l], c)), ri3);
-                cr[l] = vmul(c, ri);
-              }
+                const f32x2 ph = vmul(uu, ri3);
+                const f32x2 ps = vmul(vfma(uu, m3ri2, vmul(lam2[0], c)), ri3);
+                const f32x2 cr = vmul(c, ri);
 #pragma unroll
-              for (int p = 0; p < 3; ++p) {
-                const int l = TIED ? 0 : p;
-                const Real* w = W + p * VJP7_NW * TILE + k;
-                const f32x2 aph = vfma(ld2(w + 6 * TILE), dy, vfma(ld2(w + 5 * TILE), dx, ld2(w)));
-                const f32x2 aps =
-                    vfma(ld2(w + 3 * TILE), dy, vfma(ld2(w + 2 * TILE), dx, ld2(w + TILE)));
-                acc2[u][p] = vfma(ph[l], aph,
-                                  vfma(ps[l], aps, vfma(ld2(w + 4 * TILE), cr[l], acc2[u][p])));
+                for (int p = 0; p < 3; ++p) {
+                  const Real* w = W + p * VJP7_NW * TILE + k;
+                  acc2[u][p] =
+                      vfma(ph, wA(w), vfma(ps, wB(w), vfma(ld2(w + 4 * TILE), cr, acc2[u][p])));
+                }
+              } else {
+                // per component: phi A + psi B + w4 cos / r with A = w0 + w5 dx + w6 dy and
+                // B = w1 + w2 dx + w3 dy, regrouped by the two factors u / r^3 and cos:
+                //   (u / r^3) (A - 3 B / r^2) + cos (lambda^2 B / r^3 + w4 / r),
+                // 13 operations per component instead of 14.
+#pragma unroll
+                for (int p = 0; p < 3; ++p) {
+                  const f32x2 th = vmul(lam[p], r);
+                  const f32x2 sn = vsin(th), c = vcos(th);
+                  const f32x2 uu = vfma(th, sn, c);
+                  const Real* w = W + p * VJP7_NW * TILE + k;
+                  const f32x2 A = wA(w), B = wB(w);
+                  const f32x2 T = vfma(m3ri2, B, A);
+                  const f32x2 G = vfma(vmul(lam2[p], ri3), B, vmul(ld2(w + 4 * TILE), ri));
+                  acc2[u][p] = vfma(vmul(uu, ri3), T, vfma(c, G, acc2[u][p]));
+                }
               }
             }
           }

@@ -7,7 +7,7 @@ namespace dbie {
 
 template <typename Real, int VAR, bool TIED, int CFG, bool ROWS = false>
 KernelRef g1_ref_t() {
-  constexpr LaunchCfg c = cfg_of(CFG);
+  constexpr LaunchCfg c = cfg_of(CFG, VAR);
   const void* fn;
   if constexpr (c.minb > 1)
     fn = (const void*)&g1_kernel_mb<Real, VAR, TIED, c.p, c.nt, NSTAGE, c.minb, ROWS>;

@@ -8,16 +8,19 @@
 //   dq/dl   : z l Sl, -z l Tx, -z l Ty, l Sl - z^2 l S0
 //   d2q/dl2 : z (Sl - l Q), -z (Tx + l^2 Ux), -z (Ty + l^2 Uy), (Sl - l Q) - z^2 (S0 + l^2 Sl)
 // (dS0/dl = l Sl, dS1/dl = -l S0, dSx/dl = -l Tx, dSl/dl = -Q, dTx/dl = l Ux).  Phi = f + w_g g
-// (Eq. 8, 9, 14) is evaluated on hyper-dual numbers v + a e1 + b e2 + c e1 e2 (e1^2 = e2^2 = 0;
-// Fike & Alonso 2011), which carry first and second derivatives exactly: seeding a and b with
-// dq/dl_j and dq/dl_k (and c with d2q/dl_j^2 when j = k) gives H_jk in c.
+// (Eq. 8, 9, 14) depends on lambda only through the twelve q, and q_m only on the lambda of its
+// own component, so with F = dPhi/dq, P = d2Phi/dq2 and the 12 x dim matrix D of dq/dlambda,
+//   grad_l Phi = D^T F,   H = D^T P D + diag_j(sum over q of component j of F d2q/dl_j^2).
+// F comes from the closed-form gradient of Phi (reverse mode, written out below), and P D from
+// the same gradient evaluated on dual numbers v + d e (e^2 = 0) with the tangent of q set to one
+// column of D: one evaluation per column (three, or one for a shared lambda).
 //
 // Gradient through the search: lambda* is a stationary point, grad_l Phi(lambda*; B0) = 0, so
 // d(lambda*)/dB0 = -H^-1 d(grad_l Phi)/dB0 and
 //   dL/dB0 = A^T gB - d/dB0 [v . grad_l Phi],  v = H^-1 dL/dl,  dL/dl_p = gB_p dB_p/dl_p.
 // The second term is a transposed sum over points of seven kernel functions per component with
-// per-point weights (vjp7_kernel); the weights come from Phi's derivatives with respect to the
-// twelve q (hyper-dual again: seed a with the change of q along v, b with one q at a time).
+// per-point weights (vjp7_kernel); the weights need F and P (D v) = sum_k v_k (P D)_k, which the
+// Hessian's columns already hold.
 #include "kernels.h"
 #include "solve.cuh"
 
@@ -25,53 +28,86 @@ namespace dbie {
 
 namespace {
 
-struct HD {
-  double v, a, b, c;
+// Dual number v + d e (e^2 = 0): a value and its derivative along one direction.
+struct Du {
+  double v, d;
 };
-__device__ __forceinline__ HD hd_k(double v) { return HD{v, 0.0, 0.0, 0.0}; }
-__device__ __forceinline__ HD operator+(HD x, HD y) {
-  return HD{x.v + y.v, x.a + y.a, x.b + y.b, x.c + y.c};
+__device__ __forceinline__ Du operator+(Du x, Du y) { return Du{x.v + y.v, x.d + y.d}; }
+__device__ __forceinline__ Du operator-(Du x, Du y) { return Du{x.v - y.v, x.d - y.d}; }
+__device__ __forceinline__ Du operator*(Du x, Du y) { return Du{x.v * y.v, fma(x.v, y.d, x.d * y.v)}; }
+__device__ __forceinline__ Du operator*(Du x, double s) { return Du{x.v * s, x.d * s}; }
+__device__ __forceinline__ Du dsqrt(Du x) {
+  const double r = sqrt(x.v);
+  return Du{r, x.d * (0.5 / r)};
 }
-__device__ __forceinline__ HD operator-(HD x, HD y) {
-  return HD{x.v - y.v, x.a - y.a, x.b - y.b, x.c - y.c};
-}
-__device__ __forceinline__ HD operator*(HD x, HD y) {
-  return HD{x.v * y.v, x.v * y.a + x.a * y.v, x.v * y.b + x.b * y.v,
-            x.v * y.c + x.a * y.b + x.b * y.a + x.c * y.v};
-}
-__device__ __forceinline__ HD scale(HD x, double s) { return HD{x.v * s, x.a * s, x.b * s, x.c * s}; }
-// g(x) with g(x.v) = g0, g'(x.v) = g1, g''(x.v) = g2
-__device__ __forceinline__ HD lift(HD x, double g0, double g1, double g2) {
-  return HD{g0, g1 * x.a, g1 * x.b, g1 * x.c + g2 * x.a * x.b};
-}
-__device__ __forceinline__ HD recip(HD x) {
+__device__ __forceinline__ Du drecip(Du x) {
   const double r = 1.0 / x.v;
-  return lift(x, r, -(r * r), 2.0 * r * r * r);
-}
-// Euclidean norm of a 3-vector; derivative parts 0 at the kink |x| = 0.
-__device__ __forceinline__ HD norm3(HD x0, HD x1, HD x2) {
-  const HD s = x0 * x0 + x1 * x1 + x2 * x2;
-  if (!(s.v > 0.0)) return hd_k(0.0);
-  const double r = sqrt(s.v);
-  return lift(s, r, 0.5 / r, -0.25 / (r * s.v));
+  return Du{r, -(x.d * (r * r))};
 }
 
-// Phi = f + w_g g of Eq. 8, 9 (J = curl B, Eq. 14) on hyper-dual B (3) and G (9, G[3p+j] =
-// dB_p/dx_j); f = 0 when |J||B| = 0, g = 0 when |B| = 0.
-__device__ HD objective_hd(const HD* B, const HD* G, double g_scale, double w_g) {
-  const HD Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
-  const HD D = G[0] + G[4] + G[8];
-  const HD Cx = Jy * B[2] - Jz * B[1];
-  const HD Cy = Jz * B[0] - Jx * B[2];
-  const HD Cz = Jx * B[1] - Jy * B[0];
-  const HD nJ = norm3(Jx, Jy, Jz), nB = norm3(B[0], B[1], B[2]), nC = norm3(Cx, Cy, Cz);
-  HD phi = hd_k(0.0);
-  if (nJ.v * nB.v > 0.0) phi = nC * recip(nJ * nB);
-  if (nB.v > 0.0) {
-    const HD aD = D.v < 0.0 ? scale(D, -1.0) : D;
-    phi = phi + scale(aD * recip(nB), g_scale * w_g);
+// Phi = f + w_g g of Eq. 8, 9 (J = curl B, Eq. 14) and its gradient F with respect to
+// q = (B (3), G (9, G[3p+j] = dB_p/dx_j)).  With C = J x B:
+//   f = |C| / (|J| |B|) (0 when |J||B| = 0),   g = g_scale |D| / |B| (0 when |B| = 0),
+//   df/dJ = B x C / (|C| |J| |B|) - f J / |J|^2,   df/dB = C x J / (|C| |J| |B|) - f B / |B|^2
+// (the |C| term 0 when |C| = 0), dg/dB = -g B / |B|^2, dg/dD = g_scale sign(D) / |B| (sign(0) =
+// +1), and J, D linear in G.  Evaluated on dual numbers (branches taken on the values): the
+// value parts are Phi and F, the derivative parts their derivatives along the tangent of q.
+__device__ void objective_grad_q(const Du* q, double g_scale, double w_g, Du& phi, Du* F) {
+  const Du* B = q;
+  const Du* G = q + 3;
+  const Du Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
+  const Du D = G[0] + G[4] + G[8];
+  const Du Cx = Jy * B[2] - Jz * B[1];
+  const Du Cy = Jz * B[0] - Jx * B[2];
+  const Du Cz = Jx * B[1] - Jy * B[0];
+  const Du sJ = Jx * Jx + Jy * Jy + Jz * Jz, sB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const Du sC = Cx * Cx + Cy * Cy + Cz * Cz;
+  const Du z0{0.0, 0.0};
+  const Du nJ = sJ.v > 0.0 ? dsqrt(sJ) : z0;
+  const Du nB = sB.v > 0.0 ? dsqrt(sB) : z0;
+  const Du nC = sC.v > 0.0 ? dsqrt(sC) : z0;
+  Du gB[3] = {z0, z0, z0}, gJ[3] = {z0, z0, z0}, gD = z0;
+  phi = z0;
+  if (nJ.v * nB.v > 0.0) {
+    const Du inv = drecip(nJ * nB);
+    const Du f = nC * inv;
+    phi = f;
+    if (nC.v > 0.0) {
+      const Du k = inv * drecip(nC);
+      gJ[0] = (B[1] * Cz - B[2] * Cy) * k;
+      gJ[1] = (B[2] * Cx - B[0] * Cz) * k;
+      gJ[2] = (B[0] * Cy - B[1] * Cx) * k;
+      gB[0] = (Cy * Jz - Cz * Jy) * k;
+      gB[1] = (Cz * Jx - Cx * Jz) * k;
+      gB[2] = (Cx * Jy - Cy * Jx) * k;
+    }
+    const Du fJ = f * drecip(sJ), fB = f * drecip(sB);
+    gJ[0] = gJ[0] - Jx * fJ;
+    gJ[1] = gJ[1] - Jy * fJ;
+    gJ[2] = gJ[2] - Jz * fJ;
+    for (int i = 0; i < 3; ++i) gB[i] = gB[i] - B[i] * fB;
   }
-  return phi;
+  if (nB.v > 0.0) {
+    const double gs = g_scale * w_g;
+    const Du rB = drecip(nB);
+    const Du aD = D.v < 0.0 ? D * -1.0 : D;
+    const Du g = (aD * rB) * gs;
+    phi = phi + g;
+    gD = rB * (D.v < 0.0 ? -gs : gs);
+    const Du gb = g * drecip(sB);
+    for (int i = 0; i < 3; ++i) gB[i] = gB[i] - B[i] * gb;
+  }
+  for (int i = 0; i < 3; ++i) F[i] = gB[i];
+  // G index 3p + j: Jx = G7 - G5, Jy = G2 - G6, Jz = G3 - G1, D = G0 + G4 + G8
+  F[3 + 0] = gD;
+  F[3 + 1] = z0 - gJ[2];
+  F[3 + 2] = gJ[1];
+  F[3 + 3] = gJ[2];
+  F[3 + 4] = gD;
+  F[3 + 5] = z0 - gJ[0];
+  F[3 + 6] = z0 - gJ[1];
+  F[3 + 7] = gJ[0];
+  F[3 + 8] = gD;
 }
 
 // q (value), dq/dlambda_p and d2q/dlambda_p^2 of one query from its 30 Hessian-pass sums;
@@ -101,33 +137,48 @@ __device__ void q_derivs(const double* S, double z, const double lam[3], double 
 
 __device__ __forceinline__ int comp_of(int m) { return m < 3 ? m : (m - 3) / 3; }
 
-// Phi, its gradient and its Hessian in lambda (dim 3: per component; dim 1: one shared lambda,
-// entry 0 only).
-__device__ void hessian_of(const double q[12], const double d1[12], const double d2[12], int dim,
-                           double g_scale, double w_g, double& phi, double grad[3], double H[9]) {
-  HD B[3], G[9];
+// Phi, its lambda-gradient and lambda-Hessian (DIM 3: per component; DIM 1: one shared lambda,
+// entry 0 only), with F = dPhi/dq and the columns P D of the Hessian's first term (PD[12 k + m]).
+template <int DIM>
+__device__ void hessian_cols(const double q[12], const double d1[12], const double d2[12],
+                             double g_scale, double w_g, double& phi, double grad[3], double H[9],
+                             double F[12], double PD[12 * DIM]) {
+#pragma unroll
   for (int i = 0; i < 9; ++i) H[i] = 0.0;
   grad[0] = grad[1] = grad[2] = 0.0;
-  for (int j = 0; j < dim; ++j)
-    for (int k = j; k < dim; ++k) {
-      for (int m = 0; m < 12; ++m) {
-        const int p = comp_of(m);
-        const bool sj = dim == 1 || p == j, sk = dim == 1 || p == k;
-        HD x = hd_k(q[m]);
-        x.a = sj ? d1[m] : 0.0;
-        x.b = sk ? d1[m] : 0.0;
-        x.c = (sj && sk) ? d2[m] : 0.0;
-        if (m < 3) B[m] = x;
-        else G[m - 3] = x;
-      }
-      const HD ph = objective_hd(B, G, g_scale, w_g);
-      H[3 * j + k] = ph.c;
-      H[3 * k + j] = ph.c;
-      if (j == k) {
-        grad[j] = ph.a;
-        phi = ph.v;
-      }
+#pragma unroll
+  for (int k = 0; k < DIM; ++k) {
+    Du x[12], ph, Fd[12];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) x[m] = Du{q[m], (DIM == 1 || comp_of(m) == k) ? d1[m] : 0.0};
+    objective_grad_q(x, g_scale, w_g, ph, Fd);
+    phi = ph.v;
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      F[m] = Fd[m].v;
+      PD[12 * k + m] = Fd[m].d;
     }
+  }
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    double gj = 0.0, cj = 0.0;
+#pragma unroll
+    for (int m = 0; m < 12; ++m)
+      if (DIM == 1 || comp_of(m) == j) {
+        gj += d1[m] * F[m];
+        cj += d2[m] * F[m];
+      }
+    grad[j] = gj;
+#pragma unroll
+    for (int k = j; k < DIM; ++k) {
+      double h = j == k ? cj : 0.0;
+#pragma unroll
+      for (int m = 0; m < 12; ++m)
+        if (DIM == 1 || comp_of(m) == j) h += d1[m] * PD[12 * k + m];
+      H[3 * j + k] = h;
+      H[3 * k + j] = h;
+    }
+  }
 }
 
 // Cholesky solve of H v = r (m <= 3); false when H is not positive definite.
@@ -184,7 +235,9 @@ __global__ void finalize_hessian_kernel(int64_t n, const PlanHdr* __restrict__ p
     q_derivs(S, (double)qpos[i].z, lam, q, d1, d2);
     if (corr)   // pixel-exact near field: B and grad B move, their lambda-derivatives do not
       for (int m = 0; m < 12; ++m) q[m] += corr[12 * i + m];
-    hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
+    double F[12], PD[36];
+    if (dim == 1) hessian_cols<1>(q, d1, d2, g_scale, w_g, phi, grad, H, F, PD);
+    else hessian_cols<3>(q, d1, d2, g_scale, w_g, phi, grad, H, F, PD);
     if (phi_out) phi_out[i] = phi;
     if (grad_out)
       for (int j = 0; j < 3; ++j) grad_out[3 * i + j] = grad[j];
@@ -228,7 +281,9 @@ __global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* _
       q_derivs(S, z, lam, q, d1, d2);
       if (corr)
         for (int m = 0; m < 12; ++m) q[m] += corr[12 * i + m];
-      hessian_of(q, d1, d2, dim, g_scale, w_g, phi, grad, H);
+      double F[12], PD[36];
+      if (dim == 1) hessian_cols<1>(q, d1, d2, g_scale, w_g, phi, grad, H, F, PD);
+      else hessian_cols<3>(q, d1, d2, g_scale, w_g, phi, grad, H, F, PD);
       const double g[3] = {gB[3 * i], gB[3 * i + 1], gB[3 * i + 2]};
       double gl[3] = {0.0, 0.0, 0.0}, v[3] = {0.0, 0.0, 0.0};
       if (dim == 1) gl[0] = g[0] * d1[0] + g[1] * d1[1] + g[2] * d1[2];
@@ -240,26 +295,14 @@ __global__ void implicit_weights_kernel(int64_t n, int nptiles, const PlanHdr* _
       if (v_out)
         for (int p = 0; p < 3; ++p) v_out[3 * i + p] = vp[p];
       if (flags) flags[i] = pd ? 0 : 1;
-      // Phi's first derivatives dPhi/dq (b part) and w = (d2 Phi / dq dq) . (dq along v) (c part)
+      // Phi's first derivatives dPhi/dq and w = (d2 Phi / dq dq) . (dq along v) = sum_k v_k (P D)_k
       double Fq[12], wq[12];
+#pragma unroll
       for (int m = 0; m < 12; ++m) {
-        Fq[m] = 0.0;
-        wq[m] = 0.0;
-      }
-      if (pd) {
-        HD B[3], G[9];
-        for (int mm = 0; mm < 12; ++mm) {
-          for (int m = 0; m < 12; ++m) {
-            HD xq = hd_k(q[m]);
-            xq.a = vp[comp_of(m)] * d1[m];
-            xq.b = m == mm ? 1.0 : 0.0;
-            if (m < 3) B[m] = xq;
-            else G[m - 3] = xq;
-          }
-          const HD ph = objective_hd(B, G, g_scale, w_g);
-          Fq[mm] = ph.b;
-          wq[mm] = ph.c;
-        }
+        double w = v[0] * PD[m];
+        if (dim == 3) w = (w + v[1] * PD[12 + m]) + v[2] * PD[24 + m];
+        Fq[m] = pd ? F[m] : 0.0;
+        wq[m] = pd ? w : 0.0;
       }
       for (int p = 0; p < 3; ++p) {
         const double lp = lam[p], vl = vp[p] * lp;

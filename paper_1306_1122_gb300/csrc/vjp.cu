@@ -28,7 +28,7 @@ KernelRef vjp_ref(bool fp64, bool tied, int cfg) {
 
 // The seven-weight adjoint (gradient through the lambda search) runs once per call, after a
 // Hessian pass; one launch shape: 256 threads.  FP32: two pixels per thread, each 64-bit read of
-// the 27-field point records (two points) serving four pairs, at 123 registers (two CTAs per
+// the 27-field point records (two points) serving four pairs, at 121 registers (two CTAs per
 // SM; four pixels would need 170).  FP64: four pixels per thread.
 template <typename Real, bool TIED>
 KernelRef vjp7_ref_t() {

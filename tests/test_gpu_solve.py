@@ -278,3 +278,40 @@ def test_certified_B_to_1e5_on_cancellation_dominated_points(dbie):
     assert res["certified"][0] <= 1e-5, res
     assert res["certified"][2] > 0
     assert res["certified"][1] > 0.3          # the subsample is cancellation-dominated
+
+
+def test_certified_solve_edge_cases(dbie, small):
+    """The certified state machine (the default) at its edges: no points; max_iter = 0 (the
+    initial simplex's sort and Eq. 12 test only, possibly through near ties); a given initial
+    lambda; a batch with an empty problem; results against the oracle's search."""
+    w, pts = small
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    r0 = f.solve(torch.zeros((0, 3)))
+    assert r0["B"].shape == (0, 3)
+    ref0 = oracle_solve(w.mag, pts[:64], max_iter=0)
+    r = f.solve(torch.from_numpy(pts[:64]), dbie.Options(max_iter=0))
+    torch.cuda.synchronize()
+    assert (r["iters"] == 0).all() and (r["nfev"] == 4).all()
+    assert np.allclose(r["lam"].cpu().numpy(), ref0["lam"], rtol=0, atol=1e-15)
+    l0 = np.array([[0.05, 0.02, 0.01]] * 16)
+    r1 = f.solve(torch.from_numpy(pts[:16]), dbie.Options(max_iter=12),
+                 lambda_init=torch.from_numpy(l0), codes=12)
+    ref1 = oracle.solve(oracle_boundary(w.mag), pts[:16].astype(np.float64),
+                        oracle.Options(max_iter=12), lam0=l0)
+    codes = [bytes(row).rstrip(b"\0").decode() for row in r1["codes"].cpu().numpy()]
+    assert codes == ref1["codes"]
+    assert lam_close(r1["lam"].cpu().numpy(), ref1["lam"], 32.0).all()
+    f.close()
+    # a batch whose middle problem has no points
+    mags, ppts = _uneven_batch()
+    fields = [dbie.DBIEField.from_magnetogram(m) for m in mags[:3]]
+    sel = [ppts[0][:40], np.zeros((0, 3), np.float32), ppts[2][:30]]
+    outs = dbie.solve_batched(fields, [torch.from_numpy(p) for p in sel], codes=50)
+    torch.cuda.synchronize()
+    assert outs[1]["B"].shape == (0, 3)
+    for k in (0, 2):
+        ref = oracle_solve(mags[k], sel[k])
+        got = [bytes(row).rstrip(b"\0").decode() for row in outs[k]["codes"].cpu().numpy()]
+        assert np.mean([a == b for a, b in zip(got, ref["codes"])]) >= 0.95
+    for fl in fields:
+        fl.close()
