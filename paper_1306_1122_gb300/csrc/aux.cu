@@ -1,4 +1,5 @@
 // aux.cu -- staging, packing, near-field correction and adjoint finalisation kernels.
+#include "ff_math.cuh"
 #include "kernels.h"
 
 namespace dbie {
@@ -222,6 +223,18 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
   // (49 of 56 lane slots busy) instead of 2 of 32 (49 of 64).  The loop runs warp-uniformly so
   // the shuffles see every lane.
   constexpr int GL = 8;
+  // sin and cos of lambda r in float-float on the FP32 pipe (absolute error ~1e-13 + 5e-15 |lambda
+  // r|, far below the FP32 terms' error that the correction removes) instead of FP64 sincos,
+  // which cost most of this kernel's FP64-pipe time
+  __shared__ float4 s_tab[ff::SC_TABLE];
+  ff::fill_sincos_table(s_tab, threadIdx.x);
+  __syncthreads();
+  auto sincos_ff = [&](double th, double& s, double& c) {
+    ff::ds S, C;
+    ff::sincos_ds<float>(ff::from_double(th), s_tab, S, C);
+    s = ff::to_double(S);
+    c = ff::to_double(C);
+  };
   const int lane = threadIdx.x & 31, sub = lane & (GL - 1), grp = lane / GL;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int cnt = *near_cnt;
@@ -266,8 +279,8 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
         else
           pair_terms32<VAR, TIED>(q32, *tile_field(pd.tiles32, k, 0), *tile_field(pd.tiles32, k, 1),
                                   b32, t32);
-        pair_terms64<VAR, TIED>(q64, *tile_field(pd.tiles64, k, 0), *tile_field(pd.tiles64, k, 1),
-                                b64, t64);
+        pair_terms64_sc<VAR, TIED>(q64, *tile_field(pd.tiles64, k, 0),
+                                   *tile_field(pd.tiles64, k, 1), b64, t64, sincos_ff);
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           const int lp = TIED ? 0 : p;

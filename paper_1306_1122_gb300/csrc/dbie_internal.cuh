@@ -480,9 +480,12 @@ struct Terms64 {
 };
 // (Tx and Ty of the FP64 form are t0 * dx and t0 * dy.)
 
-template <int VAR, bool TIED>
-__device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, double px, double py,
-                                             const double b[3], Terms64<VAR, TIED>& t) {
+// FP64 pair terms; `sc(theta, s, c)` supplies sin and cos of lambda r (FP64 sincos by default).
+template <int VAR, bool TIED, typename SinCos>
+__device__ __forceinline__ void pair_terms64_sc(const Query<double, TIED>& q, double px, double py,
+                                                const double b[3], Terms64<VAR, TIED>& t,
+                                                SinCos&& sc) {
+  constexpr int NL = TIED ? 1 : 3;
   t.dx = q.x - px;
   t.dy = q.y - py;
   const double r2 = t.dx * t.dx + t.dy * t.dy + q.z2;
@@ -490,20 +493,29 @@ __device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, doubl
   const double r = r2 * ri;
   const double ri2 = ri * ri;
   const double ri3 = ri2 * ri;
+  double th[NL], s[NL], c[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    th[l] = q.l[l] * r;
+    sc(th[l], s[l], c[l]);
+  }
 #pragma unroll
   for (int p = 0; p < 3; ++p) {
     const int lp = TIED ? 0 : p;
-    double s, c;
-    const double th = q.l[lp] * r;
-    sincos(th, &s, &c);
-    const double u = th * s + c;
+    const double u = th[lp] * s[lp] + c[lp];
     const double rb = ri3 * b[p];
     t.t0[p] = u * rb;
-    if constexpr (has_grad(VAR)) t.t1[p] = (q.l2[lp] * c - 3.0 * u * ri2) * rb;
-    if constexpr (has_dlam(VAR)) t.tl[p] = c * ri * b[p];
-    if constexpr (has_hess(VAR)) t.tq[p] = s * b[p];
+    if constexpr (has_grad(VAR)) t.t1[p] = (q.l2[lp] * c[lp] - 3.0 * u * ri2) * rb;
+    if constexpr (has_dlam(VAR)) t.tl[p] = c[lp] * ri * b[p];
+    if constexpr (has_hess(VAR)) t.tq[p] = s[lp] * b[p];
     if constexpr (is_nv(VAR)) t.ph[p] = u * ri3;
   }
+}
+template <int VAR, bool TIED>
+__device__ __forceinline__ void pair_terms64(const Query<double, TIED>& q, double px, double py,
+                                             const double b[3], Terms64<VAR, TIED>& t) {
+  pair_terms64_sc<VAR, TIED>(q, px, py, b, t,
+                             [](double th, double& s, double& c) { sincos(th, &s, &c); });
 }
 
 // Address of field f of pixel (quadrature point) k in a tile-blocked boundary of nf fields.

@@ -41,6 +41,12 @@ constexpr int SUB1 = 32;  // elements per fold where one accumulator takes every
                           // the unpacked FP32 form): the per-accumulator length of the packed form
 constexpr int GROUP_UNROLL = DBIE_GROUP_UNROLL;  // 4-pixel groups unrolled within a block
 static_assert(TILE % SUB == 0 && SUB % 4 == 0, "fold blocks must tile the 256-pixel tile");
+// The Hessian pass folds its 30 sums every 128 pixels (64 terms per lane): with ten sums per
+// component the fold is ~8 % of its FP32 work at 64.  (The objective kernels keep SUB: the error
+// bound of the certified decisions is derived for that block length.)
+constexpr int SUB_HESS = 128;
+static_assert(TILE % SUB_HESS == 0, "fold blocks must tile the 256-pixel tile");
+__host__ __device__ constexpr int fold_pixels(int var) { return var == VAR_HESS ? SUB_HESS : SUB; }
 
 // Ring of NSTAGE shared-memory tile buffers filled by TMA bulk copies.  Thread 0 issues; all
 // warps consume.  `issued` / `consumed` count tiles over the CTA's lifetime, which fixes the
@@ -327,9 +333,10 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
 #pragma unroll
         for (int u = 0; u < P; ++u) q2[u] = splat_query<TIED>(q[u]);
 #pragma unroll 1
-        for (int k0 = 0; k0 < TILE; k0 += SUB) {
+        constexpr int SUBV = fold_pixels(VAR);
+        for (int k0 = 0; k0 < TILE; k0 += SUBV) {
 #pragma unroll GROUP_UNROLL
-          for (int k = k0; k < k0 + SUB; k += 4) {
+          for (int k = k0; k < k0 + SUBV; k += 4) {
             const float4 X = *reinterpret_cast<const float4*>(sx + k);
             const float4 Y = *reinterpret_cast<const float4*>(sx + TILE + k);
             const float4 BX = *reinterpret_cast<const float4*>(sx + 2 * TILE + k);

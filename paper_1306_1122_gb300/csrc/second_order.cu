@@ -12,8 +12,8 @@
 // own component, so with F = dPhi/dq, P = d2Phi/dq2 and the 12 x dim matrix D of dq/dlambda,
 //   grad_l Phi = D^T F,   H = D^T P D + diag_j(sum over q of component j of F d2q/dl_j^2).
 // F comes from the closed-form gradient of Phi (reverse mode, written out below), and P D from
-// the same gradient evaluated on dual numbers v + d e (e^2 = 0) with the tangent of q set to one
-// column of D: one evaluation per column (three, or one for a shared lambda).
+// the same gradient evaluated once on dual numbers that carry one tangent of q per column of D
+// (three tangents, or one for a shared lambda).
 //
 // Gradient through the search: lambda* is a stationary point, grad_l Phi(lambda*; B0) = 0, so
 // d(lambda*)/dB0 = -H^-1 d(grad_l Phi)/dB0 and
@@ -28,21 +28,62 @@ namespace dbie {
 
 namespace {
 
-// Dual number v + d e (e^2 = 0): a value and its derivative along one direction.
+// Dual number with K tangents, v + sum_k d_k e_k (e_j e_k = 0): a value and its derivatives
+// along K directions at once (the value arithmetic, square roots and divisions done once).
+template <int K>
 struct Du {
-  double v, d;
+  double v, d[K];
 };
-__device__ __forceinline__ Du operator+(Du x, Du y) { return Du{x.v + y.v, x.d + y.d}; }
-__device__ __forceinline__ Du operator-(Du x, Du y) { return Du{x.v - y.v, x.d - y.d}; }
-__device__ __forceinline__ Du operator*(Du x, Du y) { return Du{x.v * y.v, fma(x.v, y.d, x.d * y.v)}; }
-__device__ __forceinline__ Du operator*(Du x, double s) { return Du{x.v * s, x.d * s}; }
-__device__ __forceinline__ Du dsqrt(Du x) {
-  const double r = sqrt(x.v);
-  return Du{r, x.d * (0.5 / r)};
+template <int K>
+__device__ __forceinline__ Du<K> operator+(const Du<K>& x, const Du<K>& y) {
+  Du<K> r{x.v + y.v, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = x.d[k] + y.d[k];
+  return r;
 }
-__device__ __forceinline__ Du drecip(Du x) {
-  const double r = 1.0 / x.v;
-  return Du{r, -(x.d * (r * r))};
+template <int K>
+__device__ __forceinline__ Du<K> operator-(const Du<K>& x, const Du<K>& y) {
+  Du<K> r{x.v - y.v, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = x.d[k] - y.d[k];
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Du<K> operator*(const Du<K>& x, const Du<K>& y) {
+  Du<K> r{x.v * y.v, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = fma(x.v, y.d[k], x.d[k] * y.v);
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Du<K> operator*(const Du<K>& x, double s) {
+  Du<K> r{x.v * s, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) r.d[k] = x.d[k] * s;
+  return r;
+}
+template <int K>
+__device__ __forceinline__ Du<K> dsqrt(const Du<K>& x) {
+  const double r = sqrt(x.v), h = 0.5 / r;
+  Du<K> o{r, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) o.d[k] = x.d[k] * h;
+  return o;
+}
+template <int K>
+__device__ __forceinline__ Du<K> drecip(const Du<K>& x) {
+  const double r = 1.0 / x.v, m = -(r * r);
+  Du<K> o{r, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) o.d[k] = x.d[k] * m;
+  return o;
+}
+template <int K>
+__device__ __forceinline__ Du<K> dzero() {
+  Du<K> o{0.0, {}};
+#pragma unroll
+  for (int k = 0; k < K; ++k) o.d[k] = 0.0;
+  return o;
 }
 
 // Phi = f + w_g g of Eq. 8, 9 (J = curl B, Eq. 14) and its gradient F with respect to
@@ -51,8 +92,11 @@ __device__ __forceinline__ Du drecip(Du x) {
 //   df/dJ = B x C / (|C| |J| |B|) - f J / |J|^2,   df/dB = C x J / (|C| |J| |B|) - f B / |B|^2
 // (the |C| term 0 when |C| = 0), dg/dB = -g B / |B|^2, dg/dD = g_scale sign(D) / |B| (sign(0) =
 // +1), and J, D linear in G.  Evaluated on dual numbers (branches taken on the values): the
-// value parts are Phi and F, the derivative parts their derivatives along the tangent of q.
-__device__ void objective_grad_q(const Du* q, double g_scale, double w_g, Du& phi, Du* F) {
+// value parts are Phi and F, the derivative parts their derivatives along the tangents of q.
+template <int K>
+__device__ void objective_grad_q(const Du<K>* q, double g_scale, double w_g, Du<K>& phi,
+                                 Du<K>* F) {
+  using Du = dbie::Du<K>;
   const Du* B = q;
   const Du* G = q + 3;
   const Du Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
@@ -62,7 +106,7 @@ __device__ void objective_grad_q(const Du* q, double g_scale, double w_g, Du& ph
   const Du Cz = Jx * B[1] - Jy * B[0];
   const Du sJ = Jx * Jx + Jy * Jy + Jz * Jz, sB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
   const Du sC = Cx * Cx + Cy * Cy + Cz * Cz;
-  const Du z0{0.0, 0.0};
+  const Du z0 = dzero<K>();
   const Du nJ = sJ.v > 0.0 ? dsqrt(sJ) : z0;
   const Du nB = sB.v > 0.0 ? dsqrt(sB) : z0;
   const Du nC = sC.v > 0.0 ? dsqrt(sC) : z0;
@@ -146,18 +190,21 @@ __device__ void hessian_cols(const double q[12], const double d1[12], const doub
 #pragma unroll
   for (int i = 0; i < 9; ++i) H[i] = 0.0;
   grad[0] = grad[1] = grad[2] = 0.0;
+  // one evaluation, tangent k = column k of D (dq/dlambda_k)
+  Du<DIM> x[12], ph, Fd[12];
 #pragma unroll
-  for (int k = 0; k < DIM; ++k) {
-    Du x[12], ph, Fd[12];
+  for (int m = 0; m < 12; ++m) {
+    x[m].v = q[m];
 #pragma unroll
-    for (int m = 0; m < 12; ++m) x[m] = Du{q[m], (DIM == 1 || comp_of(m) == k) ? d1[m] : 0.0};
-    objective_grad_q(x, g_scale, w_g, ph, Fd);
-    phi = ph.v;
+    for (int k = 0; k < DIM; ++k) x[m].d[k] = (DIM == 1 || comp_of(m) == k) ? d1[m] : 0.0;
+  }
+  objective_grad_q<DIM>(x, g_scale, w_g, ph, Fd);
+  phi = ph.v;
 #pragma unroll
-    for (int m = 0; m < 12; ++m) {
-      F[m] = Fd[m].v;
-      PD[12 * k + m] = Fd[m].d;
-    }
+  for (int m = 0; m < 12; ++m) {
+    F[m] = Fd[m].v;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) PD[12 * k + m] = Fd[m].d[k];
   }
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
