@@ -231,7 +231,7 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
   __syncthreads();
   auto sincos_ff = [&](double th, double& s, double& c) {
     ff::ds S, C;
-    ff::sincos_ds<float>(ff::from_double(th), s_tab, S, C);
+    ff::sincos_ds_any(ff::from_double(th), s_tab, S, C);
     s = ff::to_double(S);
     c = ff::to_double(C);
   };

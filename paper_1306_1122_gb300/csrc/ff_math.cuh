@@ -139,15 +139,18 @@ __device__ __forceinline__ void fill_sincos_table(float4* tab, int tid) {
   }
 }
 
-// Table entry for a (possibly negative) index j in float: sin is odd, cos even.
+// Table entry for a (possibly negative) index j in float: sin is odd, cos even.  The index is
+// clamped to the table, so no input (an angle beyond the reduction's range, NaN) reads outside it.
 __device__ __forceinline__ void table_lookup(const float4* tab, float jf, ds& S, ds& C) {
-  const float4 t = tab[abs((int)jf)];
+  const float aj = fabsf(jf);
+  const float4 t = tab[aj < (float)SC_TABLE ? (int)aj : SC_TABLE - 1];   // (NaN: the last entry)
   const float sg = jf < 0.0f ? -1.0f : 1.0f;
   S = ds{t.x * sg, t.y * sg};
   C = ds{t.z, t.w};
 }
 
-// sin and cos of a float-float angle (|theta| < 12,800).  theta = k 2 pi + t by a three-part
+// sin and cos of a float-float angle (|theta| < 12,800; sincos_ds_any below takes any angle).
+// theta = k 2 pi + t by a three-part
 // Cody-Waite reduction (|t| <= pi), t = j/16 + tau (|tau| <= 1/32) against the table, then
 //   sin(tau) = tau - tau^3/6 + tau^5/120,   cos(tau) - 1 = -tau^2/2 + tau^4/24 - tau^6/720
 // (truncation below 6e-15 at |tau| = 1/32), combined by the angle-sum formulas.  Absolute error
@@ -179,6 +182,20 @@ __device__ __forceinline__ void sincos_ds(dsv<V> th, const float4* tab, dsv<V>& 
   // stay unnormalised pairs and are summed once.
   s_out = add(S, add(mul_nr(S, cm1), mul_nr(C, sn)));
   c_out = add(C, sub(mul_nr(C, cm1), mul_nr(S, sn)));
+}
+
+// sincos_ds for any angle: |theta| < SC_MAX_ARG by the reduction above, larger (rare: a search's
+// trial lambda far out) or non-finite angles by FP64 sincos.
+constexpr float SC_MAX_ARG = 12000.0f;
+__device__ __forceinline__ void sincos_ds_any(ds th, const float4* tab, ds& s_out, ds& c_out) {
+  if (fabsf(th.hi) < SC_MAX_ARG) {
+    sincos_ds<float>(th, tab, s_out, c_out);
+  } else {
+    double s, c;
+    sincos(to_double(th), &s, &c);
+    s_out = from_double(s);
+    c_out = from_double(c);
+  }
 }
 
 }  // namespace ff

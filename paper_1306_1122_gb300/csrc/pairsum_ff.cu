@@ -14,6 +14,8 @@
 // boundary tiles through an mbarrier-guarded ring filled by TMA bulk copies.  One query per
 // thread.  Tiles hold, per field (x, y, bx, by, bz), TILE float pairs (hi, lo) converted from the
 // FP64 tiles, so the pixel positions and b = B0 dA / 2 pi enter at FP64 accuracy.
+#include <type_traits>
+
 #include "ff_math.cuh"
 #include "kernels.h"
 #include "pairsum.cuh"
@@ -121,8 +123,20 @@ __global__ void __launch_bounds__(FF_NT) g1_ff_kernel(const G1Args a) {
     // without a valid query only keeps the tile ring's protocol (wait, release) and skips the
     // arithmetic
     const bool warp_busy = __any_sync(0xffffffffu, valid);
-    sweep_tiles(ring, pd.tilesff, t0, t1, tid, [&](const float* sx) {
-      if (!warp_busy) return;
+    // lambda r below the reduction range of sincos_ds for every pixel: |lambda| times the
+    // largest distance to the quadrature grid's box (pixel centres or Gauss points, both inside
+    // [x0 - |hx|, x0 + nx |hx|]); otherwise (rare: a far-out trial lambda) the warp takes the
+    // path with the FP64 fallback, so the common path stays branch-free
+    double lmax = 0.0;
+#pragma unroll
+    for (int l = 0; l < NL; ++l) lmax = fmax(lmax, fabs(lamd[l]));
+    const double ax = fabs(pd.hx), ay = fabs(pd.hy);
+    const double ex = fmax(fabs(pos.x - (pd.x0 - ax)), fabs(pos.x - (pd.x0 + pd.nx * ax)));
+    const double ey = fmax(fabs(pos.y - (pd.y0 - ay)), fabs(pos.y - (pd.y0 + pd.ny * ay)));
+    const double rmax = sqrt(ex * ex + ey * ey + (double)pos.z * pos.z);
+    const bool warp_fast =
+        __all_sync(0xffffffffu, !valid || lmax * rmax < 0.9 * (double)ff::SC_MAX_ARG);
+    auto tile_body = [&](const float* sx, auto any_angle) {
 #pragma unroll 1
       for (int k = 0; k < TILE; ++k) {
         const D X = D{ff_load(sx, 0, 0, k), ff_load(sx, 0, 1, k)};
@@ -140,7 +154,8 @@ __global__ void __launch_bounds__(FF_NT) g1_ff_kernel(const G1Args a) {
         for (int l = 0; l < NL; ++l) {
           const D th = ff::mul_nr(lam[l], r);
           D s;
-          ff::sincos_ds(th, s_tab, s, c[l]);
+          if constexpr (decltype(any_angle)::value) ff::sincos_ds_any(th, s_tab, s, c[l]);
+          else ff::sincos_ds<float>(th, s_tab, s, c[l]);
           u[l] = ff::add(ff::mul_nr(th, s), c[l]);
         }
 #pragma unroll
@@ -159,6 +174,11 @@ __global__ void __launch_bounds__(FF_NT) g1_ff_kernel(const G1Args a) {
           }
         }
       }
+    };
+    sweep_tiles(ring, pd.tilesff, t0, t1, tid, [&](const float* sx) {
+      if (!warp_busy) return;
+      if (warp_fast) tile_body(sx, std::false_type{});
+      else tile_body(sx, std::true_type{});
     });
 
     if (valid) {

@@ -75,6 +75,43 @@ def test_ff_large_lambda_r_and_value_only(dbie):
     assert e_ff <= TOL_FF, e_ff
 
 
+def test_far_lambda_beyond_the_reduction_range(dbie):
+    """lambda r past the float-float sine/cosine's Cody-Waite range (12,000 rad), as a quasi-Newton
+    trial step with a tiny curvature estimate can produce: the float-float form takes FP64 sincos
+    there and still matches the oracle (within the float-float rounding of lambda r itself,
+    ~2^-44 |lambda r|), and the mixed form, whose FP64 near field uses the same routine, returns
+    finite values up to lambda r ~ 1e9 (its FP32 terms mean little that far out)."""
+    mag = random_mag(48, 40, 11)
+    rng = np.random.default_rng(12)
+    xyz, _ = random_points(mag, 96, 13, zlo=0.3, zhi=3.0)
+    # log-uniform |lambda| from 10 to 300 per component, both signs: lambda r to ~2e4
+    lam = (rng.choice([-1.0, 1.0], (96, 3)) * 10.0 ** rng.uniform(1.0, 2.5, (96, 3))).astype(
+        np.float32)
+    got = _ff_eval(dbie, mag, xyz, lam)
+    B, G, _ = oracle.field(oracle_boundary(mag), xyz.astype(np.float64), lam.astype(np.float64))
+    sB, sG = abs_scales(mag, xyz, lam)
+    corners = np.array([[0.0, 0.0], [mag.nx - 1.0, 0.0], [0.0, mag.ny - 1.0],
+                        [mag.nx - 1.0, mag.ny - 1.0]])
+    r_far = np.sqrt(((xyz[:, None, :2] - corners[None]) ** 2).sum(-1).max(1) + xyz[:, 2] ** 2)
+    th_max = float((np.abs(lam).max(1) * r_far).max())      # largest lambda r over all pairs
+    tol = TOL_FF * max(1.0, th_max / 400.0)
+    eB = (np.abs(got["B"] - B) / sB).max()
+    eG = (np.abs(got["gradB"] - G) / sG[:, :, None]).max()
+    print(f"lambda r to {th_max:.0f}: FF B {eB:.2e}, grad B {eG:.2e} of the abs-value sums "
+          f"(gate {tol:.1e})")
+    assert th_max > 12000.0                                    # the fallback range is reached
+    assert eB <= tol and eG <= tol
+    f = dbie.DBIEField.from_magnetogram(mag)
+    for scale in (1e3, 1e5, 1e7):
+        far = (np.sign(lam) * scale).astype(np.float32)
+        for prec in (0, dbie._native.DBIE_PREC_FLOAT_FLOAT):
+            r = f.eval(torch.from_numpy(xyz), torch.from_numpy(far), grad=True,
+                       options=dbie.Options(precision=prec))
+            torch.cuda.synchronize()
+            assert torch.isfinite(r["B"]).all() and torch.isfinite(r["gradB"]).all(), (scale, prec)
+    f.close()
+
+
 def test_ff_rejected_where_not_available(dbie):
     mag = random_mag(20, 20, 3)
     xyz, lam = random_points(mag, 8, 4)
