@@ -113,3 +113,27 @@ def test_mixed_quasi_newton_quality(dbie, small):
           f"{np.median(phi_gpu):.4f}; simplex (oracle): mean evals {nm['nfev'].mean():.1f}, "
           f"median Phi {np.median(nm['phi']):.4f}")
     f.close()
+
+
+def test_searches_from_far_out_lambda(dbie):
+    """Both searches where lambda r is far outside the float-float sine/cosine's reduction range
+    (the default certified simplex re-evaluates near ties in float-float; the near field of the
+    mixed form uses the same routine): the quasi-Newton search on a 4,096-point ll128 subsample,
+    whose curvature updates can produce very long trial steps, and both searches started from
+    lambda = +-1e3 .. +-1e6 (lambda r up to ~1e8).  Every call returns without error and with
+    finite B and lambda."""
+    w = workloads.ll128(with_truth=False)
+    idx = np.sort(np.random.default_rng(77).choice(len(w.points), 4096, replace=False))
+    pts = torch.from_numpy(w.points[idx])
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    r = f.solve(pts, dbie.Options(method=1))
+    torch.cuda.synchronize()
+    assert torch.isfinite(r["B"]).all() and torch.isfinite(r["lam"]).all()
+    sub = pts[:256]
+    sgn = torch.from_numpy(np.random.default_rng(78).choice([-1.0, 1.0], (256, 3)))
+    for scale in (1e3, 1e6):
+        for method in (0, 1):
+            r = f.solve(sub, dbie.Options(method=method, max_iter=8), lambda_init=sgn * scale)
+            torch.cuda.synchronize()
+            assert torch.isfinite(r["B"]).all() and torch.isfinite(r["lam"]).all(), (scale, method)
+    f.close()
