@@ -260,10 +260,15 @@ __device__ __forceinline__ Query<Real, TIED> make_query(float4 pos, Lam4 lam) {
 
 // ---------------------------------------------------------------- FP32 lanes ----
 // The FP32 pair terms are written once for a "lane" type V: float (one pixel), or f32x2 (two
-// pixels packed in a 64-bit register pair, PTX add/sub/mul/fma.rn.f32x2).  Every packed operation
-// rounds each lane exactly like its scalar counterpart, so a packed term equals the scalar one bit
-// for bit; the SFU operations (rsqrt, sin, cos) act lane by lane.  The packed form issues one
-// instruction for two pixels' FP32 arithmetic.
+// pixels packed in a 64-bit register pair, PTX add/sub/mul/fma.rn.f32x2).  Each packed
+// instruction rounds each lane like its scalar counterpart, and the SFU operations (rsqrt, sin,
+// cos) act lane by lane.  The packed form issues one instruction for two pixels' FP32
+// arithmetic.  Sequences of packed instructions are not guaranteed to keep that rounding: with
+// the assembler's optimisation on (any level above 0), composed error-free transformations on
+// f32x2 (a square-root refinement, a float-float sine) came out different from the scalar ones,
+// as if products were fused into the following additions.  The packed terms are therefore FP32
+// terms of the same accuracy, not bit copies of the scalar terms, and float-float arithmetic
+// runs on scalar floats only.
 struct f32x2 {
   unsigned long long v;
 };
@@ -343,8 +348,10 @@ __device__ __forceinline__ Query<f32x2, TIED> splat_query(const Query<float, TIE
 //   Sl += cr * b (fused),  with rb = b / r^3, t1 = psi b = (lambda^2 c - 3 u / r^2) rb, cr = c / r,
 // so the exact contribution of a pixel is a product of two rounded FP32 factors.  Every factor
 // is computed with an explicit rounding so that the near-field kernel, which replaces these
-// contributions by FP64 ones, reproduces them bit for bit (a product of two FP32 values is exact
-// in FP64).
+// contributions by FP64 ones, reproduces the scalar form's contributions exactly (a product of
+// two FP32 values is exact in FP64); the packed form's may differ from them by a rounding of a
+// factor, which the subtraction then leaves in the sum (of the order of the FP32 terms' own
+// error).
 template <typename V, int VAR, bool TIED>
 struct TermsV {
   V dx, dy;
