@@ -202,3 +202,56 @@ def test_noise_var_matches_oracle(dbie, precision, mode):
     e = f.noise_var(torch.zeros((0, 3)), torch.zeros((0, 3), dtype=torch.float64))
     assert e.shape == (0, 3)
     f.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_hessian_on_element_rule_matches_oracle_differences(dbie, precision):
+    """dbie_hessian with Eq. 15's nine-node elements (3 x 3 Gauss points; the split-position
+    pair-sum kernels): Phi, its lambda-gradient and lambda-Hessian against central differences of
+    the oracle's element-rule Phi (steps 2^-14 in lambda, all evaluations in one oracle call).
+    FP64 form 1e-5, mixed 1e-3 relative Frobenius over the set (the differences carry ~1e-6)."""
+    mag = random_mag(25, 25, 230)
+    rng = np.random.default_rng(231)
+    n = 16
+    pts = np.stack([rng.uniform(4, 20, n), rng.uniform(4, 20, n), rng.uniform(1, 6, n)],
+                   1).astype(np.float32)
+    lam = rng.uniform(0.02, 0.08, (n, 3)) * rng.choice([-1.0, 1.0], (n, 3))
+    gs = mag.hx / 6.0
+    h = 2.0 ** -14
+    E = np.eye(3)
+    shifts = [np.zeros(3)]
+    for j in range(3):
+        shifts += [2 * h * E[j], -2 * h * E[j]]
+    for j in range(3):
+        for k in range(j + 1, 3):
+            shifts += [h * (E[j] + E[k]), h * (E[j] - E[k]), h * (E[k] - E[j]), -h * (E[j] + E[k])]
+    S = np.array(shifts)                                   # (19, 3)
+    L = (lam[:, None, :] + S[None]).reshape(-1, 3)
+    X = np.repeat(pts.astype(np.float64), len(S), axis=0)
+    bd = oracle_boundary(mag)
+    B, G, _ = oracle.field(bd, X, L, quad_order=3)
+    _, _, phi, _, _ = oracle.objective(B, G, g_scale=gs)
+    P = phi.reshape(n, len(S))
+    H = np.zeros((n, 3, 3))
+    grad = np.zeros((n, 3))
+    for j in range(3):
+        grad[:, j] = (P[:, 1 + 2 * j] - P[:, 2 + 2 * j]) / (4 * h)
+        H[:, j, j] = (P[:, 1 + 2 * j] - 2 * P[:, 0] + P[:, 2 + 2 * j]) / (4 * h * h)
+    c = 7
+    for j in range(3):
+        for k in range(j + 1, 3):
+            H[:, j, k] = H[:, k, j] = (P[:, c] - P[:, c + 1] - P[:, c + 2] + P[:, c + 3]) / (4 * h * h)
+            c += 4
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_quadrature(3)
+    r = f.hessian(torch.from_numpy(pts), torch.from_numpy(lam),
+                  dbie.Options(precision=precision))
+    torch.cuda.synchronize()
+    f.close()
+    got = {k: v.cpu().numpy() for k, v in r.items()}
+    tol = 1e-5 if precision == 1 else 1e-3
+    assert np.allclose(got["phi"], P[:, 0], rtol=1e-9 if precision == 1 else 1e-4, atol=1e-12)
+    eg = np.linalg.norm(got["grad"] - grad) / np.linalg.norm(grad)
+    eH = np.linalg.norm(got["hess"] - H) / np.linalg.norm(H)
+    print(f"element rule, precision {precision}: gradient {eg:.1e}, Hessian {eH:.1e}")
+    assert eg <= tol and eH <= tol, (eg, eH)
