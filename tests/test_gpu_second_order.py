@@ -255,3 +255,60 @@ def test_hessian_on_element_rule_matches_oracle_differences(dbie, precision):
     eH = np.linalg.norm(got["hess"] - H) / np.linalg.norm(H)
     print(f"element rule, precision {precision}: gradient {eg:.1e}, Hessian {eH:.1e}")
     assert eg <= tol and eH <= tol, (eg, eH)
+
+
+def test_implicit_vjp_on_element_rule_matches_perturbation(dbie):
+    """dbie_vjp_implicit with Eq. 15's elements (3 x 3 Gauss points; the split-position Hessian
+    pass and seven-weight sweep), FP64 form, against the derivative it stands for:
+    L(B0) = gB . B(lambda*(B0), B0) along a random direction of +-2^-6 per pixel (exact in
+    float32), lambda* re-found by Newton steps on the GPU's own FP64 gradient and Hessian after
+    each perturbation, L evaluated as <A(lambda*)^T gB, B0> with the fixed-lambda adjoint (FP64
+    lambda); central difference against <dL/dB0, direction>.  The fixed-lambda adjoint misses
+    the lambda* term by more than 5 %."""
+    mag = random_mag(25, 25, 240)
+    rng = np.random.default_rng(241)
+    n = 48
+    pts = np.stack([rng.uniform(5, 19, n), rng.uniform(5, 19, n), rng.uniform(2, 6, n)],
+                   1).astype(np.float32)
+    opt = dbie.Options(precision=1)
+    f = dbie.DBIEField.from_magnetogram(mag)
+    f.set_quadrature(3)
+    X = torch.from_numpy(pts)
+    lam = f.solve(X, dbie.Options(precision=1, max_iter=60))["lam"].cpu().numpy()
+
+    def newton(xyz, lam, iters):
+        for _ in range(iters):
+            r = f.hessian(xyz, torch.from_numpy(lam), opt)
+            g, H = r["grad"].cpu().numpy(), r["hess"].cpu().numpy()
+            lam = lam - np.linalg.solve(H, g[..., None])[..., 0]
+        return lam, g, H
+
+    lam, g, H = newton(X, lam, 8)
+    ev = np.linalg.eigvalsh(H)
+    keep = (ev[:, 0] > 0) & (ev[:, -1] < 1e3 * ev[:, 0]) & (np.abs(g).max(1) < 1e-9)
+    assert keep.sum() >= 8, keep.sum()
+    Xk, lam = X[torch.from_numpy(keep)], lam[keep]
+    gB = rng.normal(size=(int(keep.sum()), 3))
+    gB0, _, fl = f.vjp_implicit(Xk, torch.from_numpy(lam), torch.from_numpy(gB), options=opt)
+    fixed, _ = f.vjp(Xk, torch.from_numpy(lam), torch.from_numpy(gB), glam=False, options=opt)
+    torch.cuda.synchronize()
+    assert not fl.cpu().numpy().any()
+    gB0, fixed = gB0.cpu().numpy(), fixed.cpu().numpy()
+    B0 = np.stack([mag.Bx, mag.By, mag.Bz], -1).astype(np.float64)
+    d = (rng.choice([-1.0, 0.0, 1.0], B0.shape) * 2.0 ** -6).astype(np.float32)
+    L = []
+    for s in (1.0, -1.0):
+        Bs = (B0.astype(np.float32) + np.float32(s) * d)
+        f.set_boundary(*(torch.from_numpy(np.ascontiguousarray(Bs[..., p])) for p in range(3)))
+        ls, _, _ = newton(Xk, lam, 5)
+        At, _ = f.vjp(Xk, torch.from_numpy(ls), torch.from_numpy(gB), glam=False, options=opt)
+        torch.cuda.synchronize()
+        L.append(float((At.cpu().numpy() * Bs.astype(np.float64)).sum()))
+    f.close()
+    fd = (L[0] - L[1]) / 2.0
+    pred = float((gB0 * d).sum())
+    pred_fixed = float((fixed * d).sum())
+    print(f"element rule implicit adjoint: directional derivative {fd:.6e}, adjoint {pred:.6e}, "
+          f"fixed-lambda {pred_fixed:.6e}")
+    assert abs(pred - fd) <= 1e-6 * abs(fd), (pred, fd)
+    assert abs(pred_fixed - fd) > 0.05 * abs(fd)
