@@ -332,8 +332,8 @@ __device__ __forceinline__ void g1_body(const G1Args& a) {
         Query<f32x2, TIED> q2[P];
 #pragma unroll
         for (int u = 0; u < P; ++u) q2[u] = splat_query<TIED>(q[u]);
-#pragma unroll 1
         constexpr int SUBV = fold_pixels(VAR);
+#pragma unroll 1
         for (int k0 = 0; k0 < TILE; k0 += SUBV) {
 #pragma unroll GROUP_UNROLL
           for (int k = k0; k < k0 + SUBV; k += 4) {

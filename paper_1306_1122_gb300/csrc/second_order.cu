@@ -96,28 +96,28 @@ __device__ __forceinline__ Du<K> dzero() {
 template <int K>
 __device__ void objective_grad_q(const Du<K>* q, double g_scale, double w_g, Du<K>& phi,
                                  Du<K>* F) {
-  using Du = dbie::Du<K>;
-  const Du* B = q;
-  const Du* G = q + 3;
-  const Du Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
-  const Du D = G[0] + G[4] + G[8];
-  const Du Cx = Jy * B[2] - Jz * B[1];
-  const Du Cy = Jz * B[0] - Jx * B[2];
-  const Du Cz = Jx * B[1] - Jy * B[0];
-  const Du sJ = Jx * Jx + Jy * Jy + Jz * Jz, sB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
-  const Du sC = Cx * Cx + Cy * Cy + Cz * Cz;
-  const Du z0 = dzero<K>();
-  const Du nJ = sJ.v > 0.0 ? dsqrt(sJ) : z0;
-  const Du nB = sB.v > 0.0 ? dsqrt(sB) : z0;
-  const Du nC = sC.v > 0.0 ? dsqrt(sC) : z0;
-  Du gB[3] = {z0, z0, z0}, gJ[3] = {z0, z0, z0}, gD = z0;
+  using T = Du<K>;
+  const T* B = q;
+  const T* G = q + 3;
+  const T Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
+  const T D = G[0] + G[4] + G[8];
+  const T Cx = Jy * B[2] - Jz * B[1];
+  const T Cy = Jz * B[0] - Jx * B[2];
+  const T Cz = Jx * B[1] - Jy * B[0];
+  const T sJ = Jx * Jx + Jy * Jy + Jz * Jz, sB = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const T sC = Cx * Cx + Cy * Cy + Cz * Cz;
+  const T z0 = dzero<K>();
+  const T nJ = sJ.v > 0.0 ? dsqrt(sJ) : z0;
+  const T nB = sB.v > 0.0 ? dsqrt(sB) : z0;
+  const T nC = sC.v > 0.0 ? dsqrt(sC) : z0;
+  T gB[3] = {z0, z0, z0}, gJ[3] = {z0, z0, z0}, gD = z0;
   phi = z0;
   if (nJ.v * nB.v > 0.0) {
-    const Du inv = drecip(nJ * nB);
-    const Du f = nC * inv;
+    const T inv = drecip(nJ * nB);
+    const T f = nC * inv;
     phi = f;
     if (nC.v > 0.0) {
-      const Du k = inv * drecip(nC);
+      const T k = inv * drecip(nC);
       gJ[0] = (B[1] * Cz - B[2] * Cy) * k;
       gJ[1] = (B[2] * Cx - B[0] * Cz) * k;
       gJ[2] = (B[0] * Cy - B[1] * Cx) * k;
@@ -125,7 +125,7 @@ __device__ void objective_grad_q(const Du<K>* q, double g_scale, double w_g, Du<
       gB[1] = (Cz * Jx - Cx * Jz) * k;
       gB[2] = (Cx * Jy - Cy * Jx) * k;
     }
-    const Du fJ = f * drecip(sJ), fB = f * drecip(sB);
+    const T fJ = f * drecip(sJ), fB = f * drecip(sB);
     gJ[0] = gJ[0] - Jx * fJ;
     gJ[1] = gJ[1] - Jy * fJ;
     gJ[2] = gJ[2] - Jz * fJ;
@@ -133,12 +133,12 @@ __device__ void objective_grad_q(const Du<K>* q, double g_scale, double w_g, Du<
   }
   if (nB.v > 0.0) {
     const double gs = g_scale * w_g;
-    const Du rB = drecip(nB);
-    const Du aD = D.v < 0.0 ? D * -1.0 : D;
-    const Du g = (aD * rB) * gs;
+    const T rB = drecip(nB);
+    const T aD = D.v < 0.0 ? D * -1.0 : D;
+    const T g = (aD * rB) * gs;
     phi = phi + g;
     gD = rB * (D.v < 0.0 ? -gs : gs);
-    const Du gb = g * drecip(sB);
+    const T gb = g * drecip(sB);
     for (int i = 0; i < 3; ++i) gB[i] = gB[i] - B[i] * gb;
   }
   for (int i = 0; i < 3; ++i) F[i] = gB[i];
