@@ -284,8 +284,9 @@ __global__ void nearfield_kernel(const ProbDesc* __restrict__ probs,
 #pragma unroll
         for (int p = 0; p < 3; ++p) {
           const int lp = TIED ? 0 : p;
-          // FP32 contributions exactly as the pair-sum kernel added them (products of two
-          // FP32 factors, exact in FP64), replaced by the FP64 terms.
+          // FP32 contributions as the scalar FP32 code computes them (products of two FP32
+          // factors, exact in FP64; the packed kernel's can differ by a rounding of a factor),
+          // replaced by the FP64 terms.
           if constexpr (has_hess(VAR)) c[p * NS] += t64.t0[p] - (double)t32.t0[p];
           else c[p * NS] += t64.t0[p] - (double)t32.u[lp] * (double)t32.rb[p];
           if constexpr (has_grad(VAR)) {

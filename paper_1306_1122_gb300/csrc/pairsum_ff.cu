@@ -124,15 +124,16 @@ __global__ void __launch_bounds__(FF_NT) g1_ff_kernel(const G1Args a) {
     // arithmetic
     const bool warp_busy = __any_sync(0xffffffffu, valid);
     // lambda r below the reduction range of sincos_ds for every pixel: |lambda| times the
-    // largest distance to the quadrature grid's box (pixel centres or Gauss points, both inside
-    // [x0 - |hx|, x0 + nx |hx|]); otherwise (rare: a far-out trial lambda) the warp takes the
-    // path with the FP64 fallback, so the common path stays branch-free
+    // largest distance to the quadrature grid's box (pixel centres, or Gauss points of elements
+    // two node spacings wide, all inside [x0 - |hx|, x0 + 2 nx |hx|] with nx quadrature points
+    // per row); otherwise (rare: a far-out trial lambda) the warp takes the path with the FP64
+    // fallback, so the common path stays branch-free
     double lmax = 0.0;
 #pragma unroll
     for (int l = 0; l < NL; ++l) lmax = fmax(lmax, fabs(lamd[l]));
     const double ax = fabs(pd.hx), ay = fabs(pd.hy);
-    const double ex = fmax(fabs(pos.x - (pd.x0 - ax)), fabs(pos.x - (pd.x0 + pd.nx * ax)));
-    const double ey = fmax(fabs(pos.y - (pd.y0 - ay)), fabs(pos.y - (pd.y0 + pd.ny * ay)));
+    const double ex = fmax(fabs(pos.x - (pd.x0 - ax)), fabs(pos.x - (pd.x0 + 2.0 * pd.nx * ax)));
+    const double ey = fmax(fabs(pos.y - (pd.y0 - ay)), fabs(pos.y - (pd.y0 + 2.0 * pd.ny * ay)));
     const double rmax = sqrt(ex * ex + ey * ey + (double)pos.z * pos.z);
     const bool warp_fast =
         __all_sync(0xffffffffu, !valid || lmax * rmax < 0.9 * (double)ff::SC_MAX_ARG);
