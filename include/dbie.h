@@ -109,7 +109,10 @@ typedef struct {
   int32_t* status;     /* (n): DBIE_PT_CONVERGED or DBIE_PT_MAXITER */
   double* f;           /* (n): Eq. 8 at lambda* */
   double* g;           /* (n): Eq. 9 at lambda* */
-  int32_t* nfev;       /* (n): objective evaluations */
+  int32_t* nfev;       /* (n): objective evaluations of the search.  With one shared lambda, a
+                          reflection of the worst vertex through a best vertex at lambda = 0 is
+                          counted but not computed: it is the worst vertex's mirror image, where
+                          Phi (even in lambda) has that vertex's value */
   char* codes;         /* (n, codes_stride): simplex step codes R/E/O/I/S, NUL-padded */
   int32_t codes_stride;
   int32_t reserved0;

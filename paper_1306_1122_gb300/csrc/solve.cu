@@ -570,7 +570,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       for (int m = 0; m <= n; ++m) store_vert(a, g, m, v[m]);
     Vert (&w)[N + 1] = v;
     bool to_check = false, accepted = false, store_R = false, emit_shrink = false;
-    bool emit_trial = false;
+    bool emit_trial = false, mirror = false;
     int next_stage = stage;
     double xt[3] = {0.0, 0.0, 0.0};
     char code = 0;
@@ -652,8 +652,20 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         else if (iters >= a.o.max_iter) fin = PT_MAXITER;
       }
       if (fin < 0) {
-        trial(1.0 + rho, -rho, xt);
-        next_stage = ST_REFLECT;
+        if (n == 1 && w[0].l[0] == 0.0) {
+          // Mirror step: with the best vertex at lambda = 0 the reflection is -w[1], where Phi
+          // (even in lambda, Eq. 6) takes w[1]'s value exactly.  Its comparisons are settled
+          // (not below w[0], by the sort just done; not below w[1], by equality), so the step
+          // goes straight to the inside contraction, and the reflection is counted as the
+          // evaluation the search makes.  Every form then decides these exact ties as exact
+          // arithmetic does, instead of by the rounding of two sums.
+          trial(1.0 - psi, psi, xt);
+          next_stage = ST_ICONTRACT;
+          mirror = true;
+        } else {
+          trial(1.0 + rho, -rho, xt);
+          next_stage = ST_REFLECT;
+        }
         emit_trial = true;
       }
     }
@@ -700,6 +712,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
       SI(a, I_STATUS, g) = fin;
     } else {
       if (to_check) iters += 1;
+      if (mirror) nfev += 1;
       if (emit_trial) {
         double rows[1][3] = {{xt[0], xt[1], xt[2]}};
         for (int d = 0; d < 3; ++d) SD(a, D_TL + d, g) = xt[d];

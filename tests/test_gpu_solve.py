@@ -8,7 +8,11 @@ The simplex takes discrete decisions on Phi, and lambda is not unique (Sect. 2.1
     there lambda agrees to 1e-4 max(|lambda|, 1/L) on >= 99 %; B returned by the GPU equals the
     oracle's field at the GPU's own lambda* (gate of tests/gates.py);
   * mixed form without certification: B at its own lambda* and the search quality statistically
-    (near-tied decisions follow the FP32-term noise)."""
+    (near-tied decisions follow the FP32-term noise).
+With one lambda for all components (tied), a search whose best vertex is lambda = 0 reflects the
+worst vertex w to -w, where Phi, even in lambda, equals Phi(w) exactly: the GPU takes that value
+without evaluating it (and so the exact-arithmetic decision, as the oracle's bitwise-even FP64
+sums do) instead of comparing two roundings."""
 import numpy as np
 import pytest
 
@@ -132,15 +136,20 @@ def test_certified_mixed_solve_follows_oracle(dbie, small, lambda_mode):
     assert np.array_equal(got["nfev"][same], ref["nfev"][same])
 
 
-def test_certified_mixed_solve_ll128_subsample(dbie):
+@pytest.mark.parametrize("lambda_mode", [0, 1])
+def test_certified_mixed_solve_ll128_subsample(dbie, lambda_mode):
     """The same gates on a seeded 384-point subsample of the 131,072-point ll128 workload
-    (128 x 128 boundary, z up to 32 px)."""
+    (128 x 128 boundary, z up to 32 px).  With one shared lambda about 40 % of these points
+    keep lambda* = 0, and every step of their search is a mirror step."""
     w = workloads.ll128(with_truth=False)
     idx = np.sort(np.random.default_rng(128).choice(len(w.points), 384, replace=False))
-    same, lam_ok, rb, st, _, _ = certified_parity(dbie, w.mag, w.points[idx], 128.0)
+    same, lam_ok, rb, st, got, ref = certified_parity(dbie, w.mag, w.points[idx], 128.0,
+                                                      lambda_mode)
     assert same.mean() >= 0.99, same.mean()
     assert lam_ok.mean() >= 0.99, lam_ok.mean()
     assert rb["bad"].size == 0, rb
+    assert np.array_equal(got["iters"][same], ref["iters"][same])
+    assert np.array_equal(got["nfev"][same], ref["nfev"][same])
 
 
 def test_batched_matches_individual(dbie):
@@ -315,3 +324,37 @@ def test_certified_solve_edge_cases(dbie, small):
         assert np.mean([a == b for a, b in zip(got, ref["codes"])]) >= 0.95
     for fl in fields:
         fl.close()
+
+
+def test_batched_tied_lambda_matches_individual(dbie):
+    """One shared lambda per point (lambda_mode 1) through dbie_solve_batched, certified mixed
+    form (the default), over five uneven problems, against each problem's single-problem solve
+    and against the oracle: the same step codes on every point but at most one per problem, and
+    there lambda to 1e-6 relative (1e-4 against the oracle) and equal iteration and evaluation
+    counts."""
+    mags, ppts = _uneven_batch()
+    sel = [p[:60] for p in ppts]
+    opt = dbie.Options(lambda_mode=1, max_iter=40)
+    fields = [dbie.DBIEField.from_magnetogram(m) for m in mags]
+    outs = dbie.solve_batched(fields, [torch.from_numpy(p) for p in sel], opt, codes=40)
+    torch.cuda.synchronize()
+    dec = lambda t: [bytes(r).rstrip(b"\0").decode() for r in t.cpu().numpy()]
+    for mag, f, p, o in zip(mags, fields, sel, outs):
+        single = f.solve(torch.from_numpy(p), opt, codes=40)
+        torch.cuda.synchronize()
+        ref = oracle_solve(mag, p, lambda_mode=1, max_iter=40)
+        cb, cs = dec(o["codes"]), dec(single["codes"])
+        same = np.array([a == b for a, b in zip(cb, cs)])
+        on_ref = np.array([a == b for a, b in zip(cb, ref["codes"])])
+        for i in np.where(~(same & on_ref))[0]:
+            print(f"point {i}: batched {cb[i]}, single {cs[i]}, oracle {ref['codes'][i]}")
+        assert (~same).sum() <= 1 and (~on_ref).sum() <= 1, ((~same).sum(), (~on_ref).sum())
+        lb, ls = o["lam"].cpu().numpy(), single["lam"].cpu().numpy()
+        assert np.all(np.abs(lb - ls)[same] <= 1e-6 * np.maximum(np.abs(ls[same]), 1e-3))
+        assert np.allclose(lb[:, 0], lb[:, 1]) and np.allclose(lb[:, 0], lb[:, 2])
+        assert lam_close(lb[on_ref], ref["lam"][on_ref], max(mag.nx, mag.ny)).all()
+        for k in ("iters", "nfev"):
+            assert np.array_equal(o[k].cpu().numpy()[same], single[k].cpu().numpy()[same]), k
+            assert np.array_equal(o[k].cpu().numpy()[on_ref], ref[k][on_ref]), k
+    for f in fields:
+        f.close()
