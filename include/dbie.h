@@ -188,6 +188,24 @@ dbie_status dbie_eval(dbie_ctx* ctx, int64_t n, const float* xyz, const float* l
                       const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
                       double* dBdlam, double* fgphi, void* stream);
 
+/* Change of the 12 objective sums of Eq. 16 (per component p: S0 = sum u b / r^3, S1 = sum w b / r^3,
+ * Sx, Sy = sum w b (x - x_k) / r^3, (y - y_k); u = theta sin(theta) + cos(theta),
+ * w = lambda^2 cos(theta) - 3 u / r^2, theta = lambda_p r, b = B0_p dA / (2 pi); B_p = z S0,
+ * dB_p/dx = z Sx, dB_p/dy = z Sy, dB_p/dz = S0 + z^2 S1) between lambda_ref and lambda, at n points.
+ * Not in the paper: the re-evaluation step of certified simplex decisions.  The pair terms' changes
+ * come from angle-sum identities (sin and cos of (lambda + lambda_ref) r / 2 and of
+ * (lambda - lambda_ref) r / 2) in FP32, so their error is proportional to |lambda - lambda_ref|;
+ * summed over 8-pixel FP32 blocks and then in float-float.  dS (n, 12): dS[12 i + 4 p + s] for
+ * s = S0, S1, Sx, Sy.  dS_bound (n, 12) or NULL: a worst-case bound of each entry's error
+ * (polynomial in |lambda - lambda_ref| and |lambda| + |lambda_ref| over sum |B0_p| dA / (2 pi r^j),
+ * j = 0..5, plus 1e-12 of the sums at lambda_ref).  Device memory only: xyz (n, 3) float32,
+ * lambda and lambda_ref (n, 3) float64; tied != 0 reads component 0 of each lambda for all three
+ * components.  Every quadrature rule of the context (the pixel-exact near field adds nothing: it
+ * does not depend on lambda).  Asynchronous on stream; n = 0 is a no-op. */
+dbie_status dbie_eval_difference(dbie_ctx* ctx, int64_t n, const float* xyz, const double* lambda,
+                                 const double* lambda_ref, int32_t tied, double* dS,
+                                 double* dS_bound, void* stream);
+
 /* f (Eq. 8), g (Eq. 9), Phi = f + w_g g (fgphi, (n, 3)) and the exact gradient dPhi/dlambda_p
  * (dphi, (n, 3); lambda_p moves component p of B and its spatial derivatives) at n points for
  * given lambda (n, 3) float32.  Either output may be NULL, not both.  Not in the paper: the

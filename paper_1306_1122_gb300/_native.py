@@ -67,6 +67,7 @@ _SIGS = {
     "dbie_set_boundary": (_I32, [_P, _P, _P, _P, _I32, _P]),
     "dbie_eval": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P, _P, _P]),
     "dbie_objective": (_I32, [_P, _I64, _P, _P, ctypes.POINTER(dbie_options), _I32, _P, _P, _P]),
+    "dbie_eval_difference": (_I32, [_P, _I64, _P, _P, _P, _I32, _P, _P, _P]),
     "dbie_solve": (_I32, [_P, _I64, _P, ctypes.POINTER(dbie_options), _P, _I32,
                           ctypes.POINTER(dbie_solve_out), _P]),
     "dbie_solve_batched": (_I32, [_I32, _P, _P, _P, ctypes.POINTER(dbie_options), _P, _I32,
@@ -126,6 +127,10 @@ def dbie_eval(ctx, n, xyz, lam, opt, mem_kind, B, gradB, dBdlam, fgphi, stream):
 def dbie_objective(ctx, n, xyz, lam, opt, mem_kind, fgphi, dphi, stream):
     check(lib.dbie_objective(ctx, n, xyz, lam, None if opt is None else ctypes.byref(opt),
                              mem_kind, fgphi, dphi, stream))
+
+
+def dbie_eval_difference(ctx, n, xyz, lam, lam_ref, tied, dS, dS_bound, stream):
+    check(lib.dbie_eval_difference(ctx, n, xyz, lam, lam_ref, tied, dS, dS_bound, stream))
 
 
 def dbie_solve(ctx, n, xyz, opt, lambda_init, mem_kind, out: dbie_solve_out, stream):

@@ -33,6 +33,7 @@ UNITS = {
     "pairsum_f32_split.cu": [],
     "pairsum_f64.cu": [],
     "pairsum_ff.cu": [],
+    "pairsum_dif.cu": [],
     "vjp.cu": [],
     "noalloc.cu": [],
     "pxe.cu": [],

@@ -165,6 +165,7 @@ struct dbie_ctx {
   DBuf t32, t64, tff, prob, err, misc;
   DBuf st_in, st_out, st_aux;     // host-memory staging
   DBuf qpos, qlam, near_list, out, ptiles;
+  DBuf qlam0, dmsc;                // dbie_eval_difference: reference lambdas, bound sums
   DBuf trace;                     // DBIE_TRACE_ITEMS builds: item timeline of the last pass
   int64_t trace_items = 0;
   DBuf tv32, tv64, probv;         // noise-variance tiles and their problem descriptor
@@ -497,7 +498,8 @@ void dbie_destroy(dbie_ctx* c) {
   for (DBuf* b : {&c->t32, &c->t64, &c->tff, &c->prob, &c->err, &c->misc, &c->st_in, &c->st_out,
                   &c->st_aux, &c->qpos, &c->qlam, &c->near_list, &c->out, &c->ptiles, &c->tv32,
                   &c->tv64, &c->probv, &c->b0raw, &c->vtmp, &c->pxe_corr, &c->pxe_pos,
-                  &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins, &c->trace})
+                  &c->pxe_list, &c->pxe_w, &c->pxe_part, &c->pxe_bins, &c->trace, &c->qlam0,
+                  &c->dmsc})
     b->release();
   c->sb.release();
   for (auto& pr : c->pending) {
@@ -809,6 +811,63 @@ dbie_status dbie_eval(dbie_ctx* c, int64_t n, const float* xyz, const float* lam
     if (fgphi) CUDA_TRY(cudaMemcpyAsync(fgphi, dF, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
     DBIE_TRY(check_device_error(c, s));
   }
+  return DBIE_OK;
+}
+
+dbie_status dbie_eval_difference(dbie_ctx* c, int64_t n, const float* xyz,
+                                 const double* lambda, const double* lambda_ref, int32_t tied,
+                                 double* dS, double* dS_bound, void* stream) {
+  if (!c) return fail(DBIE_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(DBIE_EINVAL, "n must be >= 0");
+  if (n > ((int64_t)1 << 31) - 1) return fail(DBIE_EINVAL, "n too large");
+  if (n > 0 && (!xyz || !lambda || !lambda_ref || !dS))
+    return fail(DBIE_EINVAL, "xyz, lambda, lambda_ref and dS must not be NULL");
+  if (n == 0) return DBIE_OK;
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Misc* m = c->misc.as<Misc>();
+  DBIE_TRY(ensure(c->qpos, sizeof(float4) * n));
+  DBIE_TRY(ensure(c->qlam, sizeof(Lam4) * n));
+  DBIE_TRY(ensure(c->qlam0, sizeof(Lam4) * n));
+  launch_pack_eval(n, xyz, nullptr, lambda_ref, c->qpos.as<float4>(), c->qlam0.as<Lam4>(), nullptr,
+                   nullptr, 0, 0.0, s);
+  launch_pack_eval(n, xyz, nullptr, lambda, c->qpos.as<float4>(), c->qlam.as<Lam4>(), nullptr,
+                   nullptr, 0, 0.0, s);
+  const KernelRef k = g1_ref_dif(tied != 0);
+  const int grid = persistent_grid(k, c->device);
+  const int64_t nblk = (n + k.qper - 1) / k.qper;
+  const int64_t target = std::max<int64_t>(1, (int64_t)grid * DBIE_SPLIT_TARGET_PCT / 100);
+  int64_t nsplit = 1;
+  if (nblk < target) nsplit = std::min<int64_t>((target + nblk - 1) / nblk, c->ntiles);
+  const int64_t nitems = nblk * nsplit;
+  if (nitems > INT32_MAX / 2) return fail(DBIE_EINVAL, "too many points for one call");
+  DBIE_TRY(ensure(c->out, sizeof(double) * nitems * 12 * k.qper));
+  launch_plan_single(&m->plan, m->item_off, m->q_cnt, &m->work, (int)nitems, (int)nsplit, k.qper,
+                     (int)n, s);
+  G1Args a{};
+  a.probs = c->prob.as<ProbDesc>();
+  a.nprob = 1;
+  a.plan = &m->plan;
+  a.item_off = m->item_off;
+  a.q_cnt = m->q_cnt;
+  a.work = &m->work;
+  a.qpos = c->qpos.as<float4>();
+  a.qlam = c->qlam.as<Lam4>();
+  a.qlam0 = c->qlam0.as<Lam4>();
+  a.out = c->out.as<double>();
+  a.err = c->err.as<unsigned>();
+  DBIE_TRY(launch_kernel(k, grid, &a, s));
+  double* msc = nullptr;
+  if (dS_bound) {
+    DBIE_TRY(ensure(c->dmsc, sizeof(double) * 18 * n));
+    msc = c->dmsc.as<double>();
+    launch_msc(c->prob.as<ProbDesc>(), n, c->qpos.as<float4>(), msc, msc + 15 * n,
+               (int)std::min<int64_t>((n + 127) / 128, 32LL * c->sm_count), s);
+  }
+  launch_dif_debug(n, &m->plan, m->item_off, c->out.as<double>(), c->qlam.as<Lam4>(),
+                   c->qlam0.as<Lam4>(), msc, msc ? msc + 15 * n : nullptr, tied ? 1 : 3, dS,
+                   dS_bound, s);
+  CUDA_TRY(cudaGetLastError());
   return DBIE_OK;
 }
 
@@ -1386,7 +1445,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     for (int sd = 0; sd < 2; ++sd)
       CUDA_TRY(cudaMemsetAsync(b.fq_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
     // the error bounds' lambda-independent absolute-value sums of every point
-    launch_msc(b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), b.msc.as<double>(),
+    launch_msc(b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), b.msc.as<double>(), nullptr,
                (int)std::min<int64_t>((N + 127) / 128, 32LL * c->sm_count), s);
     CUDA_TRY(cudaGetLastError());
   }

@@ -120,6 +120,7 @@ struct G1Args {
   double* out;              // per work item a chunk of nsum * qper partial sums (see out_index)
   unsigned* err;
   unsigned long long* trace; // DBIE_TRACE_ITEMS builds: per item start, end (ns) and SM (or null)
+  const Lam4* qlam0;        // [slot] difference sums only: the reference lambda of each query
 };
 
 // Position of partial sum s of the query with local index j (within its problem) for split

@@ -36,6 +36,7 @@ struct KernelRef {
 KernelRef g1_ref_f32(int var, bool tied, int cfg, bool rows);   // pairsum_f32_*.cu
 KernelRef g1_ref_f64(int var, bool tied);            // pairsum_f64.cu
 KernelRef g1_ref_ff(int var, bool tied);             // pairsum_ff.cu (VAR_V, VAR_OBJ)
+KernelRef g1_ref_dif(bool tied);                     // pairsum_dif.cu (objective sums)
 void launch_stage_ff(const double* t64, int ntiles, float* tff, cudaStream_t s);
 KernelRef vjp_ref(bool fp64, bool tied, int cfg);    // vjp.cu
 KernelRef vjp7_ref(bool fp64, bool tied);            // vjp.cu (seven-weight adjoint)
@@ -123,8 +124,11 @@ void launch_solve_init(const SolveArgs& a, const double* lam_init, int grid, cud
 void launch_plan_round(const PlanArgs& a, cudaStream_t s);
 void launch_nm_step(const SolveArgs& a, int grid, cudaStream_t s);
 void launch_nm_refine(const SolveArgs& a, int grid, cudaStream_t s);
-void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, int grid,
-                cudaStream_t s);
+void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, double* msc0,
+                int grid, cudaStream_t s);
+void launch_dif_debug(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,
+                      const Lam4* qlam, const Lam4* qlam0, const double* msc, const double* msc0,
+                      int dim, double* dS, double* dS_bound, cudaStream_t s);
 void launch_certb_flag(const SolveArgs& a, double rel, int grid, cudaStream_t s);
 void launch_certb_apply(const SolveArgs& a, int grid, cudaStream_t s);
 

@@ -249,6 +249,23 @@ __device__ __forceinline__ const double* corr_of(const SolveArgs& a, const ProbD
 constexpr double BND_A0 = 9.5e-7, BND_A1 = 1.06e-6, BND_A2 = 1.1e-7, BND_A3 = 1.45e-6,
                  BND_A4 = 1.56e-6;
 
+// First-order bound of Phi's error from the bounds dB (3) and dG (9) of B and grad B.
+__device__ __forceinline__ double propagate_bound(const double dB[3], const double dG[9],
+                                                  const double B[3], const double G[9],
+                                                  double g, double g_scale, double w_g) {
+  const double Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
+  const double nJ = sqrt(Jx * Jx + Jy * Jy + Jz * Jz);
+  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  const double dJx = dG[7] + dG[5], dJy = dG[2] + dG[6], dJz = dG[3] + dG[1];
+  const double ndJ = sqrt(dJx * dJx + dJy * dJy + dJz * dJz);
+  const double ndB = sqrt(dB[0] * dB[0] + dB[1] * dB[1] + dB[2] * dB[2]);
+  if (!(nB > 0.0)) return 2.0;
+  double sf = nJ > 0.0 ? ndJ / nJ + ndB / nB : 1.0;
+  if (sf > 1.0) sf = 1.0;
+  const double sg = g_scale * (dG[0] + dG[4] + dG[8]) / nB + g * ndB / nB;
+  return sf + w_g * sg;
+}
+
 __device__ __forceinline__ double mixed_phi_bound(const double* M, const double lam[3], int dim,
                                                    double z, const double B[3], const double G[9],
                                                    double g, double g_scale, double w_g) {
@@ -268,17 +285,66 @@ __device__ __forceinline__ double mixed_phi_bound(const double* M, const double 
     dG[3 * p + 1] = z * sx;
     dG[3 * p + 2] = s0 + z * z * s1;
   }
-  const double Jx = G[7] - G[5], Jy = G[2] - G[6], Jz = G[3] - G[1];
-  const double nJ = sqrt(Jx * Jx + Jy * Jy + Jz * Jz);
-  const double nB = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
-  const double dJx = dG[7] + dG[5], dJy = dG[2] + dG[6], dJz = dG[3] + dG[1];
-  const double ndJ = sqrt(dJx * dJx + dJy * dJy + dJz * dJz);
-  const double ndB = sqrt(dB[0] * dB[0] + dB[1] * dB[1] + dB[2] * dB[2]);
-  if (!(nB > 0.0)) return 2.0;
-  double sf = nJ > 0.0 ? ndJ / nJ + ndB / nB : 1.0;
-  if (sf > 1.0) sf = 1.0;
-  const double sg = g_scale * (dG[0] + dG[4] + dG[8]) / nB + g * ndB / nB;
-  return sf + w_g * sg;
+  return propagate_bound(dB, dG, B, G, g, g_scale, w_g);
+}
+
+// Error bounds of the difference sums (pairsum_dif.cu) that take a point's float-float
+// reference sums at lambda_0 to lambda_a, per component p, with dl = |lambda_a - lambda_0| and
+// L = |lambda_a| + |lambda_0|.  Every product of a pixel's difference terms carries a factor
+// |delta| = dl r / 2 (or dl).  With the operation accuracies of mixed_phi_bound (SFU sine and
+// cosine of sigma within 3.3e-7 + 1.1e-7 |sigma| absolute, sigma, delta and r within 3.2e-7
+// relative, the Taylor sine and cosine of delta within 3e-8, FP32 rounding, and sums over blocks
+// of 8 pixels in FP32) the changes du of u and dw of psi r^3 are in error by at most
+//   dl (2.1e-6 r + 2.6e-6 L r^2 + 1.1e-7 L^2 r^3)                   (du, b / r^3 included)
+//   dl (6.3e-6 / r + 1.22e-5 L + 2.6e-6 L^2 r + 1.1e-7 L^3 r^2)     (dw)
+// (|du| <= dl L r^2 and |dw| <= dl (5 L + L^2 r) bound the relative roundings), and summed with
+// |b| / r^3 they become polynomials in dl and L over the point's sums M_j = sum_k |b_pk| / r^j,
+// j = 0..5.  The coefficients below are twice those.  The float-float reference sums add 1e-12
+// of their absolute-value sums (their measured error is at most 1.4e-13 of them).
+constexpr double DIF_C00 = 4.2e-6, DIF_C01 = 5.2e-6, DIF_C02 = 2.2e-7;
+constexpr double DIF_C10 = 1.3e-5, DIF_C11 = 2.4e-5, DIF_C12 = 5.2e-6, DIF_C13 = 2.2e-7;
+constexpr double DIF_FF = 1e-12;
+
+// e[4 p + s]: bounds of S0, S1, Sx, Sy of component p (M: M_1..M_5 per component, M0: M_0).
+__device__ __forceinline__ void dif_sum_bounds(const double* M, const double* M0,
+                                               const double la[3], const double l0[3], int dim,
+                                               double e[12]) {
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    const int q = dim == 1 ? 0 : p;
+    const double dl = fabs(la[q] - l0[q]);
+    const double L = fabs(la[q]) + fabs(l0[q]), L2 = L * L, L3 = L2 * L;
+    const double R = fabs(l0[q]), R2 = R * R;
+    const double* m = M + 5 * p;   // m[j - 1] = M_j
+    const double m0 = M0[p];
+    const double e0 = dl * (DIF_C00 * m[1] + DIF_C01 * L * m[0] + DIF_C02 * L2 * m0) +
+                      DIF_FF * (m[2] + R * m[1]);
+    const double e1 = dl * (DIF_C10 * m[3] + DIF_C11 * L * m[2] + DIF_C12 * L2 * m[1] +
+                            DIF_C13 * L3 * m[0]) +
+                      DIF_FF * (3.0 * m[4] + 3.0 * R * m[3] + R2 * m[2]);
+    const double ex = dl * (DIF_C10 * m[2] + DIF_C11 * L * m[1] + DIF_C12 * L2 * m[0] +
+                            DIF_C13 * L3 * m0) +
+                      DIF_FF * (3.0 * m[3] + 3.0 * R * m[2] + R2 * m[1]);
+    e[4 * p + 0] = e0;
+    e[4 * p + 1] = e1;
+    e[4 * p + 2] = ex;
+    e[4 * p + 3] = ex;
+  }
+}
+
+// Phi bound of a value assembled from reference plus difference sums with sum bounds e.
+__device__ __forceinline__ double dif_phi_bound(const double e[12], double z, const double B[3],
+                                                const double G[9], double g, double g_scale,
+                                                double w_g) {
+  double dB[3], dG[9];
+#pragma unroll
+  for (int p = 0; p < 3; ++p) {
+    dB[p] = z * e[4 * p];
+    dG[3 * p + 0] = z * e[4 * p + 2];
+    dG[3 * p + 1] = z * e[4 * p + 3];
+    dG[3 * p + 2] = e[4 * p] + z * z * e[4 * p + 1];
+  }
+  return propagate_bound(dB, dG, B, G, g, g_scale, w_g);
 }
 
 // The first near tie of a step: a comparison whose two values differ by no more than `band`
@@ -812,18 +878,19 @@ void launch_plan_round(const PlanArgs& a, cudaStream_t s) { plan_round_kernel<<<
 // quadrature points of the point's problem.  FP32 terms summed per tile, tiles summed in FP64
 // (relative error below 1e-4: a scale, not a result).
 __global__ void msc_kernel(const ProbDesc* __restrict__ probs, int64_t N,
-                           const float4* __restrict__ ppos, double* __restrict__ msc) {
+                           const float4* __restrict__ ppos, double* __restrict__ msc,
+                           double* __restrict__ msc0) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < N;
        g += (int64_t)gridDim.x * blockDim.x) {
     const float4 pos = ppos[g];
     const ProbDesc& pd = probs[__float_as_int(pos.w)];
     const float z2 = __fmul_rn(pos.z, pos.z);
-    double tot[15];
+    double tot[15], tot0[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 0; i < 15; ++i) tot[i] = 0.0;
     for (int t = 0; t < pd.ntiles; ++t) {
       const float* T = pd.tiles32 + (int64_t)t * pd.nf32 * TILE;
-      float acc[15];
+      float acc[15], acc0[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < 15; ++i) acc[i] = 0.f;
 #pragma unroll 2
@@ -832,6 +899,8 @@ __global__ void msc_kernel(const ProbDesc* __restrict__ probs, int64_t N,
         const float ri = rsqrtf(dx * dx + dy * dy + z2);
         const float b[3] = {fabsf(__ldg(T + 2 * TILE + e)), fabsf(__ldg(T + 3 * TILE + e)),
                             fabsf(__ldg(T + 4 * TILE + e))};
+#pragma unroll
+        for (int p = 0; p < 3; ++p) acc0[p] += b[p];
         float wj = ri;
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
@@ -842,15 +911,50 @@ __global__ void msc_kernel(const ProbDesc* __restrict__ probs, int64_t N,
       }
 #pragma unroll
       for (int i = 0; i < 15; ++i) tot[i] += (double)acc[i];
+#pragma unroll
+      for (int p = 0; p < 3; ++p) tot0[p] += (double)acc0[p];
     }
 #pragma unroll
     for (int i = 0; i < 15; ++i) msc[15 * g + i] = tot[i];
+    if (msc0)
+#pragma unroll
+      for (int p = 0; p < 3; ++p) msc0[3 * g + p] = tot0[p];
   }
 }
 
-void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, int grid,
-                cudaStream_t s) {
-  if (N > 0) msc_kernel<<<grid, 128, 0, s>>>(probs, N, ppos, msc);
+void launch_msc(const ProbDesc* probs, int64_t N, const float4* ppos, double* msc, double* msc0,
+                int grid, cudaStream_t s) {
+  if (N > 0) msc_kernel<<<grid, 128, 0, s>>>(probs, N, ppos, msc, msc0);
+}
+
+// Difference sums of n queries of one problem (slots 0..n-1) and their bounds (debug entry).
+__global__ void dif_debug_kernel(int64_t n, const PlanHdr* __restrict__ plan,
+                                 const int32_t* __restrict__ item_off,
+                                 const double* __restrict__ out, const Lam4* __restrict__ qlam,
+                                 const Lam4* __restrict__ qlam0, const double* __restrict__ msc,
+                                 const double* __restrict__ msc0, int dim, double* dS,
+                                 double* dS_bound) {
+  const PlanHdr h = *plan;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int s = 0; s < 12; ++s) dS[12 * i + s] = gather_sum(out, h, item_off, 0, i, 12, s);
+    if (dS_bound) {
+      const double la[3] = {qlam[i].x, qlam[i].y, qlam[i].z};
+      const double l0[3] = {qlam0[i].x, qlam0[i].y, qlam0[i].z};
+      double e[12];
+      dif_sum_bounds(msc + 15 * i, msc0 + 3 * i, la, l0, dim, e);
+      for (int s = 0; s < 12; ++s) dS_bound[12 * i + s] = e[s];
+    }
+  }
+}
+
+void launch_dif_debug(int64_t n, const PlanHdr* plan, const int32_t* item_off, const double* out,
+                      const Lam4* qlam, const Lam4* qlam0, const double* msc, const double* msc0,
+                      int dim, double* dS, double* dS_bound, cudaStream_t s) {
+  const int64_t nb = (n + 127) / 128;
+  if (n > 0)
+    dif_debug_kernel<<<(int)(nb < 1024 ? nb : 1024), 128, 0, s>>>(
+        n, plan, item_off, out, qlam, qlam0, msc, msc0, dim, dS, dS_bound);
 }
 
 // ------------------------------------------------------------------ certified B ----

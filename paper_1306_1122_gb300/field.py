@@ -132,6 +132,19 @@ class DBIEField:
                          N.DBIE_MEM_DEVICE, _ptr(F), _ptr(D), _stream())
         return dict(f=F[:, 0], g=F[:, 1], phi=F[:, 2], dphi=D)
 
+    def eval_difference(self, xyz, lam, lam_ref, tied=False, bound=True):
+        """Change of the 12 objective sums between lam_ref and lam (n, 12 float64; per component
+        S0, S1, Sx, Sy) and, with bound, the worst-case bound of each entry's error."""
+        xyz = _dev_f32(xyz, self.device).reshape(-1, 3)
+        lam = _dev_f64(lam, self.device).reshape(-1, 3)
+        lam_ref = _dev_f64(lam_ref, self.device).reshape(-1, 3)
+        n = xyz.shape[0]
+        dS = torch.empty((n, 12), device=self.device, dtype=torch.float64)
+        dSb = torch.empty((n, 12), device=self.device, dtype=torch.float64) if bound else None
+        N.dbie_eval_difference(self._h, n, _ptr(xyz), _ptr(lam), _ptr(lam_ref), int(bool(tied)),
+                               _ptr(dS), _ptr(dSb), _stream())
+        return (dS, dSb) if bound else dS
+
     def _solve_out(self, n, codes):
         kw = dict(device=self.device)
         r = dict(B=torch.empty((n, 3), dtype=torch.float64, **kw),
