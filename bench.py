@@ -184,7 +184,8 @@ def run_ours(args):
         st = N.dbie_get_stats(h, True)   # synchronises: pair-sum kernel event timings
         stats_out.append(dict(queries=st.queries, rounds=st.rounds, obj_ms=st.objective_ms,
                               launches=st.launches, obj_pairs=st.objective_pairs, ties=st.ties,
-                              ff_pairs=st.refine_pairs, ff_ms=st.refine_ms))
+                              ff_pairs=st.refine_pairs, ff_ms=st.refine_ms, difs=st.difs,
+                              dif_pairs=st.dif_pairs, dif_ms=st.dif_ms))
         return r
 
     P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
@@ -288,7 +289,8 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "points": n, "boundary": [m.ny, m.nx],
                    "precision": "mixed (FP32 pair terms, float-float sums, FP64 near field "
                                 "z<=2px, FP64 objective and simplex; near-tied simplex "
-                                "decisions re-evaluated in the float-float form)",
+                                "decisions re-evaluated in the float-float form, or as "
+                                "differences from a float-float reference value)",
                    "fwd_bwd": "solve (Nelder-Mead, tol 1e-6, max 50 it) + adjoint + dL/dlambda",
                    "pairs_per_step": pairs_step, "simplex_rounds": rounds,
                    "objective_evals": q, "l2": "flushed before each step (256 MB write)",
@@ -309,7 +311,13 @@ def run_ours(args):
             "near_tie_frac_of_evals": stats[-1]["ties"] / max(1, q),
             "float_float_pairs_per_step": stats[-1]["ff_pairs"],
             "float_float_ms_per_step": sum(s["ff_ms"] for s in stats) / args.steps,
-            "band": 0.02},
+            "difference_values_per_step": stats[-1]["difs"],
+            "difference_pairs_per_step": stats[-1]["dif_pairs"],
+            "difference_ms_per_step": sum(s["dif_ms"] for s in stats) / args.steps,
+            "difference_pairs_per_s": (stats[-1]["dif_pairs"] /
+                                       (sum(s["dif_ms"] for s in stats) / args.steps / 1e3))
+            if any(s["dif_ms"] for s in stats) else None,
+            "band": 0.02, "band_difference": 0.02},
         "roofline": {"bound": "alu", "pipe": "MUFU (rsqrt, sin, cos)",
                      "kernel": "g1_kernel<float, objective, per-component lambda>",
                      "achieved": achieved, "peak": peak, "unit": "T MUFU-op/s",
@@ -323,10 +331,11 @@ def run_ours(args):
                                     "2070 MHz max SM clock"},
         "e2e": {"value": e2e_value, "unit": "pair-evals/s",
                 "h2d_bytes_per_step": int(h2d[-1]), "d2h_bytes_per_step": int(d2h[-1])},
-        # per step: staging 5 (checks, FP32/FP64 and float-float tiles), solve 4 + 7 per round (plan, pair sums, near field, simplex step;
-        # float-float plan, pair sums, simplex step), backward 9 (pack, plan, adjoint, finalize;
-        # pack, plan, pair sums, near field, finalize)
-        "gpu_launches": int(args.steps * (5 + 4 + 7 * rounds + 9)),
+        # per step: staging 5 (checks, FP32/FP64 and float-float tiles), solve 4 + 9 per round
+        # (plan, pair sums, near field, simplex step; float-float plan and pair sums, difference
+        # plan and pair sums, simplex step), backward 9 (pack, plan, adjoint, finalize; pack,
+        # plan, pair sums, near field, finalize)
+        "gpu_launches": int(args.steps * (5 + 4 + 9 * rounds + 9)),
         "clocks": clocks,
         "wall_s": wall,
     }
@@ -396,6 +405,7 @@ def fp64_compare(w, npts, dev):
             "near_ties": int(st["ties"]), "objective_evals": int(st["queries"]),
             "near_tie_frac_of_evals": st["ties"] / max(1, st["queries"]),
             "float_float_pairs": st["refine_pairs"], "float_float_ms": st["refine_ms"],
+            "difference_values": st["difs"], "difference_ms": st["dif_ms"],
             "objective_ms": st["objective_ms"]}
     tm, rm, _ = out["mixed"]
     res["mixed"]["B_vs_fp64_at_mixed_lambda"] = b_error_stats(f, w.mag, w.points[idx],

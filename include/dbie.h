@@ -99,6 +99,18 @@ typedef struct {
                           again in float-float at lambda*.  0 disables; default 0.02 (the largest measured gap of a
                           decision that the FP32-term sums flipped was 0.009 times that sum of
                           bounds).  Not used by the FP64 form or the quasi-Newton search. */
+  double certify_ref;  /* certified decisions, second level: once a point has a float-float value
+                          (its reference), near-tied values of that point that lie close to the
+                          reference in lambda are first re-evaluated as the reference's sums plus
+                          the difference sums of dbie_eval_difference, whose error bound shrinks
+                          with |lambda - lambda_ref|; such a value is near-tied again when it is
+                          within certify_ref times that bound (plus the other value's radius), and
+                          then goes to float-float.  Without a reference, a near tie of two
+                          mixed-form values re-evaluates the one with the larger bound in
+                          float-float first.  0 disables the level (every near tie in
+                          float-float); default 0.02 (the mixed form's band: on 16,384 ll128 and
+                          2,048 ar512 points the search took the FP64 form's step sequence on
+                          every point with it). */
 } dbie_options;
 
 /* Per-point outputs of dbie_solve; every pointer may be NULL except B and lambda. */
@@ -132,6 +144,10 @@ typedef struct {
   double refine_ms;        /* CUDA-event time of the float-float passes (while profiling) */
   int64_t b_refined;       /* certified decisions: points whose final B the error bound did not
                               certify to 1e-5 relative, re-evaluated in float-float at lambda* */
+  int64_t difs;            /* certified decisions: near-tied values re-evaluated as differences
+                              from the point's float-float reference (certify_ref) */
+  double dif_pairs;        /* their point x pixel pairs */
+  double dif_ms;           /* CUDA-event time of the difference passes (while profiling) */
 } dbie_stats;
 
 /* Fill `opt` with the defaults listed above. */

@@ -29,7 +29,7 @@ class dbie_options(ctypes.Structure):
                 ("simplex_step", ctypes.c_double), ("w_g", ctypes.c_double),
                 ("g_scale", ctypes.c_double), ("precision", ctypes.c_int32),
                 ("method", ctypes.c_int32), ("near_z", ctypes.c_double),
-                ("certify", ctypes.c_double)]
+                ("certify", ctypes.c_double), ("certify_ref", ctypes.c_double)]
 
 
 class dbie_solve_out(ctypes.Structure):
@@ -45,7 +45,8 @@ class dbie_stats(ctypes.Structure):
                 ("objective_ms", ctypes.c_double), ("rounds", ctypes.c_int64),
                 ("queries", ctypes.c_int64), ("ties", ctypes.c_int64),
                 ("refine_pairs", ctypes.c_double), ("refine_ms", ctypes.c_double),
-                ("b_refined", ctypes.c_int64)]
+                ("b_refined", ctypes.c_int64), ("difs", ctypes.c_int64),
+                ("dif_pairs", ctypes.c_double), ("dif_ms", ctypes.c_double)]
 
 
 class DBIEError(RuntimeError):

@@ -85,16 +85,19 @@ struct SolveBufs {
   DBuf qpos[2], qlam[2], q_cnt[2], act[2], near[2];
   DBuf msc, fout, fq_cnt_pass, fitem_off;            // certified decisions
   DBuf fpos[2], flam[2], fq_cnt[2], ref[2];
+  DBuf dout, dq_cnt_pass, ditem_off;                  // its difference level
+  DBuf dpos[2], dlam[2], dlam0[2], dq_cnt[2];
   cudaGraphExec_t exec = nullptr;
   std::vector<unsigned char> key;   // launch arguments the cached graph was captured with
-  std::vector<cudaEvent_t> ev;      // profiling events inside the graph (4 per round)
+  std::vector<cudaEvent_t> ev;      // profiling events inside the graph (6 per round)
   void release() {
     for (DBuf* b : {&probs, &ppos, &lam0, &sd, &si, &q_cnt_pass, &item_off, &ctrl, &out, &res,
-                    &codes, &corr, &msc, &fout, &fq_cnt_pass, &fitem_off})
+                    &codes, &corr, &msc, &fout, &fq_cnt_pass, &fitem_off, &dout, &dq_cnt_pass,
+                    &ditem_off})
       b->release();
     for (int s = 0; s < 2; ++s)
       for (DBuf* b : {&qpos[s], &qlam[s], &q_cnt[s], &act[s], &near[s], &fpos[s], &flam[s],
-                      &fq_cnt[s], &ref[s]})
+                      &fq_cnt[s], &ref[s], &dpos[s], &dlam[s], &dlam0[s], &dq_cnt[s]})
         b->release();
     if (exec) cudaGraphExecDestroy(exec);
     exec = nullptr;
@@ -121,6 +124,12 @@ struct SolveCtrl {
   int32_t pad2;
   unsigned long long stat_ties;
   double stat_ff_pairs;
+  // and its difference level
+  PlanHdr dplan;
+  int32_t dwork;
+  int32_t pad3;
+  unsigned long long stat_difs;
+  double stat_dif_pairs;
 };
 
 int device_sm_count(int dev) {
@@ -214,6 +223,8 @@ dbie_status check_opts(const dbie_options& o) {
     return fail(DBIE_EINVAL, "method must be DBIE_METHOD_SIMPLEX or DBIE_METHOD_QUASI_NEWTON");
   if (!(o.certify >= 0) || !std::isfinite(o.certify))
     return fail(DBIE_EINVAL, "certify must be finite and >= 0");
+  if (!(o.certify_ref >= 0) || !std::isfinite(o.certify_ref))
+    return fail(DBIE_EINVAL, "certify_ref must be finite and >= 0");
   if (!std::isfinite(o.simplex_step) || !std::isfinite(o.w_g) || !std::isfinite(o.g_scale) ||
       !std::isfinite(o.near_z) || !std::isfinite(o.eps_f) || !std::isfinite(o.eps_g))
     return fail(DBIE_EINVAL, "options must be finite");
@@ -480,6 +491,7 @@ void dbie_default_options(dbie_options* o) {
   o->eps_g = 1e-4;
   o->tol = 1e-6;
   o->certify = 0.02;
+  o->certify_ref = 0.02;
   o->max_iter = 50;
   o->lambda_mode = DBIE_LAMBDA_PER_COMPONENT;
   o->simplex_step = 0.0;
@@ -1348,6 +1360,13 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   const int target_ff = std::max(1, (int)((int64_t)grid_ff * DBIE_FF_SPLIT_TARGET_PCT / 100));
   const int64_t fitems_cap = std::max<int64_t>((2 * N + kf.qper - 1) / kf.qper + nprob,
                                                2LL * target_ff) + 1;
+  // difference level of the re-evaluation (values near the point's float-float reference)
+  const bool dif_on = cert && o.certify_ref > 0;
+  const KernelRef kd = g1_ref_dif(tied);
+  const int grid_dif = dif_on ? persistent_grid(kd, c->device) : 0;
+  const int target_dif = std::max(1, (int)((int64_t)grid_dif * DBIE_FF_SPLIT_TARGET_PCT / 100));
+  const int64_t ditems_cap = std::max<int64_t>((2 * N + kd.qper - 1) / kd.qper + nprob,
+                                               2LL * target_dif) + 1;
 
   DBIE_TRY(ensure(b.probs, sizeof(ProbDesc) * nprob));
   DBIE_TRY(ensure(b.ppos, sizeof(float4) * N));
@@ -1367,7 +1386,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (!fp64) DBIE_TRY(ensure(b.near[sd], sizeof(int32_t) * Qcap));
   }
   if (cert) {
-    DBIE_TRY(ensure(b.msc, sizeof(double) * 15 * N));
+    DBIE_TRY(ensure(b.msc, sizeof(double) * 18 * N));
     DBIE_TRY(ensure(b.fout, sizeof(double) * fitems_cap * 12 * kf.qper));
     DBIE_TRY(ensure(b.fq_cnt_pass, sizeof(int32_t) * nprob));
     DBIE_TRY(ensure(b.fitem_off, sizeof(int32_t) * (nprob + 1)));
@@ -1376,6 +1395,17 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       DBIE_TRY(ensure(b.flam[sd], sizeof(Lam4) * 2 * N));
       DBIE_TRY(ensure(b.fq_cnt[sd], sizeof(int32_t) * nprob));
       DBIE_TRY(ensure(b.ref[sd], sizeof(int32_t) * N));
+    }
+  }
+  if (dif_on) {
+    DBIE_TRY(ensure(b.dout, sizeof(double) * ditems_cap * 12 * kd.qper));
+    DBIE_TRY(ensure(b.dq_cnt_pass, sizeof(int32_t) * nprob));
+    DBIE_TRY(ensure(b.ditem_off, sizeof(int32_t) * (nprob + 1)));
+    for (int sd = 0; sd < 2; ++sd) {
+      DBIE_TRY(ensure(b.dpos[sd], sizeof(float4) * 2 * N));
+      DBIE_TRY(ensure(b.dlam[sd], sizeof(Lam4) * 2 * N));
+      DBIE_TRY(ensure(b.dlam0[sd], sizeof(Lam4) * 2 * N));
+      DBIE_TRY(ensure(b.dq_cnt[sd], sizeof(int32_t) * nprob));
     }
   }
   bool any_init = false;
@@ -1444,8 +1474,12 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   if (cert) {
     for (int sd = 0; sd < 2; ++sd)
       CUDA_TRY(cudaMemsetAsync(b.fq_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
+    if (dif_on)
+      for (int sd = 0; sd < 2; ++sd)
+        CUDA_TRY(cudaMemsetAsync(b.dq_cnt[sd].p, 0, sizeof(int32_t) * nprob, s));
     // the error bounds' lambda-independent absolute-value sums of every point
-    launch_msc(b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), b.msc.as<double>(), nullptr,
+    launch_msc(b.probs.as<ProbDesc>(), N, b.ppos.as<float4>(), b.msc.as<double>(),
+               b.msc.as<double>() + 15 * N,
                (int)std::min<int64_t>((N + 127) / 128, 32LL * c->sm_count), s);
     CUDA_TRY(cudaGetLastError());
   }
@@ -1483,16 +1517,20 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     a.cur = RoundBuf{b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(), b.q_cnt[cur].as<int32_t>(),
                      b.act[cur].as<int32_t>(), &ctrl->act_cnt[cur], b.near[cur].as<int32_t>(),
                      &ctrl->near_cnt[cur], b.fpos[cur].as<float4>(), b.flam[cur].as<Lam4>(),
-                     b.fq_cnt[cur].as<int32_t>(), b.ref[cur].as<int32_t>(), &ctrl->ref_cnt[cur]};
+                     b.fq_cnt[cur].as<int32_t>(), b.ref[cur].as<int32_t>(), &ctrl->ref_cnt[cur],
+                     b.dpos[cur].as<float4>(), b.dlam[cur].as<Lam4>(), b.dlam0[cur].as<Lam4>(),
+                     b.dq_cnt[cur].as<int32_t>()};
     a.nxt = RoundBuf{b.qpos[nx_].as<float4>(), b.qlam[nx_].as<Lam4>(), b.q_cnt[nx_].as<int32_t>(),
                      b.act[nx_].as<int32_t>(), &ctrl->act_cnt[nx_], b.near[nx_].as<int32_t>(),
                      &ctrl->near_cnt[nx_], b.fpos[nx_].as<float4>(), b.flam[nx_].as<Lam4>(),
-                     b.fq_cnt[nx_].as<int32_t>(), b.ref[nx_].as<int32_t>(), &ctrl->ref_cnt[nx_]};
+                     b.fq_cnt[nx_].as<int32_t>(), b.ref[nx_].as<int32_t>(), &ctrl->ref_cnt[nx_],
+                     b.dpos[nx_].as<float4>(), b.dlam[nx_].as<Lam4>(), b.dlam0[nx_].as<Lam4>(),
+                     b.dq_cnt[nx_].as<int32_t>()};
     a.out = b.out.as<double>();
     a.plan = &ctrl->plan;
     a.item_off = b.item_off.as<int32_t>();
     a.o = SolveOpts{o.eps_f, o.eps_g, o.tol, o.w_g, cert ? o.certify : 0.0, o.max_iter, dim,
-                    near_on ? 1 : 0, 0};
+                    near_on ? 1 : 0, 0, dif_on ? o.certify_ref : 0.0};
     a.res_B = res_B;
     a.res_lam = res_lam;
     a.res_f = res_f;
@@ -1510,6 +1548,13 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       a.fplan = &ctrl->fplan;
       a.fitem_off = b.fitem_off.as<int32_t>();
       a.stat_ties = &ctrl->stat_ties;
+      a.msc0 = b.msc.as<double>() + 15 * N;
+    }
+    if (dif_on) {
+      a.dout = b.dout.as<double>();
+      a.dplan = &ctrl->dplan;
+      a.ditem_off = b.ditem_off.as<int32_t>();
+      a.stat_difs = &ctrl->stat_difs;
     }
   }
   // Initial simplex and its queries go to side 0.
@@ -1542,6 +1587,7 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
         pa.fq_cnt_nxt = b.fq_cnt[cur ^ 1].as<int32_t>();
         pa.ref_cnt_nxt = &ctrl->ref_cnt[cur ^ 1];
       }
+      if (dif_on) pa.dq_cnt_nxt = b.dq_cnt[cur ^ 1].as<int32_t>();
       pa.round_ctr = &ctrl->round;
       pa.stat_queries = &ctrl->stat_queries;
       pa.stat_pairs = &ctrl->stat_pairs;
@@ -1559,10 +1605,10 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
       ga.err = c->err.as<unsigned>();
       // External event records become event-record nodes of the graph (plain records inside a
       // capture only order work and are never timestamped).
-      if (c->profiling) CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r], cs, cudaEventRecordExternal));
+      if (c->profiling) CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r], cs, cudaEventRecordExternal));
       DBIE_TRY(launch_kernel(k, grid, &ga, cs));
       if (c->profiling)
-        CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 1], cs, cudaEventRecordExternal));
+        CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 1], cs, cudaEventRecordExternal));
       if (near_on)
         launch_nearfield(var, tied, b.probs.as<ProbDesc>(), b.near[cur].as<int32_t>(),
                          &ctrl->near_cnt[cur], b.qpos[cur].as<float4>(), b.qlam[cur].as<Lam4>(),
@@ -1596,19 +1642,52 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
         gf.out = b.fout.as<double>();
         gf.err = c->err.as<unsigned>();
         if (c->profiling)
-          CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 2], cs, cudaEventRecordExternal));
+          CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 2], cs, cudaEventRecordExternal));
         DBIE_TRY(launch_kernel(kf, grid_ff, &gf, cs));
         if (c->profiling)
-          CUDA_TRY(cudaEventRecordWithFlags(b.ev[4 * r + 3], cs, cudaEventRecordExternal));
+          CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 3], cs, cudaEventRecordExternal));
+        if (dif_on) {
+          // ... and the near-tied values queued as differences from the points' references
+          PlanArgs pd{};
+          pd.probs = b.probs.as<ProbDesc>();
+          pd.nprob = nprob;
+          pd.qper = kd.qper;
+          pd.target_items = target_dif;
+          pd.nsplit_cap = 1 << 20;
+          pd.q_cnt_cur = b.dq_cnt[cur].as<int32_t>();
+          pd.q_cnt_pass = b.dq_cnt_pass.as<int32_t>();
+          pd.item_off = b.ditem_off.as<int32_t>();
+          pd.plan = &ctrl->dplan;
+          pd.work = &ctrl->dwork;
+          pd.stat_pairs = &ctrl->stat_dif_pairs;
+          launch_plan_round(pd, cs);
+          G1Args gd{};
+          gd.probs = b.probs.as<ProbDesc>();
+          gd.nprob = nprob;
+          gd.plan = &ctrl->dplan;
+          gd.item_off = b.ditem_off.as<int32_t>();
+          gd.q_cnt = b.dq_cnt_pass.as<int32_t>();
+          gd.work = &ctrl->dwork;
+          gd.qpos = b.dpos[cur].as<float4>();
+          gd.qlam = b.dlam[cur].as<Lam4>();
+          gd.qlam0 = b.dlam0[cur].as<Lam4>();
+          gd.out = b.dout.as<double>();
+          gd.err = c->err.as<unsigned>();
+          if (c->profiling)
+            CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 4], cs, cudaEventRecordExternal));
+          DBIE_TRY(launch_kernel(kd, grid_dif, &gd, cs));
+          if (c->profiling)
+            CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 5], cs, cudaEventRecordExternal));
+        }
         launch_nm_refine(sa[cur], nm_grid, cs);
       }
     }
     CUDA_TRY(cudaGetLastError());
     return DBIE_OK;
   };
-  if (c->profiling && b.ev.size() != 4 * K) {
+  if (c->profiling && b.ev.size() != 6 * K) {
     for (cudaEvent_t e : b.ev) cudaEventDestroy(e);
-    b.ev.assign(4 * K, nullptr);
+    b.ev.assign(6 * K, nullptr);
     for (auto& e : b.ev) CUDA_TRY(cudaEventCreate(&e));
   }
   // Capture (or reuse) the graph of K rounds; the key is every launch argument.
@@ -1640,8 +1719,9 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   // Rounds a point can take: the simplex spends at most 3 per iteration; the quasi-Newton search
   // at most 31 line-search trials (alpha = 1 ... 2^-30) per accepted step.
   // A certified step waits at most once per value it compares (4 vertices, the trial and the
-  // reflected point), each re-evaluation removing one bound.
-  const int max_rounds = (qn ? 31 : (cert ? 21 : 3)) * o.max_iter + (cert ? 14 : 8);
+  // reflected point), each re-evaluation removing one bound; twice with the difference level
+  // (a difference value that ties again goes to float-float).
+  const int max_rounds = (qn ? 31 : (dif_on ? 39 : (cert ? 21 : 3))) * o.max_iter + (cert ? 26 : 8);
   const int max_launches = max_rounds / K + 2;
   int launches = 0;
   for (;;) {
@@ -1656,14 +1736,17 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
     if (c->profiling) {
       for (int r = 0; r < K; ++r) {
         float ms = 0.f;
-        const cudaError_t te = cudaEventElapsedTime(&ms, b.ev[4 * r], b.ev[4 * r + 1]);
-        float ms_ff = 0.f;
-        const cudaError_t tf = cert ? cudaEventElapsedTime(&ms_ff, b.ev[4 * r + 2], b.ev[4 * r + 3])
+        const cudaError_t te = cudaEventElapsedTime(&ms, b.ev[6 * r], b.ev[6 * r + 1]);
+        float ms_ff = 0.f, ms_dif = 0.f;
+        const cudaError_t tf = cert ? cudaEventElapsedTime(&ms_ff, b.ev[6 * r + 2], b.ev[6 * r + 3])
                                     : cudaSuccess;
-        if (te == cudaSuccess && tf == cudaSuccess) {
+        const cudaError_t td =
+            dif_on ? cudaEventElapsedTime(&ms_dif, b.ev[6 * r + 4], b.ev[6 * r + 5]) : cudaSuccess;
+        if (te == cudaSuccess && tf == cudaSuccess && td == cudaSuccess) {
           c->stats.kernel_ms += ms;
           c->stats.objective_ms += ms;
           c->stats.refine_ms += ms_ff;
+          c->stats.dif_ms += ms_dif;
           c->stats.launches += 1;
         } else {
           (void)cudaGetLastError();  // timing unavailable: not an error of the solve
@@ -1719,6 +1802,8 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
   c->stats.queries += (int64_t)hc.stat_queries;
   c->stats.ties += (int64_t)hc.stat_ties;
   c->stats.refine_pairs += hc.stat_ff_pairs;
+  c->stats.difs += (int64_t)hc.stat_difs;
+  c->stats.dif_pairs += hc.stat_dif_pairs;
   if (cert) c->stats.b_refined += hc.ref_cnt[0];
   if (c->profiling) {
     c->stats.pair_evals += hc.stat_pairs;

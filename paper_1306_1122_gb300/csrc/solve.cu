@@ -347,16 +347,25 @@ __device__ __forceinline__ double dif_phi_bound(const double e[12], double z, co
   return propagate_bound(dB, dG, B, G, g, g_scale, w_g);
 }
 
-// The first near tie of a step: a comparison whose two values differ by no more than `band`
-// times the sum of their bounds (a value re-evaluated in float-float has bound 0).
+// The first near tie of a step: a comparison whose two values differ by no more than the sum of
+// their tie radii.  A value's radius is `band` times its bound for a mixed-form value (bound
+// s > 0), `band_d` times it for a value re-evaluated by difference (stored as -s), and 0 for a
+// value re-evaluated in float-float.
 struct TieLog {
-  double band;   // 0: decisions are not certified
-  int a, b;      // ids of the first near-tied values (-1: none)
+  double band;     // 0: decisions are not certified
+  double band_d;
+  int a, b;        // ids of the first near-tied values (-1: none)
+  __device__ __forceinline__ double radius(double s) const {
+    return s > 0.0 ? band * s : band_d * (-s);
+  }
   __device__ __forceinline__ void note(int ia, double sa, int ib, double sb, double gap) {
-    if (band > 0.0 && a < 0 && sa + sb > 0.0 && fabs(gap) <= band * (sa + sb)) {
-      a = sa > 0.0 ? ia : -1;
-      b = sb > 0.0 ? ib : -1;
-      if (a < 0) { a = b; b = -1; }
+    if (band > 0.0 && a < 0) {
+      const double r = radius(sa) + radius(sb);
+      if (r > 0.0 && fabs(gap) <= r) {
+        a = sa != 0.0 ? ia : -1;
+        b = sb != 0.0 ? ib : -1;
+        if (a < 0) { a = b; b = -1; }
+      }
     }
   }
   __device__ __forceinline__ bool lt(const Vert& x, const Vert& y) {
@@ -384,16 +393,36 @@ __device__ __forceinline__ void read_eval(const SolveArgs& a, const PlanHdr& h, 
             : 0.0;
 }
 
-// Objective of a float-float re-evaluation slot of point g (bound 0).
+// Objective of a float-float re-evaluation slot of point g (bound 0) and its 12 sums.
 __device__ __forceinline__ void read_eval_ff(const SolveArgs& a, const PlanHdr& hf, int pidx,
-                                             int64_t slot, double z, Eval& e, int64_t g) {
+                                             int64_t slot, double z, Eval& e, int64_t g,
+                                             double S[12]) {
   const ProbDesc& pd = a.probs[pidx];
   const int64_t j = slot - pd.qff_off;
-  double S[12], G[9];
+  double G[9];
 #pragma unroll
   for (int s = 0; s < 12; ++s) S[s] = gather_sum(a.fout, hf, a.fitem_off, pidx, j, 12, s);
   assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
   e.s = 0.0;
+}
+
+// Objective of a difference re-evaluation slot of point g at lambda lt: the point's float-float
+// reference sums plus the difference sums; its bound is stored negated (a difference value).
+__device__ __forceinline__ void read_eval_dif(const SolveArgs& a, const PlanHdr& hd, int pidx,
+                                              int64_t slot, double z, Eval& e, int64_t g,
+                                              const double lt[3]) {
+  const ProbDesc& pd = a.probs[pidx];
+  const int64_t j = slot - pd.qff_off;
+  double S[12], G[9];
+#pragma unroll
+  for (int s = 0; s < 12; ++s)
+    S[s] = SD(a, D_REFS + s, g) + gather_sum(a.dout, hd, a.ditem_off, pidx, j, 12, s);
+  assemble_obj(S, z, pd.g_scale, a.o.w_g, e, G, corr_of(a, pd, g, z));
+  const double l0[3] = {SD(a, D_REFL, g), SD(a, D_REFL + 1, g), SD(a, D_REFL + 2, g)};
+  double eb[12];
+  dif_sum_bounds(a.msc + 15 * g, a.msc0 + 3 * g, lt, l0, a.o.dim, eb);
+  const double sd = dif_phi_bound(eb, z, e.B, G, e.g, pd.g_scale, a.o.w_g);
+  e.s = -(sd > 0.0 ? sd : 1e-300);
 }
 
 // atomicAdd(ctr, v) for the lanes of a warp that reach it together (whatever branch they are
@@ -449,25 +478,46 @@ __device__ __forceinline__ void emit(const SolveArgs& a, int64_t g, const float4
   a.nxt.act[atomic_add_warp(a.nxt.act_cnt, 1)] = (int32_t)g;
 }
 
-// Queue the float-float re-evaluation of k (1 or 2) values of point g on side `sd` and put the
-// point on that side's waiting list; the value ids go to I_RTGT, one per byte.
-__device__ __forceinline__ void emit_ff(const SolveArgs& a, const RoundBuf& sd, int64_t g,
-                                        const float4& pos, int pidx, int k,
-                                        const double (&l)[2][3], int id0, int id1) {
+// Queue the re-evaluation of k (1 or 2) values of point g on side `sd` and put the point on that
+// side's waiting list: value j in float-float, or (dif[j]) as the difference from the point's
+// float-float reference at lambda lref.  The value ids go to I_RTGT, one per byte (| RT_DIF for
+// differences), and the first slot of each kind to I_RSLOT, I_DSLOT.
+__device__ __forceinline__ void emit_reeval(const SolveArgs& a, const RoundBuf& sd, int64_t g,
+                                            const float4& pos, int pidx, int k,
+                                            const double (&l)[2][3], int id0, int id1,
+                                            const bool (&dif)[2], const double lref[3]) {
   const ProbDesc& pd = a.probs[pidx];
-  const int base = atomic_add_warp(sd.fq_cnt + pidx, k);
-  const int64_t slot0 = pd.qff_off + base;
+  const int nd = (dif[0] ? 1 : 0) + (k > 1 && dif[1] ? 1 : 0);
+  const int nf = k - nd;
+  auto lam4 = [&](const double* x) {
+    return a.o.dim == 1 ? make_lam4(x[0], x[0], x[0]) : make_lam4(x[0], x[1], x[2]);
+  };
+  int64_t fs = 0, ds = 0;
+  if (nf > 0) fs = pd.qff_off + atomic_add_warp(sd.fq_cnt + pidx, nf);
+  if (nd > 0) ds = pd.qff_off + atomic_add_warp(sd.dq_cnt + pidx, nd);
+  SI(a, I_RSLOT, g) = (int32_t)fs;
+  SI(a, I_DSLOT, g) = (int32_t)ds;
+  int tg = 0xffff;
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     if (j >= k) break;
-    sd.fpos[slot0 + j] = pos;
-    sd.flam[slot0 + j] = a.o.dim == 1 ? make_lam4(l[j][0], l[j][0], l[j][0])
-                                      : make_lam4(l[j][0], l[j][1], l[j][2]);
+    const int id = j == 0 ? id0 : id1;
+    if (dif[j]) {
+      sd.dpos[ds] = pos;
+      sd.dlam[ds] = lam4(l[j]);
+      sd.dlam0[ds] = lam4(lref);
+      ++ds;
+    } else {
+      sd.fpos[fs] = pos;
+      sd.flam[fs] = lam4(l[j]);
+      ++fs;
+    }
+    tg = (tg & ~(0xff << (8 * j))) | (((id | (dif[j] ? RT_DIF : 0)) & 0xff) << (8 * j));
   }
-  SI(a, I_RSLOT, g) = (int32_t)slot0;
-  SI(a, I_RTGT, g) = (id0 & 0xff) | ((k > 1 ? id1 : 0xff) << 8);
+  SI(a, I_RTGT, g) = tg;
   sd.ref[atomic_add_warp(sd.ref_cnt, 1)] = (int32_t)g;
   if (a.stat_ties) atomicAdd(a.stat_ties, 1ull);
+  if (nd > 0 && a.stat_difs) atomicAdd(a.stat_difs, (unsigned long long)nd);
 }
 
 // N: the number of free lambdas (3, or 1 when the components share one).
@@ -495,6 +545,7 @@ __global__ void solve_init_kernel(const SolveArgs a, const double* __restrict__ 
     SI(a, I_NFEV, g) = 0;
     SI(a, I_STATUS, g) = PT_RUNNING;
     SI(a, I_FLAGS, g) = 0;
+    if (a.o.tie_dif > 0.0) SD(a, D_REFS, g) = __longlong_as_double(0x7ff8000000000000LL);  // NaN
     emit<N + 1>(a, g, pos, pidx, lam);
   }
 }
@@ -544,8 +595,11 @@ __global__ void nm_step_kernel(const SolveArgs a) {
   const int32_t* list = REF ? a.cur.ref : a.cur.act;
   constexpr int n = N;
   const PlanHdr h = *a.plan;
-  PlanHdr hf{};
-  if (REF) hf = *a.fplan;
+  PlanHdr hf{}, hd{};
+  if (REF) {
+    hf = *a.fplan;
+    if (a.o.tie_dif > 0.0) hd = *a.dplan;
+  }
   for (int ia = blockIdx.x * blockDim.x + threadIdx.x; ia < nact; ia += gridDim.x * blockDim.x) {
     const int64_t g = list[ia];
     const float4 pos = a.ppos[g];
@@ -604,15 +658,33 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     }
     if (stage == ST_EXPAND || stage == ST_OCONTRACT) load_r(a, g, R);
     if (REF) {
-      // apply the float-float values of this point's re-evaluated targets
+      // apply the re-evaluated values of this point's targets: the differences first (they
+      // were queued against the current reference), then the float-float values, each of which
+      // becomes the point's reference
       const int tg = SI(a, I_RTGT, g);
-      const int64_t rs = SI(a, I_RSLOT, g);
+      int64_t slot[2] = {SI(a, I_RSLOT, g), SI(a, I_DSLOT, g)};
 #pragma unroll 1
-      for (int t = 0; t < 2; ++t) {
-        const int id = (tg >> (8 * t)) & 0xff;
-        if (id == 0xff) continue;
+      for (int it = 0; it < 4; ++it) {
+        const int t = it & 1;
+        const int code = (tg >> (8 * t)) & 0xff;
+        if (code == 0xff) continue;
+        const bool dif = (code & RT_DIF) != 0;
+        if (dif != (it < 2)) continue;
+        const int id = code & ~RT_DIF;
         Eval ev;
-        read_eval_ff(a, hf, pidx, rs + t, z, ev, g);
+        double lt[3];
+        for (int d = 0; d < 3; ++d)
+          lt[d] = id == VID_E ? e.l[d] : (id == VID_R ? R.l[d] : SD(a, D_VL + 3 * id + d, g));
+        if (dif) {
+          read_eval_dif(a, hd, pidx, slot[1]++, z, ev, g, lt);
+        } else {
+          double S[12];
+          read_eval_ff(a, hf, pidx, slot[0]++, z, ev, g, S);
+          if (a.o.tie_dif > 0.0) {
+            for (int d = 0; d < 3; ++d) SD(a, D_REFL + d, g) = lt[d];
+            for (int s = 0; s < 12; ++s) SD(a, D_REFS + s, g) = S[s];
+          }
+        }
         if (id == VID_E) {
           set_value(e, ev);
         } else if (id == VID_R) {
@@ -630,7 +702,7 @@ __global__ void nm_step_kernel(const SolveArgs a) {
     // ---- the step.  With certified decisions the vertices the step starts from are in memory
     // first (the step may turn out to wait), and nothing else is written until the step is
     // known to be certain.
-    TieLog tl{a.o.tie, -1, -1};
+    TieLog tl{a.o.tie, a.o.tie_dif, -1, -1};
     if (vdirty && a.o.tie > 0.0)
 #pragma unroll
       for (int m = 0; m <= n; ++m) store_vert(a, g, m, v[m]);
@@ -748,7 +820,46 @@ __global__ void nm_step_kernel(const SolveArgs a) {
         lt[1][d] = idb < 0 ? 0.0 : idb == VID_E ? e.l[d]
                  : (idb == VID_R ? R.l[d] : SD(a, D_VL + 3 * idb + d, g));
       }
-      emit_ff(a, REF ? a.nxt : a.cur, g, pos, pidx, idb >= 0 ? 2 : 1, lt, ida, idb);
+      // A value goes to the difference pass when the point has a float-float reference, the
+      // value still carries its mixed-form bound and it lies near the reference (the difference
+      // bound, relative to the mixed one, grows as |lambda - lambda_ref| times the point's mean
+      // pixel distance sum |b| / sum |b| / r: estimated below about 0.5 here); otherwise to
+      // float-float.  Without a reference only the value with the larger bound goes to
+      // float-float: it becomes the reference, and the other value, if still near-tied, goes
+      // to the difference pass in the next round.
+      int k = idb >= 0 ? 2 : 1;
+      int id0 = ida, id1 = idb;
+      bool dif[2] = {false, false};
+      double lref[3] = {0.0, 0.0, 0.0};
+      if (a.o.tie_dif > 0.0) {
+        const double sv[2] = {
+            ida == VID_E ? e.s : (ida == VID_R ? R.s : SD(a, D_VS + ida, g)),
+            idb < 0 ? 0.0 : idb == VID_E ? e.s : (idb == VID_R ? R.s : SD(a, D_VS + idb, g))};
+        if (!isnan(SD(a, D_REFS, g))) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) lref[d] = SD(a, D_REFL + d, g);
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            bool near = j < k && sv[j] > 0.0;
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+              const int q = n == 1 ? 0 : p;
+              const double m1 = a.msc[15 * g + 5 * p];
+              const double reach = m1 > 0.0 ? a.msc0[3 * g + p] / m1 : 0.0;
+              near = near && fabs(lt[j][q] - lref[q]) * reach < 0.25;
+            }
+            dif[j] = near;
+          }
+        } else if (k == 2 && sv[0] > 0.0 && sv[1] > 0.0) {
+          k = 1;
+          if (sv[1] > sv[0]) {
+            id0 = idb;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) lt[0][d] = lt[1][d];
+          }
+        }
+      }
+      emit_reeval(a, REF ? a.nxt : a.cur, g, pos, pidx, k, lt, id0, id1, dif, lref);
       if (single) store_e(a, g, e);
       if (rdirty) store_r(a, g, R);
       SI(a, I_FLAGS, g) = flags;
@@ -868,6 +979,7 @@ __global__ void plan_round_kernel(const PlanArgs a) {
   for (int p = threadIdx.x; p < a.nprob; p += blockDim.x) {
     if (a.q_cnt_nxt) a.q_cnt_nxt[p] = 0;
     if (a.fq_cnt_nxt) a.fq_cnt_nxt[p] = 0;
+    if (a.dq_cnt_nxt) a.dq_cnt_nxt[p] = 0;
   }
 }
 

@@ -25,7 +25,11 @@ enum DField {
   D_EG = 57,
   D_EPHI = 58,
   D_ES = 59,
-  D_NFIELDS = 60
+  // certified decisions, difference level: the point's float-float reference value, lambda (3)
+  // and its 12 sums (D_REFS = NaN: no reference yet)
+  D_REFL = 60,
+  D_REFS = 63,
+  D_NFIELDS = 75
 };
 // Quasi-Newton state (same arrays, other meaning): x, grad Phi, inverse Hessian H (3 x 3),
 // direction d, B, f, g, Phi at x, line-search step alpha, grad . d, |grad|.
@@ -33,13 +37,15 @@ enum BField {
   B_X = 0, B_GR = 3, B_H = 6, B_D = 15, B_B = 18, B_F = 21, B_G = 22, B_PHI = 23, B_ALPHA = 24,
   B_GD = 25, B_GN = 26
 };
-// I_FLAGS bit F_EVAL: this step's evaluations are in the state (the step waits for a float-float
-// re-evaluation); I_RSLOT: first float-float query slot of the point's pending re-evaluation;
-// I_RTGT: its targets, one value id per byte (0..3 vertex, 4 reflected point, 5 trial point),
+// I_FLAGS bit F_EVAL: this step's evaluations are in the state (the step waits for a
+// re-evaluation); I_RSLOT, I_DSLOT: first float-float and first difference query slot of the
+// point's pending re-evaluation; I_RTGT: its targets, one per byte: value id (0..3 vertex,
+// 4 reflected point, 5 trial point) | RT_DIF when the value goes to the difference pass,
 // 0xff = none.
 enum IField { I_STAGE = 0, I_ITERS = 1, I_NFEV = 2, I_STATUS = 3, I_QSLOT = 4, I_FLAGS = 5,
-              I_RSLOT = 6, I_RTGT = 7, I_NFIELDS = 8 };
+              I_RSLOT = 6, I_RTGT = 7, I_DSLOT = 8, I_NFIELDS = 9 };
 constexpr int F_EVAL = 1;
+constexpr int RT_DIF = 0x40;
 constexpr int VID_R = 4, VID_E = 5;
 enum PtStatus { PT_RUNNING = -1, PT_CONVERGED = 0, PT_MAXITER = 1 };
 enum Stage { ST_INIT = 0, ST_REFLECT = 1, ST_EXPAND = 2, ST_OCONTRACT = 3, ST_ICONTRACT = 4,
@@ -49,6 +55,7 @@ struct SolveOpts {
   double eps_f, eps_g, tol, w_g;
   double tie;                // certified decisions: near-tie band factor (0: off)
   int32_t max_iter, dim, near_on, pad0;
+  double tie_dif;            // band factor of values re-evaluated by difference (0: level off)
 };
 
 // One ping-pong side of the per-round buffers.
@@ -66,6 +73,11 @@ struct RoundBuf {
   int32_t* fq_cnt;     // [nprob]
   int32_t* ref;        // waiting points
   int32_t* ref_cnt;    // [1]
+  // difference re-evaluation queries (value lambda, reference lambda; slots as fpos)
+  float4* dpos;
+  Lam4* dlam;
+  Lam4* dlam0;
+  int32_t* dq_cnt;     // [nprob]
 };
 
 struct SolveArgs {
@@ -96,10 +108,15 @@ struct SolveArgs {
   const double* corr;        // [N * 12] pixel-exact corrections (dB, d grad B), or null
   // certified decisions
   const double* msc;         // [N * 15] sum_k |b_pk| / r^j, j = 1..5, per component (or null)
+  const double* msc0;        // [N * 3] sum_k |b_pk| per component (difference level)
   const double* fout;        // float-float pass partial sums of the current round
   const PlanHdr* fplan;
   const int32_t* fitem_off;
+  const double* dout;        // difference pass partial sums of the current round
+  const PlanHdr* dplan;
+  const int32_t* ditem_off;
   unsigned long long* stat_ties;   // near-tie decisions sent to re-evaluation (or null)
+  unsigned long long* stat_difs;   // values re-evaluated by difference (or null)
 };
 
 struct PlanArgs {
@@ -117,6 +134,7 @@ struct PlanArgs {
   int32_t* act_cnt_nxt;
   int32_t* near_cnt_nxt;
   int32_t* fq_cnt_nxt;       // zeroed (certified decisions; may be null)
+  int32_t* dq_cnt_nxt;       // zeroed (difference level; may be null)
   int32_t* ref_cnt_nxt;
   int32_t* round_ctr;        // incremented per round
   unsigned long long* stat_queries;

@@ -37,6 +37,7 @@ class Options:
     method: int = N.DBIE_METHOD_SIMPLEX
     near_z: float = -1.0
     certify: float = 0.02
+    certify_ref: float = 0.02
 
     def c(self) -> N.dbie_options:
         o = N.dbie_default_options()

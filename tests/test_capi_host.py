@@ -33,11 +33,11 @@ def test_every_declared_symbol_is_exported(native):
 
 
 def test_struct_layouts_match_header(native):
-    # dbie_options: 3 doubles, 2 int32, 3 doubles, 2 int32, 2 doubles = 80 bytes
-    assert ctypes.sizeof(native.dbie_options) == 80
+    # dbie_options: 3 doubles, 2 int32, 3 doubles, 2 int32, 3 doubles = 88 bytes
+    assert ctypes.sizeof(native.dbie_options) == 88
     assert ctypes.sizeof(native.dbie_solve_out) == 8 * 8 + 8
-    # dbie_stats: int64, 4 doubles, 2 int64, int64, 2 doubles, int64 = 88 bytes
-    assert ctypes.sizeof(native.dbie_stats) == 88
+    # dbie_stats: int64, 4 doubles, 2 int64, int64, 2 doubles, int64, int64, 2 doubles = 112 bytes
+    assert ctypes.sizeof(native.dbie_stats) == 112
 
 
 def test_default_options(native):
@@ -46,7 +46,7 @@ def test_default_options(native):
     assert o.lambda_mode == native.DBIE_LAMBDA_PER_COMPONENT
     assert o.precision == native.DBIE_PREC_MIXED
     assert o.near_z < 0 and o.simplex_step == 0.0 and o.g_scale == 0.0 and o.w_g == 1.0
-    assert o.certify == 0.02
+    assert o.certify == 0.02 and o.certify_ref == 0.02
     assert native.dbie_version().startswith("dbie-gb300")
 
 
