@@ -36,6 +36,8 @@ SMS, MUFU_PER_SM_CLK, MAX_SM_MHZ = 152, 16, 2070.0
 MUFU_PER_PAIR = 7           # objective variant, one lambda per component: rsqrt + 3 x (sin, cos)
 FP32_PER_SM_CLK = 124       # measured FP32 FMA-pipe rate per SM and clock (of 128 lanes)
 FF_FP32_PER_PAIR = 727      # float-float objective sums: FP32 operations per point-pixel pair
+DIF_INST_PER_PAIR = 153     # difference sums: thread instructions per pair (ncu, all pipes)
+ISSUE_PER_SM_CLK = 128      # thread instructions issued per SM and clock (4 schedulers x 32)
 FP32_PER_PAIR = 44
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one objective launch, the first
 # simplex round of this workload (131,072 queries x 16,384 pixels), from one ncu capture of the
@@ -64,7 +66,7 @@ def parse_args():
     ap.add_argument("--max-points", type=int, default=200_000,
                     help="batch64: upper end of the per-problem point count")
     ap.add_argument("--case", default=None,
-                    choices=["exact_near_field", "float_float", "implicit_adjoint"],
+                    choices=["exact_near_field", "float_float", "difference", "implicit_adjoint"],
                     help="a single-kernel-family case for profiling instead of the step")
     return ap.parse_args()
 
@@ -306,6 +308,16 @@ def run_ours(args):
             "peak": SMS * FP32_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12, "unit": "T FP32-op/s",
             "per_pair": {"fp32": FF_FP32_PER_PAIR, "mufu": 1},
             "peak_source": "152 SMs x 124 FP32 ops/clk/SM (measured per-clock rate) x 2070 MHz"},
+        "roofline_difference": {
+            "bound": "alu", "pipe": "instruction issue (FP32 FMA 68 %, MUFU 16 % of it)",
+            "kernel": "g1_dif_kernel (difference sums of near-tied values from a float-float "
+            "reference)",
+            "achieved": (stats[-1]["dif_pairs"] * DIF_INST_PER_PAIR /
+                         (sum(s["dif_ms"] for s in stats) / args.steps / 1e3) / 1e12)
+            if any(s["dif_ms"] for s in stats) else None,
+            "peak": SMS * ISSUE_PER_SM_CLK * MAX_SM_MHZ * 1e6 / 1e12, "unit": "T thread-inst/s",
+            "per_pair": {"thread_instructions": DIF_INST_PER_PAIR, "mufu": 7},
+            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2070 MHz"},
         "certified_decisions": {
             "near_ties_per_step": stats[-1]["ties"],
             "near_tie_frac_of_evals": stats[-1]["ties"] / max(1, q),
@@ -339,8 +351,9 @@ def run_ours(args):
         "clocks": clocks,
         "wall_s": wall,
     }
-    rf = line["roofline_float_float"]
-    rf["frac"] = rf["achieved"] / rf["peak"] if rf["achieved"] else None
+    for key in ("roofline_float_float", "roofline_difference"):
+        rf = line[key]
+        rf["frac"] = rf["achieved"] / rf["peak"] if rf["achieved"] else None
     if rank == 0 and world == 1 and not args.no_fp64_compare:
         line["fp64_form"] = fp64_compare(w, args.fp64_points, dev)
         line["quasi_newton"] = method_compare(w, dev)
@@ -932,6 +945,36 @@ def run_case_float_float():
                       "pairs_per_s": len(pts) * w.mag.npix / (ms / 1e3)}))
 
 
+def run_case_difference():
+    """Profiling case of the difference sums (the second level of the certified decisions):
+    8,192 ll128 points x 16,384 pixels, reference lambda_p = 0.02, lambda a seeded step of up to
+    1e-3 from it (the near-tie regime), with error bounds; twice to warm up and once timed;
+    prints the CUDA-event time and pair rate."""
+    import numpy as np
+    import torch
+
+    import paper_1306_1122_gb300 as dbie
+    from synth import workloads
+    w = workloads.ll128(with_truth=False)
+    f = dbie.DBIEField.from_magnetogram(w.mag)
+    pts = torch.from_numpy(w.points[::16].copy()).cuda()
+    lam0 = torch.full((len(pts), 3), 0.02, dtype=torch.float64, device="cuda")
+    step = np.random.default_rng(16).uniform(-1e-3, 1e-3, (len(pts), 3))
+    lam = lam0 + torch.from_numpy(step).cuda()
+    for _ in range(2):
+        f.eval_difference(pts, lam, lam0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    f.eval_difference(pts, lam, lam0)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    f.close()
+    print(json.dumps({"case": "difference", "workload": "ll128 difference sums, 8192 points x "
+                      "16384 pixels, steps up to 1e-3 from lambda_p = 0.02", "ms": ms,
+                      "pairs_per_s": len(pts) * w.mag.npix / (ms / 1e3)}))
+
+
 def run_case_implicit_adjoint():
     """Profiling case of the gradient through the lambda search on the ll128 workload: tuned
     launch shapes, the simplex search of all 131,072 points, then dbie_vjp_implicit at its lambda
@@ -979,6 +1022,8 @@ def main():
         run_case_exact_near_field()
     elif args.case == "float_float":
         run_case_float_float()
+    elif args.case == "difference":
+        run_case_difference()
     elif args.case == "implicit_adjoint":
         run_case_implicit_adjoint()
     elif args.impl == "reference":
