@@ -70,6 +70,7 @@ def test_argument_errors_are_reported_on_host(native):
         lambda: lib.dbie_set_boundary(None, p, p, p, 0, None),
         lambda: lib.dbie_set_quadrature(None, 0, None),
         lambda: lib.dbie_objective(None, 1, p, p, None, 0, p, None, None),
+        lambda: lib.dbie_eval_difference(None, 1, p, p, p, 0, p, None, None),
         lambda: lib.dbie_hessian(None, 1, p, p, None, 0, p, None, None, None),
         lambda: lib.dbie_vjp_implicit(None, 1, p, p, p, None, 0, p, None, None, 0, None),
         lambda: lib.dbie_noise_var(None, 1, p, p, None, None, None, 1.0, None, 0, p, None),

@@ -43,11 +43,13 @@ def oracle_solve(mag, pts, lambda_mode=0, max_iter=50):
                         oracle.Options(lambda_mode=lambda_mode, max_iter=max_iter))
 
 
-def gpu_solve(dbie, mag, pts, precision, lambda_mode=0, max_iter=50, certify=0.02, stats=None):
+def gpu_solve(dbie, mag, pts, precision, lambda_mode=0, max_iter=50, certify=0.02, stats=None,
+              certify_ref=0.02):
     f = dbie.DBIEField.from_magnetogram(mag)
     f.set_profiling(True)
     r = f.solve(torch.from_numpy(pts), dbie.Options(precision=precision, lambda_mode=lambda_mode,
-                                                     max_iter=max_iter, certify=certify),
+                                                     max_iter=max_iter, certify=certify,
+                                                     certify_ref=certify_ref),
                 codes=max_iter)
     torch.cuda.synchronize()
     if stats is not None:
@@ -58,12 +60,12 @@ def gpu_solve(dbie, mag, pts, precision, lambda_mode=0, max_iter=50, certify=0.0
     return out
 
 
-def certified_parity(dbie, mag, pts, L, lambda_mode=0):
+def certified_parity(dbie, mag, pts, L, lambda_mode=0, certify_ref=0.02):
     """Certified mixed search against the oracle: fraction of points on the oracle's step
     sequence, fraction of those with lambda within 1e-4 max(|lambda|, 1/L), the B gate at the
     GPU's own lambda, and the solve's statistics."""
     st = {}
-    got = gpu_solve(dbie, mag, pts, 0, lambda_mode=lambda_mode, stats=st)
+    got = gpu_solve(dbie, mag, pts, 0, lambda_mode=lambda_mode, stats=st, certify_ref=certify_ref)
     ref = oracle_solve(mag, pts, lambda_mode)
     same = np.array([a == b for a, b in zip(got["codes"], ref["codes"])])
     lam_ok = lam_close(got["lam"][same], ref["lam"][same], L)
@@ -72,7 +74,7 @@ def certified_parity(dbie, mag, pts, L, lambda_mode=0):
     rb = check_B(got["B"], B, sB)
     print(f"certified mixed solve: oracle step sequence on {same.mean():.4f}, lambda within "
           f"1e-4 on {lam_ok.mean():.4f} of those; near ties {st['ties']} for "
-          f"{int(got['nfev'].sum())} evaluations")
+          f"{int(got['nfev'].sum())} evaluations, {st['difs']} values re-evaluated by difference")
     return same, lam_ok, rb, st, got, ref
 
 
@@ -136,15 +138,18 @@ def test_certified_mixed_solve_follows_oracle(dbie, small, lambda_mode):
     assert np.array_equal(got["nfev"][same], ref["nfev"][same])
 
 
-@pytest.mark.parametrize("lambda_mode", [0, 1])
-def test_certified_mixed_solve_ll128_subsample(dbie, lambda_mode):
+@pytest.mark.parametrize("lambda_mode,certify_ref", [(0, 0.02), (1, 0.02), (0, 0.0)])
+def test_certified_mixed_solve_ll128_subsample(dbie, lambda_mode, certify_ref):
     """The same gates on a seeded 384-point subsample of the 131,072-point ll128 workload
     (128 x 128 boundary, z up to 32 px).  With one shared lambda about 40 % of these points
-    keep lambda* = 0, and every step of their search is a mirror step."""
+    keep lambda* = 0, and every step of their search is a mirror step.  With the difference
+    level (the default) some near-tied values are re-evaluated by difference from the point's
+    float-float reference; with certify_ref = 0 every near tie goes to float-float."""
     w = workloads.ll128(with_truth=False)
     idx = np.sort(np.random.default_rng(128).choice(len(w.points), 384, replace=False))
     same, lam_ok, rb, st, got, ref = certified_parity(dbie, w.mag, w.points[idx], 128.0,
-                                                      lambda_mode)
+                                                      lambda_mode, certify_ref)
+    assert (st["difs"] > 0) == (certify_ref > 0), st["difs"]
     assert same.mean() >= 0.99, same.mean()
     assert lam_ok.mean() >= 0.99, lam_ok.mean()
     assert rb["bad"].size == 0, rb
