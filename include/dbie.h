@@ -198,8 +198,8 @@ dbie_status dbie_set_quadrature(dbie_ctx* ctx, int32_t order, void* stream);
  *   fgphi  (n, 3): f (Eq. 8), g (Eq. 9), Phi = f + w_g g (needs gradB's sums; opt gives g_scale, w_g).
  * B is required when n > 0, the others may be NULL.  opt may be NULL (defaults; precision and near_z are
  * read from it).  n = 0 is a no-op.  With precision DBIE_PREC_FLOAT_FLOAT the sums agree with the
- * FP64 ones to about 1e-13 of their absolute-value sums (|lambda r| < 3200); dBdlam is then
- * not available (DBIE_EINVAL). */
+ * FP64 ones to about 1e-13 of their absolute-value sums (angles lambda r of 12,000 rad and more take
+ * FP64 sine and cosine); dBdlam is then not available (DBIE_EINVAL). */
 dbie_status dbie_eval(dbie_ctx* ctx, int64_t n, const float* xyz, const float* lambda,
                       const dbie_options* opt, int32_t mem_kind, double* B, double* gradB,
                       double* dBdlam, double* fgphi, void* stream);
