@@ -1564,6 +1564,45 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
                     (int)std::min<int64_t>((N + 255) / 256, 8LL * c->sm_count), s);
   CUDA_TRY(cudaGetLastError());
 
+  // One re-evaluation pass of a round (float-float, or differences when lam0 is given): plan
+  // the queued values, run the pair sums, with profiling events ev_at and ev_at + 1 around it.
+  auto record_reeval = [&](cudaStream_t cs, const KernelRef& kr, int grid_r, int target_r,
+                           const DBuf& cnt, const DBuf& cnt_pass, const DBuf& item_off_r,
+                           PlanHdr* plan_r, int32_t* work_r, double* stat_pairs_r,
+                           const DBuf& qpos_r, const DBuf& qlam_r, const DBuf* qlam0_r,
+                           const DBuf& out_r, int ev_at) -> dbie_status {
+    PlanArgs pp{};
+    pp.probs = b.probs.as<ProbDesc>();
+    pp.nprob = nprob;
+    pp.qper = kr.qper;
+    pp.target_items = target_r;
+    pp.nsplit_cap = 1 << 20;
+    pp.q_cnt_cur = cnt.as<int32_t>();
+    pp.q_cnt_pass = cnt_pass.as<int32_t>();
+    pp.item_off = item_off_r.as<int32_t>();
+    pp.plan = plan_r;
+    pp.work = work_r;
+    pp.stat_pairs = stat_pairs_r;
+    launch_plan_round(pp, cs);
+    G1Args ga{};
+    ga.probs = b.probs.as<ProbDesc>();
+    ga.nprob = nprob;
+    ga.plan = plan_r;
+    ga.item_off = item_off_r.as<int32_t>();
+    ga.q_cnt = cnt_pass.as<int32_t>();
+    ga.work = work_r;
+    ga.qpos = qpos_r.as<float4>();
+    ga.qlam = qlam_r.as<Lam4>();
+    ga.qlam0 = qlam0_r ? qlam0_r->as<Lam4>() : nullptr;
+    ga.out = out_r.as<double>();
+    ga.err = c->err.as<unsigned>();
+    if (c->profiling)
+      CUDA_TRY(cudaEventRecordWithFlags(b.ev[ev_at], cs, cudaEventRecordExternal));
+    DBIE_TRY(launch_kernel(kr, grid_r, &ga, cs));
+    if (c->profiling)
+      CUDA_TRY(cudaEventRecordWithFlags(b.ev[ev_at + 1], cs, cudaEventRecordExternal));
+    return DBIE_OK;
+  };
   // One simplex round = plan, pair sums (objective variant), near-field correction, step.
   constexpr int K = 4;  // rounds per graph launch (even: the ping-pong side returns to 0)
   auto record_rounds = [&](cudaStream_t cs) -> dbie_status {
@@ -1616,69 +1655,15 @@ static dbie_status solve_impl(int32_t nprob, dbie_ctx* const* ctxs, const int64_
                          2 * c->sm_count, cs);
       (qn ? launch_bfgs_step : launch_nm_step)(sa[cur], nm_grid, cs);
       if (cert) {
-        // the near-tied values of this round in float-float, then the waiting steps again
-        PlanArgs pf{};
-        pf.probs = b.probs.as<ProbDesc>();
-        pf.nprob = nprob;
-        pf.qper = kf.qper;
-        pf.target_items = target_ff;
-        pf.nsplit_cap = 1 << 20;
-        pf.q_cnt_cur = b.fq_cnt[cur].as<int32_t>();
-        pf.q_cnt_pass = b.fq_cnt_pass.as<int32_t>();
-        pf.item_off = b.fitem_off.as<int32_t>();
-        pf.plan = &ctrl->fplan;
-        pf.work = &ctrl->fwork;
-        pf.stat_pairs = &ctrl->stat_ff_pairs;
-        launch_plan_round(pf, cs);
-        G1Args gf{};
-        gf.probs = b.probs.as<ProbDesc>();
-        gf.nprob = nprob;
-        gf.plan = &ctrl->fplan;
-        gf.item_off = b.fitem_off.as<int32_t>();
-        gf.q_cnt = b.fq_cnt_pass.as<int32_t>();
-        gf.work = &ctrl->fwork;
-        gf.qpos = b.fpos[cur].as<float4>();
-        gf.qlam = b.flam[cur].as<Lam4>();
-        gf.out = b.fout.as<double>();
-        gf.err = c->err.as<unsigned>();
-        if (c->profiling)
-          CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 2], cs, cudaEventRecordExternal));
-        DBIE_TRY(launch_kernel(kf, grid_ff, &gf, cs));
-        if (c->profiling)
-          CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 3], cs, cudaEventRecordExternal));
-        if (dif_on) {
-          // ... and the near-tied values queued as differences from the points' references
-          PlanArgs pd{};
-          pd.probs = b.probs.as<ProbDesc>();
-          pd.nprob = nprob;
-          pd.qper = kd.qper;
-          pd.target_items = target_dif;
-          pd.nsplit_cap = 1 << 20;
-          pd.q_cnt_cur = b.dq_cnt[cur].as<int32_t>();
-          pd.q_cnt_pass = b.dq_cnt_pass.as<int32_t>();
-          pd.item_off = b.ditem_off.as<int32_t>();
-          pd.plan = &ctrl->dplan;
-          pd.work = &ctrl->dwork;
-          pd.stat_pairs = &ctrl->stat_dif_pairs;
-          launch_plan_round(pd, cs);
-          G1Args gd{};
-          gd.probs = b.probs.as<ProbDesc>();
-          gd.nprob = nprob;
-          gd.plan = &ctrl->dplan;
-          gd.item_off = b.ditem_off.as<int32_t>();
-          gd.q_cnt = b.dq_cnt_pass.as<int32_t>();
-          gd.work = &ctrl->dwork;
-          gd.qpos = b.dpos[cur].as<float4>();
-          gd.qlam = b.dlam[cur].as<Lam4>();
-          gd.qlam0 = b.dlam0[cur].as<Lam4>();
-          gd.out = b.dout.as<double>();
-          gd.err = c->err.as<unsigned>();
-          if (c->profiling)
-            CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 4], cs, cudaEventRecordExternal));
-          DBIE_TRY(launch_kernel(kd, grid_dif, &gd, cs));
-          if (c->profiling)
-            CUDA_TRY(cudaEventRecordWithFlags(b.ev[6 * r + 5], cs, cudaEventRecordExternal));
-        }
+        // the near-tied values of this round in float-float, then those queued as differences
+        // from the points' references, then the waiting steps again
+        DBIE_TRY(record_reeval(cs, kf, grid_ff, target_ff, b.fq_cnt[cur], b.fq_cnt_pass,
+                               b.fitem_off, &ctrl->fplan, &ctrl->fwork, &ctrl->stat_ff_pairs,
+                               b.fpos[cur], b.flam[cur], nullptr, b.fout, 6 * r + 2));
+        if (dif_on)
+          DBIE_TRY(record_reeval(cs, kd, grid_dif, target_dif, b.dq_cnt[cur], b.dq_cnt_pass,
+                                 b.ditem_off, &ctrl->dplan, &ctrl->dwork, &ctrl->stat_dif_pairs,
+                                 b.dpos[cur], b.dlam[cur], &b.dlam0[cur], b.dout, 6 * r + 4));
         launch_nm_refine(sa[cur], nm_grid, cs);
       }
     }
