@@ -482,7 +482,7 @@ extern "C" {
 
 const char* dbie_last_error(void) { return g_err.c_str(); }
 
-const char* dbie_version(void) { return "dbie-gb300 0.1 (sm_103a)"; }
+const char* dbie_version(void) { return "dbie-gb300 0.2 (sm_103a)"; }
 
 void dbie_default_options(dbie_options* o) {
   if (!o) return;
